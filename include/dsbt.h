@@ -1,0 +1,162 @@
+/*
+ * dsbt.h -- C ABI of the GB300 (sm_103a) orthogonal discrete spherical Bessel
+ * transform (DSBT) of V. V. Serov, "Orthogonal fast spherical Bessel transform
+ * on uniform grid" (arXiv:1509.07115).
+ *
+ * The transform of one radial channel of angular momentum l is
+ *     b = T_l F_l psi                                   (Sec. 2.2, Eqs. (18), (24))
+ * with F_l the orthonormal sine (even l) / cosine (odd l) transform on the
+ * midpoint grid (Eq. (16)) and T_l the orthogonal Fourier-to-Bessel matrix
+ * built from derivatives of discrete Legendre orthogonal polynomials
+ * (Sec. 2.4 Eqs. (38)-(42), completed by the rows of Sec. 2.5 Eq. (43)).
+ * The inverse is psi = F_l^T T_l^T b (Eq. (25), T^{-1} = T^T).
+ *
+ * Data conventions (all arrays are caller-owned DEVICE memory unless stated):
+ *   - A channel is N consecutive samples psi_i = psi(r_i) sqrt(dr), i = 1..N,
+ *     r_i = (i - 1/2) dr, dr = r_max / N (Eq. (14)); psi = r Psi_lm.
+ *   - Output coefficient k of a channel is b_n for n = k + p_l, p_l =
+ *     [1 + (-1)^l]/2 (Eq. (17)); b_n approximates s_l c_l(k_n) sqrt(dk) with
+ *     k_n = n pi / r_max and s_l = (-1)^{ceil(l/2)} (plain sin/cos in F_l).
+ *   - Complex dtypes are interleaved (re, im); channel c starts at element c*N.
+ *   - Grouped calls take channels of all l = 0..l_max back to back, l-major:
+ *     counts[l] channels of angular momentum l (counts is a HOST array of
+ *     l_max + 1 ints; zero counts are allowed).
+ *
+ * Precision paths:
+ *   - DSBT_F64 / DSBT_C128: everything in FP64 (sine/cosine transform by an
+ *     FP64 FFT, T_l contraction by FP64 FMA).
+ *   - DSBT_F32 / DSBT_C64: FP32 FFT, T_l contraction on the tcgen05 tensor
+ *     cores as compensated split-TF32 (T = T_hi + T_lo, x = x_hi + x_lo,
+ *     T x ~ T_hi x_hi + T_hi x_lo + T_lo x_hi, FP32 accumulation in TMEM).
+ *
+ * Errors: every entry point returns an int status (DSBT_OK = 0, negative on
+ * failure) and never throws; dsbt_last_error() returns a thread-local message
+ * for the last failure on the calling thread.  Arguments are validated on the
+ * host before any launch.  Calls are asynchronous on the given stream
+ * (a cudaStream_t passed as void*, NULL = legacy default stream); a plan is
+ * immutable after creation and may be shared by several streams, but a
+ * workspace must not be used by two calls that overlap in time.
+ */
+#ifndef DSBT_H
+#define DSBT_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define DSBT_API __attribute__((visibility("default")))
+#else
+#define DSBT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DSBT_OK 0
+#define DSBT_ERR_INVALID (-1)     /* bad argument (null pointer, size, l range, dtype) */
+#define DSBT_ERR_NOMEM (-2)       /* device allocation failed during plan creation   */
+#define DSBT_ERR_PLAN_CHECK (-3)  /* plan failed its orthogonality check             */
+#define DSBT_ERR_CUDA (-4)        /* a CUDA runtime call failed                       */
+#define DSBT_ERR_TIMEOUT (-5)     /* a device-side wait gave up (see dsbt_device_status) */
+#define DSBT_ERR_UNSUPPORTED (-6) /* path not built into this plan / size unsupported */
+
+/* plan flags: which factor copies to build (at least one) */
+#define DSBT_PLAN_FP64 1   /* FP64 T_l (for DSBT_F64 / DSBT_C128 calls)            */
+#define DSBT_PLAN_TF32X3 2 /* split-TF32 T_l and T_l^T (for DSBT_F32 / DSBT_C64)  */
+
+/* element types of the caller's arrays */
+#define DSBT_F64 1  /* real double                 */
+#define DSBT_C128 2 /* complex double, interleaved  */
+#define DSBT_F32 3  /* real float                  */
+#define DSBT_C64 4  /* complex float, interleaved   */
+
+typedef struct dsbt_plan dsbt_plan;
+
+/*
+ * Build a plan for grids of N points (256 <= N <= 8192, N a power of two) and
+ * angular momenta l = 0..l_max (0 <= l_max <= 64, with ceil((l_max+1)/2) <= N).
+ * r_max only sets the momentum step dk = pi / r_max used by the kinetic phase.
+ * Runs on the current CUDA device and stream `stream`; returns once the plan is
+ * built and has passed its check.  The plan owns every device buffer it
+ * allocates (T_l in FP64 and/or split TF32, FFT twiddles); dsbt_plan_destroy
+ * frees them.  Factors are generated on the GPU in FP64 (Sec. 2.3-2.5) by the
+ * difference equation of the DLOP in x, then each T_l passes a probe check
+ * max|T^T (T x) - x| / max|x| <= 1e-12 on random x; failure returns
+ * DSBT_ERR_PLAN_CHECK and no plan.
+ */
+DSBT_API int dsbt_plan_create(int N, double r_max, int l_max, int flags, void* stream, dsbt_plan** out);
+
+/* Release every device buffer of the plan (synchronises the device first).
+ * Accepts NULL. */
+DSBT_API int dsbt_plan_destroy(dsbt_plan* plan);
+
+/* Plan facts: grid size, l_max, flags, and the largest probe error of the
+ * orthogonality check (written to whichever pointers are non-NULL). */
+DSBT_API int dsbt_plan_info(const dsbt_plan* plan, int* N, int* l_max, int* flags, double* check_err);
+
+/*
+ * Copy T_l (storage index (n - p_l, m - p_l), row-major N x N, FP64) of a plan
+ * built with DSBT_PLAN_FP64 into the caller's DEVICE buffer `dst`
+ * (N*N doubles).  For inspection and tests.
+ */
+DSBT_API int dsbt_plan_get_T(const dsbt_plan* plan, int l, double* dst, void* stream);
+
+/*
+ * Bytes of device workspace needed by a call on `total_channels` channels of
+ * element type `dtype` (any of the calls below).  The caller allocates it
+ * (256-byte aligned) and passes it with its size; its contents need not be
+ * initialised and are scratch after the call.
+ */
+DSBT_API size_t dsbt_workspace_size(const dsbt_plan* plan, int total_channels, int dtype);
+
+/*
+ * Forward DSBT of `nchan` channels of one angular momentum l:
+ *     out[c] = T_l F_l in[c],  c = 0..nchan-1   (Eqs. (18), (24)).
+ * in, out: device arrays of nchan*N elements of `dtype`; they may not overlap.
+ */
+DSBT_API int dsbt_forward(const dsbt_plan* plan, int l, int nchan, int dtype, const void* in, void* out,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
+/* Inverse DSBT: out[c] = F_l^T T_l^T in[c]  (Eq. (25), T^{-1} = T^T). */
+DSBT_API int dsbt_inverse(const dsbt_plan* plan, int l, int nchan, int dtype, const void* in, void* out,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Grouped forward / inverse over all l = 0..l_max in one call: counts[l]
+ * channels of each l, stored l-major (counts is a HOST array of l_max+1 ints).
+ * Same contract as dsbt_forward / dsbt_inverse per group.
+ */
+DSBT_API int dsbt_forward_grouped(const dsbt_plan* plan, const int* counts, int dtype, const void* in,
+                         void* out, void* workspace, size_t workspace_bytes, void* stream);
+DSBT_API int dsbt_inverse_grouped(const dsbt_plan* plan, const int* counts, int dtype, const void* in,
+                         void* out, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Free-particle kinetic step through the DSBT (the kinetic factor of the
+ * split-operator scheme, Sec. 4.1, Eq. (81), with the momentum grid of
+ * Eq. (65)): out = F^T T^T exp(-i K tau) T F in, per l group, where
+ * K = diag(k~_n^2 / 2), k~_n = n dk for n >= 1 and, for odd l, the n = 0
+ * coefficient takes k~_N = N dk.  Complex dtypes only (DSBT_C128, DSBT_C64).
+ * The phase is applied inside the forward contraction's epilogue.
+ */
+DSBT_API int dsbt_kinetic_grouped(const dsbt_plan* plan, const int* counts, int dtype, double tau,
+                         const void* in, void* out, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/*
+ * Read the plan's device status word (synchronous: waits for the device).
+ * 0 = OK; 1 = a device-side wait in a tensor-core contraction gave up after its
+ * iteration limit (the kernel then skipped its remaining work).  reset != 0
+ * clears the word afterwards.
+ */
+DSBT_API int dsbt_device_status(const dsbt_plan* plan, int reset, int* status_out);
+
+/* Thread-local text of the last error on this thread ("" if none). */
+DSBT_API const char* dsbt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSBT_H */

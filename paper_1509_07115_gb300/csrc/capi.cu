@@ -1,0 +1,300 @@
+// capi.cu -- C ABI entry points: argument checks, group tables, workspace
+// layout, and the kernel sequence of each call.
+//
+//   forward  (Eqs. (18), (24)):  in -> F_l (sine/cosine kernel) -> T_l contraction -> out
+//   inverse  (Eq. (25)):         in -> T_l^T contraction -> F_l^T kernel -> out
+//   kinetic  (Eq. (81), A = 0):  in -> F_l -> T_l with exp(-i k~^2 tau/2) in the
+//                                epilogue -> T_l^T -> F_l^T -> out
+#include <math.h>
+
+#include "plan.cuh"
+
+namespace dsbt {
+
+namespace {
+
+// TF32 split of caller data into planar lines (complex channel c -> lines 2c, 2c+1).
+__global__ void k_split_lines(const float* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo,
+                              long long total) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const float v = in[i];
+    const float h = round_tf32(v);
+    hi[i] = h;
+    lo[i] = round_tf32(v - h);
+}
+
+__global__ void k_split_lines_c(const float2* __restrict__ in, float* __restrict__ hi,
+                                float* __restrict__ lo, int N, long long total) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const long long c = i / N, n = i % N;
+    const float2 v = in[i];
+    const float hr = round_tf32(v.x), hi_ = round_tf32(v.y);
+    const size_t o = (size_t)(2 * c) * N + n;
+    hi[o] = hr;
+    lo[o] = round_tf32(v.x - hr);
+    hi[o + N] = hi_;
+    lo[o + N] = round_tf32(v.y - hi_);
+}
+
+// exp(-i k~_n^2 tau / 2) on the unified momentum grid (Eq. (65)): storage index
+// k of parity class par (0: even l, n = k + 1; 1: odd l, n = k) maps to
+// k~ = n dk, except the odd-l coefficient n = 0, which takes k~_N = N dk.
+__global__ void k_phase(double2* ph64, float2* ph32, int N, double dk, double tau) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * N) return;
+    const int par = i / N, k = i % N;
+    int n = (par == 0) ? k + 1 : k;
+    if (n == 0) n = N;
+    const double kt = n * dk;
+    double s, c;
+    sincos(-0.5 * kt * kt * tau, &s, &c);
+    if (ph64) ph64[i] = make_double2(c, s);
+    if (ph32) ph32[i] = make_float2((float)c, (float)s);
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Workspace {
+    // FP64 path
+    double* f64a;
+    double* f64b;
+    double2* ph64;
+    // TF32 path
+    float* hi_a;
+    float* lo_a;
+    float* hi_b;
+    float* lo_b;
+    float* planar;   // aliases hi_a
+    float2* ph32;
+};
+
+size_t lines_of(int total_channels, int dtype) {
+    return (size_t)total_channels * (is_complex(dtype) ? 2 : 1);
+}
+
+size_t ws_bytes(int N, int total_channels, int dtype) {
+    const size_t R = lines_of(total_channels, dtype);
+    if (is_fp64(dtype))
+        return align256(R * N * sizeof(double)) * 2 + align256(2 * (size_t)N * sizeof(double2)) + 256;
+    return align256(R * N * sizeof(float)) * 4 + align256(2 * (size_t)N * sizeof(float2)) + 256;
+}
+
+Workspace carve(void* base, int N, int total_channels, int dtype) {
+    Workspace w{};
+    const size_t R = lines_of(total_channels, dtype);
+    unsigned char* p = (unsigned char*)(((uintptr_t)base + 255) & ~(uintptr_t)255);
+    if (is_fp64(dtype)) {
+        const size_t b = align256(R * N * sizeof(double));
+        w.f64a = (double*)p;
+        w.f64b = (double*)(p + b);
+        w.ph64 = (double2*)(p + 2 * b);
+    } else {
+        const size_t b = align256(R * N * sizeof(float));
+        w.hi_a = (float*)p;
+        w.lo_a = (float*)(p + b);
+        w.hi_b = (float*)(p + 2 * b);
+        w.lo_b = (float*)(p + 3 * b);
+        w.planar = w.hi_a;
+        w.ph32 = (float2*)(p + 4 * b);
+    }
+    return w;
+}
+
+int build_groups(const dsbt_plan* p, const int* counts, int ngroups_in, const int* ls, int dtype,
+                 GroupTable& g) {
+    g.ngroups = 0;
+    int chan = 0, line = 0;
+    const int per = is_complex(dtype) ? 2 : 1;
+    for (int i = 0; i < ngroups_in; ++i) {
+        const int c = counts[i];
+        DSBT_CHECK_ARG(c >= 0, "negative channel count for l=%d", ls[i]);
+        DSBT_CHECK_ARG(ls[i] >= 0 && ls[i] <= p->l_max, "l=%d outside the plan's 0..%d", ls[i], p->l_max);
+        if (c == 0) continue;
+        DSBT_CHECK_ARG(g.ngroups < kMaxGroups, "too many groups");
+        DSBT_CHECK_ARG((long long)chan + c < (1LL << 30), "too many channels");
+        g.l[g.ngroups] = ls[i];
+        g.chan0[g.ngroups] = chan;
+        g.line0[g.ngroups] = line;
+        ++g.ngroups;
+        chan += c;
+        line += c * per;
+    }
+    g.chan0[g.ngroups] = chan;
+    g.line0[g.ngroups] = line;
+    g.total_lines = line;
+    return DSBT_OK;
+}
+
+int check_common(const dsbt_plan* p, int dtype, const void* in, void* out, void* ws, size_t ws_b,
+                 int total_channels) {
+    DSBT_CHECK_ARG(p != nullptr, "plan is NULL");
+    DSBT_CHECK_ARG(valid_dtype(dtype), "dtype=%d invalid", dtype);
+    if (total_channels == 0) return DSBT_OK;
+    DSBT_CHECK_ARG(in != nullptr && out != nullptr, "in/out is NULL");
+    DSBT_CHECK_ARG(in != out, "in and out must not alias");
+    DSBT_CHECK_ARG(ws != nullptr, "workspace is NULL");
+    const size_t need = ws_bytes(p->N, total_channels, dtype);
+    DSBT_CHECK_ARG(ws_b >= need, "workspace too small: %zu < %zu bytes", ws_b, need);
+    if (is_fp64(dtype) && !p->T64) {
+        set_error("FP64 dtype needs a plan built with DSBT_PLAN_FP64");
+        return DSBT_ERR_UNSUPPORTED;
+    }
+    if (!is_fp64(dtype) && !p->has_tmaps) {
+        set_error("FP32 dtype needs a plan built with DSBT_PLAN_TF32X3");
+        return DSBT_ERR_UNSUPPORTED;
+    }
+    return DSBT_OK;
+}
+
+int run_forward(const dsbt_plan* p, const GroupTable& g, int dtype, const void* in, void* out,
+                void* ws, cudaStream_t st) {
+    if (g.total_lines == 0) return DSBT_OK;
+    const bool cplx = is_complex(dtype);
+    Workspace w = carve(ws, p->N, g.chan0[g.ngroups], dtype);
+    int rc;
+    if (is_fp64(dtype)) {
+        rc = dct_forward_f64(p, g, cplx, (const double*)in, w.f64a, st);
+        if (rc) return rc;
+        return contract_f64(p, g, +1, w.f64a, 0, (double*)out, cplx ? 1 : 0, nullptr, st);
+    }
+    rc = dct_forward_f32(p, g, cplx, (const float*)in, w.hi_a, w.lo_a, st);
+    if (rc) return rc;
+    return contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, cplx ? kOutUserC64 : kOutUserF32, (float*)out,
+                           nullptr, nullptr, st);
+}
+
+int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* in, void* out,
+                void* ws, cudaStream_t st) {
+    if (g.total_lines == 0) return DSBT_OK;
+    const bool cplx = is_complex(dtype);
+    Workspace w = carve(ws, p->N, g.chan0[g.ngroups], dtype);
+    int rc;
+    if (is_fp64(dtype)) {
+        rc = contract_f64(p, g, -1, (const double*)in, cplx ? 1 : 0, w.f64a, 0, nullptr, st);
+        if (rc) return rc;
+        return dct_inverse_f64(p, g, cplx, w.f64a, (double*)out, st);
+    }
+    const long long total = (long long)g.chan0[g.ngroups] * p->N;
+    const int bs = 256;
+    if (cplx)
+        k_split_lines_c<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>((const float2*)in, w.hi_b, w.lo_b,
+                                                                          p->N, total);
+    else
+        k_split_lines<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>((const float*)in, w.hi_b, w.lo_b,
+                                                                        total);
+    DSBT_CUDA_TRY(cudaGetLastError());
+    rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, st);
+    if (rc) return rc;
+    return dct_inverse_f32(p, g, cplx, w.planar, (float*)out, st);
+}
+
+int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, const void* in, void* out,
+                void* ws, cudaStream_t st) {
+    if (g.total_lines == 0) return DSBT_OK;
+    Workspace w = carve(ws, p->N, g.chan0[g.ngroups], dtype);
+    const int N = p->N;
+    int rc;
+    if (is_fp64(dtype)) {
+        k_phase<<<(2 * N + 255) / 256, 256, 0, st>>>(w.ph64, nullptr, N, p->dk, tau);
+        DSBT_CUDA_TRY(cudaGetLastError());
+        rc = dct_forward_f64(p, g, true, (const double*)in, w.f64a, st);
+        if (!rc) rc = contract_f64(p, g, +1, w.f64a, 0, w.f64b, 0, w.ph64, st);
+        if (!rc) rc = contract_f64(p, g, -1, w.f64b, 0, w.f64a, 0, nullptr, st);
+        if (!rc) rc = dct_inverse_f64(p, g, true, w.f64a, (double*)out, st);
+        return rc;
+    }
+    k_phase<<<(2 * N + 255) / 256, 256, 0, st>>>(nullptr, w.ph32, N, p->dk, tau);
+    DSBT_CUDA_TRY(cudaGetLastError());
+    rc = dct_forward_f32(p, g, true, (const float*)in, w.hi_a, w.lo_a, st);
+    if (!rc) rc = contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, kOutPlanarSplit, w.hi_b, w.lo_b, w.ph32, st);
+    if (!rc) rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, st);
+    if (!rc) rc = dct_inverse_f32(p, g, true, w.planar, (float*)out, st);
+    return rc;
+}
+
+int grouped_call(int which, const dsbt_plan* p, const int* counts, int dtype, double tau, const void* in,
+                 void* out, void* ws, size_t ws_b, void* stream) {
+    DSBT_CHECK_ARG(p != nullptr, "plan is NULL");
+    DSBT_CHECK_ARG(counts != nullptr, "counts is NULL");
+    int ls[kMaxGroups];
+    long long total = 0;
+    for (int l = 0; l <= p->l_max; ++l) {
+        ls[l] = l;
+        DSBT_CHECK_ARG(counts[l] >= 0, "counts[%d] negative", l);
+        total += counts[l];
+    }
+    DSBT_CHECK_ARG(total < (1LL << 30), "too many channels");
+    int rc = check_common(p, dtype, in, out, ws, ws_b, (int)total);
+    if (rc || total == 0) return rc;
+    GroupTable g;
+    rc = build_groups(p, counts, p->l_max + 1, ls, dtype, g);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (which == 0) return run_forward(p, g, dtype, in, out, ws, st);
+    if (which == 1) return run_inverse(p, g, dtype, in, out, ws, st);
+    DSBT_CHECK_ARG(is_complex(dtype), "kinetic step needs a complex dtype");
+    DSBT_CHECK_ARG(isfinite(tau), "tau must be finite");
+    return run_kinetic(p, g, dtype, tau, in, out, ws, st);
+}
+
+int single_call(int which, const dsbt_plan* p, int l, int nchan, int dtype, const void* in, void* out,
+                void* ws, size_t ws_b, void* stream) {
+    DSBT_CHECK_ARG(p != nullptr, "plan is NULL");
+    DSBT_CHECK_ARG(l >= 0 && l <= p->l_max, "l=%d outside the plan's 0..%d", l, p->l_max);
+    DSBT_CHECK_ARG(nchan >= 0 && nchan < (1 << 30), "nchan=%d invalid", nchan);
+    int rc = check_common(p, dtype, in, out, ws, ws_b, nchan);
+    if (rc || nchan == 0) return rc;
+    GroupTable g;
+    rc = build_groups(p, &nchan, 1, &l, dtype, g);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    return which == 0 ? run_forward(p, g, dtype, in, out, ws, st) : run_inverse(p, g, dtype, in, out, ws, st);
+}
+
+}  // namespace
+
+}  // namespace dsbt
+
+using namespace dsbt;
+
+extern "C" size_t dsbt_workspace_size(const dsbt_plan* plan, int total_channels, int dtype) {
+    if (!plan || total_channels < 0 || !valid_dtype(dtype)) return 0;
+    return ws_bytes(plan->N, total_channels, dtype);
+}
+
+extern "C" int dsbt_forward(const dsbt_plan* plan, int l, int nchan, int dtype, const void* in, void* out,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+    return single_call(0, plan, l, nchan, dtype, in, out, workspace, workspace_bytes, stream);
+}
+
+extern "C" int dsbt_inverse(const dsbt_plan* plan, int l, int nchan, int dtype, const void* in, void* out,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+    return single_call(1, plan, l, nchan, dtype, in, out, workspace, workspace_bytes, stream);
+}
+
+extern "C" int dsbt_forward_grouped(const dsbt_plan* plan, const int* counts, int dtype, const void* in,
+                                    void* out, void* workspace, size_t workspace_bytes, void* stream) {
+    return grouped_call(0, plan, counts, dtype, 0.0, in, out, workspace, workspace_bytes, stream);
+}
+
+extern "C" int dsbt_inverse_grouped(const dsbt_plan* plan, const int* counts, int dtype, const void* in,
+                                    void* out, void* workspace, size_t workspace_bytes, void* stream) {
+    return grouped_call(1, plan, counts, dtype, 0.0, in, out, workspace, workspace_bytes, stream);
+}
+
+extern "C" int dsbt_kinetic_grouped(const dsbt_plan* plan, const int* counts, int dtype, double tau,
+                                    const void* in, void* out, void* workspace, size_t workspace_bytes,
+                                    void* stream) {
+    return grouped_call(2, plan, counts, dtype, tau, in, out, workspace, workspace_bytes, stream);
+}
+
+extern "C" int dsbt_device_status(const dsbt_plan* plan, int reset, int* status_out) {
+    DSBT_CHECK_ARG(plan != nullptr && status_out != nullptr, "NULL argument");
+    unsigned s = 0;
+    DSBT_CUDA_TRY(cudaMemcpy(&s, plan->status, sizeof(s), cudaMemcpyDeviceToHost));
+    *status_out = (int)s;
+    if (reset) DSBT_CUDA_TRY(cudaMemset(plan->status, 0, sizeof(unsigned)));
+    return DSBT_OK;
+}

@@ -1,0 +1,82 @@
+// common.cuh -- shared host/device helpers of the DSBT library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/dsbt.h"
+
+namespace dsbt {
+
+// ----------------------------------------------------------------- error state
+
+void set_error(const char* fmt, ...);
+
+#define DSBT_CUDA_TRY(expr)                                                            \
+    do {                                                                               \
+        cudaError_t e__ = (expr);                                                      \
+        if (e__ != cudaSuccess) {                                                      \
+            ::dsbt::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #expr,              \
+                              cudaGetErrorString(e__));                                \
+            return DSBT_ERR_CUDA;                                                      \
+        }                                                                              \
+    } while (0)
+
+#define DSBT_CHECK_ARG(cond, ...)                                                      \
+    do {                                                                               \
+        if (!(cond)) {                                                                 \
+            ::dsbt::set_error(__VA_ARGS__);                                            \
+            return DSBT_ERR_INVALID;                                                   \
+        }                                                                              \
+    } while (0)
+
+// ----------------------------------------------------------------- index helpers
+
+__host__ __device__ inline int parity_p(int l) { return (l & 1) ? 0 : 1; }   // p_l
+__host__ __device__ inline int n0_of(int l) { return (l + 2) / 2; }           // ceil((l+1)/2)
+// Number of completion rows n in [p_l, n0_l - 1] (Sec. 2.5).
+__host__ __device__ inline int n_extra(int l) { return n0_of(l) - parity_p(l); }
+
+inline bool is_complex(int dtype) { return dtype == DSBT_C128 || dtype == DSBT_C64; }
+inline bool is_fp64(int dtype) { return dtype == DSBT_F64 || dtype == DSBT_C128; }
+inline bool valid_dtype(int dtype) { return dtype >= DSBT_F64 && dtype <= DSBT_C64; }
+
+// Channel groups of one call (one group per angular momentum present).
+constexpr int kMaxGroups = 72;
+
+struct GroupTable {
+    int ngroups;
+    int total_lines;            // real lines over all groups
+    int l[kMaxGroups];          // angular momentum of the group
+    int chan0[kMaxGroups + 1];  // first channel of the group (prefix, +1 sentinel)
+    int line0[kMaxGroups + 1];  // first real line (complex channel = 2 lines)
+};
+
+// Device-side status word written by kernels whose waits gave up.
+enum : unsigned { kStatusOk = 0, kStatusTimeout = 1 };
+
+// ----------------------------------------------------------------- TF32 split
+
+// Round an FP32 value to TF32 (10 explicit mantissa bits), nearest-even.
+// Finite inputs only.
+__host__ __device__ inline float round_tf32(float x) {
+#ifdef __CUDA_ARCH__
+    uint32_t u = __float_as_uint(x);
+#else
+    uint32_t u;
+    memcpy(&u, &x, 4);
+#endif
+    u += 0x0FFFu + ((u >> 13) & 1u);
+    u &= 0xFFFFE000u;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float y;
+    memcpy(&y, &u, 4);
+    return y;
+#endif
+}
+
+}  // namespace dsbt

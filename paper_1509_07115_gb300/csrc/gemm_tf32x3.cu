@@ -1,0 +1,465 @@
+// gemm_tf32x3.cu -- compensated split-TF32 contraction with T_l on the sm_103a
+// tensor cores (tcgen05 + TMA + TMEM).
+//
+// Forward (Eq. (24)):  b[c][n] = sum_m T_l[n][m] f[c][m]     A = T_l
+// Inverse (Eq. (25)):  f[c][m] = sum_n T_l[n][m] b[c][n]     A = T_l^T
+// Both operands are split into TF32 pairs, X = X_hi + X_lo, and each K step
+// issues three MMAs into one FP32 TMEM accumulator:
+//     D += A_hi B_hi + A_hi B_lo + A_lo B_hi       (A_lo B_lo ~ 2^-22 dropped)
+// which keeps about 2^-21 relative accuracy per product while every MMA runs
+// at TF32 tensor rate.
+//
+// Tiles: 128 output rows (TMEM lanes) x up to 256 real lines (TMEM columns);
+// K in blocks of 32 (one 128-byte swizzle row of FP32).  A tile never reads the
+// zero upper triangle of T_l: forward row tile [r0, r0+128) reads K < r0+128
+// (all K when it holds completion rows); inverse tile reads the completion rows
+// (K < n_extra <= 32) and K >= r0.
+//
+// CTA roles (192 threads, one CTA per SM, persistent over a cost-ordered tile
+// list): warp 0 = TMA producer, warp 1 = TMEM owner + MMA issuer, warps 2-5 =
+// epilogue (TMEM -> registers -> global, optional kinetic phase + TF32 split).
+// Accumulators are double-buffered in TMEM (2 x 256 columns) so the epilogue of
+// one tile overlaps the MMAs of the next.  Every mbarrier wait is bounded: on
+// expiry the kernel records kStatusTimeout in the plan's status word and all
+// roles leave their loops.
+#include "plan.cuh"
+
+namespace dsbt {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 32;
+constexpr int BN_MAX = 256;
+constexpr int BBOX = 64;                           // rows per B TMA box
+constexpr int STAGES = 2;
+constexpr int A_BYTES = BM * BK * 4;               // 16 KiB
+constexpr int B_BYTES = BN_MAX * BK * 4;           // 32 KiB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int NTHREADS = 192;
+constexpr int ACC_COLS = 256;
+constexpr uint32_t kSpinLimit = 1u << 25;
+
+struct TileSpace {
+    int RT;                        // row tiles (N / 128)
+    int KB;                        // K blocks (N / 32)
+    int tpl;                       // tiles per cost level (sum of column tiles)
+    int total;                     // RT * tpl
+    int ct0[kMaxGroups + 1];       // prefix of column tiles per group
+};
+
+// ------------------------------------------------------------ PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false on timeout or when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned* status) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicExch(status, (unsigned)kStatusTimeout);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "%4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 consecutive FP32 columns from TMEM.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;               // version
+    d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M x N.
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ------------------------------------------------------------ tile decode
+
+struct Tile {
+    int g, rt, ct, nmma;
+};
+
+__device__ __forceinline__ Tile decode(const TileSpace& ts, const GroupTable& gt, int dir, int t) {
+    Tile tl;
+    const int q = t / ts.tpl, rem = t % ts.tpl;
+    tl.rt = (dir > 0) ? (q == 0 ? 0 : ts.RT - q) : q;
+    int g = 0;
+    while (g + 1 < gt.ngroups && ts.ct0[g + 1] <= rem) ++g;
+    tl.g = g;
+    tl.ct = rem - ts.ct0[g];
+    const int nl = gt.line0[g + 1] - gt.line0[g];
+    int left = nl - tl.ct * BN_MAX;
+    if (left > BN_MAX) left = BN_MAX;
+    tl.nmma = (left + 15) & ~15;
+    return tl;
+}
+
+// K-block ranges [a0, a1) and [b0, b1) of an output row tile.
+__device__ __forceinline__ void kranges(int dir, int rt, int nx, int KB, int& a0, int& a1, int& b0,
+                                        int& b1) {
+    const int r0 = rt * BM;
+    a0 = 0;
+    b0 = b1 = 0;
+    if (r0 < nx) { a1 = KB; return; }
+    if (dir > 0) { a1 = min(KB, (r0 + BM) / BK); return; }
+    a1 = (nx + BK - 1) / BK;
+    b0 = max(a1, r0 / BK);
+    b1 = KB;
+}
+
+// ------------------------------------------------------------ the kernel
+
+struct EpiArgs {
+    int mode;              // OutMode
+    float* out0;
+    float* out1;
+    const float2* phase;   // [2][N] or nullptr
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+                  const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
+                  GroupTable gt, TileSpace ts, int N, int dir, EpiArgs ep, unsigned* status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* stage_base = smem;
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* acc_full = empty + STAGES;
+    uint64_t* acc_empty = acc_full + 2;
+    uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 2 * ACC_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ts.total && ok; t += gridDim.x) {
+                const Tile tl = decode(ts, gt, dir, t);
+                const int l = gt.l[tl.g];
+                const int nx = n_extra(l);
+                int a0, a1, b0, b1;
+                kranges(dir, tl.rt, nx, ts.KB, a0, a1, b0, b1);
+                const int nbox = (tl.nmma + BBOX - 1) / BBOX;
+                const uint32_t bytes = 2 * A_BYTES + 2 * nbox * BBOX * BK * 4;
+                const int arow = l * N + tl.rt * BM;
+                const int brow = gt.line0[tl.g] + tl.ct * BN_MAX;
+                for (int seg = 0; seg < 2 && ok; ++seg) {
+                    const int k0 = seg ? b0 : a0, k1 = seg ? b1 : a1;
+                    for (int kb = k0; kb < k1; ++kb) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status)) { ok = false; break; }
+                        unsigned char* sb = stage_base + stage * STAGE_BYTES;
+                        mbar_expect_tx(&full[stage], bytes);
+                        tma_load_2d(sb, &tmA_hi, &full[stage], kb * BK, arow);
+                        tma_load_2d(sb + A_BYTES, &tmA_lo, &full[stage], kb * BK, arow);
+                        for (int b = 0; b < nbox; ++b) {
+                            tma_load_2d(sb + 2 * A_BYTES + b * BBOX * 128, &tmB_hi, &full[stage], kb * BK,
+                                        brow + b * BBOX);
+                            tma_load_2d(sb + 2 * A_BYTES + B_BYTES + b * BBOX * 128, &tmB_lo, &full[stage],
+                                        kb * BK, brow + b * BBOX);
+                        }
+                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ts.total && ok; t += gridDim.x) {
+                const Tile tl = decode(ts, gt, dir, t);
+                const int l = gt.l[tl.g];
+                const int nx = n_extra(l);
+                int a0, a1, b0, b1;
+                kranges(dir, tl.rt, nx, ts.KB, a0, a1, b0, b1);
+                const uint32_t idesc = idesc_tf32(BM, tl.nmma);
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * ACC_COLS);
+                if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1, abort_flag, status)) break;
+                tc_fence_after();
+                uint32_t accumulate = 0;
+                for (int seg = 0; seg < 2 && ok; ++seg) {
+                    const int k0 = seg ? b0 : a0, k1 = seg ? b1 : a1;
+                    for (int kb = k0; kb < k1; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
+                        const uint32_t sa_lo = sa + A_BYTES;
+                        const uint32_t sb_hi = sa + 2 * A_BYTES;
+                        const uint32_t sb_lo = sb_hi + B_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < BK / 8; ++ks) {
+                            const uint32_t off = ks * 32;   // 8 TF32 values = 32 bytes along K
+                            const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa_lo + off);
+                            const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_lo + off);
+                            mma_tf32(d_tmem, dah, dbh, idesc, accumulate);
+                            mma_tf32(d_tmem, dah, dbl, idesc, 1);
+                            mma_tf32(d_tmem, dal, dbh, idesc, 1);
+                            accumulate = 1;
+                        }
+                        mma_commit(&empty[stage]);   // frees the stage once these MMAs finish
+                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[acc]);
+                if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue (warps 2..5)
+        const int quarter = warp & 3;             // TMEM lane quarter this warp may access
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int t = blockIdx.x; t < ts.total; t += gridDim.x) {
+            const Tile tl = decode(ts, gt, dir, t);
+            if (!mbar_wait(&acc_full[acc], acc_phase, abort_flag, status)) break;
+            tc_fence_after();
+            const int l = gt.l[tl.g];
+            const int nl = gt.line0[tl.g + 1] - gt.line0[tl.g];
+            const int row = tl.rt * BM + quarter * 32 + lane;
+            const int cbase = tl.ct * BN_MAX;
+            const int ncols = min(BN_MAX, nl - cbase);
+            const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * ACC_COLS);
+            float2 ph = make_float2(1.f, 0.f);
+            if (ep.phase) ph = ep.phase[(size_t)(l & 1) * N + row];
+            for (int ch = 0; ch * 32 < tl.nmma; ++ch) {
+                float v[32];
+                tmem_ld32(taddr + ch * 32, v);
+                const int cl0 = ch * 32;
+                if (ep.mode == kOutUserC64) {
+                    float2* o = reinterpret_cast<float2*>(ep.out0);
+                    const size_t chan_base = (size_t)gt.chan0[tl.g] + (cbase >> 1);
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        if (cl0 + j < ncols) {
+                            o[(chan_base + ((cl0 + j) >> 1)) * N + row] = make_float2(v[j], v[j + 1]);
+                        }
+                    }
+                } else if (ep.mode == kOutUserF32) {
+                    const size_t chan_base = (size_t)gt.chan0[tl.g] + cbase;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (cl0 + j < ncols) ep.out0[(chan_base + cl0 + j) * N + row] = v[j];
+                } else if (ep.mode == kOutPlanarF32) {
+                    const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (cl0 + j < ncols) ep.out0[(line_base + cl0 + j) * N + row] = v[j];
+                } else {   // kOutPlanarSplit, complex pairs with optional phase
+                    const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        if (cl0 + j < ncols) {
+                            const float re = v[j] * ph.x - v[j + 1] * ph.y;
+                            const float im = v[j] * ph.y + v[j + 1] * ph.x;
+                            const float hr = round_tf32(re), hi = round_tf32(im);
+                            const size_t o = (line_base + cl0 + j) * N + row;
+                            ep.out0[o] = hr;
+                            ep.out1[o] = round_tf32(re - hr);
+                            ep.out0[o + N] = hi;
+                            ep.out1[o + N] = round_tf32(im - hi);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 2 * ACC_COLS);
+    }
+}
+
+}  // namespace
+
+int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi,
+                    const float* in_lo, int out_mode, float* out0, float* out1, const float2* phase,
+                    cudaStream_t st) {
+    if (!p->has_tmaps) {
+        set_error("split-TF32 path needs a plan built with DSBT_PLAN_TF32X3");
+        return DSBT_ERR_UNSUPPORTED;
+    }
+    const int N = p->N;
+    TileSpace ts;
+    ts.RT = N / BM;
+    ts.KB = N / BK;
+    ts.ct0[0] = 0;
+    for (int i = 0; i < g.ngroups; ++i) {
+        const int nl = g.line0[i + 1] - g.line0[i];
+        ts.ct0[i + 1] = ts.ct0[i] + (nl + BN_MAX - 1) / BN_MAX;
+    }
+    ts.tpl = ts.ct0[g.ngroups];
+    ts.total = ts.RT * ts.tpl;
+    if (ts.total == 0) return DSBT_OK;
+    if (out_mode == kOutPlanarSplit || out_mode == kOutUserC64) {
+        for (int i = 0; i < g.ngroups; ++i) {
+            if ((g.line0[i] & 1) || ((g.line0[i + 1] - g.line0[i]) & 1)) {
+                set_error("complex output needs whole channels per group");
+                return DSBT_ERR_INVALID;
+            }
+        }
+    }
+    CUtensorMap tb_hi, tb_lo;
+    int rc = encode_tmap_f32_sw128(&tb_hi, in_hi, (uint64_t)g.total_lines, N, BBOX, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&tb_lo, in_lo, (uint64_t)g.total_lines, N, BBOX, BK);
+    if (rc != DSBT_OK) return rc;
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+    static bool attr_done = false;
+    if (!attr_done) {
+        DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+        attr_done = true;
+    }
+    int dev = 0, nsm = 0;
+    DSBT_CUDA_TRY(cudaGetDevice(&dev));
+    DSBT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = ts.total < nsm ? ts.total : nsm;
+    EpiArgs ep{out_mode, out0, out1, phase};
+    const CUtensorMap& ahi = dir > 0 ? p->tm_T_hi : p->tm_Tt_hi;
+    const CUtensorMap& alo = dir > 0 ? p->tm_T_lo : p->tm_Tt_lo;
+    k_contract_tf32x3<<<grid, NTHREADS, smem, st>>>(ahi, alo, tb_hi, tb_lo, g, ts, N, dir, ep, p->status);
+    DSBT_CUDA_TRY(cudaGetLastError());
+    return DSBT_OK;
+}
+
+}  // namespace dsbt

@@ -1,0 +1,78 @@
+// plan.cuh -- internal plan layout and kernel launchers of the DSBT library.
+#pragma once
+
+#include <cuda.h>
+
+#include "common.cuh"
+
+struct dsbt_plan {
+    int N;
+    int l_max;
+    int flags;
+    int device;
+    double r_max;
+    double dk;                 // pi / r_max
+    size_t nn;                 // N * N
+    // FP64 factors, [(l_max+1)][N][N], entry (n - p_l, m - p_l) of T_l
+    double* T64;
+    // split-TF32 factors (FP32 containers holding TF32 values), same layout:
+    // T = Thi + Tlo (A operand of the forward contraction) and the transposes
+    // Tt = T^T (A operand of the inverse contraction).
+    float* Thi;
+    float* Tlo;
+    float* Tthi;
+    float* Ttlo;
+    // FFT twiddles w^t = exp(-2 pi i t / N), t < N, and the cosine-transform
+    // post-twiddles exp(-i pi k / (2N)), k < N.
+    double2* tw64;
+    double2* post64;
+    float2* tw32;
+    float2* post32;
+    unsigned* status;          // device status word (kStatusOk / kStatusTimeout)
+    double check_err;
+    bool has_tmaps;
+    CUtensorMap tm_T_hi, tm_T_lo, tm_Tt_hi, tm_Tt_lo;
+};
+
+namespace dsbt {
+
+// ---- plan build (plan.cu)
+int plan_build_factors(dsbt_plan* p, cudaStream_t st);
+
+// ---- TMA descriptors (tma.cu)
+// Encode a 2-D FP32 tensor map over a row-major [rows][cols] array with a box of
+// box_cols x box_rows and 128-byte swizzling.
+int encode_tmap_f32_sw128(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
+                          uint32_t box_rows, uint32_t box_cols);
+
+// ---- sine/cosine transforms (dct.cu)
+// Forward F_l for every channel of the group table; writes planar lines.
+//   FP64: in = double (real or interleaved complex), out64 = [lines][N] double
+//   FP32: in = float, out_hi/out_lo = TF32 split of the result, [lines][N]
+int dct_forward_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const double* in,
+                    double* out, cudaStream_t st);
+int dct_forward_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const float* in,
+                    float* out_hi, float* out_lo, cudaStream_t st);
+// Inverse F_l^T from planar lines to the caller's layout.
+int dct_inverse_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const double* in,
+                    double* out, cudaStream_t st);
+int dct_inverse_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const float* in,
+                    float* out, cudaStream_t st);
+
+// ---- FP64 contraction (gemm_f64.cu)
+// in_cplx / out_cplx = 1: the caller's interleaved complex layout (line 2j+s of a
+// group is part s of its channel j); 0: planar lines [line][N].
+// dir = +1: out = T_l in (forward), dir = -1: out = T_l^T in (inverse).
+// phase: optional complex phase per coefficient applied to the result (kinetic
+// step), indexed [parity][N] as double2; nullptr for none.
+int contract_f64(const dsbt_plan* p, const GroupTable& g, int dir, const double* in, int in_cplx,
+                 double* out, int out_cplx, const double2* phase, cudaStream_t st);
+
+// ---- split-TF32 tensor-core contraction (gemm_tf32x3.cu)
+// B operand: TF32 split lines [lines][N] (hi, lo).  Output modes:
+enum OutMode { kOutUserC64 = 0, kOutUserF32 = 1, kOutPlanarF32 = 2, kOutPlanarSplit = 3 };
+int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi,
+                    const float* in_lo, int out_mode, float* out0, float* out1,
+                    const float2* phase, cudaStream_t st);
+
+}  // namespace dsbt

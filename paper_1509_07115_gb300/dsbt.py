@@ -1,0 +1,191 @@
+"""ctypes binding of libdsbt.so (include/dsbt.h).  Argument marshalling only:
+every step of the transform runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library cannot be loaded this module raises.
+
+Tensors are torch tensors on the current CUDA device; the calls run on torch's
+current stream.  Channel layout: last axis = radial index (length N), leading
+axes flattened into channels; grouped calls take channels l-major.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+DSBT_OK = 0
+DSBT_PLAN_FP64 = 1
+DSBT_PLAN_TF32X3 = 2
+DTYPES = {torch.float64: 1, torch.complex128: 2, torch.float32: 3, torch.complex64: 4}
+
+_lib = None
+_lock = threading.Lock()
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+
+
+def load(auto_build: bool = True) -> ctypes.CDLL:
+    """Load libdsbt.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if auto_build and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libdsbt.so not found at {_build.LIB}; run "
+                               "`python -m paper_1509_07115_gb300.build`")
+        lib = ctypes.CDLL(_build.LIB)
+        vp, sz, i, d = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_double
+        lib.dsbt_plan_create.argtypes = [i, d, i, i, vp, ctypes.POINTER(vp)]
+        lib.dsbt_plan_destroy.argtypes = [vp]
+        lib.dsbt_plan_info.argtypes = [vp, _c_int_p, _c_int_p, _c_int_p, ctypes.POINTER(d)]
+        lib.dsbt_plan_get_T.argtypes = [vp, i, vp, vp]
+        lib.dsbt_workspace_size.argtypes = [vp, i, i]
+        lib.dsbt_workspace_size.restype = sz
+        for name in ("dsbt_forward", "dsbt_inverse"):
+            getattr(lib, name).argtypes = [vp, i, i, i, vp, vp, vp, sz, vp]
+        for name in ("dsbt_forward_grouped", "dsbt_inverse_grouped"):
+            getattr(lib, name).argtypes = [vp, _c_int_p, i, vp, vp, vp, sz, vp]
+        lib.dsbt_kinetic_grouped.argtypes = [vp, _c_int_p, i, d, vp, vp, vp, sz, vp]
+        lib.dsbt_device_status.argtypes = [vp, i, _c_int_p]
+        lib.dsbt_last_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+class DSBTError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != DSBT_OK:
+        msg = load().dsbt_last_error().decode(errors="replace")
+        raise DSBTError(f"{what} failed ({rc}): {msg}")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Plan:
+    """A DSBT plan: T_l factors for l = 0..l_max on an N-point grid."""
+
+    def __init__(self, N: int, r_max: float, l_max: int, fp64: bool = True, tf32x3: bool = True):
+        lib = load()
+        flags = (DSBT_PLAN_FP64 if fp64 else 0) | (DSBT_PLAN_TF32X3 if tf32x3 else 0)
+        h = ctypes.c_void_p()
+        _check(lib.dsbt_plan_create(int(N), float(r_max), int(l_max), flags, _stream(), ctypes.byref(h)),
+               "dsbt_plan_create")
+        self._h = h
+        self.N, self.r_max, self.l_max, self.flags = int(N), float(r_max), int(l_max), flags
+        self._ws = None
+
+    # -------------------------------------------------------------- plumbing
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dsbt_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        N, lm, fl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        err = ctypes.c_double()
+        _check(load().dsbt_plan_info(self._h, ctypes.byref(N), ctypes.byref(lm), ctypes.byref(fl),
+                                     ctypes.byref(err)), "dsbt_plan_info")
+        return {"N": N.value, "l_max": lm.value, "flags": fl.value, "check_err": err.value}
+
+    def workspace_bytes(self, total_channels: int, dtype: torch.dtype) -> int:
+        return int(load().dsbt_workspace_size(self._h, int(total_channels), DTYPES[dtype]))
+
+    def workspace(self, total_channels: int, dtype: torch.dtype, device=None) -> torch.Tensor:
+        nb = self.workspace_bytes(total_channels, dtype)
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(max(nb, 256), dtype=torch.uint8,
+                                   device=device or torch.cuda.current_device())
+        return self._ws
+
+    def _prep(self, x: torch.Tensor, out):
+        if not x.is_cuda:
+            raise ValueError("input must be a CUDA tensor")
+        if x.shape[-1] != self.N:
+            raise ValueError(f"last axis must be N={self.N}")
+        if x.dtype not in DTYPES:
+            raise ValueError(f"unsupported dtype {x.dtype}")
+        x = x.contiguous()
+        if out is None:
+            out = torch.empty_like(x)
+        elif out.shape != x.shape or out.dtype != x.dtype or not out.is_contiguous():
+            raise ValueError("out must match the input's shape and dtype and be contiguous")
+        return x, out
+
+    # -------------------------------------------------------------- transforms
+    def get_T(self, l: int) -> torch.Tensor:
+        T = torch.empty((self.N, self.N), dtype=torch.float64, device="cuda")
+        _check(load().dsbt_plan_get_T(self._h, int(l), ctypes.c_void_p(T.data_ptr()), _stream()),
+               "dsbt_plan_get_T")
+        return T
+
+    def _single(self, name, l, x, out, workspace):
+        x, out = self._prep(x, out)
+        nchan = x.numel() // self.N
+        ws = workspace if workspace is not None else self.workspace(nchan, x.dtype)
+        _check(getattr(load(), name)(self._h, int(l), int(nchan), DTYPES[x.dtype],
+                                     ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()), name)
+        return out
+
+    def forward(self, l: int, x: torch.Tensor, out=None, workspace=None) -> torch.Tensor:
+        """b = T_l F_l x for every channel of x (dsbt_forward)."""
+        return self._single("dsbt_forward", l, x, out, workspace)
+
+    def inverse(self, l: int, b: torch.Tensor, out=None, workspace=None) -> torch.Tensor:
+        """x = F_l^T T_l^T b (dsbt_inverse)."""
+        return self._single("dsbt_inverse", l, b, out, workspace)
+
+    def _counts(self, counts):
+        c = list(int(v) for v in counts)
+        if len(c) != self.l_max + 1:
+            raise ValueError(f"counts needs l_max+1={self.l_max + 1} entries")
+        return (ctypes.c_int * len(c))(*c), sum(c)
+
+    def _grouped(self, name, counts, x, out, workspace, tau=None):
+        x, out = self._prep(x, out)
+        arr, total = self._counts(counts)
+        if total * self.N != x.numel():
+            raise ValueError("sum(counts) * N must equal the number of input elements")
+        ws = workspace if workspace is not None else self.workspace(total, x.dtype)
+        args = [self._h, arr, DTYPES[x.dtype]]
+        if tau is not None:
+            args.append(float(tau))
+        args += [ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()]
+        _check(getattr(load(), name)(*args), name)
+        return out
+
+    def forward_grouped(self, counts, x, out=None, workspace=None) -> torch.Tensor:
+        return self._grouped("dsbt_forward_grouped", counts, x, out, workspace)
+
+    def inverse_grouped(self, counts, b, out=None, workspace=None) -> torch.Tensor:
+        return self._grouped("dsbt_inverse_grouped", counts, b, out, workspace)
+
+    def kinetic_grouped(self, counts, x, tau: float, out=None, workspace=None) -> torch.Tensor:
+        """F^T T^T exp(-i k~^2 tau / 2) T F x per l group (dsbt_kinetic_grouped)."""
+        return self._grouped("dsbt_kinetic_grouped", counts, x, out, workspace, tau=tau)
+
+    def device_status(self, reset: bool = True) -> int:
+        s = ctypes.c_int()
+        _check(load().dsbt_device_status(self._h, int(bool(reset)), ctypes.byref(s)), "dsbt_device_status")
+        return s.value
