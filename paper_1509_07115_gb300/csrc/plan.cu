@@ -13,10 +13,14 @@
 // second-order difference equation of the Hahn polynomials Q_l(x; 0, 0, M),
 //     l(l+1) Q(x) = B(x) Q(x+1) - [B(x) + D(x)] Q(x) + D(x) Q(x-1),
 //     B(x) = (x+1)(x-M),  D(x) = x(x-M-1),  Q(0) = 1,
+// written for the backward difference d(x) = Q(x+1) - Q(x) that the rows need:
+//     d(x) = [l(l+1) Q(x) + D(x) d(x-1)] / B(x),   Q(x+1) = Q(x) + d(x),
 // marching from the grid end x = 0 towards the middle.  On that side of the
 // grid the wanted polynomial is the dominant solution, so the march keeps
-// FP64 accuracy for every l <= 64 (the three-term recurrence in the degree, by
-// contrast, loses all digits in the first rows when l approaches 2n).
+// FP64 accuracy for every l <= 64, and carrying d(x) instead of Q(x) avoids
+// the cancellation of O(M^2) terms of the plain form (the three-term
+// recurrence in the degree, by contrast, loses all digits in the first rows
+// when l approaches 2n).
 #include <math.h>
 #include <stdarg.h>
 #include <stdlib.h>
@@ -39,6 +43,14 @@ void set_error(const char* fmt, ...) {
 
 // ------------------------------------------------------------------ kernels
 
+// s + c += v with Neumaier's compensation (the row norms must not lose the
+// small entries against large partial sums).
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double v) {
+    const double t = s + v;
+    c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+}
+
 // One thread per (l, storage row r): writes row r of T_l into T64 (which the
 // caller zeroed).  Two passes over x: the first accumulates ||u||^2, the
 // second writes u / ||u||, so nothing is re-read from memory.
@@ -58,47 +70,43 @@ __global__ void k_build_rows(double* __restrict__ T64, int N, int lmax) {
     if (n >= n0) {
         const double M = 2.0 * n - 1.0;
         const int X = n - p;   // differences at i = 1..X, i = n - m
-        double ss = 1.0;       // u_n = 1
+        double ss = 0.0, sc = 0.0;   // Neumaier-compensated sum of u_m^2, m < n
         for (int pass = 0; pass < 2; ++pass) {
-            const double inv = (pass == 0) ? 0.0 : 1.0 / sqrt(ss);
-            double qm1 = 0.0, q = 1.0;
+            const double inv = (pass == 0) ? 0.0 : 1.0 / sqrt(1.0 + (ss + sc));   // + u_n^2 = 1
+            double q = 1.0, d = 0.0;
             for (int x = 0; x < X; ++x) {
                 const double xd = (double)x;
                 const double B = (xd + 1.0) * (xd - M);
                 const double D = xd * (xd - M - 1.0);
-                const double qn = ((ll1 + B + D) * q - D * qm1) / B;
+                d = (ll1 * q + D * d) / B;
+                q += d;
                 const int m = n - (x + 1);
-                const double u = (qn - q) * (m == 0 ? sqrt_half : 1.0);
-                if (pass == 0) ss += u * u;
+                const double u = d * (m == 0 ? sqrt_half : 1.0);
+                if (pass == 0) neumaier_add(ss, sc, __dmul_rn(u, u));
                 else row[m - p] = u * inv;
-                qm1 = q;
-                q = qn;
             }
             if (pass == 1) row[n - p] = inv;
         }
     } else {
-        // completion row: degree d = 2n - p on the grid 0..2 N_l, x = N_l - m
-        const int d = 2 * n - p;
+        // completion row: degree e = 2n - p on the grid 0..2 N_l, x = N_l - m
+        const int e = 2 * n - p;
         const double M = 2.0 * Nl;
-        const double dd1 = (double)d * (double)(d + 1);
+        const double ee1 = (double)e * (double)(e + 1);
         const int X = Nl - p;  // x = 0..X
-        double ss = 0.0;
+        double ss = 0.0, sc = 0.0;
         for (int pass = 0; pass < 2; ++pass) {
-            const double inv = (pass == 0) ? 0.0 : 1.0 / sqrt(ss);
-            double qm1 = 0.0, q = 1.0;
+            const double inv = (pass == 0) ? 0.0 : 1.0 / sqrt(ss + sc);
+            double q = 1.0, d = 0.0;
             for (int x = 0; x <= X; ++x) {
                 const int m = Nl - x;
                 const double v = q * (m == 0 ? sqrt_half : 1.0);
-                if (pass == 0) ss += v * v;
+                if (pass == 0) neumaier_add(ss, sc, __dmul_rn(v, v));
                 else row[m - p] = v * inv;
-                if (x < X) {
-                    const double xd = (double)x;
-                    const double B = (xd + 1.0) * (xd - M);
-                    const double D = xd * (xd - M - 1.0);
-                    const double qn = ((dd1 + B + D) * q - D * qm1) / B;
-                    qm1 = q;
-                    q = qn;
-                }
+                const double xd = (double)x;
+                const double B = (xd + 1.0) * (xd - M);
+                const double D = xd * (xd - M - 1.0);
+                d = (ee1 * q + D * d) / B;
+                q += d;
             }
         }
     }
