@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 DSBT.
+
+Workload (the precision form): N = 4096 points, r_max = 409.6 (dr = 0.1),
+l = 0..63 with all m, batch 8 -> 32768 complex64 channels of seeded Gaussian-sum
+radial functions.  One step = one pass of the hot path over the whole batch:
+the kinetic round trip F_l -> T_l (with exp(-i k^2 tau/2) in its epilogue) ->
+T_l^T -> F_l^T (dsbt_kinetic_grouped), i.e. two channel-transforms per channel.
+
+Printed JSON line (rank 0):
+  value       channel-transforms/s of the split-TF32 path, inputs resident in HBM
+  e2e         same metric through the public API with pinned HOST buffers
+              (host->device copy of the inputs and device->host copy of the
+              result inside the timed region)
+  roofline    of the dominant kernel (the split-TF32 contraction), timed live
+              with CUDA events on its launch stream during the timed steps
+  fp64_gpu    the plain FP64 GPU path on a one-eighth sample (batch 1), and the
+              split-TF32 error against it (max |diff| / ||psi|| per channel)
+  cpu_baseline  the FP64 CPU oracle on a bounded sample (N = 4096, l = 1, 2)
+
+--impl reference runs the FP64 CPU oracle (the only reference this project
+has) on the same workload, a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DSBT channel-transforms/s vs plain FP64 GPU at ≤1e-6 rel err; % roofline"
+UNIT = "channel-transforms/s"
+N, R_MAX, L_MAX, BATCH, TAU = 4096, 409.6, 63, 8, 0.05
+DR = R_MAX / N
+WORKLOAD = ("precision form: N=4096, r_max=409.6, l=0..63 all m x batch 8 = 32768 complex64 "
+            "Gaussian-sum channels; step = kinetic round trip F, T (+exp(-i k^2 tau/2)), T^T, F^T")
+TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rate ratio
+FLOP_PER_CHANNEL = 6.0 * N * N   # split-TF32 contraction, one direction, per complex channel
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return pk, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def source_hash(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel_file):
+    """DRAM bytes per launch of the contraction from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    prof = os.path.join(ROOT, "profiles", "contract_tf32x3_precision_form.json")
+    try:
+        with open(prof) as fh:
+            d = json.load(fh)
+        if d.get("source_sha256_16") != source_hash(kernel_file):
+            return None
+        return d.get("dram_bytes_per_launch_full_size")
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = []
+        try:
+            self.file.seek(0)
+            for line in self.file.read().splitlines():
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            self.file.close()
+            os.unlink(self.file.name)
+        return rows
+
+    @staticmethod
+    def summarize(rows):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        busy = [s for s in sm if s is not None]
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def bad_clocks(c):
+    if any(r in c.get("reasons", []) for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")):
+        return True
+    if c.get("sm_mhz") and c.get("sm_max_mhz") and c["sm_mhz"] < 0.5 * c["sm_max_mhz"] and not c["reasons"]:
+        return True
+    return False
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+
+def oracle_sample(nchan=4, ls=(1, 2), seed=11):
+    """Times the FP64 oracle as it stands (single thread) on a bounded sample:
+    for each l in ls, nchan channels of the workload's Gaussian-sum inputs;
+    factor build (binary128 DLOP rows, explicit F_l) timed separately from the
+    transforms (naive O(N^2) sums in C).  Returns (transforms, seconds, build_s)."""
+    import numpy as np
+
+    import oracle
+    from paper_1509_07115_gb300 import inputs
+    counts = [0] * (max(ls) + 1)
+    for l in ls:
+        counts[l] = nchan
+    x = inputs.gaussian_sum(seed, N, DR, counts)
+    t_build = 0.0
+    t_xform = 0.0
+    ntr = 0
+    c0 = 0
+    dk = math.pi / R_MAX
+    for l in range(max(ls) + 1):
+        c = counts[l]
+        if not c:
+            continue
+        t0 = time.perf_counter()
+        F = oracle.F_matrix(N, l)
+        T = oracle.T_matrix(N, l)
+        t_build += time.perf_counter() - t0
+        p = oracle.p_of(l)
+        n = np.arange(N) + p
+        kt = np.where(n == 0, N, n) * dk
+        t0 = time.perf_counter()
+        f = oracle.apply(F, x[c0:c0 + c])
+        b = oracle.apply(T, f) * np.exp(-0.5j * kt * kt * TAU)
+        f2 = oracle.apply(T, b, transpose=True)
+        oracle.apply(F, f2, transpose=True)
+        t_xform += time.perf_counter() - t0
+        ntr += 2 * c
+        c0 += c
+    return ntr, t_xform, t_build
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    import numpy as np
+    from paper_1509_07115_gb300 import inputs
+    # factors for the sampled l, built once (binary128 recurrences); each step
+    # then runs the kinetic round trip of one channel, alternating l = 1 and 2
+    t0 = time.perf_counter()
+    FT = {1: (oracle.F_matrix(N, 1), oracle.T_matrix(N, 1)), 2: (oracle.F_matrix(N, 2), oracle.T_matrix(N, 2))}
+    t_build = time.perf_counter() - t0
+    x = inputs.gaussian_sum(13, N, DR, [0, 1, 1])
+    dk = math.pi / R_MAX
+    it = [0]
+
+    def step():
+        l = 1 + (it[0] % 2)
+        it[0] += 1
+        F, T = FT[l]
+        xs = x[l - 1:l]
+        n = np.arange(N) + oracle.p_of(l)
+        kt = np.where(n == 0, N, n) * dk
+        b = oracle.apply(T, oracle.apply(F, xs)) * np.exp(-0.5j * kt * kt * TAU)
+        oracle.apply(F, oracle.apply(T, b, transpose=True), transpose=True)
+        return 2
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    ntr = 0
+    for _ in range(args.steps):
+        ntr += step()
+    dt = time.perf_counter() - t0
+    value = ntr / dt
+    sample = (f"one complex channel per step (alternating l=1 and l=2) of the N=4096 workload, kinetic "
+              f"round trip by naive O(N^2) sums, single thread; factor build for l=1,2 took "
+              f"{t_build:.1f} s (excluded)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Gaussian-sum radial functions)",
+            "config": {"workload": WORKLOAD, "N": N, "l_max": L_MAX, "channels": 32768,
+                       "reference": "FP64 CPU oracle (plain C, binary128 DLOP rows), bounded sample"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1509_07115_gb300 import dsbt, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    counts = inputs.all_m_counts(L_MAX, BATCH)
+    nchan = sum(counts)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    plan = dsbt.Plan(N, R_MAX, L_MAX, fp64=not args.no_fp64, tf32x3=True)
+    x = inputs.gaussian_sum(100 + rank, N, DR, counts, dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    ws = plan.workspace(nchan, torch.complex64)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.kinetic_grouped(counts, x, TAU, out=y, workspace=ws)
+    torch.cuda.synchronize()
+
+    def timed_region():
+        dsbt.profile_enable(True)
+        n0 = dsbt.launch_count()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.kinetic_grouped(counts, x, TAU, out=y, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        launches = dsbt.launch_count() - n0
+        prof = dsbt.profile_read()
+        dsbt.profile_enable(False)
+        return e0.elapsed_time(e1), launches, prof
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, launches, prof = timed_region()
+    clocks = ClockSampler.summarize(sampler.stop())
+    if bad_clocks(clocks):
+        sampler = ClockSampler(local)
+        sampler.start()
+        ms, launches, prof = timed_region()
+        clocks = ClockSampler.summarize(sampler.stop())
+        clocks["remeasured"] = True
+    status = plan.device_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status} after the timed region")
+
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    transforms_per_step = 2 * nchan * world
+    value = transforms_per_step * args.steps / (ms_max * 1e-3)
+
+    # ---------------------------------------------------------- e2e via host buffers
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(x)
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        plan.kinetic_grouped(counts, xd, TAU, out=y, workspace=ws)
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(3, args.steps // 3)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        xd.copy_(xh, non_blocking=True)
+        plan.kinetic_grouped(counts, xd, TAU, out=y, workspace=ws)
+        yh.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
+    e2e_value = transforms_per_step * e2e_steps / (float(e2e_ms.item()) * 1e-3)
+    nbytes = x.numel() * x.element_size()
+
+    # ---------------------------------------------------------- roofline of the contraction
+    peaks, src = load_peaks()
+    k_launches, k_ms = prof.get("contract_tf32x3", (0, 0.0))
+    avg_ms = k_ms / max(1, k_launches)
+    flop_per_launch = FLOP_PER_CHANNEL * nchan
+    achieved = flop_per_launch / (avg_ms * 1e-3) / 1e12
+    peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+    kernel_file = os.path.join(ROOT, "paper_1509_07115_gb300", "csrc", "gemm_tf32x3.cu")
+    roofline = {"bound": "tensor", "kernel": "contract_tf32x3", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(kernel_file),
+                "peak_source": f"{src}: bf16 sustained x {TF32_OVER_BF16:.3f} (nominal tf32/bf16)",
+                "flop_per_launch": flop_per_launch, "avg_launch_ms": avg_ms,
+                "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (split-tf32 contraction, fp32 accumulate)",
+                "data": "synthetic (seeded Gaussian-sum radial functions r sum_j c_j r^l exp(-a_j r^2))",
+                "config": {"workload": WORKLOAD, "N": N, "r_max": R_MAX, "l_max": L_MAX, "batch": BATCH,
+                           "channels_per_gpu": nchan, "tau": TAU,
+                           "l2": "inputs larger than L2 (1.07 GB in + 1.07 GB out per step per GPU)"},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                        "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
+                "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+
+    # ---------------------------------------------------------- FP64 GPU path (sample) + error
+    if not args.no_fp64:
+        counts1 = inputs.all_m_counts(L_MAX, 1)
+        n1 = sum(counts1)
+        x64 = inputs.gaussian_sum(200 + rank, N, DR, counts1, dtype=torch.complex128, device=dev)
+        y64 = torch.empty_like(x64)
+        ws64 = torch.empty(plan.workspace_bytes(n1, torch.complex128), dtype=torch.uint8, device=dev)
+        plan.kinetic_grouped(counts1, x64, TAU, out=y64, workspace=ws64)
+        torch.cuda.synchronize()
+        f_steps = 2
+        e0.record(stream)
+        for _ in range(f_steps):
+            plan.kinetic_grouped(counts1, x64, TAU, out=y64, workspace=ws64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f_ms = e0.elapsed_time(e1) / f_steps
+        x32 = x64.to(torch.complex64)
+        y32 = torch.empty_like(x32)
+        ws32 = torch.empty(plan.workspace_bytes(n1, torch.complex64), dtype=torch.uint8, device=dev)
+        plan.kinetic_grouped(counts1, x32, TAU, out=y32, workspace=ws32)
+        b64 = plan.forward_grouped(counts1, x64, workspace=ws64)
+        b32 = plan.forward_grouped(counts1, x32, workspace=ws32)
+        nrm = torch.linalg.vector_norm(x64, dim=1)
+        err_rt = ((y32.to(torch.complex128) - y64).abs().amax(dim=1) / nrm).max().item()
+        err_fw = ((b32.to(torch.complex128) - b64).abs().amax(dim=1) / nrm).max().item()
+        drift = ((torch.linalg.vector_norm(b32.to(torch.complex128), dim=1) - nrm) / nrm).abs().max().item()
+        fp64_value = 2 * n1 / (f_ms * 1e-3)
+        if rank == 0:
+            line["fp64_gpu"] = {"value": fp64_value, "unit": UNIT,
+                                "sample": "batch 1 of the same workload (4096 complex128 channels)",
+                                "ms_per_step": f_ms, "speedup_of_split_tf32": value / world / fp64_value,
+                                "split_tf32_max_rel_err": {"kinetic_round_trip": err_rt, "forward": err_fw,
+                                                           "norm_drift": drift}}
+
+    # ---------------------------------------------------------- CPU oracle baseline
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ntr, t_x, t_b = oracle_sample()
+        line["cpu_baseline"] = {"value": ntr / t_x, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": (f"{ntr} channel-transforms (4 complex channels each of l=1 and l=2, "
+                                           f"N=4096, kinetic round trip by naive O(N^2) sums, single thread); "
+                                           f"factor build {t_b:.1f} s excluded")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -152,6 +152,20 @@ DSBT_API int dsbt_kinetic_grouped(const dsbt_plan* plan, const int* counts, int 
  */
 DSBT_API int dsbt_device_status(const dsbt_plan* plan, int reset, int* status_out);
 
+/*
+ * Launch accounting and kernel timing (tracing).  dsbt_launch_count returns the
+ * number of kernel launches the library has issued in this process.
+ * dsbt_profile_enable(1) clears earlier records and starts recording a pair of
+ * CUDA events on the launch stream around every kernel launch (0 stops);
+ * dsbt_profile_read synchronises on the recorded events of one kernel kind and
+ * returns how many launches were recorded and their summed device time in ms.
+ * dsbt_kernel_name maps a kernel id (0, 1, ...) to its name, NULL past the last.
+ */
+DSBT_API long long dsbt_launch_count(void);
+DSBT_API int dsbt_profile_enable(int on);
+DSBT_API int dsbt_profile_read(int kernel_id, int* launches, double* total_ms);
+DSBT_API const char* dsbt_kernel_name(int kernel_id);
+
 /* Thread-local text of the last error on this thread ("" if none). */
 DSBT_API const char* dsbt_last_error(void);
 

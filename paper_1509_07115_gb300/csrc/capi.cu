@@ -178,12 +178,15 @@ int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
     }
     const long long total = (long long)g.chan0[g.ngroups] * p->N;
     const int bs = 256;
+    {
+    ProfScope ps(kKSplit, st);
     if (cplx)
         k_split_lines_c<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>((const float2*)in, w.hi_b, w.lo_b,
                                                                           p->N, total);
     else
         k_split_lines<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>((const float*)in, w.hi_b, w.lo_b,
                                                                         total);
+    }
     DSBT_CUDA_TRY(cudaGetLastError());
     rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, st);
     if (rc) return rc;
@@ -197,7 +200,10 @@ int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, 
     const int N = p->N;
     int rc;
     if (is_fp64(dtype)) {
-        k_phase<<<(2 * N + 255) / 256, 256, 0, st>>>(w.ph64, nullptr, N, p->dk, tau);
+        {
+            ProfScope ps(kKPhase, st);
+            k_phase<<<(2 * N + 255) / 256, 256, 0, st>>>(w.ph64, nullptr, N, p->dk, tau);
+        }
         DSBT_CUDA_TRY(cudaGetLastError());
         rc = dct_forward_f64(p, g, true, (const double*)in, w.f64a, st);
         if (!rc) rc = contract_f64(p, g, +1, w.f64a, 0, w.f64b, 0, w.ph64, st);
@@ -205,7 +211,10 @@ int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, 
         if (!rc) rc = dct_inverse_f64(p, g, true, w.f64a, (double*)out, st);
         return rc;
     }
-    k_phase<<<(2 * N + 255) / 256, 256, 0, st>>>(nullptr, w.ph32, N, p->dk, tau);
+    {
+        ProfScope ps(kKPhase, st);
+        k_phase<<<(2 * N + 255) / 256, 256, 0, st>>>(nullptr, w.ph32, N, p->dk, tau);
+    }
     DSBT_CUDA_TRY(cudaGetLastError());
     rc = dct_forward_f32(p, g, true, (const float*)in, w.hi_a, w.lo_a, st);
     if (!rc) rc = contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, kOutPlanarSplit, w.hi_b, w.lo_b, w.ph32, st);

@@ -249,6 +249,7 @@ int dct_forward_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const do
     unsigned th; size_t sm;
     int rc = launch_cfg(k_dct_fwd<double, false>, p->N, sizeof(double2), th, sm);
     if (rc) return rc;
+    ProfScope ps(kKDctFwd, st);
     k_dct_fwd<double, false><<<nchannels(g), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, nullptr,
                                                            p->tw64, p->post64);
     DSBT_CUDA_TRY(cudaGetLastError());
@@ -261,6 +262,7 @@ int dct_forward_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const fl
     unsigned th; size_t sm;
     int rc = launch_cfg(k_dct_fwd<float, true>, p->N, sizeof(float2), th, sm);
     if (rc) return rc;
+    ProfScope ps(kKDctFwd, st);
     k_dct_fwd<float, true><<<nchannels(g), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out_hi, out_lo,
                                                          p->tw32, p->post32);
     DSBT_CUDA_TRY(cudaGetLastError());
@@ -273,6 +275,7 @@ int dct_inverse_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const do
     unsigned th; size_t sm;
     int rc = launch_cfg(k_dct_inv<double>, p->N, sizeof(double2), th, sm);
     if (rc) return rc;
+    ProfScope ps(kKDctInv, st);
     k_dct_inv<double><<<nchannels(g), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, p->tw64, p->post64);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
@@ -284,6 +287,7 @@ int dct_inverse_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const fl
     unsigned th; size_t sm;
     int rc = launch_cfg(k_dct_inv<float>, p->N, sizeof(float2), th, sm);
     if (rc) return rc;
+    ProfScope ps(kKDctInv, st);
     k_dct_inv<float><<<nchannels(g), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, p->tw32, p->post32);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;

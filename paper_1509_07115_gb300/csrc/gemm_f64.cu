@@ -244,15 +244,18 @@ int contract_f64(const dsbt_plan* p, const GroupTable& g, int dir, const double*
     OutLines lo{out, out_cplx};
     if (any_wide) {
         dim3 grid((N / BM) * max_ct, g.ngroups);
+        ProfScope ps(kKContract64, st);
         k_contract64_tile<<<grid, 256, 0, st>>>(g, p->T64, N, dir, li, lo, phase);
         DSBT_CUDA_TRY(cudaGetLastError());
     }
     if (any_narrow) {
         if (dir > 0) {
             dim3 grid((N * 32 + 255) / 256, g.ngroups);
+            ProfScope ps(kKContract64, st);
             k_contract64_rows<<<grid, 256, 0, st>>>(g, p->T64, N, li, lo, phase);
         } else {
             dim3 grid((N + 255) / 256, g.ngroups);
+            ProfScope ps(kKContract64, st);
             k_contract64_cols<<<grid, 256, 0, st>>>(g, p->T64, N, li, lo);
         }
         DSBT_CUDA_TRY(cudaGetLastError());

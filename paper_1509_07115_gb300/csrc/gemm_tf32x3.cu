@@ -4,10 +4,10 @@
 // Forward (Eq. (24)):  b[c][n] = sum_m T_l[n][m] f[c][m]     A = T_l
 // Inverse (Eq. (25)):  f[c][m] = sum_n T_l[n][m] b[c][n]     A = T_l^T
 // Both operands are split into TF32 pairs, X = X_hi + X_lo, and each K step
-// issues three MMAs into one FP32 TMEM accumulator:
-//     D += A_hi B_hi + A_hi B_lo + A_lo B_hi       (A_lo B_lo ~ 2^-22 dropped)
-// which keeps about 2^-21 relative accuracy per product while every MMA runs
-// at TF32 tensor rate.
+// issues three MMAs into FP32 TMEM accumulators:
+//     D_main += A_hi B_hi,   D_corr += A_hi B_lo + A_lo B_hi
+// (A_lo B_lo ~ 2^-22 dropped), which keeps about 2^-21 relative accuracy per
+// product while every MMA runs at TF32 tensor rate.
 //
 // Tiles: 128 output rows (TMEM lanes) x up to 256 real lines (TMEM columns);
 // K in blocks of 32 (one 128-byte swizzle row of FP32).  A tile never reads the
@@ -15,13 +15,13 @@
 // (all K when it holds completion rows); inverse tile reads the completion rows
 // (K < n_extra <= 32) and K >= r0.
 //
-// CTA roles (192 threads, one CTA per SM, persistent over a cost-ordered tile
-// list): warp 0 = TMA producer, warp 1 = TMEM owner + MMA issuer, warps 2-5 =
-// epilogue (TMEM -> registers -> global, optional kinetic phase + TF32 split).
-// Accumulators are double-buffered in TMEM (2 x 256 columns) so the epilogue of
-// one tile overlaps the MMAs of the next.  Every mbarrier wait is bounded: on
-// expiry the kernel records kStatusTimeout in the plan's status word and all
-// roles leave their loops.
+// CTA roles (320 threads, one CTA per SM, persistent over a cost-ordered tile
+// list): warp 0 = TMA producer, warp 1 = TMEM owner + MMA issuer, warps 2-9 =
+// epilogue (two warps per TMEM lane quarter, 128 columns each: drain the main
+// accumulator every KC K-blocks into FP32 registers, then the optional kinetic
+// phase + TF32 split, then global stores, which overlap the next tile's MMAs).
+// Every mbarrier wait is bounded: on expiry the kernel records kStatusTimeout
+// in the plan's status word and all roles leave their loops.
 #include "plan.cuh"
 
 namespace dsbt {
@@ -33,11 +33,12 @@ constexpr int BK = 32;
 constexpr int BN_MAX = 256;
 constexpr int BBOX = 64;                           // rows per B TMA box
 constexpr int STAGES = 2;
+constexpr int KC = 4;                              // K blocks per main-accumulator chunk
+constexpr int EPI_WARPS = 8;
 constexpr int A_BYTES = BM * BK * 4;               // 16 KiB
 constexpr int B_BYTES = BN_MAX * BK * 4;           // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int NTHREADS = 192;
-constexpr int ACC_COLS = 256;
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t kSpinLimit = 1u << 25;
 
 struct TileSpace {
@@ -196,17 +197,32 @@ __device__ __forceinline__ Tile decode(const TileSpace& ts, const GroupTable& gt
     return tl;
 }
 
-// K-block ranges [a0, a1) and [b0, b1) of an output row tile.
-__device__ __forceinline__ void kranges(int dir, int rt, int nx, int KB, int& a0, int& a1, int& b0,
-                                        int& b1) {
+// K blocks of an output row tile, as two half-open ranges [a0, a1) and
+// [b0, b1) (b empty unless the inverse reads completion rows and a diagonal
+// band).  They are walked from the last block down, so that for the smooth
+// channels of physical interest the small far-K contributions are summed
+// before the large ones.
+struct KRange {
+    int a0, a1, b0, b1;
+    __device__ __forceinline__ int count() const { return (a1 - a0) + (b1 - b0); }
+    // i-th block in walking order
+    __device__ __forceinline__ int at(int i) const {
+        const int nb = b1 - b0;
+        return (i < nb) ? (b1 - 1 - i) : (a1 - 1 - (i - nb));
+    }
+};
+
+__device__ __forceinline__ KRange kranges(int dir, int rt, int nx, int KB) {
+    KRange k;
     const int r0 = rt * BM;
-    a0 = 0;
-    b0 = b1 = 0;
-    if (r0 < nx) { a1 = KB; return; }
-    if (dir > 0) { a1 = min(KB, (r0 + BM) / BK); return; }
-    a1 = (nx + BK - 1) / BK;
-    b0 = max(a1, r0 / BK);
-    b1 = KB;
+    k.a0 = 0;
+    k.b0 = k.b1 = 0;
+    if (r0 < nx) { k.a1 = KB; return k; }
+    if (dir > 0) { k.a1 = min(KB, (r0 + BM) / BK); return k; }
+    k.a1 = (nx + BK - 1) / BK;
+    k.b0 = max(k.a1, r0 / BK);
+    k.b1 = KB;
+    return k;
 }
 
 // ------------------------------------------------------------ the kernel
@@ -218,6 +234,12 @@ struct EpiArgs {
     const float2* phase;   // [2][N] or nullptr
 };
 
+// TMEM layout (512 columns): [0, 256) main accumulator A_hi B_hi of the
+// current K chunk; [256, 512) correction accumulator A_hi B_lo + A_lo B_hi of
+// the whole tile.  The tensor cores accumulate with truncation, so the main
+// sum is restarted every KC blocks and the chunk sums are added in FP32 with
+// round-to-nearest in the epilogue's registers; the correction terms are
+// 2^-11 smaller and stay in TMEM for the whole tile.
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                   const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -227,9 +249,9 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
     unsigned char* stage_base = smem;
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* acc_full = empty + STAGES;
-    uint64_t* acc_empty = acc_full + 2;
-    uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+    uint64_t* main_full = empty + STAGES;
+    uint64_t* main_empty = main_full + 1;
+    uint32_t* tmem_slot = (uint32_t*)(main_empty + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -239,15 +261,13 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);
-        }
+        mbar_init(main_full, 1);
+        mbar_init(main_empty, EPI_WARPS);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, 2 * ACC_COLS);
+        tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -264,29 +284,26 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
             for (int t = blockIdx.x; t < ts.total && ok; t += gridDim.x) {
                 const Tile tl = decode(ts, gt, dir, t);
                 const int l = gt.l[tl.g];
-                const int nx = n_extra(l);
-                int a0, a1, b0, b1;
-                kranges(dir, tl.rt, nx, ts.KB, a0, a1, b0, b1);
+                const KRange kr = kranges(dir, tl.rt, n_extra(l), ts.KB);
                 const int nbox = (tl.nmma + BBOX - 1) / BBOX;
                 const uint32_t bytes = 2 * A_BYTES + 2 * nbox * BBOX * BK * 4;
                 const int arow = l * N + tl.rt * BM;
                 const int brow = gt.line0[tl.g] + tl.ct * BN_MAX;
-                for (int seg = 0; seg < 2 && ok; ++seg) {
-                    const int k0 = seg ? b0 : a0, k1 = seg ? b1 : a1;
-                    for (int kb = k0; kb < k1; ++kb) {
-                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status)) { ok = false; break; }
-                        unsigned char* sb = stage_base + stage * STAGE_BYTES;
-                        mbar_expect_tx(&full[stage], bytes);
-                        tma_load_2d(sb, &tmA_hi, &full[stage], kb * BK, arow);
-                        tma_load_2d(sb + A_BYTES, &tmA_lo, &full[stage], kb * BK, arow);
-                        for (int b = 0; b < nbox; ++b) {
-                            tma_load_2d(sb + 2 * A_BYTES + b * BBOX * 128, &tmB_hi, &full[stage], kb * BK,
-                                        brow + b * BBOX);
-                            tma_load_2d(sb + 2 * A_BYTES + B_BYTES + b * BBOX * 128, &tmB_lo, &full[stage],
-                                        kb * BK, brow + b * BBOX);
-                        }
-                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                const int nkb = kr.count();
+                for (int i = 0; i < nkb; ++i) {
+                    const int kb = kr.at(i);
+                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status)) { ok = false; break; }
+                    unsigned char* sb = stage_base + stage * STAGE_BYTES;
+                    mbar_expect_tx(&full[stage], bytes);
+                    tma_load_2d(sb, &tmA_hi, &full[stage], kb * BK, arow);
+                    tma_load_2d(sb + A_BYTES, &tmA_lo, &full[stage], kb * BK, arow);
+                    for (int b = 0; b < nbox; ++b) {
+                        tma_load_2d(sb + 2 * A_BYTES + b * BBOX * 128, &tmB_hi, &full[stage], kb * BK,
+                                    brow + b * BBOX);
+                        tma_load_2d(sb + 2 * A_BYTES + B_BYTES + b * BBOX * 128, &tmB_lo, &full[stage],
+                                    kb * BK, brow + b * BBOX);
                     }
+                    if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
             }
         }
@@ -295,23 +312,25 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            int acc = 0;
-            uint32_t acc_phase = 0;
+            uint32_t mphase = 0;
             bool ok = true;
+            const uint32_t d_main = tmem_base, d_corr = tmem_base + 256;
             for (int t = blockIdx.x; t < ts.total && ok; t += gridDim.x) {
                 const Tile tl = decode(ts, gt, dir, t);
                 const int l = gt.l[tl.g];
-                const int nx = n_extra(l);
-                int a0, a1, b0, b1;
-                kranges(dir, tl.rt, nx, ts.KB, a0, a1, b0, b1);
+                const KRange kr = kranges(dir, tl.rt, n_extra(l), ts.KB);
                 const uint32_t idesc = idesc_tf32(BM, tl.nmma);
-                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * ACC_COLS);
-                if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1, abort_flag, status)) break;
-                tc_fence_after();
-                uint32_t accumulate = 0;
-                for (int seg = 0; seg < 2 && ok; ++seg) {
-                    const int k0 = seg ? b0 : a0, k1 = seg ? b1 : a1;
-                    for (int kb = k0; kb < k1; ++kb) {
+                const int nkb = kr.count();
+                uint32_t acc_corr = 0;
+                for (int c0 = 0; c0 < nkb && ok; c0 += KC) {
+                    // the epilogue must have drained the previous chunk (and, at a
+                    // tile start, read the previous tile's correction sum)
+                    if (!mbar_wait(main_empty, mphase ^ 1, abort_flag, status)) { ok = false; break; }
+                    mphase ^= 1;
+                    tc_fence_after();
+                    uint32_t acc_main = 0;
+                    const int c1 = min(nkb, c0 + KC);
+                    for (int i = c0; i < c1; ++i) {
                         if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
@@ -323,82 +342,101 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
                             const uint32_t off = ks * 32;   // 8 TF32 values = 32 bytes along K
                             const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa_lo + off);
                             const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_lo + off);
-                            mma_tf32(d_tmem, dah, dbh, idesc, accumulate);
-                            mma_tf32(d_tmem, dah, dbl, idesc, 1);
-                            mma_tf32(d_tmem, dal, dbh, idesc, 1);
-                            accumulate = 1;
+                            mma_tf32(d_main, dah, dbh, idesc, acc_main);
+                            mma_tf32(d_corr, dah, dbl, idesc, acc_corr);
+                            mma_tf32(d_corr, dal, dbh, idesc, 1);
+                            acc_main = 1;
+                            acc_corr = 1;
                         }
                         mma_commit(&empty[stage]);   // frees the stage once these MMAs finish
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
+                    if (!ok) break;
+                    mma_commit(main_full);
                 }
-                if (!ok) break;
-                mma_commit(&acc_full[acc]);
-                if (++acc == 2) { acc = 0; acc_phase ^= 1; }
             }
         }
         __syncwarp();
     } else {
-        // ------------------------------------------------ epilogue (warps 2..5)
+        // ------------------------------------------------ epilogue (EPI_WARPS warps)
+        const int ew = warp - 2;
         const int quarter = warp & 3;             // TMEM lane quarter this warp may access
-        int acc = 0;
-        uint32_t acc_phase = 0;
+        const int half = ew >> 2;                 // which 128 of the 256 columns
+        uint32_t mphase = 0;
         for (int t = blockIdx.x; t < ts.total; t += gridDim.x) {
             const Tile tl = decode(ts, gt, dir, t);
-            if (!mbar_wait(&acc_full[acc], acc_phase, abort_flag, status)) break;
-            tc_fence_after();
             const int l = gt.l[tl.g];
+            const KRange kr = kranges(dir, tl.rt, n_extra(l), ts.KB);
+            const int nkb = kr.count();
             const int nl = gt.line0[tl.g + 1] - gt.line0[tl.g];
             const int row = tl.rt * BM + quarter * 32 + lane;
-            const int cbase = tl.ct * BN_MAX;
-            const int ncols = min(BN_MAX, nl - cbase);
-            const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * ACC_COLS);
-            float2 ph = make_float2(1.f, 0.f);
-            if (ep.phase) ph = ep.phase[(size_t)(l & 1) * N + row];
-            for (int ch = 0; ch * 32 < tl.nmma; ++ch) {
-                float v[32];
-                tmem_ld32(taddr + ch * 32, v);
-                const int cl0 = ch * 32;
-                if (ep.mode == kOutUserC64) {
-                    float2* o = reinterpret_cast<float2*>(ep.out0);
-                    const size_t chan_base = (size_t)gt.chan0[tl.g] + (cbase >> 1);
+            const int cbase = tl.ct * BN_MAX + half * 128;     // first line of this thread's columns
+            const int ncols = min(128, nl - cbase);           // may be <= 0
+            const int nch = (tl.nmma > half * 128) ? ((min(tl.nmma - half * 128, 128) + 31) >> 5) : 0;
+            const uint32_t tl_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+            float acc[128];
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        if (cl0 + j < ncols) {
-                            o[(chan_base + ((cl0 + j) >> 1)) * N + row] = make_float2(v[j], v[j + 1]);
-                        }
-                    }
-                } else if (ep.mode == kOutUserF32) {
-                    const size_t chan_base = (size_t)gt.chan0[tl.g] + cbase;
+            for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+            bool ok = true;
+            for (int c0 = 0; c0 < nkb; c0 += KC) {
+                if (!mbar_wait(main_full, mphase, abort_flag, status)) { ok = false; break; }
+                mphase ^= 1;
+                tc_fence_after();
+                const bool last = c0 + KC >= nkb;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (cl0 + j < ncols) ep.out0[(chan_base + cl0 + j) * N + row] = v[j];
-                } else if (ep.mode == kOutPlanarF32) {
-                    const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+                for (int ch = 0; ch < 4; ++ch) {
+                    if (ch < nch) {
+                        float v[32];
+                        tmem_ld32(tl_addr + ch * 32, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (cl0 + j < ncols) ep.out0[(line_base + cl0 + j) * N + row] = v[j];
-                } else {   // kOutPlanarSplit, complex pairs with optional phase
-                    const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+                        for (int j = 0; j < 32; ++j) acc[ch * 32 + j] += v[j];
+                        if (last) {
+                            tmem_ld32(tl_addr + 256 + ch * 32, v);
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        if (cl0 + j < ncols) {
-                            const float re = v[j] * ph.x - v[j + 1] * ph.y;
-                            const float im = v[j] * ph.y + v[j + 1] * ph.x;
-                            const float hr = round_tf32(re), hi = round_tf32(im);
-                            const size_t o = (line_base + cl0 + j) * N + row;
-                            ep.out0[o] = hr;
-                            ep.out1[o] = round_tf32(re - hr);
-                            ep.out0[o + N] = hi;
-                            ep.out1[o + N] = round_tf32(im - hi);
+                            for (int j = 0; j < 32; ++j) acc[ch * 32 + j] += v[j];
                         }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(main_empty);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[acc]);
-            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            if (!ok) break;
+            if (ncols <= 0) continue;
+            float2 ph = make_float2(1.f, 0.f);
+            if (ep.phase) ph = ep.phase[(size_t)(l & 1) * N + row];
+            if (ep.mode == kOutUserC64) {
+                float2* o = reinterpret_cast<float2*>(ep.out0);
+                const size_t chan_base = (size_t)gt.chan0[tl.g] + (cbase >> 1);
+#pragma unroll
+                for (int j = 0; j < 128; j += 2)
+                    if (j < ncols) o[(chan_base + (j >> 1)) * N + row] = make_float2(acc[j], acc[j + 1]);
+            } else if (ep.mode == kOutUserF32) {
+                const size_t chan_base = (size_t)gt.chan0[tl.g] + cbase;
+#pragma unroll
+                for (int j = 0; j < 128; ++j)
+                    if (j < ncols) ep.out0[(chan_base + j) * N + row] = acc[j];
+            } else if (ep.mode == kOutPlanarF32) {
+                const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+#pragma unroll
+                for (int j = 0; j < 128; ++j)
+                    if (j < ncols) ep.out0[(line_base + j) * N + row] = acc[j];
+            } else {   // kOutPlanarSplit: complex pairs with optional phase, TF32 split
+                const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+#pragma unroll
+                for (int j = 0; j < 128; j += 2) {
+                    if (j < ncols) {
+                        const float re = acc[j] * ph.x - acc[j + 1] * ph.y;
+                        const float im = acc[j] * ph.y + acc[j + 1] * ph.x;
+                        const float hr = round_tf32(re), hi = round_tf32(im);
+                        const size_t o = (line_base + j) * N + row;
+                        ep.out0[o] = hr;
+                        ep.out1[o] = round_tf32(re - hr);
+                        ep.out0[o + N] = hi;
+                        ep.out1[o + N] = round_tf32(im - hi);
+                    }
+                }
+            }
         }
     }
 
@@ -406,7 +444,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, 2 * ACC_COLS);
+        tmem_dealloc(tmem_base, 512);
     }
 }
 
@@ -457,6 +495,7 @@ int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const floa
     EpiArgs ep{out_mode, out0, out1, phase};
     const CUtensorMap& ahi = dir > 0 ? p->tm_T_hi : p->tm_Tt_hi;
     const CUtensorMap& alo = dir > 0 ? p->tm_T_lo : p->tm_Tt_lo;
+    ProfScope ps(kKContractTF32, st);
     k_contract_tf32x3<<<grid, NTHREADS, smem, st>>>(ahi, alo, tb_hi, tb_lo, g, ts, N, dir, ep, p->status);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;

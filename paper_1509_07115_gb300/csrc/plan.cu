@@ -196,11 +196,13 @@ int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
     {
         const long long threads = (long long)L * N;
         const int bs = 128;
+        ProfScope ps(kKPlan, st);
         k_build_rows<<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(p->T64, N, p->l_max);
         DSBT_CUDA_TRY(cudaGetLastError());
     }
     {
         const int nthreads = 256;
+        ProfScope ps(kKPlan, st);
         k_twiddles<<<(N + nthreads - 1) / nthreads, nthreads, 0, st>>>(p->tw64, p->post64, p->tw32,
                                                                        p->post32, N);
         DSBT_CUDA_TRY(cudaGetLastError());
@@ -212,6 +214,7 @@ int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
     DSBT_CUDA_TRY(cudaMallocAsync((void**)&err, sizeof(unsigned long long), st));
     DSBT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned long long), st));
     for (int probe = 0; probe < 2; ++probe) {
+        ProfScope ps(kKPlan, st);
         dim3 gf((N * 32 + 255) / 256, L);
         k_probe_fwd<<<gf, 256, 0, st>>>(p->T64, y, N, probe);
         dim3 gb((N + 255) / 256, L);
@@ -232,6 +235,7 @@ int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
     }
     if (p->flags & DSBT_PLAN_TF32X3) {
         dim3 grid(N / 32, N / 32, L), block(32, 8);
+        ProfScope ps(kKPlan, st);
         k_split_T<<<grid, block, 0, st>>>(p->T64, p->Thi, p->Tlo, p->Tthi, p->Ttlo, N);
         DSBT_CUDA_TRY(cudaGetLastError());
     }

@@ -36,6 +36,26 @@ struct dsbt_plan {
 
 namespace dsbt {
 
+// ---- launch accounting (profile.cu)
+enum KernelId {
+    kKPlan = 0, kKDctFwd, kKDctInv, kKContract64, kKContractTF32, kKPhase, kKSplit,
+    kKTdsePot, kKTdseAng, kKTdseReduce, kNumKernels
+};
+// Wraps one kernel launch: counts it and, while profiling is enabled, records
+// CUDA events on `st` before the launch and at scope exit.
+class ProfScope {
+  public:
+    ProfScope(int kid, cudaStream_t st);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+  private:
+    int kid_;
+    cudaStream_t st_;
+    cudaEvent_t a_, b_;
+};
+
 // ---- plan build (plan.cu)
 int plan_build_factors(dsbt_plan* p, cudaStream_t st);
 

@@ -53,6 +53,11 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_kinetic_grouped.argtypes = [vp, _c_int_p, i, d, vp, vp, vp, sz, vp]
         lib.dsbt_device_status.argtypes = [vp, i, _c_int_p]
         lib.dsbt_last_error.restype = ctypes.c_char_p
+        lib.dsbt_launch_count.restype = ctypes.c_longlong
+        lib.dsbt_profile_enable.argtypes = [i]
+        lib.dsbt_profile_read.argtypes = [i, _c_int_p, ctypes.POINTER(d)]
+        lib.dsbt_kernel_name.argtypes = [i]
+        lib.dsbt_kernel_name.restype = ctypes.c_char_p
         _lib = lib
         return lib
 
@@ -189,3 +194,32 @@ class Plan:
         s = ctypes.c_int()
         _check(load().dsbt_device_status(self._h, int(bool(reset)), ctypes.byref(s)), "dsbt_device_status")
         return s.value
+
+
+# ------------------------------------------------------------------ tracing
+
+def launch_count() -> int:
+    """Kernel launches issued by the library in this process."""
+    return int(load().dsbt_launch_count())
+
+
+def profile_enable(on: bool = True):
+    """Start (and clear) or stop per-kernel CUDA-event timing in the library."""
+    _check(load().dsbt_profile_enable(int(bool(on))), "dsbt_profile_enable")
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total device ms)} of the recorded launches."""
+    lib = load()
+    out = {}
+    k = 0
+    while True:
+        name = lib.dsbt_kernel_name(k)
+        if name is None:
+            break
+        n, ms = ctypes.c_int(), ctypes.c_double()
+        _check(lib.dsbt_profile_read(k, ctypes.byref(n), ctypes.byref(ms)), "dsbt_profile_read")
+        if n.value:
+            out[name.decode()] = (n.value, ms.value)
+        k += 1
+    return out
