@@ -39,12 +39,30 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DSBT channel-transforms/s vs plain FP64 GPU at ≤1e-6 rel err; % roofline"
 UNIT = "channel-transforms/s"
-N, R_MAX, L_MAX, BATCH, TAU = 4096, 409.6, 63, 8, 0.05
+WORKLOADS = {
+    # the bench workload (one GPU)
+    "precision": dict(N=4096, R_MAX=409.6, L_MAX=63, BATCH=8,
+                      desc="precision form: N=4096, r_max=409.6, l=0..63 all m x batch 8 = 32768 complex64 "
+                           "Gaussian-sum channels; step = kinetic round trip F, T (+exp(-i k^2 tau/2)), T^T, F^T"),
+    # a smaller case of the same kernels for profiler captures (inputs still > L2)
+    "small": dict(N=2048, R_MAX=204.8, L_MAX=31, BATCH=8,
+                  desc="profiling case: N=2048, r_max=204.8, l=0..31 all m x batch 8 = 8192 complex64 channels"),
+}
+TAU = 0.05
+N, R_MAX, L_MAX, BATCH = 4096, 409.6, 63, 8
 DR = R_MAX / N
-WORKLOAD = ("precision form: N=4096, r_max=409.6, l=0..63 all m x batch 8 = 32768 complex64 "
-            "Gaussian-sum channels; step = kinetic round trip F, T (+exp(-i k^2 tau/2)), T^T, F^T")
+WORKLOAD = WORKLOADS["precision"]["desc"]
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rate ratio
 FLOP_PER_CHANNEL = 6.0 * N * N   # split-TF32 contraction, one direction, per complex channel
+
+
+def select_workload(name):
+    global N, R_MAX, L_MAX, BATCH, DR, WORKLOAD, FLOP_PER_CHANNEL
+    w = WORKLOADS[name]
+    N, R_MAX, L_MAX, BATCH = w["N"], w["R_MAX"], w["L_MAX"], w["BATCH"]
+    DR = R_MAX / N
+    WORKLOAD = w["desc"]
+    FLOP_PER_CHANNEL = 6.0 * N * N
 
 
 def load_peaks():
@@ -231,7 +249,7 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Gaussian-sum radial functions)",
-            "config": {"workload": WORKLOAD, "N": N, "l_max": L_MAX, "channels": 32768,
+            "config": {"workload": WORKLOAD, "N": N, "l_max": L_MAX, "channels": sum(2 * l + 1 for l in range(L_MAX + 1)) * BATCH,
                        "reference": "FP64 CPU oracle (plain C, binary128 DLOP rows), bounded sample"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -248,7 +266,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="precision", choices=sorted(WORKLOADS),
+                    help="'small' is a reduced case for profiler captures, not a bench line")
     args = ap.parse_args()
+    select_workload(args.workload)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

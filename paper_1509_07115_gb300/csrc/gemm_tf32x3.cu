@@ -41,12 +41,18 @@ constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t kSpinLimit = 1u << 25;
 
+// Tiles are visited group by group, largest l first (the groups with the most
+// work), and inside a group by cost level (row tiles with the longest K range
+// first), then column tile.  Consecutive tiles then share a row slab of T_l in
+// L2, and a group's B lines (<= 67 MB at the largest configuration) stay in L2
+// while all its row tiles use them.
 struct TileSpace {
     int RT;                        // row tiles (N / 128)
     int KB;                        // K blocks (N / 32)
-    int tpl;                       // tiles per cost level (sum of column tiles)
-    int total;                     // RT * tpl
-    int ct0[kMaxGroups + 1];       // prefix of column tiles per group
+    int total;                     // sum over groups of RT * CT
+    int order[kMaxGroups];         // group visited at position i
+    int t0[kMaxGroups + 1];        // first tile of position i
+    int ct[kMaxGroups];            // column tiles of the group at position i
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -184,12 +190,14 @@ struct Tile {
 
 __device__ __forceinline__ Tile decode(const TileSpace& ts, const GroupTable& gt, int dir, int t) {
     Tile tl;
-    const int q = t / ts.tpl, rem = t % ts.tpl;
-    tl.rt = (dir > 0) ? (q == 0 ? 0 : ts.RT - q) : q;
-    int g = 0;
-    while (g + 1 < gt.ngroups && ts.ct0[g + 1] <= rem) ++g;
+    int i = 0;
+    while (ts.t0[i + 1] <= t) ++i;
+    const int g = ts.order[i];
+    const int local = t - ts.t0[i];
+    const int q = local / ts.ct[i];
     tl.g = g;
-    tl.ct = rem - ts.ct0[g];
+    tl.ct = local - q * ts.ct[i];
+    tl.rt = (dir > 0) ? (q == 0 ? 0 : ts.RT - q) : q;
     const int nl = gt.line0[g + 1] - gt.line0[g];
     int left = nl - tl.ct * BN_MAX;
     if (left > BN_MAX) left = BN_MAX;
@@ -461,13 +469,15 @@ int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const floa
     TileSpace ts;
     ts.RT = N / BM;
     ts.KB = N / BK;
-    ts.ct0[0] = 0;
+    ts.t0[0] = 0;
     for (int i = 0; i < g.ngroups; ++i) {
-        const int nl = g.line0[i + 1] - g.line0[i];
-        ts.ct0[i + 1] = ts.ct0[i] + (nl + BN_MAX - 1) / BN_MAX;
+        const int gi = g.ngroups - 1 - i;   // largest l first
+        const int nl = g.line0[gi + 1] - g.line0[gi];
+        ts.order[i] = gi;
+        ts.ct[i] = (nl + BN_MAX - 1) / BN_MAX;
+        ts.t0[i + 1] = ts.t0[i] + ts.RT * ts.ct[i];
     }
-    ts.tpl = ts.ct0[g.ngroups];
-    ts.total = ts.RT * ts.tpl;
+    ts.total = ts.t0[g.ngroups];
     if (ts.total == 0) return DSBT_OK;
     if (out_mode == kOutPlanarSplit || out_mode == kOutUserC64) {
         for (int i = 0; i < g.ngroups; ++i) {
