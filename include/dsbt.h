@@ -145,6 +145,25 @@ DSBT_API int dsbt_kinetic_grouped(const dsbt_plan* plan, const int* counts, int 
                          void* stream);
 
 /*
+ * Grouped forward DSBT for callers that cannot allocate device memory (their
+ * device memory is owned by a framework allocator, a cudaMalloc's implicit
+ * synchronisation is not acceptable in their loop, or their memory budget is
+ * fixed at start-up).  The paper has no counterpart: this is a deployment
+ * variant of dsbt_forward_grouped with the same arguments and results, minus
+ * the workspace.  Its scratch is a static 64 MiB device array that every GPU
+ * loading this library reserves until the process exits; a call whose
+ * dsbt_workspace_size exceeds 64 MiB (roughly sum(counts) * N > 2^21 complex
+ * samples) is rejected with DSBT_ERR_INVALID before any launch.  The call
+ * allocates nothing: the first call on a device looks up the array's device
+ * address with cudaGetSymbolAddress (so make that first call before any stream
+ * capture).  All calls on a device share the one array, so calls that may
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  The plan must belong to the current device.
+ */
+DSBT_API int dsbt_forward_grouped_noalloc(const dsbt_plan* plan, const int* counts, int dtype,
+                                          const void* in, void* out, void* stream);
+
+/*
  * Read the plan's device status word (synchronous: waits for the device).
  * 0 = OK; 1 = a device-side wait in a tensor-core contraction gave up after its
  * iteration limit (the kernel then skipped its remaining work).  reset != 0

@@ -264,6 +264,13 @@ int single_call(int which, const dsbt_plan* p, int l, int nchan, int dtype, cons
 
 }  // namespace
 
+// Grouped forward with a scratch buffer supplied by the caller of this
+// function (used by entry points that bring their own scratch memory).
+int forward_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtype, const void* in,
+                                 void* out, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+    return grouped_call(0, p, counts, dtype, 0.0, in, out, scratch, scratch_bytes, st);
+}
+
 }  // namespace dsbt
 
 using namespace dsbt;
