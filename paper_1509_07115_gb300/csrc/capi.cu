@@ -68,6 +68,7 @@ struct Workspace {
     float* lo_b;
     float* planar;   // aliases hi_a
     float2* ph32;
+    int* sched;      // tile-scheduler counter of the tensor-core contraction
 };
 
 size_t lines_of(int total_channels, int dtype) {
@@ -78,7 +79,7 @@ size_t ws_bytes(int N, int total_channels, int dtype) {
     const size_t R = lines_of(total_channels, dtype);
     if (is_fp64(dtype))
         return align256(R * N * sizeof(double)) * 2 + align256(2 * (size_t)N * sizeof(double2)) + 256;
-    return align256(R * N * sizeof(float)) * 4 + align256(2 * (size_t)N * sizeof(float2)) + 256;
+    return align256(R * N * sizeof(float)) * 4 + align256(2 * (size_t)N * sizeof(float2)) + 256 + 256;
 }
 
 Workspace carve(void* base, int N, int total_channels, int dtype) {
@@ -98,6 +99,7 @@ Workspace carve(void* base, int N, int total_channels, int dtype) {
         w.lo_b = (float*)(p + 3 * b);
         w.planar = w.hi_a;
         w.ph32 = (float2*)(p + 4 * b);
+        w.sched = (int*)(p + 4 * b + align256(2 * (size_t)N * sizeof(float2)));
     }
     return w;
 }
@@ -162,7 +164,7 @@ int run_forward(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
     rc = dct_forward_f32(p, g, cplx, (const float*)in, w.hi_a, w.lo_a, st);
     if (rc) return rc;
     return contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, cplx ? kOutUserC64 : kOutUserF32, (float*)out,
-                           nullptr, nullptr, st);
+                           nullptr, nullptr, w.sched, st);
 }
 
 int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* in, void* out,
@@ -188,7 +190,7 @@ int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
                                                                         total);
     }
     DSBT_CUDA_TRY(cudaGetLastError());
-    rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, st);
+    rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, w.sched, st);
     if (rc) return rc;
     return dct_inverse_f32(p, g, cplx, w.planar, (float*)out, st);
 }
@@ -217,8 +219,8 @@ int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, 
     }
     DSBT_CUDA_TRY(cudaGetLastError());
     rc = dct_forward_f32(p, g, true, (const float*)in, w.hi_a, w.lo_a, st);
-    if (!rc) rc = contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, kOutPlanarSplit, w.hi_b, w.lo_b, w.ph32, st);
-    if (!rc) rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, st);
+    if (!rc) rc = contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, kOutPlanarSplit, w.hi_b, w.lo_b, w.ph32, w.sched, st);
+    if (!rc) rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, w.sched, st);
     if (!rc) rc = dct_inverse_f32(p, g, true, w.planar, (float*)out, st);
     return rc;
 }

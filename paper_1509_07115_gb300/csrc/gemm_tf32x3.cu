@@ -35,11 +35,16 @@ constexpr int BBOX = 64;                           // rows per B TMA box
 constexpr int STAGES = 2;
 constexpr int KC = 4;                              // K blocks per main-accumulator chunk
 constexpr int EPI_WARPS = 8;
+constexpr int QS = 4;                              // tile-queue slots (scheduler -> MMA, epilogue)
 constexpr int A_BYTES = BM * BK * 4;               // 16 KiB
 constexpr int B_BYTES = BN_MAX * BK * 4;           // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t kSpinLimit = 1u << 25;
+// B lines are re-read by every row tile of their group: keep them in L2.
+#ifndef DSBT_B_EVICT_LAST
+#define DSBT_B_EVICT_LAST 1
+#endif
 
 // Tiles are visited group by group, largest l first (the groups with the most
 // work), and inside a group by cost level (row tiles with the longest K range
@@ -106,6 +111,22 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         "%4}], [%2];" ::"r"(smem_u32(dst)),
         "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
         : "memory");
+}
+
+// Same load with an L2 cache-policy hint (a policy from createpolicy).
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                                 int y, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
+        "[%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
@@ -207,14 +228,15 @@ __device__ __forceinline__ Tile decode(const TileSpace& ts, const GroupTable& gt
 
 // K blocks of an output row tile, as two half-open ranges [a0, a1) and
 // [b0, b1) (b empty unless the inverse reads completion rows and a diagonal
-// band).  They are walked from the last block down, so that for the smooth
-// channels of physical interest the small far-K contributions are summed
-// before the large ones.
+// band).  Forward tiles walk K upwards from 0 and inverse tiles walk it
+// downwards from N, so every tile of a group starts at the same K block and the
+// tiles running at the same time stream the same B blocks through L2.
 struct KRange {
-    int a0, a1, b0, b1;
+    int a0, a1, b0, b1, up;
     __device__ __forceinline__ int count() const { return (a1 - a0) + (b1 - b0); }
     // i-th block in walking order
     __device__ __forceinline__ int at(int i) const {
+        if (up) return (i < a1 - a0) ? (a0 + i) : (b0 + i - (a1 - a0));
         const int nb = b1 - b0;
         return (i < nb) ? (b1 - 1 - i) : (a1 - 1 - (i - nb));
     }
@@ -223,6 +245,7 @@ struct KRange {
 __device__ __forceinline__ KRange kranges(int dir, int rt, int nx, int KB) {
     KRange k;
     const int r0 = rt * BM;
+    k.up = dir > 0;
     k.a0 = 0;
     k.b0 = k.b1 = 0;
     if (r0 < nx) { k.a1 = KB; return k; }
@@ -251,7 +274,8 @@ struct EpiArgs {
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                   const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
-                  GroupTable gt, TileSpace ts, int N, int dir, EpiArgs ep, unsigned* status) {
+                  GroupTable gt, TileSpace ts, int N, int dir, EpiArgs ep, unsigned* status,
+                  int* sched) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage_base = smem;
@@ -259,7 +283,10 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
     uint64_t* empty = full + STAGES;
     uint64_t* main_full = empty + STAGES;
     uint64_t* main_empty = main_full + 1;
-    uint32_t* tmem_slot = (uint32_t*)(main_empty + 1);
+    uint64_t* tq_full = main_empty + 1;
+    uint64_t* tq_empty = tq_full + QS;
+    int* tile_q = (int*)(tq_empty + QS);
+    uint32_t* tmem_slot = (uint32_t*)(tile_q + QS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -271,6 +298,10 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
         }
         mbar_init(main_full, 1);
         mbar_init(main_empty, EPI_WARPS);
+        for (int q = 0; q < QS; ++q) {
+            mbar_init(&tq_full[q], 1);
+            mbar_init(&tq_empty[q], 1 + EPI_WARPS);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -289,7 +320,22 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ts.total && ok; t += gridDim.x) {
+#if DSBT_B_EVICT_LAST
+            const uint64_t pol_b = policy_evict_last();
+#endif
+            int qslot = 0;
+            uint32_t qphase = 0;
+            while (ok) {
+                // dynamic tile scheduler: the next tile of the ordered list goes to
+                // whichever CTA asks first, so the tiles in flight always form one
+                // contiguous window of the list (at most two groups' B lines live in L2)
+                if (!mbar_wait(&tq_empty[qslot], qphase ^ 1, abort_flag, status)) { ok = false; break; }
+                int t = atomicAdd(sched, 1);
+                if (t >= ts.total) t = -1;
+                tile_q[qslot] = t;
+                mbar_arrive(&tq_full[qslot]);
+                if (++qslot == QS) { qslot = 0; qphase ^= 1; }
+                if (t < 0) break;
                 const Tile tl = decode(ts, gt, dir, t);
                 const int l = gt.l[tl.g];
                 const KRange kr = kranges(dir, tl.rt, n_extra(l), ts.KB);
@@ -306,10 +352,17 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
                     tma_load_2d(sb, &tmA_hi, &full[stage], kb * BK, arow);
                     tma_load_2d(sb + A_BYTES, &tmA_lo, &full[stage], kb * BK, arow);
                     for (int b = 0; b < nbox; ++b) {
+#if DSBT_B_EVICT_LAST
+                        tma_load_2d_hint(sb + 2 * A_BYTES + b * BBOX * 128, &tmB_hi, &full[stage], kb * BK,
+                                         brow + b * BBOX, pol_b);
+                        tma_load_2d_hint(sb + 2 * A_BYTES + B_BYTES + b * BBOX * 128, &tmB_lo, &full[stage],
+                                         kb * BK, brow + b * BBOX, pol_b);
+#else
                         tma_load_2d(sb + 2 * A_BYTES + b * BBOX * 128, &tmB_hi, &full[stage], kb * BK,
                                     brow + b * BBOX);
                         tma_load_2d(sb + 2 * A_BYTES + B_BYTES + b * BBOX * 128, &tmB_lo, &full[stage],
                                     kb * BK, brow + b * BBOX);
+#endif
                     }
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
@@ -323,7 +376,14 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
             uint32_t mphase = 0;
             bool ok = true;
             const uint32_t d_main = tmem_base, d_corr = tmem_base + 256;
-            for (int t = blockIdx.x; t < ts.total && ok; t += gridDim.x) {
+            int qslot = 0;
+            uint32_t qphase = 0;
+            while (ok) {
+                if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status)) break;
+                const int t = ((volatile int*)tile_q)[qslot];
+                mbar_arrive(&tq_empty[qslot]);
+                if (++qslot == QS) { qslot = 0; qphase ^= 1; }
+                if (t < 0) break;
                 const Tile tl = decode(ts, gt, dir, t);
                 const int l = gt.l[tl.g];
                 const KRange kr = kranges(dir, tl.rt, n_extra(l), ts.KB);
@@ -371,7 +431,15 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
         const int quarter = warp & 3;             // TMEM lane quarter this warp may access
         const int half = ew >> 2;                 // which 128 of the 256 columns
         uint32_t mphase = 0;
-        for (int t = blockIdx.x; t < ts.total; t += gridDim.x) {
+        int qslot = 0;
+        uint32_t qphase = 0;
+        while (true) {
+            if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status)) break;
+            const int t = ((volatile int*)tile_q)[qslot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tq_empty[qslot]);
+            if (++qslot == QS) { qslot = 0; qphase ^= 1; }
+            if (t < 0) break;
             const Tile tl = decode(ts, gt, dir, t);
             const int l = gt.l[tl.g];
             const KRange kr = kranges(dir, tl.rt, n_extra(l), ts.KB);
@@ -460,7 +528,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
 
 int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi,
                     const float* in_lo, int out_mode, float* out0, float* out1, const float2* phase,
-                    cudaStream_t st) {
+                    int* sched, cudaStream_t st) {
     if (!p->has_tmaps) {
         set_error("split-TF32 path needs a plan built with DSBT_PLAN_TF32X3");
         return DSBT_ERR_UNSUPPORTED;
@@ -505,8 +573,10 @@ int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const floa
     EpiArgs ep{out_mode, out0, out1, phase};
     const CUtensorMap& ahi = dir > 0 ? p->tm_T_hi : p->tm_Tt_hi;
     const CUtensorMap& alo = dir > 0 ? p->tm_T_lo : p->tm_Tt_lo;
+    DSBT_CUDA_TRY(cudaMemsetAsync(sched, 0, sizeof(int), st));
     ProfScope ps(kKContractTF32, st);
-    k_contract_tf32x3<<<grid, NTHREADS, smem, st>>>(ahi, alo, tb_hi, tb_lo, g, ts, N, dir, ep, p->status);
+    k_contract_tf32x3<<<grid, NTHREADS, smem, st>>>(ahi, alo, tb_hi, tb_lo, g, ts, N, dir, ep, p->status,
+                                                    sched);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }

@@ -89,10 +89,11 @@ int contract_f64(const dsbt_plan* p, const GroupTable& g, int dir, const double*
                  double* out, int out_cplx, const double2* phase, cudaStream_t st);
 
 // ---- split-TF32 tensor-core contraction (gemm_tf32x3.cu)
-// B operand: TF32 split lines [lines][N] (hi, lo).  Output modes:
+// B operand: TF32 split lines [lines][N] (hi, lo).  `sched` is a device int
+// (zeroed here before the launch) for the dynamic tile scheduler.  Output modes:
 enum OutMode { kOutUserC64 = 0, kOutUserF32 = 1, kOutPlanarF32 = 2, kOutPlanarSplit = 3 };
 int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi,
                     const float* in_lo, int out_mode, float* out0, float* out1,
-                    const float2* phase, cudaStream_t st);
+                    const float2* phase, int* sched, cudaStream_t st);
 
 }  // namespace dsbt
