@@ -171,6 +171,60 @@ DSBT_API int dsbt_forward_grouped_noalloc(const dsbt_plan* plan, const int* coun
  */
 DSBT_API int dsbt_device_status(const dsbt_plan* plan, int reset, int* status_out);
 
+/* ---------------------------------------------------------------------------
+ * Split-operator TDSE through the DSBT (Sec. 4.1, Eq. (81)) for an axially
+ * symmetric state (m = 0) in a linearly polarised field in the length gauge
+ * (vector potential A = 0):  H = p^2/2 + V(r) + E(t) r cos(theta),
+ * V(r) = -Z / sqrt(r^2 + a2).  The state is psi[l][i] (complex128, l = 0..L-1,
+ * i = 0..N-1, radial samples as for the DSBT) in the l representation.  One
+ * step of length tau:  psi <- Q Kin Q psi  with
+ *   Q   = P diag(exp(-i [V(r_i) + E r_i eta_j] tau/2)) P^T on the L-point
+ *         Gauss-Legendre grid eta_j (P[l][j] = sqrt((2l+1)/2) P_l(eta_j) sqrt(w_j)),
+ *   Kin = the kinetic step of dsbt_kinetic_grouped (one channel per l).
+ * Step s uses the field sample E[s / hold] (a DEVICE array of doubles).
+ * ------------------------------------------------------------------------- */
+typedef struct dsbt_tdse dsbt_tdse;
+
+/* Propagator over a plan built with DSBT_PLAN_FP64 and l_max >= L-1 (L <= 64);
+ * the plan must outlive it.  Owns small device tables (P, V, r, eta). */
+DSBT_API int dsbt_tdse_create(const dsbt_plan* plan, int L, double tau, double Z, double a2,
+                              dsbt_tdse** out);
+DSBT_API int dsbt_tdse_destroy(dsbt_tdse* tdse);
+
+/* Host copies of the angular grid: eta[L], w[L] and P[L*L] (any may be NULL). */
+DSBT_API int dsbt_tdse_angular(const dsbt_tdse* tdse, double* eta, double* w, double* P);
+
+/* Device workspace for dsbt_tdse_propagate (checkpoint_every = 0: five states
+ * of L*N complex128 plus one DSBT workspace) or for dsbt_tdse_gradient with
+ * nsteps steps and a checkpoint every K >= 1 steps (nsteps/K + K + 7 states
+ * plus one DSBT workspace). */
+DSBT_API size_t dsbt_tdse_workspace_size(const dsbt_tdse* tdse, int nsteps, int checkpoint_every);
+
+/* Propagate psi (device, in place) by nsteps steps.  tau_sign = +1 steps
+ * forward; tau_sign = -1 applies the inverse steps (tau -> -tau) with the field
+ * samples walked backwards, so a forward run followed by a backward run returns
+ * the initial state (unitarity, Eq. (25)). */
+DSBT_API int dsbt_tdse_propagate(const dsbt_tdse* tdse, void* psi, const double* E, int nsteps,
+                                 int hold, double tau_sign, void* workspace, size_t workspace_bytes,
+                                 void* stream);
+
+/* *out (device double) = sum over r_i > r_cut and all l of |psi[l][i]|^2. */
+DSBT_API int dsbt_tdse_observable(const dsbt_tdse* tdse, const void* psi, double r_cut, double* out,
+                                  void* stream);
+
+/*
+ * Gradient of O = sum_{r_i > r_cut} |psi_S|^2 (psi_S = state after nsteps from
+ * psi0, which is not modified) with respect to the nsamples field samples E,
+ * by the adjoint method: forward sweep storing a checkpoint every
+ * checkpoint_every steps, then a backward sweep that recomputes each segment
+ * from its checkpoint and runs the adjoint step (the same step with tau ->
+ * -tau, since P and T_l are orthogonal).  Writes O (device double) and dOdE
+ * (device array of nsamples doubles).
+ */
+DSBT_API int dsbt_tdse_gradient(const dsbt_tdse* tdse, const void* psi0, const double* E, int nsamples,
+                                int nsteps, int hold, double r_cut, int checkpoint_every, double* O,
+                                double* dOdE, void* workspace, size_t workspace_bytes, void* stream);
+
 /*
  * Launch accounting and kernel timing (tracing).  dsbt_launch_count returns the
  * number of kernel launches the library has issued in this process.

@@ -1,0 +1,90 @@
+"""Split-operator TDSE oracle (test infrastructure only).
+
+Follows the step sequence of Sec. 4.1 (Eq. (81)) for an axially symmetric state
+(m = 0, N_phi = 1) with vector potential A = 0 (length gauge), so that the
+plane-wave exponential in the middle of the step is the identity:
+
+    psi_1 = exp(-i U tau/2) psi            (angular grid, U = V(r) + E r eta)
+    c_1   = B Y psi_1                      (Y = P: grid -> l;  B = T_l F_l per l)
+    c_2   = exp(-i K tau/2) c_1            (K = k~_n^2 / 2, Eq. (76), grid Eq. (65))
+    c_3   = c_2                            (A = 0)
+    c_4   = exp(-i K tau/2) c_3
+    psi_4 = Y^T B^T c_4
+    psi'  = exp(-i U tau/2) psi_4
+
+The state is kept on the (r_i, eta_j) grid, psi[j][i] = Psi(r_i, eta_j) r_i
+sqrt(dr w_j) (the DVR of Sec. 4.1).  F_l and T_l come from the FP64 oracle;
+the Gauss-Legendre rule from numpy; P[l][j] = sqrt((2l+1)/2) P_l(eta_j) sqrt(w_j)
+(orthonormal on the rule).  Matrices are applied with numpy matmul.
+"""
+from __future__ import annotations
+
+import numpy as np
+from numpy.polynomial.legendre import leggauss
+from scipy.special import eval_legendre
+
+import oracle
+
+
+def angular(L: int):
+    """(eta, w, P) of the L-point Gauss-Legendre rule, P[l][j]."""
+    eta, w = leggauss(L)
+    P = np.array([np.sqrt((2 * l + 1) / 2.0) * eval_legendre(l, eta) * np.sqrt(w) for l in range(L)])
+    return eta, w, P
+
+
+class Model:
+    def __init__(self, N: int, r_max: float, L: int, tau: float, Z: float = 1.0, a2: float = 0.5):
+        self.N, self.r_max, self.L, self.tau = N, r_max, L, tau
+        self.dr = r_max / N
+        self.r = (np.arange(1, N + 1) - 0.5) * self.dr
+        self.V = -Z / np.sqrt(self.r ** 2 + a2)
+        self.eta, self.w, self.P = angular(L)
+        self.F = [oracle.F_matrix(N, l) for l in range(L)]
+        self.T = [oracle.T_matrix(N, l) for l in range(L)]
+        dk = np.pi / r_max
+        self.kt = []
+        for l in range(L):
+            n = np.arange(N) + oracle.p_of(l)
+            self.kt.append(np.where(n == 0, N, n) * dk)   # Eq. (65): n = 0 -> k~_N
+
+    # l representation <-> angular grid (Y and Y^T)
+    def to_l(self, psi_eta):
+        return self.P @ psi_eta
+
+    def to_eta(self, c):
+        return self.P.T @ c
+
+    def potential_half(self, psi_eta, E, tau):
+        U = self.V[None, :] + E * self.r[None, :] * self.eta[:, None]
+        return np.exp(-0.5j * tau * U) * psi_eta
+
+    def step(self, psi_eta, E, tau=None):
+        tau = self.tau if tau is None else tau
+        psi1 = self.potential_half(psi_eta, E, tau)
+        c = self.to_l(psi1)
+        c4 = np.empty_like(c)
+        for l in range(self.L):
+            b = self.T[l] @ (self.F[l] @ c[l])
+            half = np.exp(-0.5j * (self.kt[l] ** 2 / 2.0) * tau)
+            b = half * (half * b)
+            c4[l] = self.F[l].T @ (self.T[l].T @ b)
+        psi4 = self.to_eta(c4)
+        return self.potential_half(psi4, E, tau)
+
+    def run(self, psi_eta, E_samples, nsteps: int, hold: int):
+        x = psi_eta.copy()
+        for s in range(nsteps):
+            x = self.step(x, E_samples[s // hold])
+        return x
+
+    def observable(self, psi_eta, r_cut: float) -> float:
+        sel = self.r > r_cut
+        return float(np.sum(np.abs(psi_eta[:, sel]) ** 2))
+
+    def gaussian_l0(self):
+        """Normalised l = 0 state r exp(-r^2/2) in the l representation."""
+        c = np.zeros((self.L, self.N), dtype=np.complex128)
+        f = self.r * np.exp(-0.5 * self.r ** 2) * np.sqrt(self.dr)
+        c[0] = f / np.linalg.norm(f)
+        return c

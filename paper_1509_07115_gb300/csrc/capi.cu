@@ -273,6 +273,14 @@ int forward_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtyp
     return grouped_call(0, p, counts, dtype, 0.0, in, out, scratch, scratch_bytes, st);
 }
 
+// Grouped kinetic step with a scratch buffer supplied by the caller of this
+// function (the TDSE propagator's inner call).
+int kinetic_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtype, double tau,
+                                 const void* in, void* out, void* scratch, size_t scratch_bytes,
+                                 cudaStream_t st) {
+    return grouped_call(2, p, counts, dtype, tau, in, out, scratch, scratch_bytes, st);
+}
+
 }  // namespace dsbt
 
 using namespace dsbt;

@@ -58,6 +58,14 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_profile_read.argtypes = [i, _c_int_p, ctypes.POINTER(d)]
         lib.dsbt_kernel_name.argtypes = [i]
         lib.dsbt_kernel_name.restype = ctypes.c_char_p
+        lib.dsbt_tdse_create.argtypes = [vp, i, d, d, d, ctypes.POINTER(vp)]
+        lib.dsbt_tdse_destroy.argtypes = [vp]
+        lib.dsbt_tdse_angular.argtypes = [vp, vp, vp, vp]
+        lib.dsbt_tdse_workspace_size.argtypes = [vp, i, i]
+        lib.dsbt_tdse_workspace_size.restype = sz
+        lib.dsbt_tdse_propagate.argtypes = [vp, vp, vp, i, i, d, vp, sz, vp]
+        lib.dsbt_tdse_observable.argtypes = [vp, vp, d, vp, vp]
+        lib.dsbt_tdse_gradient.argtypes = [vp, vp, vp, i, i, i, d, i, vp, vp, vp, sz, vp]
         _lib = lib
         return lib
 
@@ -223,3 +231,106 @@ def profile_read() -> dict:
             out[name.decode()] = (n.value, ms.value)
         k += 1
     return out
+
+
+# ------------------------------------------------------------------ TDSE
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Tdse:
+    """Split-operator TDSE (m = 0, length gauge) through the DSBT: see
+    dsbt_tdse_* in include/dsbt.h.  State: complex128 CUDA tensor [L][N]."""
+
+    def __init__(self, plan: Plan, L: int, tau: float, Z: float = 1.0, a2: float = 0.5):
+        h = ctypes.c_void_p()
+        _check(load().dsbt_tdse_create(plan.handle, int(L), float(tau), float(Z), float(a2), ctypes.byref(h)),
+               "dsbt_tdse_create")
+        self._h, self.plan, self.L, self.N, self.tau = h, plan, int(L), plan.N, float(tau)
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dsbt_tdse_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def angular(self):
+        import numpy as np
+        eta = np.empty(self.L)
+        w = np.empty(self.L)
+        P = np.empty((self.L, self.L))
+        _check(load().dsbt_tdse_angular(self._h, eta.ctypes.data_as(ctypes.c_void_p),
+                                        w.ctypes.data_as(ctypes.c_void_p), P.ctypes.data_as(ctypes.c_void_p)),
+               "dsbt_tdse_angular")
+        return eta, w, P
+
+    def workspace(self, nsteps: int, K: int = 0) -> torch.Tensor:
+        nb = int(load().dsbt_tdse_workspace_size(self._h, int(nsteps), int(K)))
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        return self._ws
+
+    def _state(self, psi):
+        if psi.dtype != torch.complex128 or not psi.is_cuda or tuple(psi.shape) != (self.L, self.N) \
+                or not psi.is_contiguous():
+            raise ValueError(f"state must be a contiguous complex128 CUDA tensor of shape ({self.L}, {self.N})")
+
+    def propagate(self, psi: torch.Tensor, E: torch.Tensor, nsteps: int, hold: int = 1,
+                  backward: bool = False) -> torch.Tensor:
+        """In-place propagation by nsteps steps (backward=True: the inverse steps)."""
+        self._state(psi)
+        E = E.to(device="cuda", dtype=torch.float64).contiguous()
+        ws = self.workspace(nsteps, 0)
+        _check(load().dsbt_tdse_propagate(self._h, _ptr(psi), _ptr(E), int(nsteps), int(hold),
+                                          -1.0 if backward else 1.0, _ptr(ws), ws.numel(), _stream()),
+               "dsbt_tdse_propagate")
+        return psi
+
+    def observable(self, psi: torch.Tensor, r_cut: float) -> torch.Tensor:
+        self._state(psi)
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check(load().dsbt_tdse_observable(self._h, _ptr(psi), float(r_cut), _ptr(out), _stream()),
+               "dsbt_tdse_observable")
+        return out[0]
+
+    def gradient(self, psi0: torch.Tensor, E: torch.Tensor, nsteps: int, hold: int, r_cut: float,
+                 K: int = 20):
+        """(O, dO/dE) by the checkpointed adjoint (dsbt_tdse_gradient)."""
+        self._state(psi0)
+        E = E.to(device="cuda", dtype=torch.float64).contiguous()
+        O = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = torch.empty(E.numel(), dtype=torch.float64, device="cuda")
+        ws = self.workspace(nsteps, K)
+        _check(load().dsbt_tdse_gradient(self._h, _ptr(psi0), _ptr(E), int(E.numel()), int(nsteps), int(hold),
+                                         float(r_cut), int(K), _ptr(O), _ptr(g), _ptr(ws), ws.numel(),
+                                         _stream()), "dsbt_tdse_gradient")
+        return O[0], g
+
+
+class TdseObservable(torch.autograd.Function):
+    """O(E) = sum_{r > r_cut} |psi(T)|^2 as a differentiable function of the
+    field samples E.  forward: propagate + observable; backward: the adjoint
+    run of dsbt_tdse_gradient (checkpoint every K steps)."""
+
+    @staticmethod
+    def forward(ctx, E, tdse, psi0, nsteps, hold, r_cut, K):
+        psi = psi0.clone()
+        tdse.propagate(psi, E, nsteps, hold)
+        O = tdse.observable(psi, r_cut).clone()
+        ctx.save_for_backward(E)
+        ctx.args = (tdse, psi0, nsteps, hold, r_cut, K)
+        return O
+
+    @staticmethod
+    def backward(ctx, gO):
+        (E,) = ctx.saved_tensors
+        tdse, psi0, nsteps, hold, r_cut, K = ctx.args
+        _, g = tdse.gradient(psi0, E.detach(), nsteps, hold, r_cut, K)
+        return gO * g.to(E.dtype), None, None, None, None, None, None
