@@ -256,6 +256,60 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- TDSE leg
+
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (nominal; not in the measured peaks)
+
+
+def tdse_leg(dsbt, inputs, torch, dev):
+    """m = 0, l = 0..63, N = 2048, dr = 0.1, soft-Coulomb, 400 steps of 0.05 with
+    200 field samples (held 2 steps): propagation and adjoint-gradient timings,
+    and the FP64 contraction's rate against the nominal FP64 peak."""
+    import numpy as np
+    Nt, L, tau, steps = 2048, 64, 0.05, 400
+    plan = dsbt.Plan(Nt, 204.8, L - 1, tf32x3=False)
+    td = dsbt.Tdse(plan, L, tau)
+    c0 = np.zeros((L, Nt), dtype=np.complex128)
+    r = (np.arange(Nt) + 0.5) * 0.1
+    f = r * np.exp(-0.5 * r * r) * np.sqrt(0.1)
+    c0[0] = f / np.linalg.norm(f)
+    psi0 = torch.from_numpy(c0).to(dev)
+    E = torch.from_numpy(inputs.tdse_field(7, 200)).to(dev)
+    psi = psi0.clone()
+    td.propagate(psi, E, 20, 2)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    psi = psi0.clone()
+    dsbt.profile_enable(True)
+    e0.record(st)
+    td.propagate(psi, E, steps, 2)
+    e1.record(st)
+    torch.cuda.synchronize()
+    prop_ms = e0.elapsed_time(e1)
+    prof = dsbt.profile_read()
+    dsbt.profile_enable(False)
+    drift = abs(torch.linalg.vector_norm(psi).item() - 1.0)
+    e0.record(st)
+    O, g = td.gradient(psi0, E, steps, 2, 50.0, K=20)
+    e1.record(st)
+    torch.cuda.synchronize()
+    grad_ms = e0.elapsed_time(e1)
+    n64, ms64 = prof.get("contract_f64", (1, 0.0))
+    flop = 2.0 * 2 * L * Nt * Nt / 2   # per launch: 2 real lines x N^2/2 MACs x 2 flop, 64 channels
+    achieved = flop / (ms64 / n64 * 1e-3) / 1e12
+    td.close()
+    plan.close()
+    return {"config": "m=0, l=0..63, N=2048, dr=0.1, 400 steps of 0.05, soft-Coulomb -1/sqrt(r^2+0.5), "
+                      "200 field samples held 2 steps, observable = norm beyond r=50, checkpoint every 20",
+            "propagate_ms_per_step": prop_ms / steps, "gradient_ms_total": grad_ms,
+            "norm_drift_400_steps": drift, "observable": O.item(),
+            "kernels_ms_per_step": {k: v[1] / steps for k, v in prof.items()},
+            "roofline_contract_f64": {"bound": "fp64", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                                      "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                                      "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}}
+
+
 # ---------------------------------------------------------------- GPU leg
 
 def main():
@@ -266,6 +320,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-tdse", action="store_true", help="skip the TDSE propagation/adjoint leg")
     ap.add_argument("--workload", default="precision", choices=sorted(WORKLOADS),
                     help="'small' is a reduced case for profiler captures, not a bench line")
     args = ap.parse_args()
@@ -428,6 +483,10 @@ def main():
                                 "ms_per_step": f_ms, "speedup_of_split_tf32": value / world / fp64_value,
                                 "split_tf32_max_rel_err": {"kinetic_round_trip": err_rt, "forward": err_fw,
                                                            "norm_drift": drift}}
+
+    # ---------------------------------------------------------- TDSE (propagator + adjoint)
+    if rank == 0 and not args.no_tdse and args.workload == "precision":
+        line["tdse"] = tdse_leg(dsbt, inputs, torch, dev)
 
     # ---------------------------------------------------------- CPU oracle baseline
     if rank == 0 and world == 1 and not args.no_cpu:

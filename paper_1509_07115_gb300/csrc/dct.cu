@@ -11,9 +11,15 @@
 // costs one FFT.  The transpose F_l^T (DCT-III) inverts those steps:
 //     V_k = conj(w_k) (X_k - i X_{N-k}) (X_N = 0),  v = IFFT(V),  x_{2j} = v_j,
 //     x_{2j+1} = v_{N-1-j}.
-// The FFT is an in-shared-memory Stockham radix-8 (+ one radix-2/4 stage) with
-// one CTA per channel; global reads and writes are coalesced along the radial
-// index.  Twiddles come from tables built once per plan.
+//
+// FFT: Stockham autosort in shared memory, radix-16 stages (16 values per
+// thread in registers, a 4 x 4 register DFT) plus one radix-2/4/8 stage, with
+// N/16 threads per line and several lines per CTA when N < 4096.  Shared
+// memory is padded by one element every 16, which makes every stage's loads
+// and stores free of bank conflicts.  Twiddles of a radix-16 butterfly come
+// from two table loads (w, w^4) and products of depth <= 3.  Global accesses
+// move two complex values per thread (16 or 32 bytes), the pair (x_{2j},
+// x_{2j+1}) that the reordering sends to v_j and v_{N-1-j}.
 #include "plan.cuh"
 
 namespace dsbt {
@@ -49,63 +55,111 @@ template <typename C> __device__ __forceinline__ void dft8(C* x) {
     C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
     dft4(e0, e1, e2, e3);
     dft4(o0, o1, o2, o3);
-    // w8^q o_q, w8 = exp(-i pi/4)
-    C t1; t1.x = h * (o1.x + o1.y); t1.y = h * (o1.y - o1.x);
-    C t2 = cmi(o2);
-    C t3; t3.x = h * (o3.y - o3.x); t3.y = -h * (o3.x + o3.y);
+    C t1; t1.x = h * (o1.x + o1.y); t1.y = h * (o1.y - o1.x);     // exp(-i pi/4) o1
+    C t2 = cmi(o2);                                               // -i o2
+    C t3; t3.x = h * (o3.y - o3.x); t3.y = -h * (o3.x + o3.y);    // exp(-3 i pi/4) o3
     x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
     x[1] = cadd(e1, t1); x[5] = csub(e1, t1);
     x[2] = cadd(e2, t2); x[6] = csub(e2, t2);
     x[3] = cadd(e3, t3); x[7] = csub(e3, t3);
 }
 
-// One Stockham stage of radix RX on the shared buffer s (in place with a
-// barrier between the register loads and the stores).  The block has exactly
-// N/8 threads, so each thread owns 8/RX butterflies.
+// 16-point DFT as 4 x 4: X[k1 + 4 k2] = sum_n2 W4^{n2 k2} W16^{n2 k1} sum_n1 x[4 n1 + n2] W4^{n1 k1}.
+template <typename C> __device__ __forceinline__ void dft16(C* x) {
+    typedef decltype(x[0].x) R;
+    const R c8 = (R)0.92387953251128675613, s8 = (R)0.38268343236508977173, h = (R)0.70710678118654752440;
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
+    // x[4 k1 + n2] holds A[n2][k1]; multiply by W16^{n2 k1}
+    C t;
+    t = x[5];  x[5].x = c8 * t.x + s8 * t.y;  x[5].y = c8 * t.y - s8 * t.x;     // W^1
+    t = x[6];  x[6].x = h * (t.x + t.y);       x[6].y = h * (t.y - t.x);         // W^2
+    t = x[7];  x[7].x = s8 * t.x + c8 * t.y;  x[7].y = s8 * t.y - c8 * t.x;     // W^3
+    t = x[9];  x[9].x = h * (t.x + t.y);       x[9].y = h * (t.y - t.x);         // W^2
+    x[10] = cmi(x[10]);                                                          // W^4
+    t = x[11]; x[11].x = h * (t.y - t.x);      x[11].y = -h * (t.x + t.y);      // W^6
+    t = x[13]; x[13].x = s8 * t.x + c8 * t.y; x[13].y = s8 * t.y - c8 * t.x;    // W^3
+    t = x[14]; x[14].x = h * (t.y - t.x);      x[14].y = -h * (t.x + t.y);      // W^6
+    t = x[15]; x[15].x = -c8 * t.x - s8 * t.y; x[15].y = s8 * t.x - c8 * t.y;  // W^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+    // x[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4 x 4 block
+    C y[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) y[k1 + 4 * k2] = x[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = y[i];
+}
+
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+// One Stockham stage of radix RX on one line's padded shared buffer s; the
+// line has T = N/16 threads (lt = thread index within the line), each owning
+// 16/RX butterflies.  Barriers are CTA-wide (all lines run the same stages).
 template <int RX, typename C>
-__device__ __forceinline__ void stockham_stage(C* s, const C* __restrict__ tw, int N, int Ls) {
-    constexpr int PER = 8 / RX;
+__device__ __forceinline__ void stockham_stage(C* s, const C* __restrict__ tw, int N, int Ls, int lt, int T) {
+    constexpr int PER = 16 / RX;
     const int nb = N / RX;
     C x[PER][RX];
-    #pragma unroll
+#pragma unroll
     for (int u = 0; u < PER; ++u) {
-        const int j = threadIdx.x + u * blockDim.x;
-        const int k = j % Ls;
-        const int tstep = (N / (Ls * RX)) * k;
-        #pragma unroll
-        for (int r = 0; r < RX; ++r) {
-            C v = s[j + r * nb];
-            if (r > 0 && k > 0) v = cmul(v, tw[r * tstep]);
-            x[u][r] = v;
+        const int j = lt + u * T;
+        const int k = j & (Ls - 1);
+        const int b = k * (N / (Ls * RX));     // twiddle w = W_N^b, factor r uses w^r
+#pragma unroll
+        for (int r = 0; r < RX; ++r) x[u][r] = s[padi(j + r * nb)];
+        if (k > 0) {
+            if (RX == 16) {
+                const C w1 = tw[b], w4 = tw[4 * b];
+                const C w2 = cmul(w1, w1), w3 = cmul(w2, w1), w8 = cmul(w4, w4), w12 = cmul(w8, w4);
+                const C lo[4] = {w1, w1, w2, w3};
+                const C hi[4] = {w4, w4, w8, w12};
+#pragma unroll
+                for (int r = 1; r < 16; ++r) {
+                    const int a = r & 3, c = r >> 2;
+                    C w;
+                    if (c == 0) w = lo[a];
+                    else if (a == 0) w = hi[c];
+                    else w = cmul(hi[c], lo[a]);
+                    x[u][r] = cmul(x[u][r], w);
+                }
+            } else {
+#pragma unroll
+                for (int r = 1; r < RX; ++r) x[u][r] = cmul(x[u][r], tw[r * b]);
+            }
         }
-        if (RX == 8) dft8(x[u]);
+        if (RX == 16) dft16(x[u]);
+        else if (RX == 8) dft8(x[u]);
         else if (RX == 4) dft4(x[u][0], x[u][1], x[u][2], x[u][3]);
         else dft2(x[u][0], x[u][1]);
     }
     __syncthreads();
-    #pragma unroll
+#pragma unroll
     for (int u = 0; u < PER; ++u) {
-        const int j = threadIdx.x + u * blockDim.x;
-        const int k = j % Ls;
+        const int j = lt + u * T;
+        const int k = j & (Ls - 1);
         const int base = (j - k) * RX + k;
-        #pragma unroll
-        for (int q = 0; q < RX; ++q) s[base + q * Ls] = x[u][q];
+#pragma unroll
+        for (int q = 0; q < RX; ++q) s[padi(base + q * Ls)] = x[u][q];
     }
     __syncthreads();
 }
 
-// Forward FFT of length N (power of two, 256..8192) in shared memory.
+// Forward FFT of length N (power of two, 256..8192).
 template <typename C>
-__device__ void fft_smem(C* s, const C* __restrict__ tw, int N) {
+__device__ __forceinline__ void fft_smem(C* s, const C* __restrict__ tw, int N, int lt, int T) {
     int Ls = 1;
     int rem = N;
-    while (rem >= 8) {
-        stockham_stage<8>(s, tw, N, Ls);
-        Ls *= 8;
-        rem /= 8;
+    while (rem >= 16) {
+        stockham_stage<16>(s, tw, N, Ls, lt, T);
+        Ls *= 16;
+        rem /= 16;
     }
-    if (rem == 4) stockham_stage<4>(s, tw, N, Ls);
-    else if (rem == 2) stockham_stage<2>(s, tw, N, Ls);
+    if (rem == 8) stockham_stage<8>(s, tw, N, Ls, lt, T);
+    else if (rem == 4) stockham_stage<4>(s, tw, N, Ls, lt, T);
+    else if (rem == 2) stockham_stage<2>(s, tw, N, Ls, lt, T);
 }
 
 __device__ __forceinline__ int find_group(const GroupTable& g, int chan) {
@@ -117,120 +171,222 @@ __device__ __forceinline__ int find_group(const GroupTable& g, int chan) {
     return lo;
 }
 
-// Forward transform.  Output: planar lines.  SPLIT: write TF32 hi/lo pair.
+template <typename C> __device__ __forceinline__ void ld_pair(const C* p, C& a, C& b);
+template <> __device__ __forceinline__ void ld_pair<float2>(const float2* p, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+template <> __device__ __forceinline__ void ld_pair<double2>(const double2* p, double2& a, double2& b) {
+    a = p[0];
+    b = p[1];
+}
+__device__ __forceinline__ void ld_real_pair(const float* p, float& a, float& b) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld_real_pair(const double* p, double& a, double& b) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = v.x;
+    b = v.y;
+}
+template <typename C> __device__ __forceinline__ void st_pair(C* p, C a, C b);
+template <> __device__ __forceinline__ void st_pair<float2>(float2* p, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+template <> __device__ __forceinline__ void st_pair<double2>(double2* p, double2 a, double2 b) {
+    p[0] = a;
+    p[1] = b;
+}
+
+// Lines per CTA: enough lines of N/16 threads to fill 256 threads.
+__host__ __device__ inline int lines_per_cta(int N) { return (N >= 4096) ? 1 : 4096 / N; }
+
+// Forward transform.  Output: planar lines.  SPLIT: write the TF32 hi/lo pair.
 template <typename R, bool SPLIT>
-__global__ void k_dct_fwd(GroupTable g, int N, int cplx, const R* __restrict__ in,
-                          R* __restrict__ out0, R* __restrict__ out1,
-                          const typename Cx<R>::T* __restrict__ tw,
-                          const typename Cx<R>::T* __restrict__ post) {
+__global__ void __launch_bounds__(512) k_dct_fwd(GroupTable g, int N, int cplx, const R* __restrict__ in,
+                                                 R* __restrict__ out0, R* __restrict__ out1,
+                                                 const typename Cx<R>::T* __restrict__ tw,
+                                                 const typename Cx<R>::T* __restrict__ post) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);
-    const int chan = blockIdx.x;
-    const int gi = find_group(g, chan);
-    const int l = g.l[gi];
+    const int T = N >> 4;
+    const int G = lines_per_cta(N);
+    const int grp = threadIdx.x / T, lt = threadIdx.x % T;
+    C* s = reinterpret_cast<C*>(smem_raw) + (size_t)grp * (N + (N >> 4));
+    const int chan = blockIdx.x * G + grp;
+    const int nchan = g.chan0[g.ngroups];
+    const bool live = chan < nchan;
+    int gi = 0, l = 0, local = 0;
+    if (live) {
+        gi = find_group(g, chan);
+        l = g.l[gi];
+        local = chan - g.chan0[gi];
+    }
     const bool even = (l & 1) == 0;
-    const int local = chan - g.chan0[gi];
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        C x;
-        if (cplx) x = reinterpret_cast<const C*>(in)[(size_t)chan * N + t];
-        else { x.x = in[(size_t)chan * N + t]; x.y = (R)0; }
-        if (even && (t & 1)) { x.x = -x.x; x.y = -x.y; }
-        const int pos = (t & 1) ? (N - 1 - (t >> 1)) : (t >> 1);
-        s[pos] = x;
+    // load pairs (x_{2j}, x_{2j+1}) -> v_j, v_{N-1-j}; all loads issued before the stores
+    C a[8], b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int j = lt + u * T;
+        if (!live) {
+            a[u].x = a[u].y = b[u].x = b[u].y = (R)0;
+        } else if (cplx) {
+            ld_pair(reinterpret_cast<const C*>(in) + (size_t)chan * N + 2 * j, a[u], b[u]);
+        } else {
+            a[u].x = in[(size_t)chan * N + 2 * j];
+            b[u].x = in[(size_t)chan * N + 2 * j + 1];
+            a[u].y = b[u].y = (R)0;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int j = lt + u * T;
+        if (even) { b[u].x = -b[u].x; b[u].y = -b[u].y; }
+        s[padi(j)] = a[u];
+        s[padi(N - 1 - j)] = b[u];
     }
     __syncthreads();
-    fft_smem(s, tw, N);
+    fft_smem(s, tw, N, lt, T);
+    if (!live) return;
     const R sc1 = (R)sqrt(2.0 / (double)N), sc0 = (R)sqrt(1.0 / (double)N);
     const int line = g.line0[gi] + (cplx ? 2 * local : local);
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const C a = s[k], b = s[(N - k) & (N - 1)];
-        const C w = post[k];
-        // X = 1/2 (w a + conj(w) b)
-        C X;
-        X.x = (R)0.5 * ((w.x * a.x - w.y * a.y) + (w.x * b.x + w.y * b.y));
-        X.y = (R)0.5 * ((w.x * a.y + w.y * a.x) + (w.x * b.y - w.y * b.x));
-        const R sc = (k == 0) ? sc0 : sc1;
-        X.x *= sc;
-        X.y *= sc;
-        const int idx = even ? (N - 1 - k) : k;
+    R* o0 = out0 + (size_t)line * N;
+    R* o1 = SPLIT ? out1 + (size_t)line * N : nullptr;
+    for (int m = lt; m < (N >> 1); m += T) {
+        C X[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int k = 2 * m + e;
+            const C a = s[padi(k)], b = s[padi((N - k) & (N - 1))];
+            const C w = post[k];
+            C v;   // 1/2 (w a + conj(w) b)
+            v.x = (R)0.5 * ((w.x * a.x - w.y * a.y) + (w.x * b.x + w.y * b.y));
+            v.y = (R)0.5 * ((w.x * a.y + w.y * a.x) + (w.x * b.y - w.y * b.x));
+            const R sc = (k == 0) ? sc0 : sc1;
+            v.x *= sc;
+            v.y *= sc;
+            X[e] = v;
+        }
+        // storage index of k: odd l -> k; even l -> N-1-k (pairs stay adjacent, order flips)
+        const int idx = even ? (N - 2 - 2 * m) : 2 * m;
+        const C lo_e = even ? X[1] : X[0], hi_e = even ? X[0] : X[1];   // elements at idx, idx+1
         if (SPLIT) {
-            const float hr = round_tf32((float)X.x), hi_ = round_tf32((float)X.y);
-            out0[(size_t)line * N + idx] = hr;
-            out1[(size_t)line * N + idx] = round_tf32((float)X.x - hr);
+            const float r0 = round_tf32((float)lo_e.x), r1 = round_tf32((float)hi_e.x);
+            *reinterpret_cast<float2*>(o0 + idx) = make_float2(r0, r1);
+            *reinterpret_cast<float2*>(o1 + idx) =
+                make_float2(round_tf32((float)lo_e.x - r0), round_tf32((float)hi_e.x - r1));
             if (cplx) {
-                out0[(size_t)(line + 1) * N + idx] = hi_;
-                out1[(size_t)(line + 1) * N + idx] = round_tf32((float)X.y - hi_);
+                const float i0 = round_tf32((float)lo_e.y), i1 = round_tf32((float)hi_e.y);
+                *reinterpret_cast<float2*>(o0 + N + idx) = make_float2(i0, i1);
+                *reinterpret_cast<float2*>(o1 + N + idx) =
+                    make_float2(round_tf32((float)lo_e.y - i0), round_tf32((float)hi_e.y - i1));
             }
         } else {
-            out0[(size_t)line * N + idx] = X.x;
-            if (cplx) out0[(size_t)(line + 1) * N + idx] = X.y;
+            o0[idx] = lo_e.x;
+            o0[idx + 1] = hi_e.x;
+            if (cplx) {
+                o0[N + idx] = lo_e.y;
+                o0[N + idx + 1] = hi_e.y;
+            }
         }
     }
 }
 
 // Inverse transform F_l^T: planar lines -> caller layout.
 template <typename R>
-__global__ void k_dct_inv(GroupTable g, int N, int cplx, const R* __restrict__ in,
-                          R* __restrict__ out, const typename Cx<R>::T* __restrict__ tw,
-                          const typename Cx<R>::T* __restrict__ post) {
+__global__ void __launch_bounds__(512) k_dct_inv(GroupTable g, int N, int cplx, const R* __restrict__ in,
+                                                 R* __restrict__ out, const typename Cx<R>::T* __restrict__ tw,
+                                                 const typename Cx<R>::T* __restrict__ post) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);
-    const int chan = blockIdx.x;
-    const int gi = find_group(g, chan);
-    const int l = g.l[gi];
+    const int T = N >> 4;
+    const int G = lines_per_cta(N);
+    const int grp = threadIdx.x / T, lt = threadIdx.x % T;
+    C* s = reinterpret_cast<C*>(smem_raw) + (size_t)grp * (N + (N >> 4));
+    const int chan = blockIdx.x * G + grp;
+    const int nchan = g.chan0[g.ngroups];
+    const bool live = chan < nchan;
+    int gi = 0, l = 0, local = 0;
+    if (live) {
+        gi = find_group(g, chan);
+        l = g.l[gi];
+        local = chan - g.chan0[gi];
+    }
     const bool even = (l & 1) == 0;
-    const int local = chan - g.chan0[gi];
-    const int line = g.line0[gi] + (cplx ? 2 * local : local);
+    const int line = live ? g.line0[gi] + (cplx ? 2 * local : local) : 0;
     const R isc1 = (R)sqrt((double)N / 2.0), isc0 = (R)sqrt((double)N);
-    // unnormalised DCT-II coefficients X_k
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const int idx = even ? (N - 1 - k) : k;
-        C X;
-        X.x = in[(size_t)line * N + idx];
-        X.y = cplx ? in[(size_t)(line + 1) * N + idx] : (R)0;
-        const R sc = (k == 0) ? isc0 : isc1;
-        X.x *= sc;
-        X.y *= sc;
-        s[k] = X;
+    // unnormalised DCT-II coefficients X_k (pairs k = 2m, 2m+1); storage pair
+    // (idx, idx+1) holds (k, k+1) for odd l and (k+1, k) for even l
+    R re[8][2], im[8][2];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int m = lt + u * T;
+        re[u][0] = re[u][1] = im[u][0] = im[u][1] = (R)0;
+        if (live) {
+            const int idx = even ? (N - 2 - 2 * m) : 2 * m;
+            const R* li = in + (size_t)line * N;
+            ld_real_pair(li + idx, re[u][0], re[u][1]);
+            if (cplx) ld_real_pair(li + N + idx, im[u][0], im[u][1]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int m = lt + u * T;
+        C X0, X1;
+        X0.x = even ? re[u][1] : re[u][0];
+        X0.y = even ? im[u][1] : im[u][0];
+        X1.x = even ? re[u][0] : re[u][1];
+        X1.y = even ? im[u][0] : im[u][1];
+        const R s0 = (m == 0) ? isc0 : isc1;
+        X0.x *= s0; X0.y *= s0;
+        X1.x *= isc1; X1.y *= isc1;
+        s[padi(2 * m)] = X0;
+        s[padi(2 * m + 1)] = X1;
     }
     __syncthreads();
-    // V_k = conj(w_k) (X_k - i X_{N-k}); store conj(V_k) for the IFFT-by-FFT
-    C vk[8];
-    int cnt = 0;
-    for (int k = threadIdx.x; k < N; k += blockDim.x, ++cnt) {
-        const C a = s[k];
+    // V_k = conj(w_k) (X_k - i X_{N-k}); keep conj(V_k) for the IFFT-by-FFT
+    C vk[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int k = lt + u * T;
+        const C a = s[padi(k)];
         C b;
-        if (k == 0) { b.x = (R)0; b.y = (R)0; } else b = s[N - k];
+        if (k == 0) { b.x = (R)0; b.y = (R)0; } else b = s[padi(N - k)];
         C t;   // a - i b
         t.x = a.x + b.y;
         t.y = a.y - b.x;
         const C v = cmulc(t, post[k]);
-        vk[cnt].x = v.x;
-        vk[cnt].y = -v.y;
+        vk[u].x = v.x;
+        vk[u].y = -v.y;
     }
     __syncthreads();
-    cnt = 0;
-    for (int k = threadIdx.x; k < N; k += blockDim.x, ++cnt) s[k] = vk[cnt];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) s[padi(lt + u * T)] = vk[u];
     __syncthreads();
-    fft_smem(s, tw, N);
+    fft_smem(s, tw, N, lt, T);
+    if (!live) return;
     const R invN = (R)(1.0 / (double)N);
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        const int pos = (t & 1) ? (N - 1 - (t >> 1)) : (t >> 1);
-        C v = s[pos];
-        v.x *= invN;
-        v.y = -v.y * invN;
-        if (even && (t & 1)) { v.x = -v.x; v.y = -v.y; }
-        if (cplx) reinterpret_cast<C*>(out)[(size_t)chan * N + t] = v;
-        else out[(size_t)chan * N + t] = v.x;
+    for (int j = lt; j < (N >> 1); j += T) {
+        C a = s[padi(j)], b = s[padi(N - 1 - j)];   // x_{2j}, x_{2j+1} (conjugated, unscaled)
+        a.x *= invN; a.y = -a.y * invN;
+        b.x *= invN; b.y = -b.y * invN;
+        if (even) { b.x = -b.x; b.y = -b.y; }
+        if (cplx) {
+            st_pair(reinterpret_cast<C*>(out) + (size_t)chan * N + 2 * j, a, b);
+        } else {
+            out[(size_t)chan * N + 2 * j] = a.x;
+            out[(size_t)chan * N + 2 * j + 1] = b.x;
+        }
     }
 }
 
 template <typename K>
 static int launch_cfg(K kernel, int N, size_t elem, unsigned& threads, size_t& smem) {
-    threads = (unsigned)(N / 8);   // N >= 256: one radix-8 butterfly per thread
-    smem = (size_t)N * elem;
+    const int G = lines_per_cta(N);
+    threads = (unsigned)(G * (N / 16));
+    smem = (size_t)G * (N + N / 16) * elem;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) {
@@ -242,6 +398,10 @@ static int launch_cfg(K kernel, int N, size_t elem, unsigned& threads, size_t& s
 }
 
 static int nchannels(const GroupTable& g) { return g.chan0[g.ngroups]; }
+static unsigned nblocks(const GroupTable& g, int N) {
+    const int G = lines_per_cta(N);
+    return (unsigned)((nchannels(g) + G - 1) / G);
+}
 
 int dct_forward_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const double* in,
                     double* out, cudaStream_t st) {
@@ -250,8 +410,8 @@ int dct_forward_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const do
     int rc = launch_cfg(k_dct_fwd<double, false>, p->N, sizeof(double2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctFwd, st);
-    k_dct_fwd<double, false><<<nchannels(g), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, nullptr,
-                                                           p->tw64, p->post64);
+    k_dct_fwd<double, false><<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, nullptr,
+                                                               p->tw64, p->post64);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -263,8 +423,8 @@ int dct_forward_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const fl
     int rc = launch_cfg(k_dct_fwd<float, true>, p->N, sizeof(float2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctFwd, st);
-    k_dct_fwd<float, true><<<nchannels(g), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out_hi, out_lo,
-                                                         p->tw32, p->post32);
+    k_dct_fwd<float, true><<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out_hi, out_lo,
+                                                             p->tw32, p->post32);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -276,7 +436,7 @@ int dct_inverse_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const do
     int rc = launch_cfg(k_dct_inv<double>, p->N, sizeof(double2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctInv, st);
-    k_dct_inv<double><<<nchannels(g), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, p->tw64, p->post64);
+    k_dct_inv<double><<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, p->tw64, p->post64);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -288,7 +448,7 @@ int dct_inverse_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const fl
     int rc = launch_cfg(k_dct_inv<float>, p->N, sizeof(float2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctInv, st);
-    k_dct_inv<float><<<nchannels(g), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, p->tw32, p->post32);
+    k_dct_inv<float><<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, p->tw32, p->post32);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }

@@ -7,10 +7,10 @@
 // completion rows stop at the diagonal; inverse tiles read the completion rows
 // plus the rows at and below the diagonal.
 //
-// Wide groups (>= 16 real lines) use a 64 x 64 shared-memory tile, 4 x 4 outputs
+// Wide groups (> 8 real lines) use a 64 x 64 shared-memory tile, 4 x 4 outputs
 // per thread.  Narrow groups (the TDSE case: one complex channel per l) use one
-// warp per output row (forward, coalesced row reads and a shuffle reduction) or
-// one thread per output column (inverse, coalesced column reads).
+// warp per output row with coalesced row reads and a shuffle reduction, on T_l
+// for the forward and on the plan's FP64 copy of T_l^T for the inverse.
 #include "plan.cuh"
 
 namespace dsbt {
@@ -148,72 +148,103 @@ __global__ void __launch_bounds__(256) k_contract64_tile(GroupTable g, const dou
     }
 }
 
-// Narrow forward: one warp per output row n, up to kNarrow lines.
-__global__ void __launch_bounds__(256) k_contract64_rows(GroupTable g, const double* __restrict__ T64,
-                                                         int N, Lines in, OutLines out,
+// Narrow groups (<= kNarrow lines): one warp per output row of A = T_l
+// (forward) or A = T_l^T (inverse), lanes along K with four independent loads in
+// flight, shuffle reduction.  Forward rows stop at the diagonal; inverse rows read
+// the completion rows (K < n_extra) and K >= the row index.  Templated on the
+// largest line count NLMAX and on the caller layouts, with the line base
+// pointers computed once per warp, so the inner loop is loads and FMAs only.
+template <int NLMAX, bool ICPLX, bool OCPLX>
+__global__ void __launch_bounds__(256) k_contract64_rows(GroupTable g, const double* __restrict__ A64,
+                                                         int N, int dir, const double* __restrict__ inb,
+                                                         double* __restrict__ outb,
                                                          const double2* __restrict__ phase) {
     const int gi = blockIdx.y;
     const int nl = group_lines(g, gi);
-    if (nl > kNarrow) return;
+    if (nl > kNarrow || nl == 0) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= N || nl == 0) return;
-    const int r = N - 1 - warp;   // longest rows first
+    if (warp >= N) return;
+    const int r = (dir > 0) ? N - 1 - warp : warp;   // longest rows first
     const int l = g.l[gi];
     const int nx = n_extra(l);
-    const double* row = T64 + ((size_t)l * N + r) * N;
-    const int kend = (r < nx) ? N : r + 1;
-    double acc[kNarrow];
+    const double* row = A64 + ((size_t)l * N + r) * N;
+    constexpr int XS = ICPLX ? 2 : 1;   // element stride of a line in the caller layout
+    const double* xp[NLMAX];
 #pragma unroll
-    for (int j = 0; j < kNarrow; ++j) acc[j] = 0.0;
-    for (int k = lane; k < kend; k += 32) {
-        const double t = row[k];
+    for (int j = 0; j < NLMAX; ++j)
+        xp[j] = ICPLX ? inb + (size_t)(g.chan0[gi] + (j >> 1)) * N * 2 + (j & 1)
+                      : inb + (size_t)(g.line0[gi] + j) * N;
+    int s0b, s0e, s1b, s1e;   // K ranges [s0b, s0e) and [s1b, s1e)
+    if (dir > 0) {
+        s0b = 0; s0e = (r < nx) ? N : r + 1; s1b = s1e = 0;
+    } else if (r < nx) {
+        s0b = 0; s0e = N; s1b = s1e = 0;
+    } else {
+        s0b = 0; s0e = nx; s1b = r; s1e = N;
+    }
+    double acc[NLMAX];
 #pragma unroll
-        for (int j = 0; j < kNarrow; ++j)
-            if (j < nl) acc[j] = fma(t, *in.ptr(g, gi, j, k, N), acc[j]);
+    for (int j = 0; j < NLMAX; ++j) acc[j] = 0.0;
+    for (int seg = 0; seg < 2; ++seg) {
+        const int kb = seg ? s1b : s0b, ke = seg ? s1e : s0e;
+        int k = kb + lane;
+        for (; k + 96 < ke; k += 128) {
+            double t[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) t[q] = row[k + 32 * q];
+#pragma unroll
+            for (int j = 0; j < NLMAX; ++j) {
+                if (j < nl) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[j] = fma(t[q], xp[j][(size_t)(k + 32 * q) * XS], acc[j]);
+                }
+            }
+        }
+        for (; k < ke; k += 32) {
+            const double t = row[k];
+#pragma unroll
+            for (int j = 0; j < NLMAX; ++j)
+                if (j < nl) acc[j] = fma(t, xp[j][(size_t)k * XS], acc[j]);
+        }
     }
 #pragma unroll
-    for (int j = 0; j < kNarrow; ++j)
+    for (int j = 0; j < NLMAX; ++j)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
     if (lane == 0) {
         const double2 ph = phase ? phase[(size_t)(l & 1) * N + r] : make_double2(1.0, 0.0);
-        for (int j = 0; j < nl; j += 2) {
-            double re = acc[j], im = (j + 1 < nl) ? acc[j + 1] : 0.0;
-            if (phase) {
-                const double t = re * ph.x - im * ph.y;
-                im = re * ph.y + im * ph.x;
-                re = t;
+#pragma unroll
+        for (int j = 0; j < NLMAX; j += 2) {   // compile-time indices keep acc[] in registers
+            if (j < nl) {
+                double re = acc[j], im = (j + 1 < nl && j + 1 < NLMAX) ? acc[(j + 1) % NLMAX] : 0.0;
+                if (phase) {
+                    const double t = re * ph.x - im * ph.y;
+                    im = re * ph.y + im * ph.x;
+                    re = t;
+                }
+                double* o0 = OCPLX ? outb + ((size_t)(g.chan0[gi] + (j >> 1)) * N + r) * 2
+                                   : outb + (size_t)(g.line0[gi] + j) * N + r;
+                *o0 = re;
+                if (j + 1 < nl) {
+                    if (OCPLX) o0[1] = im;
+                    else o0[N] = im;
+                }
             }
-            *out.ptr(g, gi, j, r, N) = re;
-            if (j + 1 < nl) *out.ptr(g, gi, j + 1, r, N) = im;
         }
     }
 }
 
-// Narrow inverse: one thread per output column m.
-__global__ void __launch_bounds__(256) k_contract64_cols(GroupTable g, const double* __restrict__ T64,
-                                                         int N, Lines in, OutLines out) {
-    const int gi = blockIdx.y;
-    const int nl = group_lines(g, gi);
-    if (nl > kNarrow) return;
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= N || nl == 0) return;
-    const int l = g.l[gi];
-    const int nx = n_extra(l);
-    const double* T = T64 + (size_t)l * N * N;
-    double acc[kNarrow];
-#pragma unroll
-    for (int j = 0; j < kNarrow; ++j) acc[j] = 0.0;
-    for (int seg = 0; seg < 2; ++seg) {
-        const int n_beg = seg ? max(m, nx) : 0, n_end = seg ? N : min(nx, N);
-        for (int n = n_beg; n < n_end; ++n) {
-            const double t = T[(size_t)n * N + m];
-#pragma unroll
-            for (int j = 0; j < kNarrow; ++j)
-                if (j < nl) acc[j] = fma(t, *in.ptr(g, gi, j, n, N), acc[j]);
-        }
-    }
-    for (int j = 0; j < nl; ++j) *out.ptr(g, gi, j, m, N) = acc[j];
+template <int NLMAX>
+static void launch_rows(dim3 grid, cudaStream_t st, const GroupTable& g, const double* A, int N, int dir,
+                        const double* in, int in_cplx, double* out, int out_cplx, const double2* phase) {
+    if (in_cplx && out_cplx)
+        k_contract64_rows<NLMAX, true, true><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase);
+    else if (in_cplx)
+        k_contract64_rows<NLMAX, true, false><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase);
+    else if (out_cplx)
+        k_contract64_rows<NLMAX, false, true><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase);
+    else
+        k_contract64_rows<NLMAX, false, false><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase);
 }
 
 }  // namespace
@@ -249,15 +280,18 @@ int contract_f64(const dsbt_plan* p, const GroupTable& g, int dir, const double*
         DSBT_CUDA_TRY(cudaGetLastError());
     }
     if (any_narrow) {
-        if (dir > 0) {
-            dim3 grid((N * 32 + 255) / 256, g.ngroups);
-            ProfScope ps(kKContract64, st);
-            k_contract64_rows<<<grid, 256, 0, st>>>(g, p->T64, N, li, lo, phase);
-        } else {
-            dim3 grid((N + 255) / 256, g.ngroups);
-            ProfScope ps(kKContract64, st);
-            k_contract64_cols<<<grid, 256, 0, st>>>(g, p->T64, N, li, lo);
+        int nlmax = 0;
+        for (int i = 0; i < g.ngroups; ++i) {
+            const int nl = g.line0[i + 1] - g.line0[i];
+            if (nl <= kNarrow) nlmax = max(nlmax, nl);
         }
+        dim3 grid((N * 32 + 255) / 256, g.ngroups);
+        const double* A = dir > 0 ? p->T64 : p->Tt64;
+        ProfScope ps(kKContract64, st);
+        if (nlmax <= 1) launch_rows<1>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase);
+        else if (nlmax <= 2) launch_rows<2>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase);
+        else if (nlmax <= 4) launch_rows<4>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase);
+        else launch_rows<8>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase);
         DSBT_CUDA_TRY(cudaGetLastError());
     }
     return DSBT_OK;

@@ -112,6 +112,18 @@ __global__ void k_build_rows(double* __restrict__ T64, int N, int lmax) {
     }
 }
 
+// FP64 transpose of T_l (32x32 shared-memory tiles).
+__global__ void k_transpose64(const double* __restrict__ T64, double* __restrict__ Tt64, int N) {
+    __shared__ double t[32][33];
+    const size_t off = (size_t)blockIdx.z * N * N;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y)
+        t[k][threadIdx.x] = T64[off + (size_t)(r0 + k) * N + c0 + threadIdx.x];
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y)
+        Tt64[off + (size_t)(c0 + k) * N + r0 + threadIdx.x] = t[threadIdx.x][k];
+}
+
 // TF32 split of T_l and of its transpose (32x32 shared-memory tiles).
 __global__ void k_split_T(const double* __restrict__ T64, float* __restrict__ Thi,
                           float* __restrict__ Tlo, float* __restrict__ Tthi,
@@ -233,6 +245,12 @@ int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
         set_error("plan check failed: max |T^T T x - x| = %.3e", e);
         return DSBT_ERR_PLAN_CHECK;
     }
+    if (p->flags & DSBT_PLAN_FP64) {
+        dim3 grid(N / 32, N / 32, L), block(32, 8);
+        ProfScope ps(kKPlan, st);
+        k_transpose64<<<grid, block, 0, st>>>(p->T64, p->Tt64, N);
+        DSBT_CUDA_TRY(cudaGetLastError());
+    }
     if (p->flags & DSBT_PLAN_TF32X3) {
         dim3 grid(N / 32, N / 32, L), block(32, 8);
         ProfScope ps(kKPlan, st);
@@ -245,6 +263,7 @@ int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
 static void plan_free(dsbt_plan* p) {
     if (!p) return;
     cudaFree(p->T64);
+    cudaFree(p->Tt64);
     cudaFree(p->Thi);
     cudaFree(p->Tlo);
     cudaFree(p->Tthi);
@@ -294,6 +313,7 @@ extern "C" int dsbt_plan_create(int N, double r_max, int l_max, int flags, void*
         return cudaMalloc(ptr, bytes) == cudaSuccess;
     };
     bool ok = alloc((void**)&p->T64, L * p->nn * sizeof(double));
+    if (ok && (flags & DSBT_PLAN_FP64)) ok = alloc((void**)&p->Tt64, L * p->nn * sizeof(double));
     if (ok && (flags & DSBT_PLAN_TF32X3)) {
         ok = alloc((void**)&p->Thi, L * p->nn * sizeof(float)) &&
              alloc((void**)&p->Tlo, L * p->nn * sizeof(float)) &&

@@ -15,6 +15,9 @@ struct dsbt_plan {
     size_t nn;                 // N * N
     // FP64 factors, [(l_max+1)][N][N], entry (n - p_l, m - p_l) of T_l
     double* T64;
+    // FP64 transposes T_l^T (same layout), kept with DSBT_PLAN_FP64 so that the
+    // inverse contraction of narrow groups also reads contiguous rows
+    double* Tt64;
     // split-TF32 factors (FP32 containers holding TF32 values), same layout:
     // T = Thi + Tlo (A operand of the forward contraction) and the transposes
     // Tt = T^T (A operand of the inverse contraction).

@@ -50,7 +50,7 @@ namespace dsbt {
 
 namespace {
 
-constexpr int TI = 32;          // radial points per tile of the angular kernel
+constexpr int TI = 16;          // radial points per tile of the angular kernel
 constexpr int kLMax = 64;
 
 // Gauss-Legendre nodes and weights by Newton's method on P_L (three-term
@@ -129,7 +129,6 @@ __global__ void __launch_bounds__(256) k_tdse_potential(const double2* __restric
     double2* xs = reinterpret_cast<double2*>(Ps + kLMax * kLMax);  // [L][TI]
     double2* xe = xs + kLMax * TI;                                 // [L][TI]
     double2* as = xe + kLMax * TI;                                 // [L][TI]
-    double2* ae = as + kLMax * TI;                                 // [L][TI]
     __shared__ double red[2][8];
     const int i0 = blockIdx.x * TI;
     const int tid = threadIdx.x;
@@ -216,7 +215,7 @@ inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int potential(const dsbt_tdse* t, const double2* x, double2* y, const double* E, int eidx, double ht,
               const double2* aux, double gscale, double* gacc, cudaStream_t st) {
-    const size_t smem = (size_t)kLMax * kLMax * sizeof(double) + 4 * (size_t)kLMax * TI * sizeof(double2);
+    const size_t smem = (size_t)kLMax * kLMax * sizeof(double) + 3 * (size_t)kLMax * TI * sizeof(double2);
     static bool attr = false;
     if (!attr) {
         DSBT_CUDA_TRY(cudaFuncSetAttribute(k_tdse_potential, cudaFuncAttributeMaxDynamicSharedMemorySize,
