@@ -74,7 +74,7 @@ extern "C" {
 typedef struct dsbt_plan dsbt_plan;
 
 /*
- * Build a plan for grids of N points (256 <= N <= 8192, N a power of two) and
+ * Build a plan for grids of N points (256 <= N <= 8192, N a multiple of 256) and
  * angular momenta l = 0..l_max (0 <= l_max <= 64, with ceil((l_max+1)/2) <= N).
  * r_max only sets the momentum step dk = pi / r_max used by the kinetic phase.
  * Runs on the current CUDA device and stream `stream`; returns once the plan is

@@ -12,9 +12,10 @@
 //     V_k = conj(w_k) (X_k - i X_{N-k}) (X_N = 0),  v = IFFT(V),  x_{2j} = v_j,
 //     x_{2j+1} = v_{N-1-j}.
 //
-// FFT: Stockham autosort in shared memory, radix-16 stages (16 values per
-// thread in registers, a 4 x 4 register DFT) plus one radix-2/4/8 stage, with
-// N/16 threads per line and several lines per CTA when N < 4096.  Shared
+// FFT: Stockham autosort in shared memory for N = 256 q (q = 1..32): radix-16
+// stages (16 values per thread in registers, a 4 x 4 register DFT), one
+// radix-2/4/8 stage, then one stage per odd prime factor of q (3..31), with
+// N/16 threads per line and several lines per CTA when N/16 < 256.  Shared
 // memory is padded by one element every 16, which makes every stage's loads
 // and stores free of bank conflicts.  Twiddles of a radix-16 butterfly come
 // from two table loads (w, w^4) and products of depth <= 3.  Global accesses
@@ -147,19 +148,93 @@ __device__ __forceinline__ void stockham_stage(C* s, const C* __restrict__ tw, i
     __syncthreads();
 }
 
-// Forward FFT of length N (power of two, 256..8192).
-template <typename C>
-__device__ __forceinline__ void fft_smem(C* s, const C* __restrict__ tw, int N, int lt, int T) {
+// One Stockham stage of odd prime radix P (3..31), used after the power-of-two
+// stages for N = 256 q.  Butterflies are spread over the line's T threads.
+// Only the twiddled inputs are held across the barrier; after it each output
+// of the P-point DFT is accumulated and stored at once, with the P-th roots of
+// unity read from shared memory (sroot, filled by the caller).
+template <int P, typename C>
+__device__ __forceinline__ void stockham_stage_odd(C* s, const C* __restrict__ tw, const C* sroot, int N,
+                                                   int Ls, int lt, int T) {
+    constexpr int PER = (16 + P - 1) / P;
+    const int nb = N / P;
+    C x[PER][P];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = lt + u * T;
+        if (j < nb) {
+            const int k = j % Ls;
+            const int b = k * (N / (Ls * P));
+#pragma unroll
+            for (int r = 0; r < P; ++r) x[u][r] = s[padi(j + r * nb)];
+            if (k > 0) {
+#pragma unroll
+                for (int r = 1; r < P; ++r) x[u][r] = cmul(x[u][r], tw[r * b]);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = lt + u * T;
+        if (j < nb) {
+            const int k = j % Ls;
+            const int base = (j - k) * P + k;
+#pragma unroll 1
+            for (int q = 0; q < P; ++q) {
+                C acc = x[u][0];
+                int e = 0;
+#pragma unroll
+                for (int r = 1; r < P; ++r) {
+                    e += q;
+                    if (e >= P) e -= P;   // e = r q mod P
+                    acc = cadd(acc, cmul(x[u][r], sroot[e]));
+                }
+                s[padi(base + q * Ls)] = acc;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Forward FFT of length N = 256 q: radix-16 stages, one radix-2/4/8 stage for
+// the rest of the power of two and, when MIXED, one stage per odd prime factor
+// of q (3..31; sroot is a 32-entry shared scratch for the roots).
+template <bool MIXED, typename C>
+__device__ __forceinline__ void fft_smem(C* s, const C* __restrict__ tw, C* sroot, int N, int lt, int T) {
     int Ls = 1;
     int rem = N;
-    while (rem >= 16) {
+    while ((rem & 15) == 0) {
         stockham_stage<16>(s, tw, N, Ls, lt, T);
         Ls *= 16;
-        rem /= 16;
+        rem >>= 4;
     }
-    if (rem == 8) stockham_stage<8>(s, tw, N, Ls, lt, T);
-    else if (rem == 4) stockham_stage<4>(s, tw, N, Ls, lt, T);
-    else if (rem == 2) stockham_stage<2>(s, tw, N, Ls, lt, T);
+    if ((rem & 7) == 0) { stockham_stage<8>(s, tw, N, Ls, lt, T); Ls *= 8; rem >>= 3; }
+    else if ((rem & 3) == 0) { stockham_stage<4>(s, tw, N, Ls, lt, T); Ls *= 4; rem >>= 2; }
+    else if ((rem & 1) == 0) { stockham_stage<2>(s, tw, N, Ls, lt, T); Ls *= 2; rem >>= 1; }
+    if (!MIXED) return;
+    const int primes[10] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+    for (int i = 0; i < 10 && rem > 1; ++i) {
+        const int p = primes[i];
+        while (rem % p == 0) {
+            for (int m = threadIdx.x; m < p; m += blockDim.x) sroot[m] = tw[m * (N / p)];   // W_p^m
+            __syncthreads();
+            switch (p) {
+                case 3: stockham_stage_odd<3>(s, tw, sroot, N, Ls, lt, T); break;
+                case 5: stockham_stage_odd<5>(s, tw, sroot, N, Ls, lt, T); break;
+                case 7: stockham_stage_odd<7>(s, tw, sroot, N, Ls, lt, T); break;
+                case 11: stockham_stage_odd<11>(s, tw, sroot, N, Ls, lt, T); break;
+                case 13: stockham_stage_odd<13>(s, tw, sroot, N, Ls, lt, T); break;
+                case 17: stockham_stage_odd<17>(s, tw, sroot, N, Ls, lt, T); break;
+                case 19: stockham_stage_odd<19>(s, tw, sroot, N, Ls, lt, T); break;
+                case 23: stockham_stage_odd<23>(s, tw, sroot, N, Ls, lt, T); break;
+                case 29: stockham_stage_odd<29>(s, tw, sroot, N, Ls, lt, T); break;
+                default: stockham_stage_odd<31>(s, tw, sroot, N, Ls, lt, T); break;
+            }
+            Ls *= p;
+            rem /= p;
+        }
+    }
 }
 
 __device__ __forceinline__ int find_group(const GroupTable& g, int chan) {
@@ -200,11 +275,12 @@ template <> __device__ __forceinline__ void st_pair<double2>(double2* p, double2
     p[1] = b;
 }
 
-// Lines per CTA: enough lines of N/16 threads to fill 256 threads.
-__host__ __device__ inline int lines_per_cta(int N) { return (N >= 4096) ? 1 : 4096 / N; }
+// Lines per CTA: as many lines of N/16 threads as fit in 256 threads (one
+// line of up to 512 threads when N/16 > 256).
+__host__ __device__ inline int lines_per_cta(int N) { return (N / 16 >= 256) ? 1 : 256 / (N / 16); }
 
 // Forward transform.  Output: planar lines.  SPLIT: write the TF32 hi/lo pair.
-template <typename R, bool SPLIT>
+template <typename R, bool SPLIT, bool MIXED>
 __global__ void __launch_bounds__(512) k_dct_fwd(GroupTable g, int N, int cplx, const R* __restrict__ in,
                                                  R* __restrict__ out0, R* __restrict__ out1,
                                                  const typename Cx<R>::T* __restrict__ tw,
@@ -248,7 +324,8 @@ __global__ void __launch_bounds__(512) k_dct_fwd(GroupTable g, int N, int cplx, 
         s[padi(N - 1 - j)] = b[u];
     }
     __syncthreads();
-    fft_smem(s, tw, N, lt, T);
+    __shared__ C sroot[32];
+    fft_smem<MIXED>(s, tw, sroot, N, lt, T);
     if (!live) return;
     const R sc1 = (R)sqrt(2.0 / (double)N), sc0 = (R)sqrt(1.0 / (double)N);
     const int line = g.line0[gi] + (cplx ? 2 * local : local);
@@ -259,7 +336,7 @@ __global__ void __launch_bounds__(512) k_dct_fwd(GroupTable g, int N, int cplx, 
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int k = 2 * m + e;
-            const C a = s[padi(k)], b = s[padi((N - k) & (N - 1))];
+            const C a = s[padi(k)], b = s[padi(k == 0 ? 0 : N - k)];
             const C w = post[k];
             C v;   // 1/2 (w a + conj(w) b)
             v.x = (R)0.5 * ((w.x * a.x - w.y * a.y) + (w.x * b.x + w.y * b.y));
@@ -295,7 +372,7 @@ __global__ void __launch_bounds__(512) k_dct_fwd(GroupTable g, int N, int cplx, 
 }
 
 // Inverse transform F_l^T: planar lines -> caller layout.
-template <typename R>
+template <typename R, bool MIXED>
 __global__ void __launch_bounds__(512) k_dct_inv(GroupTable g, int N, int cplx, const R* __restrict__ in,
                                                  R* __restrict__ out, const typename Cx<R>::T* __restrict__ tw,
                                                  const typename Cx<R>::T* __restrict__ post) {
@@ -365,7 +442,8 @@ __global__ void __launch_bounds__(512) k_dct_inv(GroupTable g, int N, int cplx, 
 #pragma unroll
     for (int u = 0; u < 16; ++u) s[padi(lt + u * T)] = vk[u];
     __syncthreads();
-    fft_smem(s, tw, N, lt, T);
+    __shared__ C sroot[32];
+    fft_smem<MIXED>(s, tw, sroot, N, lt, T);
     if (!live) return;
     const R invN = (R)(1.0 / (double)N);
     for (int j = lt; j < (N >> 1); j += T) {
@@ -403,15 +481,17 @@ static unsigned nblocks(const GroupTable& g, int N) {
     return (unsigned)((nchannels(g) + G - 1) / G);
 }
 
+static bool pow2(int N) { return (N & (N - 1)) == 0; }
+
 int dct_forward_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const double* in,
                     double* out, cudaStream_t st) {
     if (nchannels(g) == 0) return DSBT_OK;
     unsigned th; size_t sm;
-    int rc = launch_cfg(k_dct_fwd<double, false>, p->N, sizeof(double2), th, sm);
+    auto k = pow2(p->N) ? k_dct_fwd<double, false, false> : k_dct_fwd<double, false, true>;
+    int rc = launch_cfg(k, p->N, sizeof(double2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctFwd, st);
-    k_dct_fwd<double, false><<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, nullptr,
-                                                               p->tw64, p->post64);
+    k<<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, nullptr, p->tw64, p->post64);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -420,11 +500,11 @@ int dct_forward_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const fl
                     float* out_hi, float* out_lo, cudaStream_t st) {
     if (nchannels(g) == 0) return DSBT_OK;
     unsigned th; size_t sm;
-    int rc = launch_cfg(k_dct_fwd<float, true>, p->N, sizeof(float2), th, sm);
+    auto k = pow2(p->N) ? k_dct_fwd<float, true, false> : k_dct_fwd<float, true, true>;
+    int rc = launch_cfg(k, p->N, sizeof(float2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctFwd, st);
-    k_dct_fwd<float, true><<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out_hi, out_lo,
-                                                             p->tw32, p->post32);
+    k<<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out_hi, out_lo, p->tw32, p->post32);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -433,10 +513,11 @@ int dct_inverse_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const do
                     double* out, cudaStream_t st) {
     if (nchannels(g) == 0) return DSBT_OK;
     unsigned th; size_t sm;
-    int rc = launch_cfg(k_dct_inv<double>, p->N, sizeof(double2), th, sm);
+    auto k = pow2(p->N) ? k_dct_inv<double, false> : k_dct_inv<double, true>;
+    int rc = launch_cfg(k, p->N, sizeof(double2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctInv, st);
-    k_dct_inv<double><<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, p->tw64, p->post64);
+    k<<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, p->tw64, p->post64);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -445,10 +526,11 @@ int dct_inverse_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const fl
                     float* out, cudaStream_t st) {
     if (nchannels(g) == 0) return DSBT_OK;
     unsigned th; size_t sm;
-    int rc = launch_cfg(k_dct_inv<float>, p->N, sizeof(float2), th, sm);
+    auto k = pow2(p->N) ? k_dct_inv<float, false> : k_dct_inv<float, true>;
+    int rc = launch_cfg(k, p->N, sizeof(float2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctInv, st);
-    k_dct_inv<float><<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, p->tw32, p->post32);
+    k<<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, p->tw32, p->post32);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }

@@ -287,8 +287,8 @@ extern "C" int dsbt_plan_create(int N, double r_max, int l_max, int flags, void*
     g_err[0] = 0;
     DSBT_CHECK_ARG(out != nullptr, "dsbt_plan_create: out is NULL");
     *out = nullptr;
-    DSBT_CHECK_ARG(N >= 256 && N <= 8192 && (N & (N - 1)) == 0,
-                   "dsbt_plan_create: N=%d must be a power of two in [256, 8192]", N);
+    DSBT_CHECK_ARG(N >= 256 && N <= 8192 && N % 256 == 0,
+                   "dsbt_plan_create: N=%d must be a multiple of 256 in [256, 8192]", N);
     DSBT_CHECK_ARG(l_max >= 0 && l_max <= 64, "dsbt_plan_create: l_max=%d not in [0, 64]", l_max);
     DSBT_CHECK_ARG(n0_of(l_max) <= N, "dsbt_plan_create: l_max too large for N");
     DSBT_CHECK_ARG(r_max > 0.0 && isfinite(r_max), "dsbt_plan_create: r_max must be positive");

@@ -35,7 +35,7 @@ def test_argument_errors_rejected_on_host():
     lib = dsbt.load()
     h = ctypes.c_void_p()
     # N not a power of two / out of range, l_max too large, bad flags, NULL out
-    for args in [(300, 10.0, 4, 1), (128, 10.0, 4, 1), (256, 10.0, 65, 1), (256, 10.0, 4, 0),
+    for args in [(300, 10.0, 4, 1), (128, 10.0, 4, 1), (640, 10.0, 4, 1), (8448, 10.0, 4, 1), (256, 10.0, 65, 1), (256, 10.0, 4, 0),
                  (256, -1.0, 4, 1), (256, 10.0, 4, 8)]:
         assert lib.dsbt_plan_create(*args, None, ctypes.byref(h)) == -1
         assert lib.dsbt_last_error()

@@ -212,3 +212,29 @@ def test_full_size_precision_config_sampled(lib):
             assert e < TOL32, (l, e)
         c0 += c
     p.close()
+
+
+@pytest.mark.parametrize("N", [768, 1280, 2816, 7936])
+def test_non_power_of_two_grids(lib, N):
+    """N = 256 q with odd q (mixed-radix FFT stages 3..31): both precision paths
+    against the oracle on sampled rows, and the round trip on all channels."""
+    lmax = 9
+    counts = [1] * (lmax + 1)
+    counts[3] = 2
+    p = lib.Plan(N, 0.1 * N, lmax)
+    x = inputs.gaussian_sum(9, N, 0.1, counts)
+    nrm = np.linalg.norm(x, axis=1)
+    b64 = p.forward_grouped(counts, torch.from_numpy(x).cuda()).cpu().numpy()
+    b32 = p.forward_grouped(counts, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    rows = [0, 1, 5, 6, 300, N // 2 + 7, N - 1]
+    c0 = 0
+    for l, c in enumerate(counts):
+        ref = oracle.forward_rows(l, x[c0:c0 + c], rows)
+        assert rel_err_sampled(b64[c0:c0 + c][:, rows], ref, nrm[c0:c0 + c]) < TOL64, (N, l)
+        assert rel_err_sampled(b32[c0:c0 + c][:, rows], ref, nrm[c0:c0 + c]) < TOL32, (N, l)
+        c0 += c
+    y64 = p.inverse_grouped(counts, torch.from_numpy(b64).cuda()).cpu().numpy()
+    assert rel_err(y64, x) < TOL64
+    y32 = p.inverse_grouped(counts, torch.from_numpy(b32).cuda()).cpu().numpy()
+    assert rel_err(y32, x) < 2 * TOL32
+    p.close()
