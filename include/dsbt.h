@@ -225,6 +225,52 @@ DSBT_API int dsbt_tdse_gradient(const dsbt_tdse* tdse, const void* psi0, const d
                                 int nsteps, int hold, double r_cut, int checkpoint_every, double* O,
                                 double* dOdE, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batch of uneven transforms (different grids and l_max) sharing one factor
+ * set.  The regular rows of T_l (Sec. 2.4) do not depend on the grid size N;
+ * only the completion rows (Sec. 2.5, Eq. (43)) do.  A batch builds the
+ * split-TF32 factors once at (N_max, max l_max) plus, per distinct N, a table of
+ * the first 32 rows, and runs the contraction of every transform in one
+ * persistent launch per direction.  Complex64 data only.
+ *
+ * Layout of the caller's batch arrays: transforms t = 0..ntrans-1 back to back;
+ * transform t holds sum_l counts_t[l] channels of N[t] complex samples, l-major.
+ * counts is the concatenation of the per-transform count arrays (l_max[t] + 1
+ * entries each).  All transforms share the radial step dr (r_max_t = N[t] dr).
+ * ------------------------------------------------------------------------- */
+typedef struct dsbt_batch dsbt_batch;
+
+/* N[t] a multiple of 256 in [256, 8192], 0 <= l_max[t] <= 64.  The batch owns
+ * its factors, tables, workspace and tensor maps (about
+ * 16 B (max l_max + 1) N_max^2 + 16 B per complex sample of the batch).  With
+ * autotune_tiles != 0 it times the contraction's tile order (transform-major
+ * or l-major) and column-tile width (128/192/256 lines) on its own shapes and
+ * keeps the fastest.  Synchronises the stream. */
+DSBT_API int dsbt_batch_create(int ntrans, const int* N, const int* l_max, const int* counts, double dr,
+                               int autotune_tiles, void* stream, dsbt_batch** out);
+DSBT_API int dsbt_batch_destroy(dsbt_batch* batch);
+
+/* Complex elements of one batch array, the chosen tile order and width, and
+ * the six autotuner timings in ms (order-major, widths 128/192/256). */
+DSBT_API int dsbt_batch_info(const dsbt_batch* batch, long long* total_elems, int* order, int* bn_cap,
+                             float* tune_ms);
+
+/* Forward DSBT of every channel of the batch (DEVICE arrays, complex64). */
+DSBT_API int dsbt_batch_forward(const dsbt_batch* batch, const void* in, void* out, void* stream);
+
+/* Kinetic step (as dsbt_kinetic_grouped, with k~_n = n pi / (N_t dr) per
+ * transform) of every channel of the batch. */
+DSBT_API int dsbt_batch_kinetic(const dsbt_batch* batch, double tau, const void* in, void* out, void* stream);
+
+/* Capture dsbt_batch_kinetic(batch, tau, in, out) into an executable CUDA
+ * graph (after one uncaptured run); replay it with dsbt_graph_launch on any
+ * stream, free it with dsbt_graph_destroy.  The graph keeps the pointers in
+ * and out: replays read and write those buffers. */
+DSBT_API int dsbt_batch_capture_kinetic(const dsbt_batch* batch, double tau, const void* in, void* out,
+                                        void** graph_exec);
+DSBT_API int dsbt_graph_launch(void* graph_exec, void* stream);
+DSBT_API int dsbt_graph_destroy(void* graph_exec);
+
 /*
  * Launch accounting and kernel timing (tracing).  dsbt_launch_count returns the
  * number of kernel launches the library has issued in this process.

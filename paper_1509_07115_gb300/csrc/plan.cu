@@ -51,19 +51,20 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double v) {
     s = t;
 }
 
-// One thread per (l, storage row r): writes row r of T_l into T64 (which the
-// caller zeroed).  Two passes over x: the first accumulates ||u||^2, the
-// second writes u / ||u||, so nothing is re-read from memory.
-__global__ void k_build_rows(double* __restrict__ T64, int N, int lmax) {
+// One thread per (l, storage row r < R): writes row r of T_l into
+// T64[l][r][0..N) (which the caller zeroed; R = N builds the whole matrix).
+// Two passes over x: the first accumulates ||u||^2, the second writes u / ||u||,
+// so nothing is re-read from memory.
+__global__ void k_build_rows(double* __restrict__ T64, int N, int lmax, int R) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (long long)(lmax + 1) * N) return;
-    const int l = (int)(gid / N);
-    const int r = (int)(gid % N);
+    if (gid >= (long long)(lmax + 1) * R) return;
+    const int l = (int)(gid / R);
+    const int r = (int)(gid % R);
     const int p = parity_p(l);
     const int n = r + p;
     const int n0 = n0_of(l);
     const int Nl = N + p - 1;
-    double* row = T64 + ((size_t)l * N + r) * (size_t)N;
+    double* row = T64 + ((size_t)l * R + r) * (size_t)N;
     const double ll1 = (double)l * (double)(l + 1);
     const double sqrt_half = 0.70710678118654752440;
 
@@ -201,6 +202,17 @@ __global__ void k_twiddles(double2* tw64, double2* post64, float2* tw32, float2*
 
 // ------------------------------------------------------------------ host side
 
+// Rows r < R of T_l (l = 0..lmax) for a grid of N points, FP64, into
+// dst[l][r][N] (device, zeroed here).
+int build_first_rows(double* dst, int N, int lmax, int R, cudaStream_t st) {
+    DSBT_CUDA_TRY(cudaMemsetAsync(dst, 0, (size_t)(lmax + 1) * R * N * sizeof(double), st));
+    const long long threads = (long long)(lmax + 1) * R;
+    ProfScope ps(kKPlan, st);
+    k_build_rows<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(dst, N, lmax, R);
+    DSBT_CUDA_TRY(cudaGetLastError());
+    return DSBT_OK;
+}
+
 int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
     const int N = p->N, L = p->l_max + 1;
     const size_t bytes64 = (size_t)L * p->nn * sizeof(double);
@@ -209,7 +221,7 @@ int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
         const long long threads = (long long)L * N;
         const int bs = 128;
         ProfScope ps(kKPlan, st);
-        k_build_rows<<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(p->T64, N, p->l_max);
+        k_build_rows<<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(p->T64, N, p->l_max, N);
         DSBT_CUDA_TRY(cudaGetLastError());
     }
     {
@@ -260,6 +272,34 @@ int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
     return DSBT_OK;
 }
 
+// A plan that holds only the FFT twiddles of an N-point grid (no factors):
+// used by the batch of uneven transforms for its sine/cosine kernels.
+int plan_twiddles_only(int N, double r_max, cudaStream_t st, dsbt_plan** out) {
+    dsbt_plan* p = new (std::nothrow) dsbt_plan();
+    if (!p) return DSBT_ERR_NOMEM;
+    p->N = N;
+    p->l_max = -1;
+    p->r_max = r_max;
+    p->dk = M_PI / r_max;
+    p->nn = (size_t)N * N;
+    cudaGetDevice(&p->device);
+    bool ok = cudaMalloc((void**)&p->tw64, N * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void**)&p->post64, N * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void**)&p->tw32, N * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc((void**)&p->post32, N * sizeof(float2)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(p->tw64); cudaFree(p->post64); cudaFree(p->tw32); cudaFree(p->post32);
+        delete p;
+        set_error("plan_twiddles_only: device allocation failed");
+        return DSBT_ERR_NOMEM;
+    }
+    k_twiddles<<<(N + 255) / 256, 256, 0, st>>>(p->tw64, p->post64, p->tw32, p->post32, N);
+    DSBT_CUDA_TRY(cudaGetLastError());
+    *out = p;
+    return DSBT_OK;
+}
+
 static void plan_free(dsbt_plan* p) {
     if (!p) return;
     cudaFree(p->T64);
@@ -275,6 +315,8 @@ static void plan_free(dsbt_plan* p) {
     cudaFree(p->status);
     delete p;
 }
+
+void plan_release(dsbt_plan* p) { plan_free(p); }
 
 }  // namespace dsbt
 

@@ -59,8 +59,14 @@ class ProfScope {
     cudaEvent_t a_, b_;
 };
 
+// Turns event recording on/off without clearing records; returns the old state.
+int profile_set_enabled(int on);
+
 // ---- plan build (plan.cu)
 int plan_build_factors(dsbt_plan* p, cudaStream_t st);
+int build_first_rows(double* dst, int N, int lmax, int R, cudaStream_t st);
+int plan_twiddles_only(int N, double r_max, cudaStream_t st, dsbt_plan** out);
+void plan_release(dsbt_plan* p);
 
 // ---- TMA descriptors (tma.cu)
 // Encode a 2-D FP32 tensor map over a row-major [rows][cols] array with a box of

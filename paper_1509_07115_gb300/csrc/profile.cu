@@ -49,6 +49,8 @@ ProfScope::~ProfScope() {
     }
 }
 
+int profile_set_enabled(int on) { return g_enabled.exchange(on ? 1 : 0); }
+
 }  // namespace dsbt
 
 using namespace dsbt;

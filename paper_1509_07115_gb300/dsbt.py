@@ -58,6 +58,15 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_profile_read.argtypes = [i, _c_int_p, ctypes.POINTER(d)]
         lib.dsbt_kernel_name.argtypes = [i]
         lib.dsbt_kernel_name.restype = ctypes.c_char_p
+        lib.dsbt_batch_create.argtypes = [i, _c_int_p, _c_int_p, _c_int_p, d, i, vp, ctypes.POINTER(vp)]
+        lib.dsbt_batch_destroy.argtypes = [vp]
+        lib.dsbt_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), _c_int_p, _c_int_p,
+                                        ctypes.POINTER(ctypes.c_float)]
+        lib.dsbt_batch_forward.argtypes = [vp, vp, vp, vp]
+        lib.dsbt_batch_kinetic.argtypes = [vp, d, vp, vp, vp]
+        lib.dsbt_batch_capture_kinetic.argtypes = [vp, d, vp, vp, ctypes.POINTER(vp)]
+        lib.dsbt_graph_launch.argtypes = [vp, vp]
+        lib.dsbt_graph_destroy.argtypes = [vp]
         lib.dsbt_tdse_create.argtypes = [vp, i, d, d, d, ctypes.POINTER(vp)]
         lib.dsbt_tdse_destroy.argtypes = [vp]
         lib.dsbt_tdse_angular.argtypes = [vp, vp, vp, vp]
@@ -82,6 +91,10 @@ def _check(rc: int, what: str):
 
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
 
 
 class Plan:
@@ -233,11 +246,95 @@ def profile_read() -> dict:
     return out
 
 
+# ------------------------------------------------------------------ batch of uneven transforms
+
+class Batch:
+    """Uneven transforms sharing one factor set (dsbt_batch_* in include/dsbt.h).
+    transforms: list of (N_t, l_max_t, counts_t) with counts_t[l] channels of l.
+    Batch arrays: complex64 CUDA tensors of total_elems elements, transforms back
+    to back, each [sum(counts_t)][N_t] l-major."""
+
+    def __init__(self, transforms, dr: float, autotune: bool = True):
+        Ns = [int(t[0]) for t in transforms]
+        lms = [int(t[1]) for t in transforms]
+        cnt = []
+        for (N, lm, c) in transforms:
+            if len(c) != lm + 1:
+                raise ValueError("counts_t needs l_max_t + 1 entries")
+            cnt += [int(v) for v in c]
+        arr = lambda v: (ctypes.c_int * len(v))(*v)
+        h = ctypes.c_void_p()
+        _check(load().dsbt_batch_create(len(Ns), arr(Ns), arr(lms), arr(cnt), float(dr), int(bool(autotune)),
+                                        _stream(), ctypes.byref(h)), "dsbt_batch_create")
+        self._h = h
+        self.transforms = [(Ns[k], lms[k], list(transforms[k][2])) for k in range(len(Ns))]
+        self.dr = float(dr)
+        self._graphs = []
+
+    def close(self):
+        for g in self._graphs:
+            load().dsbt_graph_destroy(g)
+        self._graphs = []
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dsbt_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        n, o, b = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_float * 6)()
+        _check(load().dsbt_batch_info(self._h, ctypes.byref(n), ctypes.byref(o), ctypes.byref(b), ms),
+               "dsbt_batch_info")
+        return {"total_elems": n.value, "order": ["transform-major", "l-major"][o.value], "bn_cap": b.value,
+                "tune_ms": {f"{['transform-major', 'l-major'][k // 3]}/{[128, 192, 256][k % 3]}": ms[k]
+                            for k in range(6)}}
+
+    def offsets(self):
+        """Complex-element offset of each transform in a batch array."""
+        off, out = 0, []
+        for (N, lm, c) in self.transforms:
+            out.append(off)
+            off += sum(c) * N
+        return out
+
+    def _check_arr(self, x):
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("batch arrays are contiguous complex64 CUDA tensors")
+        if x.numel() != self.info()["total_elems"]:
+            raise ValueError("batch array has the wrong number of elements")
+
+    def forward(self, x, out=None):
+        self._check_arr(x)
+        out = torch.empty_like(x) if out is None else out
+        _check(load().dsbt_batch_forward(self._h, _ptr(x), _ptr(out), _stream()), "dsbt_batch_forward")
+        return out
+
+    def kinetic(self, x, tau: float, out=None):
+        self._check_arr(x)
+        out = torch.empty_like(x) if out is None else out
+        _check(load().dsbt_batch_kinetic(self._h, float(tau), _ptr(x), _ptr(out), _stream()), "dsbt_batch_kinetic")
+        return out
+
+    def capture_kinetic(self, x, tau: float, out):
+        """CUDA graph of kinetic(x, tau, out); returns a handle for launch_graph."""
+        self._check_arr(x)
+        g = ctypes.c_void_p()
+        _check(load().dsbt_batch_capture_kinetic(self._h, float(tau), _ptr(x), _ptr(out), ctypes.byref(g)),
+               "dsbt_batch_capture_kinetic")
+        self._graphs.append(g)
+        return g
+
+    @staticmethod
+    def launch_graph(g):
+        _check(load().dsbt_graph_launch(g, _stream()), "dsbt_graph_launch")
+
+
 # ------------------------------------------------------------------ TDSE
-
-def _ptr(t):
-    return ctypes.c_void_p(t.data_ptr())
-
 
 class Tdse:
     """Split-operator TDSE (m = 0, length gauge) through the DSBT: see
