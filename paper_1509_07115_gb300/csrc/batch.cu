@@ -17,8 +17,10 @@
 // one dynamic queue, and the TMA producer chooses the factor source per tile.
 // The batch owns its workspace and tensor maps, so a whole step can be captured
 // into one CUDA graph (dsbt_batch_capture_kinetic).  An autotuner times the
-// tile order (transform-major / l-major) and the column-tile width (128, 192,
-// 256 lines) on the batch's own shapes at creation and keeps the fastest.
+// tile order (transform-major; l-major; l-major with row tiles interleaved
+// across transforms so that tiles reading the same slab of the shared factors
+// run together) and the column-tile width (128, 192, 256 lines) on the batch's
+// own shapes at creation and keeps the fastest.
 #include <math.h>
 
 #include <algorithm>
@@ -82,10 +84,10 @@ struct KR {
     }
 };
 
-__device__ __forceinline__ KR kranges(int dir, int rt, int nx, int KB) {
+__device__ __forceinline__ KR kranges(int dir, int rt, int nx, int KB, int walk_up) {
     KR k;
     const int r0 = rt * BM;
-    k.up = dir > 0;
+    k.up = (dir > 0) || walk_up;
     k.a0 = 0;
     k.b0 = k.b1 = 0;
     if (r0 < nx) { k.a1 = KB; return k; }
@@ -100,7 +102,19 @@ struct BTile {
     int g, rt, ct, nmma;
 };
 
-__device__ __forceinline__ BTile bdecode(const BGroup* __restrict__ gs, int ng, int dir, int bn_cap, int t) {
+__device__ __forceinline__ BTile bdecode(const BGroup* __restrict__ gs, int ng, int dir, int bn_cap, int t,
+                                        const int2* __restrict__ tl_list) {
+    if (tl_list) {   // explicit tile list: (group, rt << 8 | column tile)
+        const int2 e = tl_list[t];
+        BTile tl;
+        tl.g = e.x;
+        tl.rt = e.y >> 8;
+        tl.ct = e.y & 255;
+        int left = gs[e.x].nl - tl.ct * bn_cap;
+        if (left > bn_cap) left = bn_cap;
+        tl.nmma = (left + 15) & ~15;
+        return tl;
+    }
     int lo = 0, hi = ng - 1;
     while (lo < hi) {   // last group with t0 <= t
         const int mid = (lo + hi + 1) >> 1;
@@ -126,7 +140,8 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                  const __grid_constant__ CUtensorMap tI_hi, const __grid_constant__ CUtensorMap tI_lo,
                  const BGroup* __restrict__ groups, int ngroups, int total, const BTrans* __restrict__ trans,
                  const BMaps* __restrict__ tmaps, const BMaps* __restrict__ cmaps, int Nmax, int dir, int mode,
-                 int bn_cap, float2* __restrict__ out_user, unsigned* status, int* sched) {
+                 int bn_cap, float2* __restrict__ out_user, unsigned* status, int* sched,
+                 const int2* __restrict__ tl_list, int walk_up) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage_base = smem;
@@ -180,9 +195,9 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                 mbar_arrive(&tq_full[qslot]);
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
                 if (t < 0) break;
-                const BTile tl = bdecode(groups, ngroups, dir, bn_cap, t);
+                const BTile tl = bdecode(groups, ngroups, dir, bn_cap, t, tl_list);
                 const BGroup G = groups[tl.g];
-                const KR kr = kranges(dir, tl.rt, n_extra(G.l), G.N / BK);
+                const KR kr = kranges(dir, tl.rt, n_extra(G.l), G.N / BK, walk_up);
                 const int nbox = (tl.nmma + BBOX - 1) / BBOX;
                 const uint32_t bytes = 2 * A_BYTES + 2 * nbox * BBOX * BK * 4;
                 const int brow = G.bline0 + tl.ct * bn_cap;
@@ -240,9 +255,9 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                 mbar_arrive(&tq_empty[qslot]);
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
                 if (t < 0) break;
-                const BTile tl = bdecode(groups, ngroups, dir, bn_cap, t);
+                const BTile tl = bdecode(groups, ngroups, dir, bn_cap, t, tl_list);
                 const BGroup G = groups[tl.g];
-                const KR kr = kranges(dir, tl.rt, n_extra(G.l), G.N / BK);
+                const KR kr = kranges(dir, tl.rt, n_extra(G.l), G.N / BK, walk_up);
                 const uint32_t idesc = idesc_tf32(BM, tl.nmma);
                 const int nkb = kr.count();
                 uint32_t acc_corr = 0;
@@ -294,9 +309,9 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
             if (lane == 0) mbar_arrive(&tq_empty[qslot]);
             if (++qslot == QS) { qslot = 0; qphase ^= 1; }
             if (t < 0) break;
-            const BTile tl = bdecode(groups, ngroups, dir, bn_cap, t);
+            const BTile tl = bdecode(groups, ngroups, dir, bn_cap, t, tl_list);
             const BGroup G = groups[tl.g];
-            const KR kr = kranges(dir, tl.rt, n_extra(G.l), G.N / BK);
+            const KR kr = kranges(dir, tl.rt, n_extra(G.l), G.N / BK, walk_up);
             const int nkb = kr.count();
             const int N = G.N;
             const int row = tl.rt * BM + quarter * 32 + lane;
@@ -429,11 +444,12 @@ struct dsbt_batch {
     dsbt::BTrans* trans_d = nullptr;
     dsbt::BMaps* tmaps_d = nullptr;
     dsbt::BMaps* cmaps_d = nullptr;
-    dsbt::BGroup* groups_d[2] = {nullptr, nullptr};   // two tile orders
-    int ngroups = 0, total_tiles[2] = {0, 0};   // tiles per order at the current width
+    dsbt::BGroup* groups_d[3] = {nullptr, nullptr, nullptr};   // per tile order
+    int2* tiles_d[2] = {nullptr, nullptr};                       // order 2: forward / inverse tile lists
+    int ngroups = 0, total_tiles[3] = {0, 0, 0};   // tiles per order at the current width
     int* sched = nullptr;
     int order = 0, bn_cap = 256;          // autotuned
-    float tune_ms[2][3] = {{0}};
+    float tune_ms[3][3] = {{0}};
     std::vector<dsbt::GroupTable> gtab;   // per transform, for the sine/cosine kernels
 };
 
@@ -452,6 +468,9 @@ void batch_free(dsbt_batch* b) {
     cudaFree(b->cmaps_d);
     cudaFree(b->groups_d[0]);
     cudaFree(b->groups_d[1]);
+    cudaFree(b->groups_d[2]);
+    cudaFree(b->tiles_d[0]);
+    cudaFree(b->tiles_d[1]);
     cudaFree(b->sched);
     delete b;
 }
@@ -473,7 +492,7 @@ std::vector<BGroup> make_groups(const dsbt_batch* b, int order, int bn_cap, int*
             if (x.t != y.t) return tw[x.t] > tw[y.t] || (tw[x.t] == tw[y.t] && x.t < y.t);
             return x.l > y.l;
         });
-    } else {            // l-major: all transforms' groups of the same l together
+    } else {            // l-major (orders 1, 2): all transforms' groups of the same l together
         std::stable_sort(items.begin(), items.end(), [&](const Item& x, const Item& y) {
             if (x.l != y.l) return x.l > y.l;
             return b->N[x.t] > b->N[y.t];
@@ -502,6 +521,29 @@ std::vector<BGroup> make_groups(const dsbt_batch* b, int order, int bn_cap, int*
     return gs;
 }
 
+// Order 2: within each l (descending), tiles by row tile across all transforms
+// that have it (forward: longest K first, rt = RT-1 .. 1 then rt = 0;
+// inverse: rt = 0 .. RT-1), so tiles reading the same slab of the shared T_l
+// (or T_l^T) run at the same time.  Entries: (group, rt << 8 | column tile).
+std::vector<int2> make_tile_list(const std::vector<BGroup>& gs, int dir) {
+    std::vector<int2> out;
+    size_t i = 0;
+    while (i < gs.size()) {
+        size_t j = i;
+        int rtmax = 0;
+        while (j < gs.size() && gs[j].l == gs[i].l) { rtmax = std::max(rtmax, gs[j].N / BM); ++j; }
+        std::vector<int> rts;
+        if (dir > 0) { for (int rt = rtmax - 1; rt >= 1; --rt) rts.push_back(rt); rts.push_back(0); }
+        else for (int rt = 0; rt < rtmax; ++rt) rts.push_back(rt);
+        for (int rt : rts)
+            for (size_t g = i; g < j; ++g)
+                if (rt < gs[g].N / BM)
+                    for (int c = 0; c < gs[g].ct; ++c) out.push_back(make_int2((int)g, (rt << 8) | c));
+        i = j;
+    }
+    return out;
+}
+
 int upload_groups(dsbt_batch* b, int order, int bn_cap, cudaStream_t st) {
     int total = 0;
     std::vector<BGroup> gs = make_groups(b, order, bn_cap, &total);
@@ -511,6 +553,25 @@ int upload_groups(dsbt_batch* b, int order, int bn_cap, cudaStream_t st) {
         DSBT_CUDA_TRY(cudaMalloc((void**)&b->groups_d[order], gs.size() * sizeof(BGroup)));
     DSBT_CUDA_TRY(cudaMemcpyAsync(b->groups_d[order], gs.data(), gs.size() * sizeof(BGroup),
                                   cudaMemcpyHostToDevice, st));
+    if (order == 2) {
+        for (const BGroup& g : gs)
+            if (g.ct > 255) {   // the tile list packs the column tile into 8 bits
+                set_error("group of %d lines too wide for the row-interleaved order", g.nl);
+                return DSBT_ERR_UNSUPPORTED;
+            }
+        for (int d = 0; d < 2; ++d) {
+            std::vector<int2> tl = make_tile_list(gs, d == 0 ? +1 : -1);
+            if ((int)tl.size() != total) {
+                set_error("tile list size mismatch");
+                return DSBT_ERR_INVALID;
+            }
+            cudaFree(b->tiles_d[d]);
+            b->tiles_d[d] = nullptr;
+            DSBT_CUDA_TRY(cudaMalloc((void**)&b->tiles_d[d], tl.size() * sizeof(int2)));
+            DSBT_CUDA_TRY(cudaMemcpyAsync(b->tiles_d[d], tl.data(), tl.size() * sizeof(int2),
+                                          cudaMemcpyHostToDevice, st));
+        }
+    }
     DSBT_CUDA_TRY(cudaStreamSynchronize(st));
     return DSBT_OK;
 }
@@ -535,7 +596,9 @@ int launch_contract(const dsbt_batch* b, int order, int bn_cap, int total, int d
     k_contract_batch<<<grid, NTHREADS, smem, st>>>(s->tm_T_hi, s->tm_T_lo, b->tF96_hi, b->tF96_lo, s->tm_Tt_hi,
                                                    s->tm_Tt_lo, b->groups_d[order], b->ngroups, total,
                                                    b->trans_d, b->tmaps_d, b->cmaps_d, b->Nmax, dir, mode, bn_cap,
-                                                   out_user, s->status, b->sched);
+                                                   out_user, s->status, b->sched,
+                                                   order == 2 ? b->tiles_d[dir > 0 ? 0 : 1] : nullptr,
+                                                   order == 2 ? 1 : 0);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -574,14 +637,17 @@ int autotune(dsbt_batch* b, cudaStream_t st) {
     DSBT_CUDA_TRY(cudaEventCreate(&e0));
     DSBT_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int order = 0; order < 2; ++order) {
+    for (int order = 0; order < 3; ++order) {
         for (int ci = 0; ci < 3; ++ci) {
             const int cap = kBnCaps[ci];
-            int total = 0;
-            std::vector<BGroup> gs = make_groups(b, order, cap, &total);
-            DSBT_CUDA_TRY(cudaMemcpyAsync(b->groups_d[order], gs.data(), gs.size() * sizeof(BGroup),
-                                          cudaMemcpyHostToDevice, st));
-            int rc = launch_contract(b, order, cap, total, +1, kModeSplit, nullptr, st);   // warm-up
+            int rc = upload_groups(b, order, cap, st);
+            if (rc == DSBT_ERR_UNSUPPORTED && order == 2) {   // not offered for this batch
+                b->tune_ms[order][ci] = -1.f;
+                continue;
+            }
+            if (rc) return rc;
+            const int total = b->total_tiles[order];
+            rc = launch_contract(b, order, cap, total, +1, kModeSplit, nullptr, st);   // warm-up
             if (rc) return rc;
             DSBT_CUDA_TRY(cudaEventRecord(e0, st));
             rc = launch_contract(b, order, cap, total, +1, kModeSplit, nullptr, st);
@@ -600,10 +666,10 @@ int autotune(dsbt_batch* b, cudaStream_t st) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // final group tables for the chosen width (both orders kept consistent)
-    for (int order = 0; order < 2; ++order) {
+    // final group tables for the chosen width (all orders kept consistent)
+    for (int order = 0; order < 3; ++order) {
         int rc = upload_groups(b, order, b->bn_cap, st);
-        if (rc) return rc;
+        if (rc && !(rc == DSBT_ERR_UNSUPPORTED && order == 2)) return rc;
     }
     return DSBT_OK;
 }
@@ -772,8 +838,9 @@ extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, con
         set_error("dsbt_batch_create: table upload failed");
         return DSBT_ERR_CUDA;
     }
-    for (int order = 0; order < 2; ++order) {
+    for (int order = 0; order < 3; ++order) {
         rc = upload_groups(b, order, 256, st);
+        if (rc == DSBT_ERR_UNSUPPORTED && order == 2) { rc = DSBT_OK; continue; }
         if (rc) { batch_free(b); return rc; }
     }
     if (autotune_tiles) {
@@ -798,8 +865,25 @@ extern "C" int dsbt_batch_info(const dsbt_batch* b, long long* total_elems, int*
     if (order) *order = b->order;
     if (bn_cap) *bn_cap = b->bn_cap;
     if (tune_ms)
-        for (int o = 0; o < 2; ++o)
+        for (int o = 0; o < 3; ++o)
             for (int c = 0; c < 3; ++c) tune_ms[o * 3 + c] = b->tune_ms[o][c];
+    return DSBT_OK;
+}
+
+extern "C" int dsbt_batch_set_tiles(dsbt_batch* b, int order, int bn_cap, void* stream) {
+    DSBT_CHECK_ARG(b != nullptr, "dsbt_batch_set_tiles: NULL batch");
+    DSBT_CHECK_ARG(order >= 0 && order <= 2, "dsbt_batch_set_tiles: order %d not in 0..2", order);
+    DSBT_CHECK_ARG(bn_cap == 128 || bn_cap == 192 || bn_cap == 256, "dsbt_batch_set_tiles: width %d", bn_cap);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = upload_groups(b, order, bn_cap, st);
+    if (rc) return rc;
+    for (int o = 0; o < 3; ++o) {   // keep every order's table at the new width
+        if (o == order) continue;
+        rc = upload_groups(b, o, bn_cap, st);
+        if (rc && !(rc == DSBT_ERR_UNSUPPORTED && o == 2)) return rc;
+    }
+    b->order = order;
+    b->bn_cap = bn_cap;
     return DSBT_OK;
 }
 

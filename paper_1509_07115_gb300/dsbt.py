@@ -62,6 +62,7 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_batch_destroy.argtypes = [vp]
         lib.dsbt_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), _c_int_p, _c_int_p,
                                         ctypes.POINTER(ctypes.c_float)]
+        lib.dsbt_batch_set_tiles.argtypes = [vp, i, i, vp]
         lib.dsbt_batch_forward.argtypes = [vp, vp, vp, vp]
         lib.dsbt_batch_kinetic.argtypes = [vp, d, vp, vp, vp]
         lib.dsbt_batch_capture_kinetic.argtypes = [vp, d, vp, vp, ctypes.POINTER(vp)]
@@ -287,12 +288,19 @@ class Batch:
 
     def info(self) -> dict:
         n, o, b = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
-        ms = (ctypes.c_float * 6)()
+        ms = (ctypes.c_float * 9)()
         _check(load().dsbt_batch_info(self._h, ctypes.byref(n), ctypes.byref(o), ctypes.byref(b), ms),
                "dsbt_batch_info")
-        return {"total_elems": n.value, "order": ["transform-major", "l-major"][o.value], "bn_cap": b.value,
-                "tune_ms": {f"{['transform-major', 'l-major'][k // 3]}/{[128, 192, 256][k % 3]}": ms[k]
-                            for k in range(6)}}
+        names = self.TILE_ORDERS
+        return {"total_elems": n.value, "order": names[o.value], "bn_cap": b.value,
+                "tune_ms": {f"{names[k // 3]}/{[128, 192, 256][k % 3]}": ms[k] for k in range(9)}}
+
+    TILE_ORDERS = ("transform-major", "l-major", "l-major/row-interleaved")
+
+    def set_tiles(self, order: str, bn_cap: int):
+        """Pin the contraction's tile order (one of TILE_ORDERS) and width."""
+        _check(load().dsbt_batch_set_tiles(self._h, self.TILE_ORDERS.index(order), int(bn_cap), _stream()),
+               "dsbt_batch_set_tiles")
 
     def offsets(self):
         """Complex-element offset of each transform in a batch array."""

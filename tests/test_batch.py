@@ -25,10 +25,7 @@ def make(lib):
     return b, trs, xs, x
 
 
-def test_batch_forward_matches_oracle_per_grid(lib):
-    b, trs, xs, x = make(lib)
-    info = b.info()
-    assert info["bn_cap"] in (128, 192, 256) and all(v > 0 for v in info["tune_ms"].values())
+def check_forward(b, trs, xs, x):
     y = b.forward(x).cpu().numpy()
     offs = b.offsets()
     for k, (N, lm, c) in enumerate(trs):
@@ -42,6 +39,31 @@ def test_batch_forward_matches_oracle_per_grid(lib):
                 e = (np.abs(yk[c0:c0 + c[l]][:, rows] - ref).max(axis=1) / np.linalg.norm(xin, axis=1)).max()
                 assert e < 1e-6, (N, l, e)
             c0 += c[l]
+
+
+def test_batch_forward_matches_oracle_per_grid(lib):
+    b, trs, xs, x = make(lib)
+    info = b.info()
+    assert info["bn_cap"] in (128, 192, 256) and all(v > 0 for v in info["tune_ms"].values())
+    check_forward(b, trs, xs, x)
+    b.close()
+
+
+def test_every_tile_order_and_width(lib):
+    """The pinned tile orders and widths give the oracle's forward and the same
+    kinetic step (up to FP32 rounding order of the inverse's K walk)."""
+    b, trs, xs, x = make(lib)
+    b.set_tiles("transform-major", 256)
+    ref = b.kinetic(x, 0.05)          # channels have unit norm: absolute error is relative
+    for order in b.TILE_ORDERS:
+        for cap in (128, 192, 256):
+            b.set_tiles(order, cap)
+            info = b.info()
+            assert info["order"] == order and info["bn_cap"] == cap
+            check_forward(b, trs, xs, x)
+            e = (b.kinetic(x, 0.05) - ref).abs().max().item()
+            assert e < 1e-6, (order, cap, e)
+    b.close()
 
 
 def test_batch_kinetic_matches_single_plan_and_graph(lib):
@@ -64,4 +86,50 @@ def test_batch_kinetic_matches_single_plan_and_graph(lib):
     b.launch_graph(g)
     torch.cuda.synchronize()
     assert torch.equal(out, y)
+    b.close()
+
+
+def test_full_uneven_workload_sampled(lib):
+    """64 transforms, N ~ U{512..8192 step 256}, l_max ~ U{8..64} (seed 0), 2l+1
+    channels per l: forward outputs of the largest and a small transform on
+    sampled rows against the oracle at their own N; kinetic norm conservation on
+    every channel."""
+    work = inputs.grouped_workload(0)
+    trs = [(N, lm, [2 * l + 1 for l in range(lm + 1)]) for N, lm in work]
+    b = lib.Batch(trs, 0.1, autotune=False)
+    xs = [inputs.gaussian_sum(300 + k, N, 0.1, c, dtype=torch.complex64, device="cuda").reshape(-1)
+          for k, (N, lm, c) in enumerate(trs)]
+    x = torch.cat(xs)
+    y = b.forward(x)
+    b.set_tiles("l-major/row-interleaved", 256)       # the same outputs from the interleaved tile list
+    assert (b.forward(x) - y).abs().max().item() < 1e-6
+    b.set_tiles("l-major", 256)
+    offs = b.offsets()
+    big = max(range(len(trs)), key=lambda i: trs[i][0] * 100 + trs[i][1])
+    small = min(range(len(trs)), key=lambda i: trs[i][0])
+    for k in (big, small):
+        N, lm, c = trs[k]
+        yk = y[offs[k]:offs[k] + sum(c) * N].reshape(-1, N).cpu().numpy()
+        xk = x[offs[k]:offs[k] + sum(c) * N].reshape(-1, N).cpu().numpy().astype(np.complex128)
+        c0 = 0
+        for l in range(lm + 1):
+            if l in (0, 1, lm // 2, lm):
+                sel = [c0, c0 + c[l] - 1]
+                rows = [0, 1, 31, 32, 200, N - 1]
+                ref = oracle.forward_rows(l, xk[sel], rows)
+                e = (np.abs(yk[sel][:, rows] - ref).max(axis=1) / np.linalg.norm(xk[sel], axis=1)).max()
+                assert e < 1e-6, (N, l, e)
+            c0 += c[l]
+    z = b.kinetic(x, 0.05)
+    torch.cuda.synchronize()
+    start = 0
+    worst = 0.0
+    for k, (N, lm, c) in enumerate(trs):
+        n = sum(c) * N
+        a = x[start:start + n].reshape(-1, N).to(torch.complex128)
+        bz = z[start:start + n].reshape(-1, N).to(torch.complex128)
+        na, nb = torch.linalg.vector_norm(a, dim=1), torch.linalg.vector_norm(bz, dim=1)
+        worst = max(worst, ((nb - na) / na).abs().max().item())
+        start += n
+    assert worst < 2e-6, worst
     b.close()
