@@ -243,25 +243,28 @@ typedef struct dsbt_batch dsbt_batch;
 /* N[t] a multiple of 256 in [256, 8192], 0 <= l_max[t] <= 64.  The batch owns
  * its factors, tables, workspace and tensor maps (about
  * 16 B (max l_max + 1) N_max^2 + 16 B per complex sample of the batch).  With
- * autotune_tiles != 0 it times the contraction's tile order (transform-major,
- * l-major, or l-major with row tiles interleaved across transforms) and
- * column-tile width (128/192/256 lines) on its own shapes and keeps the
- * fastest.  Synchronises the stream. */
+ * autotune_tiles != 0 it times the contraction's tile order (see
+ * dsbt_batch_set_tiles) and column-tile width (128/192/256 lines) on its own
+ * shapes and keeps the fastest; otherwise it takes order 3 at width 256.
+ * Synchronises the stream. */
 DSBT_API int dsbt_batch_create(int ntrans, const int* N, const int* l_max, const int* counts, double dr,
                                int autotune_tiles, void* stream, dsbt_batch** out);
 DSBT_API int dsbt_batch_destroy(dsbt_batch* batch);
 
 /* Complex elements of one batch array, the chosen tile order and width, and
- * the nine autotuner timings in ms (order-major, widths 128/192/256). */
+ * the twelve autotuner timings in ms (order-major, widths 128/192/256; zero
+ * when the batch was created without autotuning). */
 DSBT_API int dsbt_batch_info(const dsbt_batch* batch, long long* total_elems, int* order, int* bn_cap,
                              float* tune_ms);
 
-/* Pin the contraction's tile order (0 transform-major, 1 l-major, 2 l-major
- * with row tiles interleaved across transforms) and column-tile width (128,
- * 192 or 256 lines), overriding the autotuner.  DSBT_ERR_INVALID for other
- * values, DSBT_ERR_UNSUPPORTED for order 2 when a (transform, l) group spans
- * more than 255 column tiles.  Results do not depend on the tiling except
- * through FP32 rounding order.  Synchronises the stream. */
+/* Pin the contraction's tile order and column-tile width (128, 192 or 256
+ * lines), overriding the autotuner.  Orders: 0 transform-major, 1 l-major
+ * (each (transform, l) group's tiles together), 2 l-major with row tiles
+ * interleaved across the transforms of one l, 3 as 2 with 32-line segments of
+ * different transforms packed into one tile.  DSBT_ERR_INVALID for other
+ * values.  Results do not depend on the tiling except through FP32 rounding
+ * order.  Graphs captured earlier stay valid and keep their own tiling.
+ * Synchronises the stream. */
 DSBT_API int dsbt_batch_set_tiles(dsbt_batch* batch, int order, int bn_cap, void* stream);
 
 /* Forward DSBT of every channel of the batch (DEVICE arrays, complex64). */

@@ -12,16 +12,21 @@
 // T^T.  Memory: 4 x 4 B x (l_max+1) N_max^2 for the shared set plus
 // 4 x 4 B x (l_max+1) x 32 x N per distinct N.
 //
-// The batched contraction is the split-TF32 kernel of gemm_tf32x3.cu with a
-// device-side list of (transform, l) groups: tiles of all transforms come from
-// one dynamic queue, and the TMA producer chooses the factor source per tile.
-// The batch owns its workspace and tensor maps, so a whole step can be captured
-// into one CUDA graph (dsbt_batch_capture_kinetic).  An autotuner times the
-// tile order (transform-major; l-major; l-major with row tiles interleaved
-// across transforms so that tiles reading the same slab of the shared factors
-// run together) and the column-tile width (128, 192, 256 lines) on the batch's
-// own shapes at creation and keeps the fastest.
+// The batched contraction is the split-TF32 kernel of gemm_tf32x3.cu driven by
+// a device-side tile list: tiles of all transforms come from one dynamic queue,
+// and the TMA producer chooses the factor source per tile.  A tile's B operand
+// is up to eight 32-line segments, each from any (transform, l) group, so the
+// narrow groups of one l (2(2l+1) lines each) from many transforms fill one
+// 256-column MMA against one shared slab of T_l.  The batch owns its workspace
+// and tensor maps, so a whole step can be captured into one CUDA graph
+// (dsbt_batch_capture_kinetic).  An autotuner times the tile order
+// (transform-major; l-major; l-major with row tiles interleaved across
+// transforms; the same with segments of different transforms packed into one
+// tile) and the column-tile width (128, 192, 256 lines) on the batch's own
+// shapes at creation and keeps the fastest.
 #include <math.h>
+
+#include <string.h>
 
 #include <algorithm>
 #include <new>
@@ -39,7 +44,8 @@ using namespace tc;
 constexpr int BM = 128;
 constexpr int BK = 32;
 constexpr int BN_MAX = 256;
-constexpr int BBOX = 64;
+constexpr int SEG = 32;            // lines per B segment (one TMA box)
+constexpr int SEG_MAX = BN_MAX / SEG;
 constexpr int STAGES = 2;
 constexpr int KC = 4;
 constexpr int EPI_WARPS = 8;
@@ -49,13 +55,27 @@ constexpr int B_BYTES = BN_MAX * BK * 4;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr int CROWS = 32;   // rows of the per-N tables (>= every completion-row count)
+constexpr int kOrders = 4;  // tile orders offered to the autotuner
 
 struct BGroup {
     int t, l, N, nl;   // transform, angular momentum, grid, real lines
     int bline0;        // first line of the group in the transform's planar buffers
-    int ct, t0;        // column tiles, first tile
     int cidx;          // distinct-N index of the per-N tables
     long long uoff;    // complex-element offset of the group's first channel (caller layout)
+};
+
+// One output tile: rows [rt BM, rt BM + BM) of T_l (forward) or T_l^T
+// (inverse) against up to SEG_MAX segments of SEG lines.  A segment is lines
+// [c, c + SEG) of one (transform, l) group; lines past the group's end are
+// computed and discarded.  Segments of one tile may come from different
+// transforms: the rows of the shared factors a forward tile with rt >= 1 reads
+// do not depend on N.  Tiles that read per-N rows (forward rt = 0, every
+// inverse tile) hold segments of one grid N only.
+struct __align__(16) PTile {
+    int l, rt, N, cidx;   // N: grid of the K range (the smallest segment grid), cidx: its per-N tables
+    int nseg, pad0, pad1, pad2;
+    int g[SEG_MAX];       // group of each segment
+    int c[SEG_MAX];       // first line of the segment in its group
 };
 
 struct BTrans {
@@ -84,6 +104,9 @@ struct KR {
     }
 };
 
+// K blocks of a tile: the forward T_l is dense in its completion rows (n < nx)
+// and lower triangular below; T_l^T is dense in its first nx columns and upper
+// triangular.
 __device__ __forceinline__ KR kranges(int dir, int rt, int nx, int KB, int walk_up) {
     KR k;
     const int r0 = rt * BM;
@@ -98,50 +121,14 @@ __device__ __forceinline__ KR kranges(int dir, int rt, int nx, int KB, int walk_
     return k;
 }
 
-struct BTile {
-    int g, rt, ct, nmma;
-};
-
-__device__ __forceinline__ BTile bdecode(const BGroup* __restrict__ gs, int ng, int dir, int bn_cap, int t,
-                                        const int2* __restrict__ tl_list) {
-    if (tl_list) {   // explicit tile list: (group, rt << 8 | column tile)
-        const int2 e = tl_list[t];
-        BTile tl;
-        tl.g = e.x;
-        tl.rt = e.y >> 8;
-        tl.ct = e.y & 255;
-        int left = gs[e.x].nl - tl.ct * bn_cap;
-        if (left > bn_cap) left = bn_cap;
-        tl.nmma = (left + 15) & ~15;
-        return tl;
-    }
-    int lo = 0, hi = ng - 1;
-    while (lo < hi) {   // last group with t0 <= t
-        const int mid = (lo + hi + 1) >> 1;
-        if (gs[mid].t0 <= t) lo = mid; else hi = mid - 1;
-    }
-    const BGroup& G = gs[lo];
-    BTile tl;
-    const int local = t - G.t0;
-    const int q = local / G.ct;
-    tl.g = lo;
-    tl.ct = local - q * G.ct;
-    const int RT = G.N / BM;
-    tl.rt = (dir > 0) ? (q == 0 ? 0 : RT - q) : q;
-    int left = G.nl - tl.ct * bn_cap;
-    if (left > bn_cap) left = bn_cap;
-    tl.nmma = (left + 15) & ~15;
-    return tl;
-}
-
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constant__ CUtensorMap tF_lo,
                  const __grid_constant__ CUtensorMap tF96_hi, const __grid_constant__ CUtensorMap tF96_lo,
                  const __grid_constant__ CUtensorMap tI_hi, const __grid_constant__ CUtensorMap tI_lo,
-                 const BGroup* __restrict__ groups, int ngroups, int total, const BTrans* __restrict__ trans,
-                 const BMaps* __restrict__ tmaps, const BMaps* __restrict__ cmaps, int Nmax, int dir, int mode,
-                 int bn_cap, float2* __restrict__ out_user, unsigned* status, int* sched,
-                 const int2* __restrict__ tl_list, int walk_up) {
+                 const PTile* __restrict__ tiles, int total, const BGroup* __restrict__ groups,
+                 const BTrans* __restrict__ trans, const BMaps* __restrict__ tmaps, const BMaps* __restrict__ cmaps,
+                 int Nmax, int dir, int mode, float2* __restrict__ out_user, unsigned* status, int* sched,
+                 int walk_up) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage_base = smem;
@@ -181,6 +168,8 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer + tile scheduler
+        __shared__ const CUtensorMap* mseg[SEG_MAX];   // per segment: B tensor map and first line
+        __shared__ int yseg[SEG_MAX];
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
@@ -195,14 +184,15 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                 mbar_arrive(&tq_full[qslot]);
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
                 if (t < 0) break;
-                const BTile tl = bdecode(groups, ngroups, dir, bn_cap, t, tl_list);
-                const BGroup G = groups[tl.g];
-                const KR kr = kranges(dir, tl.rt, n_extra(G.l), G.N / BK, walk_up);
-                const int nbox = (tl.nmma + BBOX - 1) / BBOX;
-                const uint32_t bytes = 2 * A_BYTES + 2 * nbox * BBOX * BK * 4;
-                const int brow = G.bline0 + tl.ct * bn_cap;
-                const CUtensorMap* mb_hi = &tmaps[G.t].m[dir > 0 ? 0 : 2];
-                const CUtensorMap* mb_lo = &tmaps[G.t].m[dir > 0 ? 1 : 3];
+                const PTile& tl = tiles[t];
+                const int l = tl.l, rt = tl.rt, tN = tl.N, cidx = tl.cidx, nseg = tl.nseg;
+                const KR kr = kranges(dir, rt, n_extra(l), tN / BK, walk_up);
+                for (int s = 0; s < nseg; ++s) {
+                    const BGroup& G = groups[tl.g[s]];
+                    mseg[s] = &tmaps[G.t].m[dir > 0 ? 0 : 2];   // hi map; lo map follows it
+                    yseg[s] = G.bline0 + tl.c[s];
+                }
+                const uint32_t bytes = 2 * A_BYTES + 2 * nseg * SEG * BK * 4;
                 const int nkb = kr.count();
                 for (int i = 0; i < nkb; ++i) {
                     const int kb = kr.at(i);
@@ -210,30 +200,29 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                     unsigned char* sb = stage_base + stage * STAGE_BYTES;
                     mbar_expect_tx(&full[stage], bytes);
                     if (dir > 0) {
-                        if (tl.rt == 0) {   // rows 0..31 from the per-N table, 32..127 shared
-                            tma_load_2d(sb, &cmaps[G.cidx].m[0], &full[stage], kb * BK, G.l * CROWS);
-                            tma_load_2d(sb + A_BYTES, &cmaps[G.cidx].m[1], &full[stage], kb * BK, G.l * CROWS);
-                            tma_load_2d(sb + CROWS * 128, &tF96_hi, &full[stage], kb * BK, G.l * Nmax + CROWS);
+                        if (rt == 0) {   // rows 0..31 from the per-N table, 32..127 shared
+                            tma_load_2d(sb, &cmaps[cidx].m[0], &full[stage], kb * BK, l * CROWS);
+                            tma_load_2d(sb + A_BYTES, &cmaps[cidx].m[1], &full[stage], kb * BK, l * CROWS);
+                            tma_load_2d(sb + CROWS * 128, &tF96_hi, &full[stage], kb * BK, l * Nmax + CROWS);
                             tma_load_2d(sb + A_BYTES + CROWS * 128, &tF96_lo, &full[stage], kb * BK,
-                                        G.l * Nmax + CROWS);
+                                        l * Nmax + CROWS);
                         } else {
-                            tma_load_2d(sb, &tF_hi, &full[stage], kb * BK, G.l * Nmax + tl.rt * BM);
-                            tma_load_2d(sb + A_BYTES, &tF_lo, &full[stage], kb * BK, G.l * Nmax + tl.rt * BM);
+                            tma_load_2d(sb, &tF_hi, &full[stage], kb * BK, l * Nmax + rt * BM);
+                            tma_load_2d(sb + A_BYTES, &tF_lo, &full[stage], kb * BK, l * Nmax + rt * BM);
                         }
                     } else {
                         if (kb == 0) {      // K block 0 (rows n < 32 of T) from the per-N table
-                            tma_load_2d(sb, &cmaps[G.cidx].m[2], &full[stage], 0, G.l * G.N + tl.rt * BM);
-                            tma_load_2d(sb + A_BYTES, &cmaps[G.cidx].m[3], &full[stage], 0,
-                                        G.l * G.N + tl.rt * BM);
+                            tma_load_2d(sb, &cmaps[cidx].m[2], &full[stage], 0, l * tN + rt * BM);
+                            tma_load_2d(sb + A_BYTES, &cmaps[cidx].m[3], &full[stage], 0, l * tN + rt * BM);
                         } else {
-                            tma_load_2d(sb, &tI_hi, &full[stage], kb * BK, G.l * Nmax + tl.rt * BM);
-                            tma_load_2d(sb + A_BYTES, &tI_lo, &full[stage], kb * BK, G.l * Nmax + tl.rt * BM);
+                            tma_load_2d(sb, &tI_hi, &full[stage], kb * BK, l * Nmax + rt * BM);
+                            tma_load_2d(sb + A_BYTES, &tI_lo, &full[stage], kb * BK, l * Nmax + rt * BM);
                         }
                     }
-                    for (int b = 0; b < nbox; ++b) {
-                        tma_load_2d(sb + 2 * A_BYTES + b * BBOX * 128, mb_hi, &full[stage], kb * BK, brow + b * BBOX);
-                        tma_load_2d(sb + 2 * A_BYTES + B_BYTES + b * BBOX * 128, mb_lo, &full[stage], kb * BK,
-                                    brow + b * BBOX);
+                    for (int s = 0; s < nseg; ++s) {
+                        tma_load_2d(sb + 2 * A_BYTES + s * SEG * 128, mseg[s], &full[stage], kb * BK, yseg[s]);
+                        tma_load_2d(sb + 2 * A_BYTES + B_BYTES + s * SEG * 128, mseg[s] + 1, &full[stage], kb * BK,
+                                    yseg[s]);
                     }
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
@@ -255,10 +244,9 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                 mbar_arrive(&tq_empty[qslot]);
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
                 if (t < 0) break;
-                const BTile tl = bdecode(groups, ngroups, dir, bn_cap, t, tl_list);
-                const BGroup G = groups[tl.g];
-                const KR kr = kranges(dir, tl.rt, n_extra(G.l), G.N / BK, walk_up);
-                const uint32_t idesc = idesc_tf32(BM, tl.nmma);
+                const PTile& tl = tiles[t];
+                const KR kr = kranges(dir, tl.rt, n_extra(tl.l), tl.N / BK, walk_up);
+                const uint32_t idesc = idesc_tf32(BM, tl.nseg * SEG);
                 const int nkb = kr.count();
                 uint32_t acc_corr = 0;
                 for (int c0 = 0; c0 < nkb && ok; c0 += KC) {
@@ -309,15 +297,12 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
             if (lane == 0) mbar_arrive(&tq_empty[qslot]);
             if (++qslot == QS) { qslot = 0; qphase ^= 1; }
             if (t < 0) break;
-            const BTile tl = bdecode(groups, ngroups, dir, bn_cap, t, tl_list);
-            const BGroup G = groups[tl.g];
-            const KR kr = kranges(dir, tl.rt, n_extra(G.l), G.N / BK, walk_up);
+            const PTile& tl = tiles[t];
+            const int l = tl.l, rt = tl.rt;
+            const KR kr = kranges(dir, rt, n_extra(l), tl.N / BK, walk_up);
             const int nkb = kr.count();
-            const int N = G.N;
-            const int row = tl.rt * BM + quarter * 32 + lane;
-            const int cbase = tl.ct * bn_cap + half * 128;
-            const int ncols = min(min(128, tl.nmma - half * 128), G.nl - cbase);
-            const int nch = (tl.nmma > half * 128) ? ((min(tl.nmma - half * 128, 128) + 31) >> 5) : 0;
+            const int row = rt * BM + quarter * 32 + lane;
+            const int nch = min(max(tl.nseg - half * 4, 0), 4);   // my segments: half * 4 + ch
             const uint32_t tl_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
             float acc[128];
 #pragma unroll
@@ -347,33 +332,41 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                 if (lane == 0) mbar_arrive(main_empty);
             }
             if (!ok) break;
-            if (ncols <= 0) continue;
-            const BTrans T = trans[G.t];
-            if (mode == kModeUserC64) {
-                float2* o = out_user + G.uoff + (size_t)(cbase >> 1) * N;
 #pragma unroll
-                for (int j = 0; j < 128; j += 2)
-                    if (j < ncols) o[(size_t)(j >> 1) * N + row] = make_float2(acc[j], acc[j + 1]);
-            } else if (mode == kModePlanar) {
-                float* o = T.a_hi + (size_t)(G.bline0 + cbase) * N;
+            for (int ch = 0; ch < 4; ++ch) {
+                if (ch >= nch) continue;
+                const int s = half * 4 + ch;
+                const BGroup G = groups[tl.g[s]];
+                const int c = tl.c[s];
+                const int nv = min(SEG, G.nl - c);   // valid lines of the segment
+                const int N = G.N;
+                const BTrans& T = trans[G.t];
+                if (mode == kModeUserC64) {
+                    float2* o = out_user + G.uoff + (size_t)(c >> 1) * N;
 #pragma unroll
-                for (int j = 0; j < 128; ++j)
-                    if (j < ncols) o[(size_t)j * N + row] = acc[j];
-            } else {
-                const float2 ph = T.phase[(size_t)(G.l & 1) * N + row];
-                float* oh = T.b_hi + (size_t)(G.bline0 + cbase) * N;
-                float* ol = T.b_lo + (size_t)(G.bline0 + cbase) * N;
+                    for (int j = 0; j < SEG; j += 2)
+                        if (j < nv) o[(size_t)(j >> 1) * N + row] = make_float2(acc[ch * 32 + j], acc[ch * 32 + j + 1]);
+                } else if (mode == kModePlanar) {
+                    float* o = T.a_hi + (size_t)(G.bline0 + c) * N;
 #pragma unroll
-                for (int j = 0; j < 128; j += 2) {
-                    if (j < ncols) {
-                        const float re = acc[j] * ph.x - acc[j + 1] * ph.y;
-                        const float im = acc[j] * ph.y + acc[j + 1] * ph.x;
-                        const float hr = round_tf32(re), hi = round_tf32(im);
-                        const size_t o = (size_t)j * N + row;
-                        oh[o] = hr;
-                        ol[o] = round_tf32(re - hr);
-                        oh[o + N] = hi;
-                        ol[o + N] = round_tf32(im - hi);
+                    for (int j = 0; j < SEG; ++j)
+                        if (j < nv) o[(size_t)j * N + row] = acc[ch * 32 + j];
+                } else {
+                    const float2 ph = T.phase[(size_t)(l & 1) * N + row];
+                    float* oh = T.b_hi + (size_t)(G.bline0 + c) * N;
+                    float* ol = T.b_lo + (size_t)(G.bline0 + c) * N;
+#pragma unroll
+                    for (int j = 0; j < SEG; j += 2) {
+                        if (j < nv) {
+                            const float re = acc[ch * 32 + j] * ph.x - acc[ch * 32 + j + 1] * ph.y;
+                            const float im = acc[ch * 32 + j] * ph.y + acc[ch * 32 + j + 1] * ph.x;
+                            const float hr = round_tf32(re), hi = round_tf32(im);
+                            const size_t o = (size_t)j * N + row;
+                            oh[o] = hr;
+                            ol[o] = round_tf32(re - hr);
+                            oh[o + N] = hi;
+                            ol[o + N] = round_tf32(im - hi);
+                        }
                     }
                 }
             }
@@ -423,6 +416,11 @@ __global__ void k_split_comp(const double* __restrict__ rows, float* __restrict_
 
 inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+struct TileSet {
+    PTile* d[2] = {nullptr, nullptr};   // forward, inverse
+    int n[2] = {0, 0};
+};
+
 }  // namespace
 }  // namespace dsbt
 
@@ -444,12 +442,12 @@ struct dsbt_batch {
     dsbt::BTrans* trans_d = nullptr;
     dsbt::BMaps* tmaps_d = nullptr;
     dsbt::BMaps* cmaps_d = nullptr;
-    dsbt::BGroup* groups_d[3] = {nullptr, nullptr, nullptr};   // per tile order
-    int2* tiles_d[2] = {nullptr, nullptr};                       // order 2: forward / inverse tile lists
-    int ngroups = 0, total_tiles[3] = {0, 0, 0};   // tiles per order at the current width
+    std::vector<dsbt::BGroup> groups_h;
+    dsbt::BGroup* groups_d = nullptr;
+    dsbt::TileSet sets[dsbt::kOrders][3];  // tile lists per (order, width), built on demand
     int* sched = nullptr;
-    int order = 0, bn_cap = 256;          // autotuned
-    float tune_ms[3][3] = {{0}};
+    int order = 3, ci = 2;                 // selected order and width index (autotuned)
+    float tune_ms[dsbt::kOrders][3] = {{0}};
     std::vector<dsbt::GroupTable> gtab;   // per transform, for the sine/cosine kernels
 };
 
@@ -466,118 +464,199 @@ void batch_free(dsbt_batch* b) {
     cudaFree(b->trans_d);
     cudaFree(b->tmaps_d);
     cudaFree(b->cmaps_d);
-    cudaFree(b->groups_d[0]);
-    cudaFree(b->groups_d[1]);
-    cudaFree(b->groups_d[2]);
-    cudaFree(b->tiles_d[0]);
-    cudaFree(b->tiles_d[1]);
+    cudaFree(b->groups_d);
+    for (auto& row : b->sets)
+        for (auto& ts : row) {
+            cudaFree(ts.d[0]);
+            cudaFree(ts.d[1]);
+        }
     cudaFree(b->sched);
     delete b;
 }
 
 const int kBnCaps[3] = {128, 192, 256};
 
-// Group list in one of two orders; returns the tile count for bn_cap.
-std::vector<BGroup> make_groups(const dsbt_batch* b, int order, int bn_cap, int* total) {
-    struct Item { int t, l; double work; };
-    std::vector<Item> items;
-    for (int t = 0; t < b->T; ++t)
-        for (int l = 0; l <= b->lmax[t]; ++l)
-            if (b->counts[b->counts_off[t] + l] > 0)
-                items.push_back({t, l, (double)b->counts[b->counts_off[t] + l] * b->N[t] * b->N[t]});
-    if (order == 0) {   // transform-major: largest transform first, l descending inside
-        std::vector<double> tw(b->T, 0.0);
-        for (auto& it : items) tw[it.t] += it.work;
-        std::stable_sort(items.begin(), items.end(), [&](const Item& x, const Item& y) {
-            if (x.t != y.t) return tw[x.t] > tw[y.t] || (tw[x.t] == tw[y.t] && x.t < y.t);
-            return x.l > y.l;
-        });
-    } else {            // l-major (orders 1, 2): all transforms' groups of the same l together
-        std::stable_sort(items.begin(), items.end(), [&](const Item& x, const Item& y) {
-            if (x.l != y.l) return x.l > y.l;
-            return b->N[x.t] > b->N[y.t];
-        });
-    }
+// (transform, l) groups with at least one channel, transform-major.
+std::vector<BGroup> make_groups(const dsbt_batch* b) {
     std::vector<BGroup> gs;
-    int t0 = 0;
-    for (auto& it : items) {
-        BGroup G;
-        G.t = it.t;
-        G.l = it.l;
-        G.N = b->N[it.t];
-        const int off = b->counts_off[it.t];
-        int chan_before = 0;
-        for (int l = 0; l < it.l; ++l) chan_before += b->counts[off + l];
-        G.nl = 2 * b->counts[off + it.l];
-        G.bline0 = 2 * chan_before;
-        G.ct = (G.nl + bn_cap - 1) / bn_cap;
-        G.t0 = t0;
-        G.cidx = b->cidx[it.t];
-        G.uoff = b->uoff[it.t] + (long long)chan_before * G.N;
-        t0 += (G.N / BM) * G.ct;
-        gs.push_back(G);
+    for (int t = 0; t < b->T; ++t) {
+        const int off = b->counts_off[t];
+        int chan = 0;
+        for (int l = 0; l <= b->lmax[t]; ++l) {
+            const int c = b->counts[off + l];
+            if (c > 0) {
+                BGroup G;
+                G.t = t;
+                G.l = l;
+                G.N = b->N[t];
+                G.nl = 2 * c;
+                G.bline0 = 2 * chan;
+                G.cidx = b->cidx[t];
+                G.uoff = b->uoff[t] + (long long)chan * G.N;
+                gs.push_back(G);
+            }
+            chan += c;
+        }
     }
-    *total = t0;
     return gs;
 }
 
-// Order 2: within each l (descending), tiles by row tile across all transforms
-// that have it (forward: longest K first, rt = RT-1 .. 1 then rt = 0;
-// inverse: rt = 0 .. RT-1), so tiles reading the same slab of the shared T_l
-// (or T_l^T) run at the same time.  Entries: (group, rt << 8 | column tile).
-std::vector<int2> make_tile_list(const std::vector<BGroup>& gs, int dir) {
-    std::vector<int2> out;
+// Packs the segments of a list of groups, in order, into tiles of at most
+// segcap segments at row tile rt of l.
+struct TileBuilder {
+    std::vector<PTile> out;
+    int segcap = SEG_MAX;
+    void add(const std::vector<BGroup>& gs, const std::vector<int>& gi, int l, int rt) {
+        PTile cur;
+        memset(&cur, 0, sizeof(cur));
+        for (int g : gi)
+            for (int c = 0; c < gs[g].nl; c += SEG) {
+                if (cur.nseg == segcap) {
+                    out.push_back(cur);
+                    memset(&cur, 0, sizeof(cur));
+                }
+                if (cur.nseg == 0 || gs[g].N < cur.N) {
+                    cur.N = gs[g].N;
+                    cur.cidx = gs[g].cidx;
+                }
+                cur.l = l;
+                cur.rt = rt;
+                cur.g[cur.nseg] = g;
+                cur.c[cur.nseg] = c;
+                ++cur.nseg;
+            }
+        if (cur.nseg) out.push_back(cur);
+    }
+};
+
+// Tile list of one direction (dir > 0 forward).  Orders: 0 transform-major
+// (largest transform first, l descending), 1 l-major (l descending, N
+// descending), both with each group's tiles together; 2 l-major with row tiles
+// interleaved across the transforms of one l, so tiles reading the same slab of
+// the shared factors run together; 3 as 2 with segments of different transforms
+// packed into one tile.  Forward row tiles run longest K first with rt = 0 last
+// (orders 2, 3) or first (orders 0, 1); inverse row tiles ascending.
+std::vector<PTile> make_tiles(const dsbt_batch* b, const std::vector<BGroup>& gs, int order, int segcap, int dir) {
+    std::vector<int> idx(gs.size());
+    for (size_t i = 0; i < gs.size(); ++i) idx[i] = (int)i;
+    if (order == 0) {
+        std::vector<double> tw(b->T, 0.0);
+        for (const BGroup& G : gs) tw[G.t] += (double)G.nl * G.N * G.N;
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+            const BGroup &X = gs[x], &Y = gs[y];
+            if (X.t != Y.t) return tw[X.t] > tw[Y.t] || (tw[X.t] == tw[Y.t] && X.t < Y.t);
+            return X.l > Y.l;
+        });
+    } else {
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+            const BGroup &X = gs[x], &Y = gs[y];
+            if (X.l != Y.l) return X.l > Y.l;
+            return X.N > Y.N;
+        });
+    }
+    TileBuilder tb;
+    tb.segcap = segcap;
+    if (order <= 1) {
+        for (int g : idx) {
+            const int RT = gs[g].N / BM;
+            for (int q = 0; q < RT; ++q) {
+                const int rt = (dir > 0) ? (q == 0 ? 0 : RT - q) : q;
+                tb.add(gs, {g}, gs[g].l, rt);
+            }
+        }
+        return tb.out;
+    }
     size_t i = 0;
-    while (i < gs.size()) {
+    while (i < idx.size()) {
+        const int l = gs[idx[i]].l;
         size_t j = i;
-        int rtmax = 0;
-        while (j < gs.size() && gs[j].l == gs[i].l) { rtmax = std::max(rtmax, gs[j].N / BM); ++j; }
+        while (j < idx.size() && gs[idx[j]].l == l) ++j;
+        const int rtmax = gs[idx[i]].N / BM;   // N descending inside the block
         std::vector<int> rts;
-        if (dir > 0) { for (int rt = rtmax - 1; rt >= 1; --rt) rts.push_back(rt); rts.push_back(0); }
-        else for (int rt = 0; rt < rtmax; ++rt) rts.push_back(rt);
-        for (int rt : rts)
-            for (size_t g = i; g < j; ++g)
-                if (rt < gs[g].N / BM)
-                    for (int c = 0; c < gs[g].ct; ++c) out.push_back(make_int2((int)g, (rt << 8) | c));
+        if (dir > 0) {
+            for (int rt = rtmax - 1; rt >= 1; --rt) rts.push_back(rt);
+            rts.push_back(0);
+        } else {
+            for (int rt = 0; rt < rtmax; ++rt) rts.push_back(rt);
+        }
+        for (int rt : rts) {
+            if (order == 2) {
+                for (size_t k = i; k < j; ++k)
+                    if (rt < gs[idx[k]].N / BM) tb.add(gs, {idx[k]}, l, rt);
+            } else if (dir > 0 && rt >= 1) {   // N-independent rows: pack all grids
+                std::vector<int> gi;
+                for (size_t k = i; k < j; ++k)
+                    if (rt < gs[idx[k]].N / BM) gi.push_back(idx[k]);
+                tb.add(gs, gi, l, rt);
+            } else {                           // per-N rows: pack within one grid
+                size_t k = i;
+                while (k < j) {
+                    const int N = gs[idx[k]].N;
+                    std::vector<int> gi;
+                    while (k < j && gs[idx[k]].N == N) gi.push_back(idx[k++]);
+                    if (rt < N / BM) tb.add(gs, gi, l, rt);
+                }
+            }
+        }
         i = j;
     }
-    return out;
+    return tb.out;
 }
 
-int upload_groups(dsbt_batch* b, int order, int bn_cap, cudaStream_t st) {
-    int total = 0;
-    std::vector<BGroup> gs = make_groups(b, order, bn_cap, &total);
-    b->ngroups = (int)gs.size();
-    b->total_tiles[order] = total;
-    if (!b->groups_d[order])
-        DSBT_CUDA_TRY(cudaMalloc((void**)&b->groups_d[order], gs.size() * sizeof(BGroup)));
-    DSBT_CUDA_TRY(cudaMemcpyAsync(b->groups_d[order], gs.data(), gs.size() * sizeof(BGroup),
-                                  cudaMemcpyHostToDevice, st));
-    if (order == 2) {
-        for (const BGroup& g : gs)
-            if (g.ct > 255) {   // the tile list packs the column tile into 8 bits
-                set_error("group of %d lines too wide for the row-interleaved order", g.nl);
-                return DSBT_ERR_UNSUPPORTED;
-            }
-        for (int d = 0; d < 2; ++d) {
-            std::vector<int2> tl = make_tile_list(gs, d == 0 ? +1 : -1);
-            if ((int)tl.size() != total) {
-                set_error("tile list size mismatch");
-                return DSBT_ERR_INVALID;
-            }
-            cudaFree(b->tiles_d[d]);
-            b->tiles_d[d] = nullptr;
-            DSBT_CUDA_TRY(cudaMalloc((void**)&b->tiles_d[d], tl.size() * sizeof(int2)));
-            DSBT_CUDA_TRY(cudaMemcpyAsync(b->tiles_d[d], tl.data(), tl.size() * sizeof(int2),
-                                          cudaMemcpyHostToDevice, st));
+// Host check of a tile list against the rules the kernel relies on.
+bool tiles_valid(const std::vector<BGroup>& gs, const std::vector<PTile>& ts, int dir) {
+    for (const PTile& p : ts) {
+        if (p.nseg < 1 || p.nseg > SEG_MAX) return false;
+        for (int s = 0; s < p.nseg; ++s) {
+            const BGroup& G = gs[p.g[s]];
+            if (G.l != p.l || p.c[s] < 0 || p.c[s] >= G.nl || p.c[s] % SEG) return false;
+            if (p.rt >= G.N / BM || G.N < p.N) return false;
+            if ((dir < 0 || p.rt == 0) && (G.N != p.N || G.cidx != p.cidx)) return false;
         }
+    }
+    return true;
+}
+
+// Builds (once) the forward and inverse tile lists of one (order, width)
+// variant.  Lists are immutable once built, so graphs captured with one stay
+// valid when another variant is selected.
+int ensure_tiles(dsbt_batch* b, int order, int ci, cudaStream_t st) {
+    TileSet& ts = b->sets[order][ci];
+    if (ts.d[0]) return DSBT_OK;
+    for (int d = 0; d < 2; ++d) {
+        const int dir = d == 0 ? +1 : -1;
+        std::vector<PTile> tl = make_tiles(b, b->groups_h, order, kBnCaps[ci] / SEG, dir);
+        if (!tiles_valid(b->groups_h, tl, dir)) {
+            set_error("internal error: invalid tile list (order %d, width %d)", order, kBnCaps[ci]);
+            return DSBT_ERR_INVALID;
+        }
+        ts.n[d] = (int)tl.size();
+        if (cudaMalloc((void**)&ts.d[d], std::max<size_t>(1, tl.size()) * sizeof(PTile)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("tile list allocation failed");
+            return DSBT_ERR_NOMEM;
+        }
+        DSBT_CUDA_TRY(cudaMemcpyAsync(ts.d[d], tl.data(), tl.size() * sizeof(PTile), cudaMemcpyHostToDevice, st));
     }
     DSBT_CUDA_TRY(cudaStreamSynchronize(st));
     return DSBT_OK;
 }
 
-int launch_contract(const dsbt_batch* b, int order, int bn_cap, int total, int dir, int mode, float2* out_user,
-                    cudaStream_t st) {
+void free_tiles(TileSet& ts) {
+    cudaFree(ts.d[0]);
+    cudaFree(ts.d[1]);
+    ts.d[0] = ts.d[1] = nullptr;
+    ts.n[0] = ts.n[1] = 0;
+}
+
+int launch_contract(const dsbt_batch* b, int order, int ci, int dir, int mode, float2* out_user, cudaStream_t st) {
+    const TileSet& ts = b->sets[order][ci];
+    const int d = dir > 0 ? 0 : 1;
+    const int total = ts.n[d];
+    if (!ts.d[d]) {
+        set_error("internal error: tile list not built");
+        return DSBT_ERR_INVALID;
+    }
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
     static bool attr = false;
     if (!attr) {
@@ -594,11 +673,9 @@ int launch_contract(const dsbt_batch* b, int order, int bn_cap, int total, int d
     const dsbt_plan* s = b->shared;
     ProfScope ps(kKContractTF32, st);
     k_contract_batch<<<grid, NTHREADS, smem, st>>>(s->tm_T_hi, s->tm_T_lo, b->tF96_hi, b->tF96_lo, s->tm_Tt_hi,
-                                                   s->tm_Tt_lo, b->groups_d[order], b->ngroups, total,
-                                                   b->trans_d, b->tmaps_d, b->cmaps_d, b->Nmax, dir, mode, bn_cap,
-                                                   out_user, s->status, b->sched,
-                                                   order == 2 ? b->tiles_d[dir > 0 ? 0 : 1] : nullptr,
-                                                   order == 2 ? 1 : 0);
+                                                   s->tm_Tt_lo, ts.d[d], total, b->groups_d, b->trans_d, b->tmaps_d,
+                                                   b->cmaps_d, b->Nmax, dir, mode, out_user, s->status, b->sched,
+                                                   order >= 2 ? 1 : 0);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -615,11 +692,9 @@ int run_batch(const dsbt_batch* b, int kinetic, double tau, const float* in, flo
         rc = dct_forward_f32(tp, b->gtab[t], true, in + 2 * b->uoff[t], b->trans_h[t].a_hi, b->trans_h[t].a_lo, st);
         if (rc) return rc;
     }
-    const int total = b->total_tiles[b->order];
-    if (!kinetic)
-        return launch_contract(b, b->order, b->bn_cap, total, +1, kModeUserC64, (float2*)out, st);
-    rc = launch_contract(b, b->order, b->bn_cap, total, +1, kModeSplit, nullptr, st);
-    if (!rc) rc = launch_contract(b, b->order, b->bn_cap, total, -1, kModePlanar, nullptr, st);
+    if (!kinetic) return launch_contract(b, b->order, b->ci, +1, kModeUserC64, (float2*)out, st);
+    rc = launch_contract(b, b->order, b->ci, +1, kModeSplit, nullptr, st);
+    if (!rc) rc = launch_contract(b, b->order, b->ci, -1, kModePlanar, nullptr, st);
     if (rc) return rc;
     for (int t = 0; t < b->T; ++t) {
         const dsbt_plan* tp = b->tw[b->cidx[t]];
@@ -630,28 +705,22 @@ int run_batch(const dsbt_batch* b, int kinetic, double tau, const float* in, flo
 }
 
 // Times the forward contraction for each (order, column-tile width) on the
-// batch's own shapes (workspace contents do not affect the timing) and keeps
-// the fastest.
+// batch's own shapes (workspace contents do not affect the timing), keeps the
+// fastest and frees the other tile lists (no graph can hold them yet).
 int autotune(dsbt_batch* b, cudaStream_t st) {
     cudaEvent_t e0, e1;
     DSBT_CUDA_TRY(cudaEventCreate(&e0));
     DSBT_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int order = 0; order < 3; ++order) {
-        for (int ci = 0; ci < 3; ++ci) {
-            const int cap = kBnCaps[ci];
-            int rc = upload_groups(b, order, cap, st);
-            if (rc == DSBT_ERR_UNSUPPORTED && order == 2) {   // not offered for this batch
-                b->tune_ms[order][ci] = -1.f;
-                continue;
-            }
-            if (rc) return rc;
-            const int total = b->total_tiles[order];
-            rc = launch_contract(b, order, cap, total, +1, kModeSplit, nullptr, st);   // warm-up
-            if (rc) return rc;
+    int rc = DSBT_OK;
+    for (int order = 0; order < kOrders && !rc; ++order) {
+        for (int ci = 0; ci < 3 && !rc; ++ci) {
+            rc = ensure_tiles(b, order, ci, st);
+            if (!rc) rc = launch_contract(b, order, ci, +1, kModeSplit, nullptr, st);   // warm-up
+            if (rc) break;
             DSBT_CUDA_TRY(cudaEventRecord(e0, st));
-            rc = launch_contract(b, order, cap, total, +1, kModeSplit, nullptr, st);
-            if (rc) return rc;
+            rc = launch_contract(b, order, ci, +1, kModeSplit, nullptr, st);
+            if (rc) break;
             DSBT_CUDA_TRY(cudaEventRecord(e1, st));
             DSBT_CUDA_TRY(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -660,17 +729,16 @@ int autotune(dsbt_batch* b, cudaStream_t st) {
             if (ms < best) {
                 best = ms;
                 b->order = order;
-                b->bn_cap = cap;
+                b->ci = ci;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // final group tables for the chosen width (all orders kept consistent)
-    for (int order = 0; order < 3; ++order) {
-        int rc = upload_groups(b, order, b->bn_cap, st);
-        if (rc && !(rc == DSBT_ERR_UNSUPPORTED && order == 2)) return rc;
-    }
+    if (rc) return rc;
+    for (int order = 0; order < kOrders; ++order)
+        for (int ci = 0; ci < 3; ++ci)
+            if (order != b->order || ci != b->ci) free_tiles(b->sets[order][ci]);
     return DSBT_OK;
 }
 
@@ -803,10 +871,10 @@ extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, con
         T.nlines = b->nlines[t];
         b->trans_h.push_back(T);
         const uint64_t rows = (uint64_t)std::max(1, b->nlines[t]);
-        rc = encode_tmap_f32_sw128(&tm[t].m[0], T.a_hi, rows, N[t], BBOX, 32);
-        if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[1], T.a_lo, rows, N[t], BBOX, 32);
-        if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[2], T.b_hi, rows, N[t], BBOX, 32);
-        if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[3], T.b_lo, rows, N[t], BBOX, 32);
+        rc = encode_tmap_f32_sw128(&tm[t].m[0], T.a_hi, rows, N[t], SEG, 32);
+        if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[1], T.a_lo, rows, N[t], SEG, 32);
+        if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[2], T.b_hi, rows, N[t], SEG, 32);
+        if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[3], T.b_lo, rows, N[t], SEG, 32);
         if (rc) { batch_free(b); return rc; }
         // sine/cosine group table of this transform (channels l-major)
         GroupTable g;
@@ -838,11 +906,19 @@ extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, con
         set_error("dsbt_batch_create: table upload failed");
         return DSBT_ERR_CUDA;
     }
-    for (int order = 0; order < 3; ++order) {
-        rc = upload_groups(b, order, 256, st);
-        if (rc == DSBT_ERR_UNSUPPORTED && order == 2) { rc = DSBT_OK; continue; }
-        if (rc) { batch_free(b); return rc; }
+    b->groups_h = make_groups(b);
+    if (!b->groups_h.empty()) {
+        const size_t gb = b->groups_h.size() * sizeof(BGroup);
+        if (cudaMalloc((void**)&b->groups_d, gb) != cudaSuccess ||
+            cudaMemcpy(b->groups_d, b->groups_h.data(), gb, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            batch_free(b);
+            set_error("dsbt_batch_create: group table upload failed");
+            return DSBT_ERR_CUDA;
+        }
     }
+    rc = ensure_tiles(b, b->order, b->ci, st);
+    if (rc) { batch_free(b); return rc; }
     if (autotune_tiles) {
         rc = autotune(b, st);
         if (rc) { batch_free(b); return rc; }
@@ -863,27 +939,24 @@ extern "C" int dsbt_batch_info(const dsbt_batch* b, long long* total_elems, int*
     DSBT_CHECK_ARG(b != nullptr, "dsbt_batch_info: NULL batch");
     if (total_elems) *total_elems = b->total_elems;
     if (order) *order = b->order;
-    if (bn_cap) *bn_cap = b->bn_cap;
+    if (bn_cap) *bn_cap = kBnCaps[b->ci];
     if (tune_ms)
-        for (int o = 0; o < 3; ++o)
+        for (int o = 0; o < kOrders; ++o)
             for (int c = 0; c < 3; ++c) tune_ms[o * 3 + c] = b->tune_ms[o][c];
     return DSBT_OK;
 }
 
 extern "C" int dsbt_batch_set_tiles(dsbt_batch* b, int order, int bn_cap, void* stream) {
     DSBT_CHECK_ARG(b != nullptr, "dsbt_batch_set_tiles: NULL batch");
-    DSBT_CHECK_ARG(order >= 0 && order <= 2, "dsbt_batch_set_tiles: order %d not in 0..2", order);
-    DSBT_CHECK_ARG(bn_cap == 128 || bn_cap == 192 || bn_cap == 256, "dsbt_batch_set_tiles: width %d", bn_cap);
-    cudaStream_t st = (cudaStream_t)stream;
-    int rc = upload_groups(b, order, bn_cap, st);
+    DSBT_CHECK_ARG(order >= 0 && order < kOrders, "dsbt_batch_set_tiles: order %d not in 0..%d", order, kOrders - 1);
+    int ci = -1;
+    for (int c = 0; c < 3; ++c)
+        if (kBnCaps[c] == bn_cap) ci = c;
+    DSBT_CHECK_ARG(ci >= 0, "dsbt_batch_set_tiles: width %d not 128, 192 or 256", bn_cap);
+    const int rc = ensure_tiles(b, order, ci, (cudaStream_t)stream);
     if (rc) return rc;
-    for (int o = 0; o < 3; ++o) {   // keep every order's table at the new width
-        if (o == order) continue;
-        rc = upload_groups(b, o, bn_cap, st);
-        if (rc && !(rc == DSBT_ERR_UNSUPPORTED && o == 2)) return rc;
-    }
     b->order = order;
-    b->bn_cap = bn_cap;
+    b->ci = ci;
     return DSBT_OK;
 }
 

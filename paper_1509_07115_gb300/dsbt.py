@@ -288,14 +288,14 @@ class Batch:
 
     def info(self) -> dict:
         n, o, b = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
-        ms = (ctypes.c_float * 9)()
+        ms = (ctypes.c_float * 12)()
         _check(load().dsbt_batch_info(self._h, ctypes.byref(n), ctypes.byref(o), ctypes.byref(b), ms),
                "dsbt_batch_info")
         names = self.TILE_ORDERS
         return {"total_elems": n.value, "order": names[o.value], "bn_cap": b.value,
-                "tune_ms": {f"{names[k // 3]}/{[128, 192, 256][k % 3]}": ms[k] for k in range(9)}}
+                "tune_ms": {f"{names[k // 3]}/{[128, 192, 256][k % 3]}": ms[k] for k in range(12)}}
 
-    TILE_ORDERS = ("transform-major", "l-major", "l-major/row-interleaved")
+    TILE_ORDERS = ("transform-major", "l-major", "l-major/row-interleaved", "l-major/packed")
 
     def set_tiles(self, order: str, bn_cap: int):
         """Pin the contraction's tile order (one of TILE_ORDERS) and width."""
