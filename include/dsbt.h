@@ -257,6 +257,15 @@ DSBT_API int dsbt_batch_destroy(dsbt_batch* batch);
 DSBT_API int dsbt_batch_info(const dsbt_batch* batch, long long* total_elems, int* order, int* bn_cap,
                              float* tune_ms);
 
+/* Host-only planning check (no device is touched): builds the forward and
+ * inverse tile lists the batch described by (ntrans, N, l_max, counts) would
+ * use at (order, bn_cap), checks them against the kernel's rules, and returns
+ * their lengths and the forward list's B-operand lines (segments x 32; the
+ * padding overhead is seg_lines / real lines).  DSBT_ERR_INVALID for bad
+ * arguments or a list that breaks a rule.  NULL outputs are skipped. */
+DSBT_API int dsbt_batch_tiles(int ntrans, const int* N, const int* l_max, const int* counts, int order, int bn_cap,
+                              int* ntiles_fwd, int* ntiles_inv, long long* seg_lines);
+
 /* Pin the contraction's tile order and column-tile width (128, 192 or 256
  * lines), overriding the autotuner.  Orders: 0 transform-major, 1 l-major
  * (each (transform, l) group's tiles together), 2 l-major with row tiles

@@ -64,19 +64,92 @@ struct BGroup {
     long long uoff;    // complex-element offset of the group's first channel (caller layout)
 };
 
+struct KR {
+    int a0, a1, b0, b1, up;
+    __device__ __forceinline__ int count() const { return (a1 - a0) + (b1 - b0); }
+    __device__ __forceinline__ int at(int i) const {
+        if (up) return (i < a1 - a0) ? (a0 + i) : (b0 + i - (a1 - a0));
+        const int nb = b1 - b0;
+        return (i < nb) ? (b1 - 1 - i) : (a1 - 1 - (i - nb));
+    }
+};
+
+// K blocks of a tile: the forward T_l is dense in its completion rows (n < nx)
+// and lower triangular below; T_l^T is dense in its first nx columns and upper
+// triangular.
+__device__ __forceinline__ KR kranges(int dir, int rt, int nx, int KB) {
+    KR k;
+    const int r0 = rt * BM;
+    k.up = 1;
+    k.a0 = 0;
+    k.b0 = k.b1 = 0;
+    if (r0 < nx) { k.a1 = KB; return k; }
+    if (dir > 0) { k.a1 = min(KB, (r0 + BM) / BK); return k; }
+    k.a1 = (nx + BK - 1) / BK;
+    k.b0 = max(k.a1, r0 / BK);
+    k.b1 = KB;
+    return k;
+}
+
 // One output tile: rows [rt BM, rt BM + BM) of T_l (forward) or T_l^T
 // (inverse) against up to SEG_MAX segments of SEG lines.  A segment is lines
 // [c, c + SEG) of one (transform, l) group; lines past the group's end are
 // computed and discarded.  Segments of one tile may come from different
-// transforms: the rows of the shared factors a forward tile with rt >= 1 reads
-// do not depend on N.  Tiles that read per-N rows (forward rt = 0, every
-// inverse tile) hold segments of one grid N only.
+// transforms.  The rows of the shared factors a forward tile with rt >= 1
+// reads do not depend on N; a forward tile with rt = 0 reads per-N rows and
+// holds one grid.  An inverse tile may hold several grids ("classes", N
+// descending, contiguous): its K range ends at the largest N (the B operand of
+// a smaller grid reads zeros past its own N through the tensor map bounds),
+// and K block 0, which comes from each grid's own per-N table, runs as one
+// sub-step per class on that class's columns.
 struct __align__(16) PTile {
-    int l, rt, N, cidx;   // N: grid of the K range (the smallest segment grid), cidx: its per-N tables
-    int nseg, pad0, pad1, pad2;
+    int l, rt, N, cidx;   // N: grid of the K range, cidx: per-N tables of a one-grid tile
+    int nseg, ncls, pad0, pad1;
     int g[SEG_MAX];       // group of each segment
     int c[SEG_MAX];       // first line of the segment in its group
+    unsigned char cend[SEG_MAX];   // one past the last segment of each class
 };
+
+// Steps of one tile: K blocks ascending, with K block 0 (when in range) split
+// into ns sub-steps, one per class of an inverse tile.  The main accumulator
+// restarts at chunk boundaries: the first chunk holds the sub-steps and the
+// next KC - 1 K blocks, later chunks KC K blocks, so no column accumulates
+// more than KC K blocks in one chunk.
+struct Steps {
+    KR kr;
+    int ns, nsteps, c0len;
+    bool kb0;
+    __device__ __forceinline__ int kb(int i) const {
+        if (!kb0) return kr.at(i);
+        return (i < ns) ? 0 : kr.at(i - ns + 1);
+    }
+    __device__ __forceinline__ int chunk_end(int start) const {
+        return min(nsteps, start == 0 ? c0len : start + KC);
+    }
+};
+
+__device__ __forceinline__ Steps make_steps(int dir, const PTile& tl) {
+    Steps sp;
+    sp.kr = kranges(dir, tl.rt, n_extra(tl.l), tl.N / BK);
+    const int n = sp.kr.count();
+    sp.kb0 = n > 0 && sp.kr.at(0) == 0;
+    sp.ns = (sp.kb0 && dir < 0) ? tl.ncls : 1;
+    sp.nsteps = sp.kb0 ? n - 1 + sp.ns : n;
+    sp.c0len = sp.kb0 ? sp.ns + KC - 1 : KC;
+    return sp;
+}
+
+// Segments [s0, s1) a step reads: one class in an inverse tile's K block 0
+// sub-steps, else all.
+__device__ __forceinline__ void step_segments(int dir, const PTile& tl, const Steps& sp, int i, int* s0, int* s1) {
+    if (dir < 0 && sp.kb0 && i < sp.ns) {
+        *s0 = i == 0 ? 0 : tl.cend[i - 1];
+        *s1 = tl.cend[i];
+    } else {
+        *s0 = 0;
+        *s1 = tl.nseg;
+    }
+}
 
 struct BTrans {
     float* a_hi;       // forward B operand / inverse output (planar FP32 aliases a_hi)
@@ -94,41 +167,13 @@ struct __align__(64) BMaps {
 
 enum : int { kModeUserC64 = 0, kModeSplit = 1, kModePlanar = 2 };
 
-struct KR {
-    int a0, a1, b0, b1, up;
-    __device__ __forceinline__ int count() const { return (a1 - a0) + (b1 - b0); }
-    __device__ __forceinline__ int at(int i) const {
-        if (up) return (i < a1 - a0) ? (a0 + i) : (b0 + i - (a1 - a0));
-        const int nb = b1 - b0;
-        return (i < nb) ? (b1 - 1 - i) : (a1 - 1 - (i - nb));
-    }
-};
-
-// K blocks of a tile: the forward T_l is dense in its completion rows (n < nx)
-// and lower triangular below; T_l^T is dense in its first nx columns and upper
-// triangular.
-__device__ __forceinline__ KR kranges(int dir, int rt, int nx, int KB, int walk_up) {
-    KR k;
-    const int r0 = rt * BM;
-    k.up = (dir > 0) || walk_up;
-    k.a0 = 0;
-    k.b0 = k.b1 = 0;
-    if (r0 < nx) { k.a1 = KB; return k; }
-    if (dir > 0) { k.a1 = min(KB, (r0 + BM) / BK); return k; }
-    k.a1 = (nx + BK - 1) / BK;
-    k.b0 = max(k.a1, r0 / BK);
-    k.b1 = KB;
-    return k;
-}
-
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constant__ CUtensorMap tF_lo,
                  const __grid_constant__ CUtensorMap tF96_hi, const __grid_constant__ CUtensorMap tF96_lo,
                  const __grid_constant__ CUtensorMap tI_hi, const __grid_constant__ CUtensorMap tI_lo,
                  const PTile* __restrict__ tiles, int total, const BGroup* __restrict__ groups,
                  const BTrans* __restrict__ trans, const BMaps* __restrict__ tmaps, const BMaps* __restrict__ cmaps,
-                 int Nmax, int dir, int mode, float2* __restrict__ out_user, unsigned* status, int* sched,
-                 int walk_up) {
+                 int Nmax, int dir, int mode, float2* __restrict__ out_user, unsigned* status, int* sched) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage_base = smem;
@@ -185,22 +230,23 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
                 if (t < 0) break;
                 const PTile& tl = tiles[t];
-                const int l = tl.l, rt = tl.rt, tN = tl.N, cidx = tl.cidx, nseg = tl.nseg;
-                const KR kr = kranges(dir, rt, n_extra(l), tN / BK, walk_up);
+                const int l = tl.l, rt = tl.rt, nseg = tl.nseg;
+                const Steps sp = make_steps(dir, tl);
                 for (int s = 0; s < nseg; ++s) {
                     const BGroup& G = groups[tl.g[s]];
                     mseg[s] = &tmaps[G.t].m[dir > 0 ? 0 : 2];   // hi map; lo map follows it
                     yseg[s] = G.bline0 + tl.c[s];
                 }
-                const uint32_t bytes = 2 * A_BYTES + 2 * nseg * SEG * BK * 4;
-                const int nkb = kr.count();
-                for (int i = 0; i < nkb; ++i) {
-                    const int kb = kr.at(i);
+                for (int i = 0; i < sp.nsteps; ++i) {
+                    const int kb = sp.kb(i);
+                    int s0, s1;
+                    step_segments(dir, tl, sp, i, &s0, &s1);
                     if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status)) { ok = false; break; }
                     unsigned char* sb = stage_base + stage * STAGE_BYTES;
-                    mbar_expect_tx(&full[stage], bytes);
+                    mbar_expect_tx(&full[stage], 2 * A_BYTES + 2 * (s1 - s0) * SEG * BK * 4);
                     if (dir > 0) {
                         if (rt == 0) {   // rows 0..31 from the per-N table, 32..127 shared
+                            const int cidx = tl.cidx;
                             tma_load_2d(sb, &cmaps[cidx].m[0], &full[stage], kb * BK, l * CROWS);
                             tma_load_2d(sb + A_BYTES, &cmaps[cidx].m[1], &full[stage], kb * BK, l * CROWS);
                             tma_load_2d(sb + CROWS * 128, &tF96_hi, &full[stage], kb * BK, l * Nmax + CROWS);
@@ -211,15 +257,16 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                             tma_load_2d(sb + A_BYTES, &tF_lo, &full[stage], kb * BK, l * Nmax + rt * BM);
                         }
                     } else {
-                        if (kb == 0) {      // K block 0 (rows n < 32 of T) from the per-N table
-                            tma_load_2d(sb, &cmaps[cidx].m[2], &full[stage], 0, l * tN + rt * BM);
-                            tma_load_2d(sb + A_BYTES, &cmaps[cidx].m[3], &full[stage], 0, l * tN + rt * BM);
+                        if (kb == 0) {      // K block 0 (rows n < 32 of T) from the class's per-N table
+                            const BGroup& G = groups[tl.g[s0]];
+                            tma_load_2d(sb, &cmaps[G.cidx].m[2], &full[stage], 0, l * G.N + rt * BM);
+                            tma_load_2d(sb + A_BYTES, &cmaps[G.cidx].m[3], &full[stage], 0, l * G.N + rt * BM);
                         } else {
                             tma_load_2d(sb, &tI_hi, &full[stage], kb * BK, l * Nmax + rt * BM);
                             tma_load_2d(sb + A_BYTES, &tI_lo, &full[stage], kb * BK, l * Nmax + rt * BM);
                         }
                     }
-                    for (int s = 0; s < nseg; ++s) {
+                    for (int s = s0; s < s1; ++s) {
                         tma_load_2d(sb + 2 * A_BYTES + s * SEG * 128, mseg[s], &full[stage], kb * BK, yseg[s]);
                         tma_load_2d(sb + 2 * A_BYTES + B_BYTES + s * SEG * 128, mseg[s] + 1, &full[stage], kb * BK,
                                     yseg[s]);
@@ -245,39 +292,43 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
                 if (t < 0) break;
                 const PTile& tl = tiles[t];
-                const KR kr = kranges(dir, tl.rt, n_extra(tl.l), tl.N / BK, walk_up);
-                const uint32_t idesc = idesc_tf32(BM, tl.nseg * SEG);
-                const int nkb = kr.count();
-                uint32_t acc_corr = 0;
-                for (int c0 = 0; c0 < nkb && ok; c0 += KC) {
+                const Steps sp = make_steps(dir, tl);
+                const uint32_t idesc_all = idesc_tf32(BM, tl.nseg * SEG);
+                for (int c0 = 0; c0 < sp.nsteps && ok;) {
+                    const int c1 = sp.chunk_end(c0);
                     if (!mbar_wait(main_empty, mphase ^ 1, abort_flag, status)) { ok = false; break; }
                     mphase ^= 1;
                     tc_fence_after();
-                    uint32_t acc_main = 0;
-                    const int c1 = min(nkb, c0 + KC);
                     for (int i = c0; i < c1; ++i) {
+                        int s0, s1;
+                        step_segments(dir, tl, sp, i, &s0, &s1);
+                        // first write of these columns in this chunk (main) / in this tile (correction)
+                        const bool sub = s1 - s0 != tl.nseg;
+                        const uint32_t fresh_main = (i == c0 || sub) ? 0u : 1u;
+                        const uint32_t fresh_corr = (i == 0 || sub) ? 0u : 1u;
+                        const uint32_t idesc = sub ? idesc_tf32(BM, (s1 - s0) * SEG) : idesc_all;
+                        const uint32_t col0 = (uint32_t)(s0 * SEG);
                         if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
                         const uint32_t sa_lo = sa + A_BYTES;
-                        const uint32_t sb_hi = sa + 2 * A_BYTES;
+                        const uint32_t sb_hi = sa + 2 * A_BYTES + s0 * SEG * 128;
                         const uint32_t sb_lo = sb_hi + B_BYTES;
 #pragma unroll
                         for (int ks = 0; ks < BK / 8; ++ks) {
                             const uint32_t off = ks * 32;
                             const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa_lo + off);
                             const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_lo + off);
-                            mma_tf32(d_main, dah, dbh, idesc, acc_main);
-                            mma_tf32(d_corr, dah, dbl, idesc, acc_corr);
-                            mma_tf32(d_corr, dal, dbh, idesc, 1);
-                            acc_main = 1;
-                            acc_corr = 1;
+                            mma_tf32(d_main + col0, dah, dbh, idesc, ks == 0 ? fresh_main : 1u);
+                            mma_tf32(d_corr + col0, dah, dbl, idesc, ks == 0 ? fresh_corr : 1u);
+                            mma_tf32(d_corr + col0, dal, dbh, idesc, 1);
                         }
                         mma_commit(&empty[stage]);
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                     if (!ok) break;
                     mma_commit(main_full);
+                    c0 = c1;
                 }
             }
         }
@@ -299,8 +350,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
             if (t < 0) break;
             const PTile& tl = tiles[t];
             const int l = tl.l, rt = tl.rt;
-            const KR kr = kranges(dir, rt, n_extra(l), tl.N / BK, walk_up);
-            const int nkb = kr.count();
+            const Steps sp = make_steps(dir, tl);
             const int row = rt * BM + quarter * 32 + lane;
             const int nch = min(max(tl.nseg - half * 4, 0), 4);   // my segments: half * 4 + ch
             const uint32_t tl_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
@@ -308,11 +358,13 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
 #pragma unroll
             for (int j = 0; j < 128; ++j) acc[j] = 0.f;
             bool ok = true;
-            for (int c0 = 0; c0 < nkb; c0 += KC) {
+            for (int c0 = 0; c0 < sp.nsteps;) {
+                const int c1 = sp.chunk_end(c0);
                 if (!mbar_wait(main_full, mphase, abort_flag, status)) { ok = false; break; }
                 mphase ^= 1;
                 tc_fence_after();
-                const bool last = c0 + KC >= nkb;
+                const bool last = c1 == sp.nsteps;
+                c0 = c1;
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) {
                     if (ch < nch) {
@@ -502,30 +554,44 @@ std::vector<BGroup> make_groups(const dsbt_batch* b) {
 }
 
 // Packs the segments of a list of groups, in order, into tiles of at most
-// segcap segments at row tile rt of l.
+// segcap segments at row tile rt of l.  A forward tile's K range is that of
+// its smallest grid (all grids hold rows up to (rt + 1) BM); an inverse tile's
+// is that of its first, largest grid, and its classes are the runs of equal N.
 struct TileBuilder {
     std::vector<PTile> out;
     int segcap = SEG_MAX;
+    int dir = 1;
+    void push(PTile& cur, const std::vector<BGroup>& gs) {
+        if (!cur.nseg) return;
+        cur.ncls = 0;
+        for (int s = 0; s < cur.nseg; ++s) {
+            const BGroup& G = gs[cur.g[s]];
+            if (dir > 0) {
+                if (s == 0 || G.N < cur.N) { cur.N = G.N; cur.cidx = G.cidx; }
+            } else if (s == 0) {
+                cur.N = G.N;
+                cur.cidx = G.cidx;
+            }
+            const bool new_class = dir < 0 && s > 0 && G.N != gs[cur.g[s - 1]].N;
+            if (new_class) cur.cend[cur.ncls++] = (unsigned char)s;
+        }
+        cur.cend[cur.ncls++] = (unsigned char)cur.nseg;
+        out.push_back(cur);
+        memset(&cur, 0, sizeof(cur));
+    }
     void add(const std::vector<BGroup>& gs, const std::vector<int>& gi, int l, int rt) {
         PTile cur;
         memset(&cur, 0, sizeof(cur));
         for (int g : gi)
             for (int c = 0; c < gs[g].nl; c += SEG) {
-                if (cur.nseg == segcap) {
-                    out.push_back(cur);
-                    memset(&cur, 0, sizeof(cur));
-                }
-                if (cur.nseg == 0 || gs[g].N < cur.N) {
-                    cur.N = gs[g].N;
-                    cur.cidx = gs[g].cidx;
-                }
+                if (cur.nseg == segcap) push(cur, gs);
                 cur.l = l;
                 cur.rt = rt;
                 cur.g[cur.nseg] = g;
                 cur.c[cur.nseg] = c;
                 ++cur.nseg;
             }
-        if (cur.nseg) out.push_back(cur);
+        push(cur, gs);
     }
 };
 
@@ -556,6 +622,7 @@ std::vector<PTile> make_tiles(const dsbt_batch* b, const std::vector<BGroup>& gs
     }
     TileBuilder tb;
     tb.segcap = segcap;
+    tb.dir = dir;
     if (order <= 1) {
         for (int g : idx) {
             const int RT = gs[g].N / BM;
@@ -583,18 +650,18 @@ std::vector<PTile> make_tiles(const dsbt_batch* b, const std::vector<BGroup>& gs
             if (order == 2) {
                 for (size_t k = i; k < j; ++k)
                     if (rt < gs[idx[k]].N / BM) tb.add(gs, {idx[k]}, l, rt);
-            } else if (dir > 0 && rt >= 1) {   // N-independent rows: pack all grids
+            } else if (dir < 0 || rt >= 1) {   // pack all grids that hold row tile rt
                 std::vector<int> gi;
                 for (size_t k = i; k < j; ++k)
                     if (rt < gs[idx[k]].N / BM) gi.push_back(idx[k]);
                 tb.add(gs, gi, l, rt);
-            } else {                           // per-N rows: pack within one grid
+            } else {                           // forward rt = 0 reads per-N rows: one grid per tile
                 size_t k = i;
                 while (k < j) {
                     const int N = gs[idx[k]].N;
                     std::vector<int> gi;
                     while (k < j && gs[idx[k]].N == N) gi.push_back(idx[k++]);
-                    if (rt < N / BM) tb.add(gs, gi, l, rt);
+                    tb.add(gs, gi, l, rt);
                 }
             }
         }
@@ -606,13 +673,23 @@ std::vector<PTile> make_tiles(const dsbt_batch* b, const std::vector<BGroup>& gs
 // Host check of a tile list against the rules the kernel relies on.
 bool tiles_valid(const std::vector<BGroup>& gs, const std::vector<PTile>& ts, int dir) {
     for (const PTile& p : ts) {
-        if (p.nseg < 1 || p.nseg > SEG_MAX) return false;
+        if (p.nseg < 1 || p.nseg > SEG_MAX || p.ncls < 1 || p.ncls > p.nseg || p.cend[p.ncls - 1] != p.nseg)
+            return false;
+        int cls = 0;
         for (int s = 0; s < p.nseg; ++s) {
             const BGroup& G = gs[p.g[s]];
             if (G.l != p.l || p.c[s] < 0 || p.c[s] >= G.nl || p.c[s] % SEG) return false;
-            if (p.rt >= G.N / BM || G.N < p.N) return false;
-            if ((dir < 0 || p.rt == 0) && (G.N != p.N || G.cidx != p.cidx)) return false;
+            if (p.rt >= G.N / BM) return false;   // every output row exists in the segment's grid
+            if (s == p.cend[cls]) ++cls;
+            const BGroup& F = gs[p.g[cls == 0 ? 0 : p.cend[cls - 1]]];   // first segment of the class
+            if (dir < 0 && (G.N != F.N || G.cidx != F.cidx)) return false;
+            if (dir > 0) {
+                if (G.N < p.N || (p.rt == 0 && (G.N != p.N || G.cidx != p.cidx))) return false;
+            } else {
+                if (G.N > p.N || (cls > 0 && G.N >= gs[p.g[p.cend[cls - 1] - 1]].N)) return false;
+            }
         }
+        if (dir > 0 && p.ncls != 1) return false;
     }
     return true;
 }
@@ -674,8 +751,7 @@ int launch_contract(const dsbt_batch* b, int order, int ci, int dir, int mode, f
     ProfScope ps(kKContractTF32, st);
     k_contract_batch<<<grid, NTHREADS, smem, st>>>(s->tm_T_hi, s->tm_T_lo, b->tF96_hi, b->tF96_lo, s->tm_Tt_hi,
                                                    s->tm_Tt_lo, ts.d[d], total, b->groups_d, b->trans_d, b->tmaps_d,
-                                                   b->cmaps_d, b->Nmax, dir, mode, out_user, s->status, b->sched,
-                                                   order >= 2 ? 1 : 0);
+                                                   b->cmaps_d, b->Nmax, dir, mode, out_user, s->status, b->sched);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -747,36 +823,28 @@ int autotune(dsbt_batch* b, cudaStream_t st) {
 
 using namespace dsbt;
 
-extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, const int* counts, double dr,
-                                 int autotune_tiles, void* stream, dsbt_batch** out) {
-    DSBT_CHECK_ARG(out != nullptr && N != nullptr && l_max != nullptr && counts != nullptr,
-                   "dsbt_batch_create: NULL argument");
-    *out = nullptr;
-    DSBT_CHECK_ARG(ntrans >= 1 && ntrans <= 4096, "dsbt_batch_create: ntrans=%d out of range", ntrans);
-    DSBT_CHECK_ARG(dr > 0.0 && isfinite(dr), "dsbt_batch_create: dr must be positive");
-    cudaStream_t st = (cudaStream_t)stream;
-    dsbt_batch* b = new (std::nothrow) dsbt_batch();
-    if (!b) return DSBT_ERR_NOMEM;
+namespace dsbt {
+namespace {
+
+// Host-side description of a batch (sizes, offsets, distinct grids); touches
+// no device memory.
+int batch_describe(dsbt_batch* b, int ntrans, const int* N, const int* l_max, const int* counts, double dr) {
+    DSBT_CHECK_ARG(N != nullptr && l_max != nullptr && counts != nullptr, "dsbt_batch: NULL argument");
+    DSBT_CHECK_ARG(ntrans >= 1 && ntrans <= 4096, "dsbt_batch: ntrans=%d out of range", ntrans);
+    DSBT_CHECK_ARG(dr > 0.0 && isfinite(dr), "dsbt_batch: dr must be positive");
     b->T = ntrans;
     b->dr = dr;
     int off = 0;
     long long uoff = 0;
     for (int t = 0; t < ntrans; ++t) {
-        if (!(N[t] >= 256 && N[t] <= 8192 && N[t] % 256 == 0) || !(l_max[t] >= 0 && l_max[t] <= 64)) {
-            delete b;
-            set_error("dsbt_batch_create: transform %d: N=%d, l_max=%d not supported", t, N[t], l_max[t]);
-            return DSBT_ERR_INVALID;
-        }
+        DSBT_CHECK_ARG(N[t] >= 256 && N[t] <= 8192 && N[t] % 256 == 0 && l_max[t] >= 0 && l_max[t] <= 64,
+                       "dsbt_batch: transform %d: N=%d, l_max=%d not supported", t, N[t], l_max[t]);
         b->N.push_back(N[t]);
         b->lmax.push_back(l_max[t]);
         b->counts_off.push_back(off);
         int nc = 0;
         for (int l = 0; l <= l_max[t]; ++l) {
-            if (counts[off + l] < 0) {
-                delete b;
-                set_error("dsbt_batch_create: negative count");
-                return DSBT_ERR_INVALID;
-            }
+            DSBT_CHECK_ARG(counts[off + l] >= 0 && counts[off + l] <= (1 << 24), "dsbt_batch: bad channel count");
             b->counts.push_back(counts[off + l]);
             nc += counts[off + l];
         }
@@ -787,16 +855,6 @@ extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, con
         uoff += (long long)nc * N[t];
         b->Nmax = std::max(b->Nmax, N[t]);
         b->L = std::max(b->L, l_max[t] + 1);
-    }
-    b->total_elems = uoff;
-    // shared factors at (N_max, l_max)
-    int rc = dsbt_plan_create(b->Nmax, b->Nmax * dr, b->L - 1, DSBT_PLAN_TF32X3, stream, &b->shared);
-    if (rc) { batch_free(b); return rc; }
-    rc = encode_tmap_f32_sw128(&b->tF96_hi, b->shared->Thi, (uint64_t)b->L * b->Nmax, b->Nmax, 96, 32);
-    if (!rc) rc = encode_tmap_f32_sw128(&b->tF96_lo, b->shared->Tlo, (uint64_t)b->L * b->Nmax, b->Nmax, 96, 32);
-    if (rc) { batch_free(b); return rc; }
-    // distinct grids: twiddles and per-N tables
-    for (int t = 0; t < ntrans; ++t) {
         auto it = std::find(b->dN.begin(), b->dN.end(), N[t]);
         if (it == b->dN.end()) {
             b->cidx.push_back((int)b->dN.size());
@@ -805,6 +863,56 @@ extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, con
             b->cidx.push_back((int)(it - b->dN.begin()));
         }
     }
+    b->total_elems = uoff;
+    b->groups_h = make_groups(b);
+    return DSBT_OK;
+}
+
+}  // namespace
+}  // namespace dsbt
+
+extern "C" int dsbt_batch_tiles(int ntrans, const int* N, const int* l_max, const int* counts, int order,
+                                int bn_cap, int* ntiles_fwd, int* ntiles_inv, long long* seg_lines) {
+    DSBT_CHECK_ARG(order >= 0 && order < kOrders, "dsbt_batch_tiles: order %d not in 0..%d", order, kOrders - 1);
+    DSBT_CHECK_ARG(bn_cap == 128 || bn_cap == 192 || bn_cap == 256, "dsbt_batch_tiles: width %d", bn_cap);
+    dsbt_batch tmp;
+    int rc = batch_describe(&tmp, ntrans, N, l_max, counts, 1.0);
+    if (rc) return rc;
+    long long lines = 0;
+    for (int d = 0; d < 2; ++d) {
+        const int dir = d == 0 ? +1 : -1;
+        std::vector<PTile> tl = make_tiles(&tmp, tmp.groups_h, order, bn_cap / SEG, dir);
+        if (!tiles_valid(tmp.groups_h, tl, dir)) {
+            set_error("dsbt_batch_tiles: invalid tile list (order %d, width %d, dir %d)", order, bn_cap, dir);
+            return DSBT_ERR_INVALID;
+        }
+        if (d == 0 && ntiles_fwd) *ntiles_fwd = (int)tl.size();
+        if (d == 1 && ntiles_inv) *ntiles_inv = (int)tl.size();
+        if (d == 0)
+            for (const PTile& p : tl) lines += (long long)p.nseg * SEG;
+    }
+    if (seg_lines) *seg_lines = lines;
+    return DSBT_OK;
+}
+
+extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, const int* counts, double dr,
+                                 int autotune_tiles, void* stream, dsbt_batch** out) {
+    DSBT_CHECK_ARG(out != nullptr, "dsbt_batch_create: NULL argument");
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    dsbt_batch* b = new (std::nothrow) dsbt_batch();
+    if (!b) return DSBT_ERR_NOMEM;
+    {
+        const int rc0 = batch_describe(b, ntrans, N, l_max, counts, dr);
+        if (rc0) { delete b; return rc0; }
+    }
+    // shared factors at (N_max, l_max)
+    int rc = dsbt_plan_create(b->Nmax, b->Nmax * dr, b->L - 1, DSBT_PLAN_TF32X3, stream, &b->shared);
+    if (rc) { batch_free(b); return rc; }
+    rc = encode_tmap_f32_sw128(&b->tF96_hi, b->shared->Thi, (uint64_t)b->L * b->Nmax, b->Nmax, 96, 32);
+    if (!rc) rc = encode_tmap_f32_sw128(&b->tF96_lo, b->shared->Tlo, (uint64_t)b->L * b->Nmax, b->Nmax, 96, 32);
+    if (rc) { batch_free(b); return rc; }
+    // distinct grids: twiddles and per-N tables
     const int ND = (int)b->dN.size();
     size_t comp_elems = 0, comp64_max = 0;
     for (int d = 0; d < ND; ++d) {
@@ -906,7 +1014,6 @@ extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, con
         set_error("dsbt_batch_create: table upload failed");
         return DSBT_ERR_CUDA;
     }
-    b->groups_h = make_groups(b);
     if (!b->groups_h.empty()) {
         const size_t gb = b->groups_h.size() * sizeof(BGroup);
         if (cudaMalloc((void**)&b->groups_d, gb) != cudaSuccess ||

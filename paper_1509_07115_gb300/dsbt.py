@@ -63,6 +63,8 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), _c_int_p, _c_int_p,
                                         ctypes.POINTER(ctypes.c_float)]
         lib.dsbt_batch_set_tiles.argtypes = [vp, i, i, vp]
+        lib.dsbt_batch_tiles.argtypes = [i, _c_int_p, _c_int_p, _c_int_p, i, i, _c_int_p, _c_int_p,
+                                         ctypes.POINTER(ctypes.c_longlong)]
         lib.dsbt_batch_forward.argtypes = [vp, vp, vp, vp]
         lib.dsbt_batch_kinetic.argtypes = [vp, d, vp, vp, vp]
         lib.dsbt_batch_capture_kinetic.argtypes = [vp, d, vp, vp, ctypes.POINTER(vp)]
@@ -248,6 +250,20 @@ def profile_read() -> dict:
 
 
 # ------------------------------------------------------------------ batch of uneven transforms
+
+def batch_tiles(transforms, order: str, bn_cap: int) -> dict:
+    """Host-only tile planning of a batch (dsbt_batch_tiles): forward and
+    inverse tile counts and the forward B-operand lines, without a device."""
+    Ns = [int(t[0]) for t in transforms]
+    lms = [int(t[1]) for t in transforms]
+    cnt = [int(v) for t in transforms for v in t[2]]
+    arr = lambda v: (ctypes.c_int * len(v))(*v)
+    f, i, sl = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check(load().dsbt_batch_tiles(len(Ns), arr(Ns), arr(lms), arr(cnt), Batch.TILE_ORDERS.index(order),
+                                   int(bn_cap), ctypes.byref(f), ctypes.byref(i), ctypes.byref(sl)),
+           "dsbt_batch_tiles")
+    return {"forward": f.value, "inverse": i.value, "seg_lines": sl.value}
+
 
 class Batch:
     """Uneven transforms sharing one factor set (dsbt_batch_* in include/dsbt.h).

@@ -46,3 +46,30 @@ def test_argument_errors_rejected_on_host():
     assert lib.dsbt_forward_grouped(None, counts, 2, None, None, None, 0, None) == -1
     assert lib.dsbt_workspace_size(None, 1, 2) == 0
     assert lib.dsbt_plan_destroy(None) == 0
+
+
+def test_batch_tile_planning_on_host():
+    """Tile lists of every order and width obey the kernel's rules (checked by
+    the library) for the seeded 64-transform workload and a small uneven batch;
+    packing across transforms never adds tiles, and every order covers the same
+    segments."""
+    from paper_1509_07115_gb300 import dsbt, inputs
+    small = [(N, lm, [2 * l + 1 for l in range(lm + 1)])
+             for N, lm in [(256, 3), (768, 9), (512, 6), (1280, 12), (256, 20), (1024, 2)]]
+    small[1][2][4] = 0
+    big = [(N, lm, [2 * l + 1 for l in range(lm + 1)]) for N, lm in inputs.grouped_workload(0)]
+    for trs in (small, big):
+        real = sum(2 * c * (N // 128) for N, lm, cs in trs for c in cs)   # real lines x row tiles
+        for cap in (128, 192, 256):
+            r = {o: dsbt.batch_tiles(trs, o, cap) for o in dsbt.Batch.TILE_ORDERS}
+            seg = {v["seg_lines"] for v in r.values()}
+            assert len(seg) == 1 and seg.pop() >= real
+            packed, single = r["l-major/packed"], r["l-major/row-interleaved"]
+            assert packed["forward"] <= single["forward"] and packed["inverse"] <= single["inverse"]
+            assert r["transform-major"]["forward"] == single["forward"]
+    import ctypes
+    lib = dsbt.load()
+    one = (ctypes.c_int * 1)
+    assert lib.dsbt_batch_tiles(1, one(256), one(0), one(1), 4, 256, None, None, None) == -1
+    assert lib.dsbt_batch_tiles(1, one(256), one(0), one(1), 0, 100, None, None, None) == -1
+    assert lib.dsbt_batch_tiles(1, one(300), one(0), one(1), 0, 256, None, None, None) == -1
