@@ -14,7 +14,8 @@
 //
 // FFT: Stockham autosort in shared memory for N = 256 q (q = 1..32): radix-16
 // stages (16 values per thread in registers, a 4 x 4 register DFT), one
-// radix-2/4/8 stage, then one stage per odd prime factor of q (3..31), with
+// radix-2/4/8 stage, then one direct radix-Q stage for the odd part Q of q
+// (kernels are instantiated per Q), with
 // N/16 threads per line and several lines per CTA when N/16 < 256.  Shared
 // memory is padded by one element every 16, which makes every stage's loads
 // and stores free of bank conflicts.  Twiddles of a radix-16 butterfly come
@@ -148,28 +149,43 @@ __device__ __forceinline__ void stockham_stage(C* s, const C* __restrict__ tw, i
     __syncthreads();
 }
 
-// One Stockham stage of odd prime radix P (3..31), used after the power-of-two
-// stages for N = 256 q.  Butterflies are spread over the line's T threads.
-// Only the twiddled inputs are held across the barrier; after it each output
-// of the P-point DFT is accumulated and stored at once, with the P-th roots of
-// unity read from shared memory (sroot, filled by the caller).
-template <int P, typename C>
+template <typename C> struct Re;
+template <> struct Re<float2> { typedef float T; };
+template <> struct Re<double2> { typedef double T; };
+
+// The last Stockham stage for N = 256 q: radix Q = the odd part of q (3..31,
+// prime or not), a direct DFT per butterfly spread over the line's T threads.
+// Inputs are paired, S_r = y_r + y_{Q-r} and D_r = y_r - y_{Q-r}, so outputs q
+// and Q - q share one pass: X_q = A - iB, X_{Q-q} = A + iB with
+// A = y_0 + sum_r S_r cos(2 pi r q / Q), B = sum_r D_r sin(2 pi r q / Q).
+// Only S, D and y_0 are held across the barrier; the Q-th roots of unity come
+// from shared memory (sroot[m] = exp(-2 pi i m / Q), filled by the caller).
+template <int Q, typename C>
 __device__ __forceinline__ void stockham_stage_odd(C* s, const C* __restrict__ tw, const C* sroot, int N,
                                                    int Ls, int lt, int T) {
-    constexpr int PER = (16 + P - 1) / P;
-    const int nb = N / P;
-    C x[PER][P];
+    typedef typename Re<C>::T R;
+    constexpr int PER = (16 + Q - 1) / Q;
+    constexpr int H = (Q - 1) / 2;
+    const int nb = N / Q;
+    C y0[PER], S[PER][H], D[PER][H];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int j = lt + u * T;
         if (j < nb) {
             const int k = j % Ls;
-            const int b = k * (N / (Ls * P));
+            const int b = k * (N / (Ls * Q));
+            C x[Q];
 #pragma unroll
-            for (int r = 0; r < P; ++r) x[u][r] = s[padi(j + r * nb)];
+            for (int r = 0; r < Q; ++r) x[r] = s[padi(j + r * nb)];
             if (k > 0) {
 #pragma unroll
-                for (int r = 1; r < P; ++r) x[u][r] = cmul(x[u][r], tw[r * b]);
+                for (int r = 1; r < Q; ++r) x[r] = cmul(x[r], tw[r * b]);
+            }
+            y0[u] = x[0];
+#pragma unroll
+            for (int r = 1; r <= H; ++r) {
+                S[u][r - 1] = cadd(x[r], x[Q - r]);
+                D[u][r - 1] = csub(x[r], x[Q - r]);
             }
         }
     }
@@ -179,28 +195,44 @@ __device__ __forceinline__ void stockham_stage_odd(C* s, const C* __restrict__ t
         const int j = lt + u * T;
         if (j < nb) {
             const int k = j % Ls;
-            const int base = (j - k) * P + k;
+            const int base = (j - k) * Q + k;
+            C X0 = y0[u];
+#pragma unroll
+            for (int r = 0; r < H; ++r) X0 = cadd(X0, S[u][r]);
+            s[padi(base)] = X0;
 #pragma unroll 1
-            for (int q = 0; q < P; ++q) {
-                C acc = x[u][0];
+            for (int q = 1; q <= H; ++q) {
+                C A = y0[u], B;
+                B.x = B.y = (R)0;
                 int e = 0;
 #pragma unroll
-                for (int r = 1; r < P; ++r) {
+                for (int r = 1; r <= H; ++r) {
                     e += q;
-                    if (e >= P) e -= P;   // e = r q mod P
-                    acc = cadd(acc, cmul(x[u][r], sroot[e]));
+                    if (e >= Q) e -= Q;   // e = r q mod Q
+                    const C w = sroot[e];
+                    const R c = w.x, sn = -w.y;
+                    A.x += S[u][r - 1].x * c;
+                    A.y += S[u][r - 1].y * c;
+                    B.x += D[u][r - 1].x * sn;
+                    B.y += D[u][r - 1].y * sn;
                 }
-                s[padi(base + q * Ls)] = acc;
+                C Xq, Xm;
+                Xq.x = A.x + B.y;
+                Xq.y = A.y - B.x;
+                Xm.x = A.x - B.y;
+                Xm.y = A.y + B.x;
+                s[padi(base + q * Ls)] = Xq;
+                s[padi(base + (Q - q) * Ls)] = Xm;
             }
         }
     }
     __syncthreads();
 }
 
-// Forward FFT of length N = 256 q: radix-16 stages, one radix-2/4/8 stage for
-// the rest of the power of two and, when MIXED, one stage per odd prime factor
-// of q (3..31; sroot is a 32-entry shared scratch for the roots).
-template <bool MIXED, typename C>
+// Forward FFT of length N = 256 q, q = 2^a Q: radix-16 stages, one radix-2/4/8
+// stage for the rest of the power of two and, when Q > 1, one radix-Q stage
+// (sroot is a 32-entry shared scratch for its roots).
+template <int Q, typename C>
 __device__ __forceinline__ void fft_smem(C* s, const C* __restrict__ tw, C* sroot, int N, int lt, int T) {
     int Ls = 1;
     int rem = N;
@@ -212,29 +244,10 @@ __device__ __forceinline__ void fft_smem(C* s, const C* __restrict__ tw, C* sroo
     if ((rem & 7) == 0) { stockham_stage<8>(s, tw, N, Ls, lt, T); Ls *= 8; rem >>= 3; }
     else if ((rem & 3) == 0) { stockham_stage<4>(s, tw, N, Ls, lt, T); Ls *= 4; rem >>= 2; }
     else if ((rem & 1) == 0) { stockham_stage<2>(s, tw, N, Ls, lt, T); Ls *= 2; rem >>= 1; }
-    if (!MIXED) return;
-    const int primes[10] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
-    for (int i = 0; i < 10 && rem > 1; ++i) {
-        const int p = primes[i];
-        while (rem % p == 0) {
-            for (int m = threadIdx.x; m < p; m += blockDim.x) sroot[m] = tw[m * (N / p)];   // W_p^m
-            __syncthreads();
-            switch (p) {
-                case 3: stockham_stage_odd<3>(s, tw, sroot, N, Ls, lt, T); break;
-                case 5: stockham_stage_odd<5>(s, tw, sroot, N, Ls, lt, T); break;
-                case 7: stockham_stage_odd<7>(s, tw, sroot, N, Ls, lt, T); break;
-                case 11: stockham_stage_odd<11>(s, tw, sroot, N, Ls, lt, T); break;
-                case 13: stockham_stage_odd<13>(s, tw, sroot, N, Ls, lt, T); break;
-                case 17: stockham_stage_odd<17>(s, tw, sroot, N, Ls, lt, T); break;
-                case 19: stockham_stage_odd<19>(s, tw, sroot, N, Ls, lt, T); break;
-                case 23: stockham_stage_odd<23>(s, tw, sroot, N, Ls, lt, T); break;
-                case 29: stockham_stage_odd<29>(s, tw, sroot, N, Ls, lt, T); break;
-                default: stockham_stage_odd<31>(s, tw, sroot, N, Ls, lt, T); break;
-            }
-            Ls *= p;
-            rem /= p;
-        }
-    }
+    if (Q == 1) return;
+    for (int m = threadIdx.x; m < Q; m += blockDim.x) sroot[m] = tw[m * (N / Q)];   // W_Q^m
+    __syncthreads();
+    stockham_stage_odd<(Q > 1 ? Q : 3)>(s, tw, sroot, N, Ls, lt, T);
 }
 
 __device__ __forceinline__ int find_group(const GroupTable& g, int chan) {
@@ -280,7 +293,7 @@ template <> __device__ __forceinline__ void st_pair<double2>(double2* p, double2
 __host__ __device__ inline int lines_per_cta(int N) { return (N / 16 >= 256) ? 1 : 256 / (N / 16); }
 
 // Forward transform.  Output: planar lines.  SPLIT: write the TF32 hi/lo pair.
-template <typename R, bool SPLIT, bool MIXED>
+template <typename R, bool SPLIT, int Q>
 __global__ void __launch_bounds__(512) k_dct_fwd(GroupTable g, int N, int cplx, const R* __restrict__ in,
                                                  R* __restrict__ out0, R* __restrict__ out1,
                                                  const typename Cx<R>::T* __restrict__ tw,
@@ -325,7 +338,7 @@ __global__ void __launch_bounds__(512) k_dct_fwd(GroupTable g, int N, int cplx, 
     }
     __syncthreads();
     __shared__ C sroot[32];
-    fft_smem<MIXED>(s, tw, sroot, N, lt, T);
+    fft_smem<Q>(s, tw, sroot, N, lt, T);
     if (!live) return;
     const R sc1 = (R)sqrt(2.0 / (double)N), sc0 = (R)sqrt(1.0 / (double)N);
     const int line = g.line0[gi] + (cplx ? 2 * local : local);
@@ -372,7 +385,7 @@ __global__ void __launch_bounds__(512) k_dct_fwd(GroupTable g, int N, int cplx, 
 }
 
 // Inverse transform F_l^T: planar lines -> caller layout.
-template <typename R, bool MIXED>
+template <typename R, int Q>
 __global__ void __launch_bounds__(512) k_dct_inv(GroupTable g, int N, int cplx, const R* __restrict__ in,
                                                  R* __restrict__ out, const typename Cx<R>::T* __restrict__ tw,
                                                  const typename Cx<R>::T* __restrict__ post) {
@@ -443,7 +456,7 @@ __global__ void __launch_bounds__(512) k_dct_inv(GroupTable g, int N, int cplx, 
     for (int u = 0; u < 16; ++u) s[padi(lt + u * T)] = vk[u];
     __syncthreads();
     __shared__ C sroot[32];
-    fft_smem<MIXED>(s, tw, sroot, N, lt, T);
+    fft_smem<Q>(s, tw, sroot, N, lt, T);
     if (!live) return;
     const R invN = (R)(1.0 / (double)N);
     for (int j = lt; j < (N >> 1); j += T) {
@@ -481,13 +494,48 @@ static unsigned nblocks(const GroupTable& g, int N) {
     return (unsigned)((nchannels(g) + G - 1) / G);
 }
 
-static bool pow2(int N) { return (N & (N - 1)) == 0; }
+// Odd part Q of q = N / 256; every N = 256 q with q <= 32 has Q in 1..31.
+static int odd_part(int N) {
+    int q = N / 256;
+    while (q > 0 && (q & 1) == 0) q >>= 1;
+    return q;
+}
+
+#define DSBT_DCT_Q_CASES(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21) X(23) X(25) X(27) X(29) X(31)
+
+template <typename R>
+using FwdKernel = void (*)(GroupTable, int, int, const R*, R*, R*, const typename Cx<R>::T*, const typename Cx<R>::T*);
+template <typename R>
+using InvKernel = void (*)(GroupTable, int, int, const R*, R*, const typename Cx<R>::T*, const typename Cx<R>::T*);
+
+template <typename R, bool SPLIT>
+static FwdKernel<R> fwd_kernel(int N) {
+    switch (odd_part(N)) {
+#define DSBT_CASE(q) \
+    case q: return k_dct_fwd<R, SPLIT, q>;
+        DSBT_DCT_Q_CASES(DSBT_CASE)
+#undef DSBT_CASE
+    }
+    return nullptr;
+}
+
+template <typename R>
+static InvKernel<R> inv_kernel(int N) {
+    switch (odd_part(N)) {
+#define DSBT_CASE(q) \
+    case q: return k_dct_inv<R, q>;
+        DSBT_DCT_Q_CASES(DSBT_CASE)
+#undef DSBT_CASE
+    }
+    return nullptr;
+}
 
 int dct_forward_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const double* in,
                     double* out, cudaStream_t st) {
     if (nchannels(g) == 0) return DSBT_OK;
     unsigned th; size_t sm;
-    auto k = pow2(p->N) ? k_dct_fwd<double, false, false> : k_dct_fwd<double, false, true>;
+    FwdKernel<double> k = fwd_kernel<double, false>(p->N);
+    DSBT_CHECK_ARG(k != nullptr, "dct: N=%d not of the form 256 q, q <= 32", p->N);
     int rc = launch_cfg(k, p->N, sizeof(double2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctFwd, st);
@@ -500,7 +548,8 @@ int dct_forward_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const fl
                     float* out_hi, float* out_lo, cudaStream_t st) {
     if (nchannels(g) == 0) return DSBT_OK;
     unsigned th; size_t sm;
-    auto k = pow2(p->N) ? k_dct_fwd<float, true, false> : k_dct_fwd<float, true, true>;
+    FwdKernel<float> k = fwd_kernel<float, true>(p->N);
+    DSBT_CHECK_ARG(k != nullptr, "dct: N=%d not of the form 256 q, q <= 32", p->N);
     int rc = launch_cfg(k, p->N, sizeof(float2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctFwd, st);
@@ -513,7 +562,8 @@ int dct_inverse_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const do
                     double* out, cudaStream_t st) {
     if (nchannels(g) == 0) return DSBT_OK;
     unsigned th; size_t sm;
-    auto k = pow2(p->N) ? k_dct_inv<double, false> : k_dct_inv<double, true>;
+    InvKernel<double> k = inv_kernel<double>(p->N);
+    DSBT_CHECK_ARG(k != nullptr, "dct: N=%d not of the form 256 q, q <= 32", p->N);
     int rc = launch_cfg(k, p->N, sizeof(double2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctInv, st);
@@ -526,7 +576,8 @@ int dct_inverse_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const fl
                     float* out, cudaStream_t st) {
     if (nchannels(g) == 0) return DSBT_OK;
     unsigned th; size_t sm;
-    auto k = pow2(p->N) ? k_dct_inv<float, false> : k_dct_inv<float, true>;
+    InvKernel<float> k = inv_kernel<float>(p->N);
+    DSBT_CHECK_ARG(k != nullptr, "dct: N=%d not of the form 256 q, q <= 32", p->N);
     int rc = launch_cfg(k, p->N, sizeof(float2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctInv, st);

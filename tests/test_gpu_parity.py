@@ -214,10 +214,12 @@ def test_full_size_precision_config_sampled(lib):
     p.close()
 
 
-@pytest.mark.parametrize("N", [768, 1280, 2816, 7936])
+@pytest.mark.parametrize("N", [768, 1280, 1536, 2304, 2816, 3840, 5376, 6400, 6912, 7936])
 def test_non_power_of_two_grids(lib, N):
-    """N = 256 q with odd q (mixed-radix FFT stages 3..31): both precision paths
-    against the oracle on sampled rows, and the round trip on all channels."""
+    """N = 256 q, q not a power of two (radix-16 stages, a radix-2 stage for
+    q = 6, and one radix-Q stage for the odd part Q of q: primes 3, 5, 11, 31
+    and composites 9, 15, 21, 25, 27): both precision paths against the oracle
+    on sampled rows, and the round trip on all channels."""
     lmax = 9
     counts = [1] * (lmax + 1)
     counts[3] = 2
