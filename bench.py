@@ -47,6 +47,11 @@ WORKLOADS = {
     # a smaller case of the same kernels for profiler captures (inputs still > L2)
     "small": dict(N=2048, R_MAX=204.8, L_MAX=31, BATCH=8,
                   desc="profiling case: N=2048, r_max=204.8, l=0..31 all m x batch 8 = 8192 complex64 channels"),
+    # non-power-of-two grids (radix-Q sine/cosine stages) for profiler captures, inputs > L2
+    "grid7936": dict(N=7936, R_MAX=793.6, L_MAX=1, BATCH=800,
+                     desc="profiling case: N=7936 (256 x 31), l=0..1 all m x batch 800 = 3200 complex64 channels"),
+    "grid4352": dict(N=4352, R_MAX=435.2, L_MAX=1, BATCH=1500,
+                     desc="profiling case: N=4352 (256 x 17), l=0..1 all m x batch 1500 = 6000 complex64 channels"),
 }
 TAU = 0.05
 N, R_MAX, L_MAX, BATCH = 4096, 409.6, 63, 8

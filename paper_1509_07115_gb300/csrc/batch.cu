@@ -296,10 +296,29 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                 const uint32_t idesc_all = idesc_tf32(BM, tl.nseg * SEG);
                 for (int c0 = 0; c0 < sp.nsteps && ok;) {
                     const int c1 = sp.chunk_end(c0);
+                    // Inside a tile (c0 > 0: a full-width K block, never a sub-step), the
+                    // first step's correction products go out before the wait for the
+                    // epilogue to drain the main accumulator.
+                    const bool pre = c0 > 0;
+                    if (pre) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
+                        const uint32_t sb_hi = sa + 2 * A_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < BK / 8; ++ks) {
+                            const uint32_t off = ks * 32;
+                            const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa + A_BYTES + off);
+                            const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_hi + B_BYTES + off);
+                            mma_tf32(d_corr, dah, dbl, idesc_all, 1);
+                            mma_tf32(d_corr, dal, dbh, idesc_all, 1);
+                        }
+                    }
                     if (!mbar_wait(main_empty, mphase ^ 1, abort_flag, status)) { ok = false; break; }
                     mphase ^= 1;
                     tc_fence_after();
                     for (int i = c0; i < c1; ++i) {
+                        const bool early = pre && i == c0;   // correction products already issued
                         int s0, s1;
                         step_segments(dir, tl, sp, i, &s0, &s1);
                         // first write of these columns in this chunk (main) / in this tile (correction)
@@ -308,8 +327,10 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                         const uint32_t fresh_corr = (i == 0 || sub) ? 0u : 1u;
                         const uint32_t idesc = sub ? idesc_tf32(BM, (s1 - s0) * SEG) : idesc_all;
                         const uint32_t col0 = (uint32_t)(s0 * SEG);
-                        if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
-                        tc_fence_after();
+                        if (!early) {
+                            if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                            tc_fence_after();
+                        }
                         const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
                         const uint32_t sa_lo = sa + A_BYTES;
                         const uint32_t sb_hi = sa + 2 * A_BYTES + s0 * SEG * 128;
@@ -320,8 +341,10 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                             const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa_lo + off);
                             const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_lo + off);
                             mma_tf32(d_main + col0, dah, dbh, idesc, ks == 0 ? fresh_main : 1u);
-                            mma_tf32(d_corr + col0, dah, dbl, idesc, ks == 0 ? fresh_corr : 1u);
-                            mma_tf32(d_corr + col0, dal, dbh, idesc, 1);
+                            if (!early) {
+                                mma_tf32(d_corr + col0, dah, dbl, idesc, ks == 0 ? fresh_corr : 1u);
+                                mma_tf32(d_corr + col0, dal, dbh, idesc, 1);
+                            }
                         }
                         mma_commit(&empty[stage]);
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }

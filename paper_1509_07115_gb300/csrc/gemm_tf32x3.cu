@@ -250,16 +250,39 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
                 const int nkb = kr.count();
                 uint32_t acc_corr = 0;
                 for (int c0 = 0; c0 < nkb && ok; c0 += KC) {
+                    const int c1 = min(nkb, c0 + KC);
+                    // Inside a tile, the first K block's correction products (which do
+                    // not touch the main accumulator) go out before the wait for the
+                    // epilogue to drain the main accumulator, keeping the tensor pipe
+                    // busy during the drain.  At a tile start the epilogue may still be
+                    // reading the previous tile's correction sum, so nothing goes early.
+                    const bool pre = c0 > 0;
+                    if (pre) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
+                        const uint32_t sb_hi = sa + 2 * A_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < BK / 8; ++ks) {
+                            const uint32_t off = ks * 32;
+                            const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa + A_BYTES + off);
+                            const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_hi + B_BYTES + off);
+                            mma_tf32(d_corr, dah, dbl, idesc, 1);
+                            mma_tf32(d_corr, dal, dbh, idesc, 1);
+                        }
+                    }
                     // the epilogue must have drained the previous chunk (and, at a
                     // tile start, read the previous tile's correction sum)
                     if (!mbar_wait(main_empty, mphase ^ 1, abort_flag, status)) { ok = false; break; }
                     mphase ^= 1;
                     tc_fence_after();
                     uint32_t acc_main = 0;
-                    const int c1 = min(nkb, c0 + KC);
                     for (int i = c0; i < c1; ++i) {
-                        if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
-                        tc_fence_after();
+                        const bool early = pre && i == c0;   // correction products already issued
+                        if (!early) {
+                            if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                            tc_fence_after();
+                        }
                         const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
                         const uint32_t sa_lo = sa + A_BYTES;
                         const uint32_t sb_hi = sa + 2 * A_BYTES;
@@ -270,8 +293,10 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
                             const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa_lo + off);
                             const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_lo + off);
                             mma_tf32(d_main, dah, dbh, idesc, acc_main);
-                            mma_tf32(d_corr, dah, dbl, idesc, acc_corr);
-                            mma_tf32(d_corr, dal, dbh, idesc, 1);
+                            if (!early) {
+                                mma_tf32(d_corr, dah, dbl, idesc, acc_corr);
+                                mma_tf32(d_corr, dal, dbh, idesc, 1);
+                            }
                             acc_main = 1;
                             acc_corr = 1;
                         }
