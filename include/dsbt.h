@@ -164,6 +164,32 @@ DSBT_API int dsbt_forward_grouped_noalloc(const dsbt_plan* plan, const int* coun
                                           const void* in, void* out, void* stream);
 
 /*
+ * Grouped transforms of HOST-resident channels (same layouts and results as
+ * dsbt_forward_grouped / dsbt_inverse_grouped / dsbt_kinetic_grouped, which
+ * see): the channels are cut into nchunks contiguous ranges (0 = 8; clamped to
+ * the channel count) and streamed through the GPU so that the host-to-device
+ * copy of one chunk, the transform of the previous one and the device-to-host
+ * copy of the one before overlap (two internal streams plus `stream`).  host_in
+ * and host_out should be pinned (cudaHostAlloc / cudaHostRegister): pageable
+ * memory gives the same results without the overlap.  The workspace is a
+ * DEVICE buffer of dsbt_host_workspace_size bytes (two input and two output
+ * slots of one chunk plus the transform workspace of one chunk).  Asynchronous:
+ * work on `stream` issued later runs after host_out is written; the caller
+ * synchronises `stream` before reading host_out.  Errors as the device calls,
+ * checked before any copy is issued.
+ */
+DSBT_API size_t dsbt_host_workspace_size(const dsbt_plan* plan, const int* counts, int dtype, int nchunks);
+DSBT_API int dsbt_forward_grouped_host(const dsbt_plan* plan, const int* counts, int dtype, const void* host_in,
+                                       void* host_out, int nchunks, void* workspace, size_t workspace_bytes,
+                                       void* stream);
+DSBT_API int dsbt_inverse_grouped_host(const dsbt_plan* plan, const int* counts, int dtype, const void* host_in,
+                                       void* host_out, int nchunks, void* workspace, size_t workspace_bytes,
+                                       void* stream);
+DSBT_API int dsbt_kinetic_grouped_host(const dsbt_plan* plan, const int* counts, int dtype, double tau,
+                                       const void* host_in, void* host_out, int nchunks, void* workspace,
+                                       size_t workspace_bytes, void* stream);
+
+/*
  * Read the plan's device status word (synchronous: waits for the device).
  * 0 = OK; 1 = a device-side wait in a tensor-core contraction gave up after its
  * iteration limit (the kernel then skipped its remaining work).  reset != 0

@@ -273,6 +273,13 @@ int forward_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtyp
     return grouped_call(0, p, counts, dtype, 0.0, in, out, scratch, scratch_bytes, st);
 }
 
+// Grouped forward (which = 0), inverse (1) or kinetic step (2) on device
+// buffers with a caller-supplied workspace (the host-streamed entry points).
+int grouped_device_call(int which, const dsbt_plan* p, const int* counts, int dtype, double tau,
+                        const void* in, void* out, void* ws, size_t ws_b, cudaStream_t st) {
+    return grouped_call(which, p, counts, dtype, tau, in, out, ws, ws_b, st);
+}
+
 // Grouped kinetic step with a scratch buffer supplied by the caller of this
 // function (the TDSE propagator's inner call).
 int kinetic_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtype, double tau,

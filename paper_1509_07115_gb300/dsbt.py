@@ -51,6 +51,11 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         for name in ("dsbt_forward_grouped", "dsbt_inverse_grouped"):
             getattr(lib, name).argtypes = [vp, _c_int_p, i, vp, vp, vp, sz, vp]
         lib.dsbt_kinetic_grouped.argtypes = [vp, _c_int_p, i, d, vp, vp, vp, sz, vp]
+        lib.dsbt_host_workspace_size.restype = sz
+        lib.dsbt_host_workspace_size.argtypes = [vp, _c_int_p, i, i]
+        for name in ("dsbt_forward_grouped_host", "dsbt_inverse_grouped_host"):
+            getattr(lib, name).argtypes = [vp, _c_int_p, i, vp, vp, i, vp, sz, vp]
+        lib.dsbt_kinetic_grouped_host.argtypes = [vp, _c_int_p, i, d, vp, vp, i, vp, sz, vp]
         lib.dsbt_device_status.argtypes = [vp, i, _c_int_p]
         lib.dsbt_last_error.restype = ctypes.c_char_p
         lib.dsbt_launch_count.restype = ctypes.c_longlong
@@ -213,6 +218,44 @@ class Plan:
     def kinetic_grouped(self, counts, x, tau: float, out=None, workspace=None) -> torch.Tensor:
         """F^T T^T exp(-i k~^2 tau / 2) T F x per l group (dsbt_kinetic_grouped)."""
         return self._grouped("dsbt_kinetic_grouped", counts, x, out, workspace, tau=tau)
+
+    # ------------------------------------------- host-resident channels, streamed
+    def host_workspace(self, counts, dtype: torch.dtype, chunks: int = 0) -> torch.Tensor:
+        arr, _ = self._counts(counts)
+        nb = int(load().dsbt_host_workspace_size(self._h, arr, DTYPES[dtype], int(chunks)))
+        if nb == 0:
+            raise DSBTError("dsbt_host_workspace_size failed: " + (load().dsbt_last_error() or b"").decode())
+        return torch.empty(nb, dtype=torch.uint8, device=torch.cuda.current_device())
+
+    def _grouped_host(self, name, counts, x, out, chunks, workspace, tau=None):
+        if x.is_cuda or x.dtype not in DTYPES or not x.is_contiguous() or x.shape[-1] != self.N:
+            raise ValueError("input must be a contiguous CPU tensor (pinned for overlap) with last axis N")
+        arr, total = self._counts(counts)
+        if total * self.N != x.numel():
+            raise ValueError("sum(counts) * N must equal the number of input elements")
+        if out is None:
+            out = torch.empty_like(x, pin_memory=x.is_pinned())
+        elif out.is_cuda or out.shape != x.shape or out.dtype != x.dtype or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CPU tensor matching the input")
+        ws = workspace if workspace is not None else self.host_workspace(counts, x.dtype, chunks)
+        args = [self._h, arr, DTYPES[x.dtype]]
+        if tau is not None:
+            args.append(float(tau))
+        args += [ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(chunks),
+                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()]
+        _check(getattr(load(), name)(*args), name)
+        return out
+
+    def forward_grouped_host(self, counts, x, out=None, chunks: int = 0, workspace=None) -> torch.Tensor:
+        """dsbt_forward_grouped on host tensors, streamed in chunks (asynchronous on
+        the current stream: synchronise before reading `out`)."""
+        return self._grouped_host("dsbt_forward_grouped_host", counts, x, out, chunks, workspace)
+
+    def inverse_grouped_host(self, counts, b, out=None, chunks: int = 0, workspace=None) -> torch.Tensor:
+        return self._grouped_host("dsbt_inverse_grouped_host", counts, b, out, chunks, workspace)
+
+    def kinetic_grouped_host(self, counts, x, tau: float, out=None, chunks: int = 0, workspace=None):
+        return self._grouped_host("dsbt_kinetic_grouped_host", counts, x, out, chunks, workspace, tau=tau)
 
     def device_status(self, reset: bool = True) -> int:
         s = ctypes.c_int()
