@@ -80,19 +80,22 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def source_hash(path):
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+def source_hash(paths):
+    m = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            m.update(fh.read())
+    return m.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_file):
+def ncu_traffic():
     """DRAM bytes per launch of the contraction from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+    if it was taken on the current kernel sources (else None)."""
     prof = os.path.join(ROOT, "profiles", "contract_tf32x3_precision_form.json")
     try:
         with open(prof) as fh:
             d = json.load(fh)
-        if d.get("source_sha256_16") != source_hash(kernel_file):
+        if d.get("source_sha256_16") != source_hash(d["source_files"]):
             return None
         return d.get("dram_bytes_per_launch_full_size")
     except Exception:
@@ -502,9 +505,9 @@ def main():
     flop_per_launch = FLOP_PER_CHANNEL * nchan
     achieved = flop_per_launch / (avg_ms * 1e-3) / 1e12
     peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
-    kernel_file = os.path.join(ROOT, "paper_1509_07115_gb300", "csrc", "gemm_tf32x3.cu")
+    traffic = ncu_traffic() if args.workload == "precision" else None
     roofline = {"bound": "tensor", "kernel": "contract_tf32x3", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(kernel_file),
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{src}: bf16 sustained x {TF32_OVER_BF16:.3f} (nominal tf32/bf16)",
                 "flop_per_launch": flop_per_launch, "avg_launch_ms": avg_ms,
                 "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
