@@ -177,7 +177,7 @@ def bad_clocks(c):
 
 # ---------------------------------------------------------------- CPU oracle leg
 
-def oracle_sample(nchan=4, ls=(1, 2), seed=11):
+def oracle_sample(nchan=16, ls=(1, 2), seed=11):
     """Times the FP64 oracle as it stands (single thread) on a bounded sample:
     for each l in ls, nchan channels of the workload's Gaussian-sum inputs;
     factor build (binary128 DLOP rows, explicit F_l) timed separately from the
@@ -574,7 +574,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         ntr, t_x, t_b = oracle_sample()
         line["cpu_baseline"] = {"value": ntr / t_x, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": (f"{ntr} channel-transforms (4 complex channels each of l=1 and l=2, "
+                                "sample": (f"{ntr} channel-transforms (16 complex channels each of l=1 and l=2, "
                                            f"N=4096, kinetic round trip by naive O(N^2) sums, single thread); "
                                            f"factor build {t_b:.1f} s excluded")}
     if rank == 0:
