@@ -154,76 +154,64 @@ template <> struct Re<float2> { typedef float T; };
 template <> struct Re<double2> { typedef double T; };
 
 // The last Stockham stage for N = 256 q: radix Q = the odd part of q (3..31,
-// prime or not), a direct DFT per butterfly spread over the line's T threads.
+// prime or not), a direct DFT per butterfly.  In the last stage (Ls = N/Q)
+// butterfly j reads and writes the same Q elements j + r N/Q, so each thread
+// finishes one butterfly before the next without a barrier in between.
 // Inputs are paired, S_r = y_r + y_{Q-r} and D_r = y_r - y_{Q-r}, so outputs q
 // and Q - q share one pass: X_q = A - iB, X_{Q-q} = A + iB with
 // A = y_0 + sum_r S_r cos(2 pi r q / Q), B = sum_r D_r sin(2 pi r q / Q).
-// Only S, D and y_0 are held across the barrier; the Q-th roots of unity come
-// from shared memory (sroot[m] = exp(-2 pi i m / Q), filled by the caller).
+// The Q-th roots of unity come from shared memory (sroot[m] = exp(-2 pi i m / Q),
+// filled by the caller).
 template <int Q, typename C>
-__device__ __forceinline__ void stockham_stage_odd(C* s, const C* __restrict__ tw, const C* sroot, int N,
-                                                   int Ls, int lt, int T) {
+__device__ __forceinline__ void stockham_last_odd(C* s, const C* __restrict__ tw, const C* sroot, int N,
+                                                  int lt, int T) {
     typedef typename Re<C>::T R;
-    constexpr int PER = (16 + Q - 1) / Q;
     constexpr int H = (Q - 1) / 2;
     const int nb = N / Q;
-    C y0[PER], S[PER][H], D[PER][H];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int j = lt + u * T;
-        if (j < nb) {
-            const int k = j % Ls;
-            const int b = k * (N / (Ls * Q));
+    for (int j = lt; j < nb; j += T) {
+        C y0, S[H], D[H];
+        {
             C x[Q];
 #pragma unroll
             for (int r = 0; r < Q; ++r) x[r] = s[padi(j + r * nb)];
-            if (k > 0) {
+            if (j > 0) {
 #pragma unroll
-                for (int r = 1; r < Q; ++r) x[r] = cmul(x[r], tw[r * b]);
+                for (int r = 1; r < Q; ++r) x[r] = cmul(x[r], tw[r * j]);
             }
-            y0[u] = x[0];
+            y0 = x[0];
 #pragma unroll
             for (int r = 1; r <= H; ++r) {
-                S[u][r - 1] = cadd(x[r], x[Q - r]);
-                D[u][r - 1] = csub(x[r], x[Q - r]);
+                S[r - 1] = cadd(x[r], x[Q - r]);
+                D[r - 1] = csub(x[r], x[Q - r]);
             }
         }
-    }
-    __syncthreads();
+        C X0 = y0;
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int j = lt + u * T;
-        if (j < nb) {
-            const int k = j % Ls;
-            const int base = (j - k) * Q + k;
-            C X0 = y0[u];
-#pragma unroll
-            for (int r = 0; r < H; ++r) X0 = cadd(X0, S[u][r]);
-            s[padi(base)] = X0;
+        for (int r = 0; r < H; ++r) X0 = cadd(X0, S[r]);
+        s[padi(j)] = X0;
 #pragma unroll 1
-            for (int q = 1; q <= H; ++q) {
-                C A = y0[u], B;
-                B.x = B.y = (R)0;
-                int e = 0;
+        for (int q = 1; q <= H; ++q) {
+            C A = y0, B;
+            B.x = B.y = (R)0;
+            int e = 0;
 #pragma unroll
-                for (int r = 1; r <= H; ++r) {
-                    e += q;
-                    if (e >= Q) e -= Q;   // e = r q mod Q
-                    const C w = sroot[e];
-                    const R c = w.x, sn = -w.y;
-                    A.x += S[u][r - 1].x * c;
-                    A.y += S[u][r - 1].y * c;
-                    B.x += D[u][r - 1].x * sn;
-                    B.y += D[u][r - 1].y * sn;
-                }
-                C Xq, Xm;
-                Xq.x = A.x + B.y;
-                Xq.y = A.y - B.x;
-                Xm.x = A.x - B.y;
-                Xm.y = A.y + B.x;
-                s[padi(base + q * Ls)] = Xq;
-                s[padi(base + (Q - q) * Ls)] = Xm;
+            for (int r = 1; r <= H; ++r) {
+                e += q;
+                if (e >= Q) e -= Q;   // e = r q mod Q
+                const C w = sroot[e];
+                const R c = w.x, sn = -w.y;
+                A.x += S[r - 1].x * c;
+                A.y += S[r - 1].y * c;
+                B.x += D[r - 1].x * sn;
+                B.y += D[r - 1].y * sn;
             }
+            C Xq, Xm;
+            Xq.x = A.x + B.y;
+            Xq.y = A.y - B.x;
+            Xm.x = A.x - B.y;
+            Xm.y = A.y + B.x;
+            s[padi(j + q * nb)] = Xq;
+            s[padi(j + (Q - q) * nb)] = Xm;
         }
     }
     __syncthreads();
@@ -247,7 +235,7 @@ __device__ __forceinline__ void fft_smem(C* s, const C* __restrict__ tw, C* sroo
     if (Q == 1) return;
     for (int m = threadIdx.x; m < Q; m += blockDim.x) sroot[m] = tw[m * (N / Q)];   // W_Q^m
     __syncthreads();
-    stockham_stage_odd<(Q > 1 ? Q : 3)>(s, tw, sroot, N, Ls, lt, T);
+    stockham_last_odd<(Q > 1 ? Q : 3)>(s, tw, sroot, N, lt, T);   // Ls = N / Q here
 }
 
 __device__ __forceinline__ int find_group(const GroupTable& g, int chan) {
@@ -293,8 +281,10 @@ template <> __device__ __forceinline__ void st_pair<double2>(double2* p, double2
 __host__ __device__ inline int lines_per_cta(int N) { return (N / 16 >= 256) ? 1 : 256 / (N / 16); }
 
 // Forward transform.  Output: planar lines.  SPLIT: write the TF32 hi/lo pair.
+// FP32 kernels: at most 64 registers, so two CTAs of
+// up to 512 threads (one line of N/16 threads each) fit on an SM.
 template <typename R, bool SPLIT, int Q>
-__global__ void __launch_bounds__(512) k_dct_fwd(GroupTable g, int N, int cplx, const R* __restrict__ in,
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTable g, int N, int cplx, const R* __restrict__ in,
                                                  R* __restrict__ out0, R* __restrict__ out1,
                                                  const typename Cx<R>::T* __restrict__ tw,
                                                  const typename Cx<R>::T* __restrict__ post) {
@@ -386,7 +376,7 @@ __global__ void __launch_bounds__(512) k_dct_fwd(GroupTable g, int N, int cplx, 
 
 // Inverse transform F_l^T: planar lines -> caller layout.
 template <typename R, int Q>
-__global__ void __launch_bounds__(512) k_dct_inv(GroupTable g, int N, int cplx, const R* __restrict__ in,
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_inv(GroupTable g, int N, int cplx, const R* __restrict__ in,
                                                  R* __restrict__ out, const typename Cx<R>::T* __restrict__ tw,
                                                  const typename Cx<R>::T* __restrict__ post) {
     typedef typename Cx<R>::T C;
