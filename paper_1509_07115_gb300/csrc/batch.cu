@@ -165,6 +165,13 @@ struct __align__(64) BMaps {
     CUtensorMap m[4];
 };
 
+// Per-transform B maps: a_hi, a_lo, b_hi, b_lo with boxes of 32, 64 and 128
+// lines (index 4 * log2(lines / 32) + buffer), so runs of 2 or 4 contiguous
+// segments of one group move with one TMA load per buffer.
+struct __align__(64) TMaps {
+    CUtensorMap m[12];
+};
+
 enum : int { kModeUserC64 = 0, kModeSplit = 1, kModePlanar = 2 };
 
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -172,7 +179,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                  const __grid_constant__ CUtensorMap tF96_hi, const __grid_constant__ CUtensorMap tF96_lo,
                  const __grid_constant__ CUtensorMap tI_hi, const __grid_constant__ CUtensorMap tI_lo,
                  const PTile* __restrict__ tiles, int total, const BGroup* __restrict__ groups,
-                 const BTrans* __restrict__ trans, const BMaps* __restrict__ tmaps, const BMaps* __restrict__ cmaps,
+                 const BTrans* __restrict__ trans, const TMaps* __restrict__ tmaps, const BMaps* __restrict__ cmaps,
                  int Nmax, int dir, int mode, float2* __restrict__ out_user, unsigned* status, int* sched) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -213,8 +220,9 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer + tile scheduler
-        __shared__ const CUtensorMap* mseg[SEG_MAX];   // per segment: B tensor map and first line
-        __shared__ int yseg[SEG_MAX];
+        __shared__ const CUtensorMap* mseg[SEG_MAX];   // per segment: 32-line B map, first line and
+        __shared__ int yseg[SEG_MAX];                   // the contiguous run of segments it starts
+        __shared__ int rseg[SEG_MAX];
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
@@ -237,6 +245,9 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                     mseg[s] = &tmaps[G.t].m[dir > 0 ? 0 : 2];   // hi map; lo map follows it
                     yseg[s] = G.bline0 + tl.c[s];
                 }
+                for (int s = nseg - 1; s >= 0; --s)   // segments s, s+1, ... of one group, contiguous
+                    rseg[s] = (s + 1 < nseg && tl.g[s + 1] == tl.g[s] && tl.c[s + 1] == tl.c[s] + SEG)
+                                  ? rseg[s + 1] + 1 : 1;
                 for (int i = 0; i < sp.nsteps; ++i) {
                     const int kb = sp.kb(i);
                     int s0, s1;
@@ -266,10 +277,14 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                             tma_load_2d(sb + A_BYTES, &tI_lo, &full[stage], kb * BK, l * Nmax + rt * BM);
                         }
                     }
-                    for (int s = s0; s < s1; ++s) {
-                        tma_load_2d(sb + 2 * A_BYTES + s * SEG * 128, mseg[s], &full[stage], kb * BK, yseg[s]);
-                        tma_load_2d(sb + 2 * A_BYTES + B_BYTES + s * SEG * 128, mseg[s] + 1, &full[stage], kb * BK,
+                    for (int s = s0; s < s1;) {
+                        const int run = min(rseg[s], s1 - s);
+                        const int len = run >= 4 ? 4 : (run >= 2 ? 2 : 1);   // segments in this load
+                        const CUtensorMap* m = mseg[s] + (len == 4 ? 8 : (len == 2 ? 4 : 0));
+                        tma_load_2d(sb + 2 * A_BYTES + s * SEG * 128, m, &full[stage], kb * BK, yseg[s]);
+                        tma_load_2d(sb + 2 * A_BYTES + B_BYTES + s * SEG * 128, m + 1, &full[stage], kb * BK,
                                     yseg[s]);
+                        s += len;
                     }
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
@@ -515,7 +530,7 @@ struct dsbt_batch {
     size_t ws_bytes = 0;
     std::vector<dsbt::BTrans> trans_h;
     dsbt::BTrans* trans_d = nullptr;
-    dsbt::BMaps* tmaps_d = nullptr;
+    dsbt::TMaps* tmaps_d = nullptr;
     dsbt::BMaps* cmaps_d = nullptr;
     std::vector<dsbt::BGroup> groups_h;
     dsbt::BGroup* groups_d = nullptr;
@@ -988,7 +1003,7 @@ extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, con
     }
     b->ws_bytes = wbytes;
     cudaMemsetAsync(b->ws, 0, wbytes, st);
-    std::vector<BMaps> tm(ntrans);
+    std::vector<TMaps> tm(ntrans);
     for (int t = 0; t < ntrans; ++t) {
         BTrans T;
         const size_t lb = a256((size_t)b->nlines[t] * N[t] * sizeof(float));
@@ -1002,10 +1017,13 @@ extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, con
         T.nlines = b->nlines[t];
         b->trans_h.push_back(T);
         const uint64_t rows = (uint64_t)std::max(1, b->nlines[t]);
-        rc = encode_tmap_f32_sw128(&tm[t].m[0], T.a_hi, rows, N[t], SEG, 32);
-        if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[1], T.a_lo, rows, N[t], SEG, 32);
-        if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[2], T.b_hi, rows, N[t], SEG, 32);
-        if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[3], T.b_lo, rows, N[t], SEG, 32);
+        for (int k = 0; k < 3 && !rc; ++k) {
+            const int box = SEG << k;
+            rc = encode_tmap_f32_sw128(&tm[t].m[4 * k + 0], T.a_hi, rows, N[t], box, 32);
+            if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[4 * k + 1], T.a_lo, rows, N[t], box, 32);
+            if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[4 * k + 2], T.b_hi, rows, N[t], box, 32);
+            if (!rc) rc = encode_tmap_f32_sw128(&tm[t].m[4 * k + 3], T.b_lo, rows, N[t], box, 32);
+        }
         if (rc) { batch_free(b); return rc; }
         // sine/cosine group table of this transform (channels l-major)
         GroupTable g;
@@ -1026,10 +1044,10 @@ extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, con
         b->gtab.push_back(g);
     }
     bool ok = cudaMalloc((void**)&b->trans_d, ntrans * sizeof(BTrans)) == cudaSuccess &&
-              cudaMalloc((void**)&b->tmaps_d, ntrans * sizeof(BMaps)) == cudaSuccess &&
+              cudaMalloc((void**)&b->tmaps_d, ntrans * sizeof(TMaps)) == cudaSuccess &&
               cudaMalloc((void**)&b->cmaps_d, ND * sizeof(BMaps)) == cudaSuccess;
     ok = ok && cudaMemcpy(b->trans_d, b->trans_h.data(), ntrans * sizeof(BTrans), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(b->tmaps_d, tm.data(), ntrans * sizeof(BMaps), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->tmaps_d, tm.data(), ntrans * sizeof(TMaps), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(b->cmaps_d, cm.data(), ND * sizeof(BMaps), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
