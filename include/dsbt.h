@@ -61,9 +61,11 @@ extern "C" {
 #define DSBT_ERR_TIMEOUT (-5)     /* a device-side wait gave up (see dsbt_device_status) */
 #define DSBT_ERR_UNSUPPORTED (-6) /* path not built into this plan / size unsupported */
 
-/* plan flags: which factor copies to build (at least one) */
+/* plan flags: which factor copies to build (at least one of the first two) */
 #define DSBT_PLAN_FP64 1   /* FP64 T_l (for DSBT_F64 / DSBT_C128 calls)            */
 #define DSBT_PLAN_TF32X3 2 /* split-TF32 T_l and T_l^T (for DSBT_F32 / DSBT_C64)  */
+#define DSBT_PLAN_KCORR 4  /* kinetic phase with the corrected momenta k_nl (Sec. 3,
+                              Eq. (kcorr)) instead of k~_n (see dsbt_plan_get_k) */
 
 /* element types of the caller's arrays */
 #define DSBT_F64 1  /* real double                 */
@@ -101,6 +103,18 @@ DSBT_API int dsbt_plan_info(const dsbt_plan* plan, int* N, int* l_max, int* flag
  * (N*N doubles).  For inspection and tests.
  */
 DSBT_API int dsbt_plan_get_T(const dsbt_plan* plan, int l, double* dst, void* stream);
+
+/*
+ * Copy the N momenta that the kinetic phase of this plan uses for angular
+ * momentum l (storage index s = n - p_l) into the HOST array host_out.
+ * Without DSBT_PLAN_KCORR: k~_n = n dk (n = 0 of odd l -> N dk, Eq. (65)).
+ * With it (Sec. 3, Eq. (kcorr)): on the regular rows n >= n0_l,
+ * k_nl = x_m / r_max with x_m the m-th positive zero (m = n - floor(l/2)) of
+ * chi_l(x) = x j_l(x) for even l, of chi_l'(x) for odd l; the completion rows
+ * keep k~_n.  The table is computed on the host in FP64 at plan creation
+ * (relative accuracy ~1e-16).  Synchronous.
+ */
+DSBT_API int dsbt_plan_get_k(const dsbt_plan* plan, int l, double* host_out);
 
 /*
  * Bytes of device workspace needed by a call on `total_channels` channels of
@@ -216,6 +230,11 @@ typedef struct dsbt_tdse dsbt_tdse;
 DSBT_API int dsbt_tdse_create(const dsbt_plan* plan, int L, double tau, double Z, double a2,
                               dsbt_tdse** out);
 DSBT_API int dsbt_tdse_destroy(dsbt_tdse* tdse);
+
+/* Replace the radial potential V(r_i) (the soft-Coulomb default of
+ * dsbt_tdse_create) with the caller's n = N HOST values on the midpoint grid
+ * r_i = (i + 1/2) dr, i = 0..N-1.  Synchronous. */
+DSBT_API int dsbt_tdse_set_potential(dsbt_tdse* tdse, const double* V, int n);
 
 /* Host copies of the angular grid: eta[L], w[L] and P[L*L] (any may be NULL). */
 DSBT_API int dsbt_tdse_angular(const dsbt_tdse* tdse, double* eta, double* w, double* P);

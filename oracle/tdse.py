@@ -34,17 +34,26 @@ def angular(L: int):
 
 
 class Model:
-    def __init__(self, N: int, r_max: float, L: int, tau: float, Z: float = 1.0, a2: float = 0.5):
+    """kcorr=True: the kinetic energy of Eq. (76) uses the corrected momenta
+    k_nl of Sec. 3 (oracle/kcorr.py) instead of k~_n.  V: optional radial
+    potential on the grid (default the soft Coulomb -Z / sqrt(r^2 + a2))."""
+
+    def __init__(self, N: int, r_max: float, L: int, tau: float, Z: float = 1.0, a2: float = 0.5,
+                 kcorr: bool = False, V=None):
         self.N, self.r_max, self.L, self.tau = N, r_max, L, tau
         self.dr = r_max / N
         self.r = (np.arange(1, N + 1) - 0.5) * self.dr
-        self.V = -Z / np.sqrt(self.r ** 2 + a2)
+        self.V = -Z / np.sqrt(self.r ** 2 + a2) if V is None else np.asarray(V, dtype=np.float64)
         self.eta, self.w, self.P = angular(L)
         self.F = [oracle.F_matrix(N, l) for l in range(L)]
         self.T = [oracle.T_matrix(N, l) for l in range(L)]
         dk = np.pi / r_max
         self.kt = []
         for l in range(L):
+            if kcorr:
+                from oracle import kcorr as kc
+                self.kt.append(kc.k_table(N, r_max, l))
+                continue
             n = np.arange(N) + oracle.p_of(l)
             self.kt.append(np.where(n == 0, N, n) * dk)   # Eq. (65): n = 0 -> k~_N
 

@@ -41,18 +41,30 @@ __global__ void k_split_lines_c(const float2* __restrict__ in, float* __restrict
 // exp(-i k~_n^2 tau / 2) on the unified momentum grid (Eq. (65)): storage index
 // k of parity class par (0: even l, n = k + 1; 1: odd l, n = k) maps to
 // k~ = n dk, except the odd-l coefficient n = 0, which takes k~_N = N dk.
-__global__ void k_phase(double2* ph64, float2* ph32, int N, double dk, double tau) {
+// Kinetic phase table exp(-i k^2 tau / 2): rows = 2 by parity of l with
+// k = k~_n = n dk (n = 0 -> N dk) when knl is NULL, else rows = l_max + 1 with
+// the plan's corrected momenta knl[l][s].
+__global__ void k_phase(double2* ph64, float2* ph32, int N, double dk, double tau, const double* __restrict__ knl,
+                        int rows) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 2 * N) return;
-    const int par = i / N, k = i % N;
-    int n = (par == 0) ? k + 1 : k;
-    if (n == 0) n = N;
-    const double kt = n * dk;
+    if (i >= rows * N) return;
+    double kt;
+    if (knl) {
+        kt = knl[i];
+    } else {
+        const int par = i / N, k = i % N;
+        int n = (par == 0) ? k + 1 : k;
+        if (n == 0) n = N;
+        kt = n * dk;
+    }
     double s, c;
     sincos(-0.5 * kt * kt * tau, &s, &c);
     if (ph64) ph64[i] = make_double2(c, s);
     if (ph32) ph32[i] = make_float2((float)c, (float)s);
 }
+
+// Rows of the phase table (see k_phase).
+inline int phase_rows(const dsbt_plan* p) { return p->knl ? p->l_max + 1 : 2; }
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -75,14 +87,18 @@ size_t lines_of(int total_channels, int dtype) {
     return (size_t)total_channels * (is_complex(dtype) ? 2 : 1);
 }
 
-size_t ws_bytes(int N, int total_channels, int dtype) {
+size_t ws_bytes(const dsbt_plan* p, int total_channels, int dtype) {
     const size_t R = lines_of(total_channels, dtype);
+    const int N = p->N;
+    const size_t PR = (size_t)phase_rows(p) * N;
     if (is_fp64(dtype))
-        return align256(R * N * sizeof(double)) * 2 + align256(2 * (size_t)N * sizeof(double2)) + 256;
-    return align256(R * N * sizeof(float)) * 4 + align256(2 * (size_t)N * sizeof(float2)) + 256 + 256;
+        return align256(R * N * sizeof(double)) * 2 + align256(PR * sizeof(double2)) + 256;
+    return align256(R * N * sizeof(float)) * 4 + align256(PR * sizeof(float2)) + 256 + 256;
 }
 
-Workspace carve(void* base, int N, int total_channels, int dtype) {
+Workspace carve(const dsbt_plan* pl, void* base, int total_channels, int dtype) {
+    const int N = pl->N;
+    const size_t PR = (size_t)phase_rows(pl) * N;
     Workspace w{};
     const size_t R = lines_of(total_channels, dtype);
     unsigned char* p = (unsigned char*)(((uintptr_t)base + 255) & ~(uintptr_t)255);
@@ -99,7 +115,7 @@ Workspace carve(void* base, int N, int total_channels, int dtype) {
         w.lo_b = (float*)(p + 3 * b);
         w.planar = w.hi_a;
         w.ph32 = (float2*)(p + 4 * b);
-        w.sched = (int*)(p + 4 * b + align256(2 * (size_t)N * sizeof(float2)));
+        w.sched = (int*)(p + 4 * b + align256(PR * sizeof(float2)));
     }
     return w;
 }
@@ -137,7 +153,7 @@ int check_common(const dsbt_plan* p, int dtype, const void* in, void* out, void*
     DSBT_CHECK_ARG(in != nullptr && out != nullptr, "in/out is NULL");
     DSBT_CHECK_ARG(in != out, "in and out must not alias");
     DSBT_CHECK_ARG(ws != nullptr, "workspace is NULL");
-    const size_t need = ws_bytes(p->N, total_channels, dtype);
+    const size_t need = ws_bytes(p, total_channels, dtype);
     DSBT_CHECK_ARG(ws_b >= need, "workspace too small: %zu < %zu bytes", ws_b, need);
     if (is_fp64(dtype) && !p->T64) {
         set_error("FP64 dtype needs a plan built with DSBT_PLAN_FP64");
@@ -154,7 +170,7 @@ int run_forward(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
                 void* ws, cudaStream_t st) {
     if (g.total_lines == 0) return DSBT_OK;
     const bool cplx = is_complex(dtype);
-    Workspace w = carve(ws, p->N, g.chan0[g.ngroups], dtype);
+    Workspace w = carve(p, ws, g.chan0[g.ngroups], dtype);
     int rc;
     if (is_fp64(dtype)) {
         rc = dct_forward_f64(p, g, cplx, (const double*)in, w.f64a, st);
@@ -171,7 +187,7 @@ int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
                 void* ws, cudaStream_t st) {
     if (g.total_lines == 0) return DSBT_OK;
     const bool cplx = is_complex(dtype);
-    Workspace w = carve(ws, p->N, g.chan0[g.ngroups], dtype);
+    Workspace w = carve(p, ws, g.chan0[g.ngroups], dtype);
     int rc;
     if (is_fp64(dtype)) {
         rc = contract_f64(p, g, -1, (const double*)in, cplx ? 1 : 0, w.f64a, 0, nullptr, st);
@@ -198,13 +214,14 @@ int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
 int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, const void* in, void* out,
                 void* ws, cudaStream_t st) {
     if (g.total_lines == 0) return DSBT_OK;
-    Workspace w = carve(ws, p->N, g.chan0[g.ngroups], dtype);
+    Workspace w = carve(p, ws, g.chan0[g.ngroups], dtype);
     const int N = p->N;
     int rc;
     if (is_fp64(dtype)) {
         {
             ProfScope ps(kKPhase, st);
-            k_phase<<<(2 * N + 255) / 256, 256, 0, st>>>(w.ph64, nullptr, N, p->dk, tau);
+            const int rows = phase_rows(p);
+            k_phase<<<(rows * N + 255) / 256, 256, 0, st>>>(w.ph64, nullptr, N, p->dk, tau, p->knl, rows);
         }
         DSBT_CUDA_TRY(cudaGetLastError());
         rc = dct_forward_f64(p, g, true, (const double*)in, w.f64a, st);
@@ -215,7 +232,8 @@ int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, 
     }
     {
         ProfScope ps(kKPhase, st);
-        k_phase<<<(2 * N + 255) / 256, 256, 0, st>>>(nullptr, w.ph32, N, p->dk, tau);
+        const int rows = phase_rows(p);
+        k_phase<<<(rows * N + 255) / 256, 256, 0, st>>>(nullptr, w.ph32, N, p->dk, tau, p->knl, rows);
     }
     DSBT_CUDA_TRY(cudaGetLastError());
     rc = dct_forward_f32(p, g, true, (const float*)in, w.hi_a, w.lo_a, st);
@@ -294,7 +312,7 @@ using namespace dsbt;
 
 extern "C" size_t dsbt_workspace_size(const dsbt_plan* plan, int total_channels, int dtype) {
     if (!plan || total_channels < 0 || !valid_dtype(dtype)) return 0;
-    return ws_bytes(plan->N, total_channels, dtype);
+    return ws_bytes(plan, total_channels, dtype);
 }
 
 extern "C" int dsbt_forward(const dsbt_plan* plan, int l, int nchan, int dtype, const void* in, void* out,

@@ -62,7 +62,7 @@ __device__ __forceinline__ void k_ranges(int dir, int r0, int rows, int nx, int 
 
 __global__ void __launch_bounds__(256) k_contract64_tile(GroupTable g, const double* __restrict__ T64,
                                                          int N, int dir, Lines in, OutLines out,
-                                                         const double2* __restrict__ phase) {
+                                                         const double2* __restrict__ phase, int per_l) {
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BC + 1];
     const int gi = blockIdx.y;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) k_contract64_tile(GroupTable g, const dou
             __syncthreads();
         }
     }
-    const int par = l & 1;
+    const int par = per_l ? l : (l & 1);   // phase row: per l, or by parity
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int r = r0 + ty * 4 + i;
@@ -158,7 +158,7 @@ template <int NLMAX, bool ICPLX, bool OCPLX>
 __global__ void __launch_bounds__(256) k_contract64_rows(GroupTable g, const double* __restrict__ A64,
                                                          int N, int dir, const double* __restrict__ inb,
                                                          double* __restrict__ outb,
-                                                         const double2* __restrict__ phase) {
+                                                         const double2* __restrict__ phase, int per_l) {
     const int gi = blockIdx.y;
     const int nl = group_lines(g, gi);
     if (nl > kNarrow || nl == 0) return;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_contract64_rows(GroupTable g, const dou
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
     if (lane == 0) {
-        const double2 ph = phase ? phase[(size_t)(l & 1) * N + r] : make_double2(1.0, 0.0);
+        const double2 ph = phase ? phase[(size_t)(per_l ? l : (l & 1)) * N + r] : make_double2(1.0, 0.0);
 #pragma unroll
         for (int j = 0; j < NLMAX; j += 2) {   // compile-time indices keep acc[] in registers
             if (j < nl) {
@@ -236,15 +236,15 @@ __global__ void __launch_bounds__(256) k_contract64_rows(GroupTable g, const dou
 
 template <int NLMAX>
 static void launch_rows(dim3 grid, cudaStream_t st, const GroupTable& g, const double* A, int N, int dir,
-                        const double* in, int in_cplx, double* out, int out_cplx, const double2* phase) {
+                        const double* in, int in_cplx, double* out, int out_cplx, const double2* phase, int per_l) {
     if (in_cplx && out_cplx)
-        k_contract64_rows<NLMAX, true, true><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase);
+        k_contract64_rows<NLMAX, true, true><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase, per_l);
     else if (in_cplx)
-        k_contract64_rows<NLMAX, true, false><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase);
+        k_contract64_rows<NLMAX, true, false><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase, per_l);
     else if (out_cplx)
-        k_contract64_rows<NLMAX, false, true><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase);
+        k_contract64_rows<NLMAX, false, true><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase, per_l);
     else
-        k_contract64_rows<NLMAX, false, false><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase);
+        k_contract64_rows<NLMAX, false, false><<<grid, 256, 0, st>>>(g, A, N, dir, in, out, phase, per_l);
 }
 
 }  // namespace
@@ -260,6 +260,7 @@ int contract_f64(const dsbt_plan* p, const GroupTable& g, int dir, const double*
         return DSBT_ERR_INVALID;
     }
     const int N = p->N;
+    const int per_l = p->knl != nullptr;   // phase table rows per l (corrected momenta) or by parity
     int max_ct = 0, any_wide = 0, any_narrow = 0;
     for (int i = 0; i < g.ngroups; ++i) {
         const int nl = g.line0[i + 1] - g.line0[i];
@@ -276,7 +277,7 @@ int contract_f64(const dsbt_plan* p, const GroupTable& g, int dir, const double*
     if (any_wide) {
         dim3 grid((N / BM) * max_ct, g.ngroups);
         ProfScope ps(kKContract64, st);
-        k_contract64_tile<<<grid, 256, 0, st>>>(g, p->T64, N, dir, li, lo, phase);
+        k_contract64_tile<<<grid, 256, 0, st>>>(g, p->T64, N, dir, li, lo, phase, per_l);
         DSBT_CUDA_TRY(cudaGetLastError());
     }
     if (any_narrow) {
@@ -288,10 +289,10 @@ int contract_f64(const dsbt_plan* p, const GroupTable& g, int dir, const double*
         dim3 grid((N * 32 + 255) / 256, g.ngroups);
         const double* A = dir > 0 ? p->T64 : p->Tt64;
         ProfScope ps(kKContract64, st);
-        if (nlmax <= 1) launch_rows<1>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase);
-        else if (nlmax <= 2) launch_rows<2>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase);
-        else if (nlmax <= 4) launch_rows<4>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase);
-        else launch_rows<8>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase);
+        if (nlmax <= 1) launch_rows<1>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase, per_l);
+        else if (nlmax <= 2) launch_rows<2>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase, per_l);
+        else if (nlmax <= 4) launch_rows<4>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase, per_l);
+        else launch_rows<8>(grid, st, g, A, N, dir, in, in_cplx, out, out_cplx, phase, per_l);
         DSBT_CUDA_TRY(cudaGetLastError());
     }
     return DSBT_OK;

@@ -121,7 +121,8 @@ struct EpiArgs {
     int mode;              // OutMode
     float* out0;
     float* out1;
-    const float2* phase;   // [2][N] or nullptr
+    const float2* phase;   // [2][N] by parity of l, [l_max+1][N] when per_l, or nullptr
+    int per_l;
 };
 
 // TMEM layout (512 columns): [0, 256) main accumulator A_hi B_hi of the
@@ -364,7 +365,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
             if (!ok) break;
             if (ncols <= 0) continue;
             float2 ph = make_float2(1.f, 0.f);
-            if (ep.phase) ph = ep.phase[(size_t)(l & 1) * N + row];
+            if (ep.phase) ph = ep.phase[(size_t)(ep.per_l ? l : (l & 1)) * N + row];
             if (ep.mode == kOutUserC64) {
                 float2* o = reinterpret_cast<float2*>(ep.out0);
                 const size_t chan_base = (size_t)gt.chan0[tl.g] + (cbase >> 1);
@@ -454,7 +455,7 @@ int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const floa
     DSBT_CUDA_TRY(cudaGetDevice(&dev));
     DSBT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int grid = ts.total < nsm ? ts.total : nsm;
-    EpiArgs ep{out_mode, out0, out1, phase};
+    EpiArgs ep{out_mode, out0, out1, phase, p->knl != nullptr};
     const CUtensorMap& ahi = dir > 0 ? p->tm_T_hi : p->tm_Tt_hi;
     const CUtensorMap& alo = dir > 0 ? p->tm_T_lo : p->tm_Tt_lo;
     DSBT_CUDA_TRY(cudaMemsetAsync(sched, 0, sizeof(int), st));

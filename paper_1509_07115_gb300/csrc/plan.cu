@@ -304,6 +304,7 @@ static void plan_free(dsbt_plan* p) {
     if (!p) return;
     cudaFree(p->T64);
     cudaFree(p->Tt64);
+    cudaFree(p->knl);
     cudaFree(p->Thi);
     cudaFree(p->Tlo);
     cudaFree(p->Tthi);
@@ -335,7 +336,7 @@ extern "C" int dsbt_plan_create(int N, double r_max, int l_max, int flags, void*
     DSBT_CHECK_ARG(n0_of(l_max) <= N, "dsbt_plan_create: l_max too large for N");
     DSBT_CHECK_ARG(r_max > 0.0 && isfinite(r_max), "dsbt_plan_create: r_max must be positive");
     DSBT_CHECK_ARG((flags & (DSBT_PLAN_FP64 | DSBT_PLAN_TF32X3)) != 0 &&
-                       (flags & ~(DSBT_PLAN_FP64 | DSBT_PLAN_TF32X3)) == 0,
+                       (flags & ~(DSBT_PLAN_FP64 | DSBT_PLAN_TF32X3 | DSBT_PLAN_KCORR)) == 0,
                    "dsbt_plan_create: flags=%d invalid", flags);
     cudaStream_t st = (cudaStream_t)stream;
     dsbt_plan* p = new (std::nothrow) dsbt_plan();
@@ -367,6 +368,7 @@ extern "C" int dsbt_plan_create(int N, double r_max, int l_max, int flags, void*
          alloc((void**)&p->tw32, N * sizeof(float2)) &&
          alloc((void**)&p->post32, N * sizeof(float2)) &&
          alloc((void**)&p->status, sizeof(unsigned));
+    if (ok && (flags & DSBT_PLAN_KCORR)) ok = alloc((void**)&p->knl, L * N * sizeof(double));
     if (!ok) {
         cudaGetLastError();
         plan_free(p);
@@ -377,6 +379,15 @@ extern "C" int dsbt_plan_create(int N, double r_max, int l_max, int flags, void*
         plan_free(p);
         set_error("dsbt_plan_create: memset failed");
         return DSBT_ERR_CUDA;
+    }
+    if (flags & DSBT_PLAN_KCORR) {   // corrected momenta, computed on the host
+        std::vector<double> k;
+        kcorr_table(N, r_max, l_max, k);
+        if (cudaMemcpy(p->knl, k.data(), k.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            plan_free(p);
+            set_error("dsbt_plan_create: momentum table upload failed");
+            return DSBT_ERR_CUDA;
+        }
     }
     int rc = plan_build_factors(p, st);
     if (rc == DSBT_OK && (flags & DSBT_PLAN_TF32X3)) {

@@ -1,6 +1,8 @@
 // plan.cuh -- internal plan layout and kernel launchers of the DSBT library.
 #pragma once
 
+#include <vector>
+
 #include <cuda.h>
 
 #include "common.cuh"
@@ -31,6 +33,9 @@ struct dsbt_plan {
     double2* post64;
     float2* tw32;
     float2* post32;
+    // corrected momenta [(l_max+1)][N] of DSBT_PLAN_KCORR (else nullptr: the
+    // kinetic phase uses k~_n = n dk by parity)
+    double* knl;
     unsigned* status;          // device status word (kStatusOk / kStatusTimeout)
     double check_err;
     bool has_tmaps;
@@ -71,6 +76,8 @@ void plan_release(dsbt_plan* p);
 // ---- TMA descriptors (tma.cu)
 // Encode a 2-D FP32 tensor map over a row-major [rows][cols] array with a box of
 // box_cols x box_rows and 128-byte swizzling.
+void kcorr_table(int N, double r_max, int l_max, std::vector<double>& out);
+
 int encode_tmap_f32_sw128(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
                           uint32_t box_rows, uint32_t box_cols);
 

@@ -331,6 +331,14 @@ extern "C" int dsbt_tdse_create(const dsbt_plan* plan, int L, double tau, double
     return DSBT_OK;
 }
 
+extern "C" int dsbt_tdse_set_potential(dsbt_tdse* t, const double* V, int n) {
+    DSBT_CHECK_ARG(t != nullptr && V != nullptr, "dsbt_tdse_set_potential: NULL argument");
+    DSBT_CHECK_ARG(n == t->N, "dsbt_tdse_set_potential: %d values for a grid of %d points", n, t->N);
+    for (int i = 0; i < n; ++i) DSBT_CHECK_ARG(isfinite(V[i]), "dsbt_tdse_set_potential: V[%d] not finite", i);
+    DSBT_CUDA_TRY(cudaMemcpy(t->V, V, n * sizeof(double), cudaMemcpyHostToDevice));
+    return DSBT_OK;
+}
+
 extern "C" int dsbt_tdse_destroy(dsbt_tdse* t) {
     if (!t) return DSBT_OK;
     cudaDeviceSynchronize();

@@ -19,6 +19,7 @@ from . import build as _build
 DSBT_OK = 0
 DSBT_PLAN_FP64 = 1
 DSBT_PLAN_TF32X3 = 2
+DSBT_PLAN_KCORR = 4
 DTYPES = {torch.float64: 1, torch.complex128: 2, torch.float32: 3, torch.complex64: 4}
 
 _lib = None
@@ -44,6 +45,7 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_plan_destroy.argtypes = [vp]
         lib.dsbt_plan_info.argtypes = [vp, _c_int_p, _c_int_p, _c_int_p, ctypes.POINTER(d)]
         lib.dsbt_plan_get_T.argtypes = [vp, i, vp, vp]
+        lib.dsbt_plan_get_k.argtypes = [vp, i, vp]
         lib.dsbt_workspace_size.argtypes = [vp, i, i]
         lib.dsbt_workspace_size.restype = sz
         for name in ("dsbt_forward", "dsbt_inverse"):
@@ -78,6 +80,7 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_tdse_create.argtypes = [vp, i, d, d, d, ctypes.POINTER(vp)]
         lib.dsbt_tdse_destroy.argtypes = [vp]
         lib.dsbt_tdse_angular.argtypes = [vp, vp, vp, vp]
+        lib.dsbt_tdse_set_potential.argtypes = [vp, vp, i]
         lib.dsbt_tdse_workspace_size.argtypes = [vp, i, i]
         lib.dsbt_tdse_workspace_size.restype = sz
         lib.dsbt_tdse_propagate.argtypes = [vp, vp, vp, i, i, d, vp, sz, vp]
@@ -108,9 +111,11 @@ def _ptr(t):
 class Plan:
     """A DSBT plan: T_l factors for l = 0..l_max on an N-point grid."""
 
-    def __init__(self, N: int, r_max: float, l_max: int, fp64: bool = True, tf32x3: bool = True):
+    def __init__(self, N: int, r_max: float, l_max: int, fp64: bool = True, tf32x3: bool = True,
+                 kcorr: bool = False):
         lib = load()
-        flags = (DSBT_PLAN_FP64 if fp64 else 0) | (DSBT_PLAN_TF32X3 if tf32x3 else 0)
+        flags = (DSBT_PLAN_FP64 if fp64 else 0) | (DSBT_PLAN_TF32X3 if tf32x3 else 0) | \
+            (DSBT_PLAN_KCORR if kcorr else 0)
         h = ctypes.c_void_p()
         _check(lib.dsbt_plan_create(int(N), float(r_max), int(l_max), flags, _stream(), ctypes.byref(h)),
                "dsbt_plan_create")
@@ -256,6 +261,13 @@ class Plan:
 
     def kinetic_grouped_host(self, counts, x, tau: float, out=None, chunks: int = 0, workspace=None):
         return self._grouped_host("dsbt_kinetic_grouped_host", counts, x, out, chunks, workspace, tau=tau)
+
+    def get_k(self, l: int):
+        """Momenta of the kinetic phase for angular momentum l (dsbt_plan_get_k)."""
+        import numpy as np
+        k = np.empty(self.N)
+        _check(load().dsbt_plan_get_k(self._h, int(l), k.ctypes.data_as(ctypes.c_void_p)), "dsbt_plan_get_k")
+        return k
 
     def device_status(self, reset: bool = True) -> int:
         s = ctypes.c_int()
@@ -424,6 +436,13 @@ class Tdse:
             self.close()
         except Exception:
             pass
+
+    def set_potential(self, V):
+        """Radial potential V(r_i) on the plan's midpoint grid (N values)."""
+        import numpy as np
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        _check(load().dsbt_tdse_set_potential(self._h, V.ctypes.data_as(ctypes.c_void_p), int(V.size)),
+               "dsbt_tdse_set_potential")
 
     def angular(self):
         import numpy as np

@@ -1,0 +1,42 @@
+"""Exact solution of the 3-D harmonic oscillator in a uniform time-dependent
+field (the benchmark of Sec. 4.3), projected on the DSBT-DVR state layout.
+
+H = p^2/2 + r^2/2 + F(t) z.  The ground state stays a Gaussian displaced to the
+classical path:  Psi = pi^{-3/4} exp(-(x^2 + y^2)/2 - (z - a)^2/2 + i p (z - a)
++ i (g - t)),  a' = p,  p' = -a - F,  g' = p^2/2 - a^2/2 - F a - 1/2,  all zero
+at t = 0 (the x, y factors contribute exp(-i t/2) each).  In the state layout
+of the propagator (l = 0..L-1, m = 0): psi_l(r_i) = sqrt(dr) r_i
+sqrt(2 pi) int Psi(r_i, eta) Pbar_l(eta) d eta with Pbar_l = sqrt((2l+1)/2) P_l.
+"""
+import math
+
+import numpy as np
+from numpy.polynomial.legendre import leggauss
+from scipy.integrate import solve_ivp
+from scipy.special import eval_legendre
+
+A0 = 0.25
+
+
+def field(t, omega):
+    """Coefficient F(t) of z in the Hamiltonian (the -qE(t) z of the coordinate
+    gauge with qE = omega A0 cos(omega t))."""
+    return -omega * A0 * math.cos(omega * t)
+
+
+def classical(T, omega):
+    def f(t, y):
+        F = field(t, omega)
+        return [y[1], -y[0] - F, 0.5 * y[1] ** 2 - 0.5 * y[0] ** 2 - F * y[0] - 0.5]
+    s = solve_ivp(f, (0.0, T), [0.0, 0.0, 0.0], rtol=1e-12, atol=1e-14, method="DOP853")
+    return s.y[:, -1]
+
+
+def state(r, dr, L, T, omega, nquad=200):
+    """psi_l(r_i) of the exact solution at time T, array [L][N]."""
+    a, p, g = classical(T, omega) if T > 0 else (0.0, 0.0, 0.0)
+    x, w = leggauss(nquad)
+    Pb = np.array([np.sqrt((2 * l + 1) / 2.0) * eval_legendre(l, x) for l in range(L)])
+    psi = np.pi ** -0.75 * np.exp(-(r[None, :] ** 2 + a * a) / 2 - 1j * p * a + 1j * (g - T)
+                                 + (a + 1j * p) * r[None, :] * x[:, None])
+    return np.sqrt(dr) * r[None, :] * (np.sqrt(2 * np.pi) * (Pb * w) @ psi)
