@@ -231,6 +231,22 @@ DSBT_API int dsbt_tdse_create(const dsbt_plan* plan, int L, double tau, double Z
                               dsbt_tdse** out);
 DSBT_API int dsbt_tdse_destroy(dsbt_tdse* tdse);
 
+/*
+ * Velocity-gauge steps (Eq. (81) with the vector potential A(t) along z):
+ * psi <- exp(-iU tau/2) Y^T B^T exp(-iK tau/2) Ytilde exp(i A k~_n eta tau)
+ *        Ytilde^dagger exp(-iK tau/2) B Y exp(-iU tau/2) psi,
+ * U = V(r) + E r eta as in dsbt_tdse_propagate (E may be NULL: no length-gauge
+ * field), A[s / hold] the vector-potential sample of step s (DEVICE array,
+ * NULL: A = 0), Ytilde the angular transform with the i^l factors of the
+ * modified spherical harmonics taken on the momentum grid k~_n = n dk.  The
+ * kinetic half phases use the plan's momenta (dsbt_plan_get_k).  Workspace as
+ * dsbt_tdse_workspace_size(tdse, nsteps, 0).  tau_sign = -1 runs the inverse
+ * steps with the samples in reverse.
+ */
+DSBT_API int dsbt_tdse_propagate_velocity(const dsbt_tdse* tdse, void* psi, const double* E, const double* A,
+                                          int nsteps, int hold, double tau_sign, void* workspace,
+                                          size_t workspace_bytes, void* stream);
+
 /* Replace the radial potential V(r_i) (the soft-Coulomb default of
  * dsbt_tdse_create) with the caller's n = N HOST values on the midpoint grid
  * r_i = (i + 1/2) dr, i = 0..N-1.  Synchronous. */

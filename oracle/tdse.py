@@ -81,6 +81,39 @@ class Model:
         psi4 = self.to_eta(c4)
         return self.potential_half(psi4, E, tau)
 
+    def step_velocity(self, psi_eta, E, A, tau=None):
+        """Eq. (81) with the vector potential A along z: between the two kinetic
+        half steps, phi = Ytilde^dagger c on the momentum grid k~_n = n dk
+        (Ytilde[l][j] = i^l P[l][j]), phi *= exp(i A k~_n eta_j tau), c = Ytilde
+        phi.  The paper's spherical-wave coefficients are s_l times this
+        library's (sine/cosine sign convention, s_l = (-1)^ceil(l/2))."""
+        tau = self.tau if tau is None else tau
+        N, L = self.N, self.L
+        psi1 = self.potential_half(psi_eta, E, tau)
+        c = self.to_l(psi1)
+        coef = np.zeros((L, N), dtype=complex)        # [l][n - 1], n = 1..N
+        for l in range(L):
+            b = self.T[l] @ (self.F[l] @ c[l])
+            b = np.exp(-0.25j * self.kt[l] ** 2 * tau) * b
+            s_l = (-1) ** ((l + 1) // 2)
+            n = np.arange(N) + oracle.p_of(l)
+            slot = np.where(n == 0, N, n) - 1
+            coef[l, slot] = s_l * b
+        kt = np.arange(1, N + 1) * np.pi / self.r_max
+        il = np.array([1j ** l for l in range(L)])
+        phi = (np.conj(il)[:, None] * self.P).T @ coef                  # [j][n]
+        phi = np.exp(1j * A * kt[None, :] * self.eta[:, None] * tau) * phi
+        coef = (il[:, None] * self.P) @ phi                              # [l][n]
+        c4 = np.empty_like(c)
+        for l in range(L):
+            s_l = (-1) ** ((l + 1) // 2)
+            n = np.arange(N) + oracle.p_of(l)
+            slot = np.where(n == 0, N, n) - 1
+            b = np.exp(-0.25j * self.kt[l] ** 2 * tau) * (s_l * coef[l, slot])
+            c4[l] = self.F[l].T @ (self.T[l].T @ b)
+        psi4 = self.to_eta(c4)
+        return self.potential_half(psi4, E, tau)
+
     def run(self, psi_eta, E_samples, nsteps: int, hold: int):
         x = psi_eta.copy()
         for s in range(nsteps):

@@ -29,6 +29,8 @@
 
 namespace dsbt {
 
+int grouped_device_call(int which, const dsbt_plan* p, const int* counts, int dtype, double tau,
+                        const void* in, void* out, void* ws, size_t ws_b, cudaStream_t st);
 int kinetic_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtype, double tau,
                                  const void* in, void* out, void* scratch, size_t scratch_bytes,
                                  cudaStream_t st);
@@ -191,6 +193,83 @@ __global__ void __launch_bounds__(256) k_tdse_potential(const double2* __restric
     }
 }
 
+// The momentum-space middle of the velocity-gauge step (Eq. (81)) on a tile of
+// TI momentum slots n = 1..N (k~_n = n dk, Eq. (65)), in place on the DSBT
+// coefficients c[l][s] (storage s = n - 1 for even l; s = n for odd l, with
+// n = N stored at s = 0):
+//   half kinetic phase exp(-i k^2 tau/4)  (k = the plan's momentum of (l, s)),
+//   phi = Ytilde^dagger c  (phi_j = sum_l (-i)^l s_l P[l][j] c_l),
+//   phi_j *= exp(i A k~_n eta_j tau),
+//   c = Ytilde phi  (c_l = i^l s_l sum_j P[l][j] phi_j),  half kinetic phase.
+// s_l = (-1)^ceil(l/2) converts this library's sine/cosine sign convention to
+// the spherical-wave coefficients of Ytilde, so (-i)^l s_l = 1 (even l) or i
+// (odd l).  A is the vector potential sample of this step.
+__global__ void __launch_bounds__(256) k_tdse_velocity(double2* c, const double* __restrict__ P,
+                                                       const double* __restrict__ eta,
+                                                       const double* __restrict__ knl, double dk, int L,
+                                                       int N, const double* __restrict__ A, int aidx,
+                                                       double tau) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    double* Ps = reinterpret_cast<double*>(sm);                    // [L][L]
+    double2* xs = reinterpret_cast<double2*>(Ps + kLMax * kLMax);  // [L][TI]
+    double2* xe = xs + kLMax * TI;                                 // [L][TI]
+    const int n0 = 1 + blockIdx.x * TI;
+    const int tid = threadIdx.x;
+    for (int k = tid; k < L * L; k += blockDim.x) Ps[k] = P[k];
+    for (int k = tid; k < L * TI; k += blockDim.x) {   // gather, half kinetic phase, (-i)^l s_l
+        const int l = k / TI, t = k % TI;
+        const int n = n0 + t;
+        double2 v = make_double2(0.0, 0.0);
+        if (n <= N) {
+            const int sidx = (l & 1) ? (n % N) : n - 1;
+            const double km = knl ? knl[(size_t)l * N + sidx] : n * dk;
+            double sn, cs;
+            sincos(-0.25 * km * km * tau, &sn, &cs);
+            v = cmul2(c[(size_t)l * N + sidx], make_double2(cs, sn));
+            if (l & 1) v = make_double2(-v.y, v.x);   // times i
+        }
+        xs[k] = v;
+    }
+    __syncthreads();
+    const double Av = A ? A[aidx] : 0.0;
+    for (int k = tid; k < L * TI; k += blockDim.x) {   // to the angular grid, A . P phase
+        const int j = k / TI, t = k % TI;
+        double2 s = make_double2(0.0, 0.0);
+        for (int l = 0; l < L; ++l) {
+            const double pj = Ps[l * L + j];
+            const double2 v = xs[l * TI + t];
+            s.x = fma(pj, v.x, s.x);
+            s.y = fma(pj, v.y, s.y);
+        }
+        const int n = n0 + t;
+        if (n <= N) {
+            double sn, cs;
+            sincos(Av * (n * dk) * eta[j] * tau, &sn, &cs);
+            s = cmul2(s, make_double2(cs, sn));
+        }
+        xe[k] = s;
+    }
+    __syncthreads();
+    for (int k = tid; k < L * TI; k += blockDim.x) {   // back to l, i^l s_l, half kinetic phase, scatter
+        const int l = k / TI, t = k % TI;
+        const int n = n0 + t;
+        if (n > N) continue;
+        double2 s = make_double2(0.0, 0.0);
+        for (int j = 0; j < L; ++j) {
+            const double pl = Ps[l * L + j];
+            const double2 v = xe[j * TI + t];
+            s.x = fma(pl, v.x, s.x);
+            s.y = fma(pl, v.y, s.y);
+        }
+        if (l & 1) s = make_double2(s.y, -s.x);   // times -i
+        const int sidx = (l & 1) ? (n % N) : n - 1;
+        const double km = knl ? knl[(size_t)l * N + sidx] : n * dk;
+        double sn, cs;
+        sincos(-0.25 * km * km * tau, &sn, &cs);
+        c[(size_t)l * N + sidx] = cmul2(s, make_double2(cs, sn));
+    }
+}
+
 // out += sum_{r_i > rc} sum_l |x[l][i]|^2 ; with lam != nullptr also writes
 // lam = x on r_i > rc and 0 elsewhere (the projector Pi).
 __global__ void k_tdse_observable(const double2* __restrict__ x, double2* __restrict__ lam,
@@ -243,6 +322,33 @@ int step(const dsbt_tdse* t, const double2* in, double2* out, double2* tmp, cons
     int rc = potential(t, in, tmp, E, eidx, 0.5 * tau, nullptr, 0.0, nullptr, st);
     if (!rc) rc = kinetic_grouped_with_scratch(t->plan, counts, DSBT_C128, tau, tmp, out, kws, kws_b, st);
     if (!rc) rc = potential(t, out, out, E, eidx, 0.5 * tau, nullptr, 0.0, nullptr, st);
+    return rc;
+}
+
+// One velocity-gauge step (Eq. (81)): potential half step (U = V + E r eta),
+// forward DSBT, momentum-space middle (k_tdse_velocity), inverse DSBT,
+// potential half step.  c: one state of scratch for the coefficients.
+int step_velocity(const dsbt_tdse* t, const double2* in, double2* out, double2* tmp, double2* c,
+                  const double* E, const double* A, int idx, double tau, const int* counts, void* kws,
+                  size_t kws_b, cudaStream_t st) {
+    int rc = potential(t, in, tmp, E, idx, 0.5 * tau, nullptr, 0.0, nullptr, st);
+    if (!rc) rc = grouped_device_call(0, t->plan, counts, DSBT_C128, 0.0, tmp, c, kws, kws_b, st);
+    if (rc) return rc;
+    {
+        const size_t smem = (size_t)kLMax * kLMax * sizeof(double) + 2 * (size_t)kLMax * TI * sizeof(double2);
+        static bool attr = false;
+        if (!attr) {
+            DSBT_CUDA_TRY(cudaFuncSetAttribute(k_tdse_velocity, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+            attr = true;
+        }
+        ProfScope ps(kKTdseAng, st);
+        k_tdse_velocity<<<(t->N + TI - 1) / TI, 256, smem, st>>>(c, t->P, t->eta, t->plan->knl, t->plan->dk,
+                                                                 t->L, t->N, A, idx, tau);
+        DSBT_CUDA_TRY(cudaGetLastError());
+    }
+    rc = grouped_device_call(1, t->plan, counts, DSBT_C128, 0.0, c, out, kws, kws_b, st);
+    if (!rc) rc = potential(t, out, out, E, idx, 0.5 * tau, nullptr, 0.0, nullptr, st);
     return rc;
 }
 
@@ -389,6 +495,30 @@ extern "C" int dsbt_tdse_propagate(const dsbt_tdse* t, void* psi, const double* 
         // forward in time: sample s / hold; backward (tau < 0): the samples in reverse
         const int eidx = (tau_sign > 0) ? s / hold : (nsteps - 1 - s) / hold;
         rc = step(t, x, w.a, w.tmp, E, eidx, tau, counts.data(), w.kws, w.kws_b, st);
+        if (rc) return rc;
+        DSBT_CUDA_TRY(cudaMemcpyAsync(x, w.a, state_bytes(t), cudaMemcpyDeviceToDevice, st));
+    }
+    return DSBT_OK;
+}
+
+extern "C" int dsbt_tdse_propagate_velocity(const dsbt_tdse* t, void* psi, const double* E, const double* A,
+                                            int nsteps, int hold, double tau_sign, void* workspace,
+                                            size_t workspace_bytes, void* stream) {
+    DSBT_CHECK_ARG(t != nullptr && psi != nullptr, "tdse: NULL argument");
+    DSBT_CHECK_ARG(nsteps >= 0 && hold >= 1, "tdse: nsteps >= 0 and hold >= 1 required");
+    DSBT_CHECK_ARG(workspace != nullptr && workspace_bytes >= dsbt_tdse_workspace_size(t, nsteps, 0),
+                   "tdse: workspace too small (need %zu bytes)", dsbt_tdse_workspace_size(t, nsteps, 0));
+    DSBT_CHECK_ARG(tau_sign == 1.0 || tau_sign == -1.0, "tdse: tau_sign must be +1 or -1");
+    cudaStream_t st = (cudaStream_t)stream;
+    TdseWs w;
+    ws_layout(t, nsteps, 0, &w, workspace);
+    std::vector<int> counts(t->plan->l_max + 1, 0);
+    for (int l = 0; l < t->L; ++l) counts[l] = 1;
+    double2* x = (double2*)psi;
+    const double tau = tau_sign * t->tau;
+    for (int s = 0; s < nsteps; ++s) {
+        const int idx = (tau_sign > 0) ? s / hold : (nsteps - 1 - s) / hold;
+        int rc = step_velocity(t, x, w.a, w.tmp, w.mu, E, A, idx, tau, counts.data(), w.kws, w.kws_b, st);
         if (rc) return rc;
         DSBT_CUDA_TRY(cudaMemcpyAsync(x, w.a, state_bytes(t), cudaMemcpyDeviceToDevice, st));
     }

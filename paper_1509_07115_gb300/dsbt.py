@@ -81,6 +81,7 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_tdse_destroy.argtypes = [vp]
         lib.dsbt_tdse_angular.argtypes = [vp, vp, vp, vp]
         lib.dsbt_tdse_set_potential.argtypes = [vp, vp, i]
+        lib.dsbt_tdse_propagate_velocity.argtypes = [vp, vp, vp, vp, i, i, d, vp, sz, vp]
         lib.dsbt_tdse_workspace_size.argtypes = [vp, i, i]
         lib.dsbt_tdse_workspace_size.restype = sz
         lib.dsbt_tdse_propagate.argtypes = [vp, vp, vp, i, i, d, vp, sz, vp]
@@ -474,6 +475,19 @@ class Tdse:
         _check(load().dsbt_tdse_propagate(self._h, _ptr(psi), _ptr(E), int(nsteps), int(hold),
                                           -1.0 if backward else 1.0, _ptr(ws), ws.numel(), _stream()),
                "dsbt_tdse_propagate")
+        return psi
+
+    def propagate_velocity(self, psi: torch.Tensor, A: torch.Tensor, nsteps: int, hold: int = 1, E=None,
+                           backward: bool = False) -> torch.Tensor:
+        """In-place velocity-gauge propagation (dsbt_tdse_propagate_velocity):
+        A (and optionally E) per hold steps."""
+        self._state(psi)
+        A = A.to(device="cuda", dtype=torch.float64).contiguous()
+        Ep = None if E is None else E.to(device="cuda", dtype=torch.float64).contiguous()
+        ws = self.workspace(nsteps, 0)
+        _check(load().dsbt_tdse_propagate_velocity(self._h, _ptr(psi), None if Ep is None else _ptr(Ep), _ptr(A),
+                                                   int(nsteps), int(hold), -1.0 if backward else 1.0, _ptr(ws),
+                                                   ws.numel(), _stream()), "dsbt_tdse_propagate_velocity")
         return psi
 
     def observable(self, psi: torch.Tensor, r_cut: float) -> torch.Tensor:

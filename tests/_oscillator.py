@@ -4,7 +4,9 @@ field (the benchmark of Sec. 4.3), projected on the DSBT-DVR state layout.
 H = p^2/2 + r^2/2 + F(t) z.  The ground state stays a Gaussian displaced to the
 classical path:  Psi = pi^{-3/4} exp(-(x^2 + y^2)/2 - (z - a)^2/2 + i p (z - a)
 + i (g - t)),  a' = p,  p' = -a - F,  g' = p^2/2 - a^2/2 - F a - 1/2,  all zero
-at t = 0 (the x, y factors contribute exp(-i t/2) each).  In the state layout
+at t = 0 (the x, y factors contribute exp(-i t/2) each).  In the velocity gauge
+(A(t) = -A0 sin(omega t), F = dA/dt) the state is exp(i int A^2/2) exp(i A z)
+times the length-gauge state.  In the state layout
 of the propagator (l = 0..L-1, m = 0): psi_l(r_i) = sqrt(dr) r_i
 sqrt(2 pi) int Psi(r_i, eta) Pbar_l(eta) d eta with Pbar_l = sqrt((2l+1)/2) P_l.
 """
@@ -16,6 +18,18 @@ from scipy.integrate import solve_ivp
 from scipy.special import eval_legendre
 
 A0 = 0.25
+
+
+def vector_potential(t, omega):
+    """A(t) = -A0 sin(omega t) of the velocity gauge (q E = -dA/dt)."""
+    return -A0 * math.sin(omega * t)
+
+
+def velocity_state(r, dr, L, T, omega):
+    """Exact velocity-gauge state: H_v = p^2/2 - A p + r^2/2 (no A^2/2 term) gives
+    psi_v = exp(i int_0^T A^2/2 dt) exp(i A(T) z) psi_length."""
+    phase = 0.5 * A0 ** 2 * (T / 2 - math.sin(2 * omega * T) / (4 * omega))
+    return state(r, dr, L, T, omega, kick=vector_potential(T, omega)) * np.exp(1j * phase)
 
 
 def field(t, omega):
@@ -32,11 +46,12 @@ def classical(T, omega):
     return s.y[:, -1]
 
 
-def state(r, dr, L, T, omega, nquad=200):
-    """psi_l(r_i) of the exact solution at time T, array [L][N]."""
+def state(r, dr, L, T, omega, nquad=200, kick=0.0):
+    """psi_l(r_i) of the exact solution at time T, array [L][N]; kick multiplies
+    the state by exp(i kick z) (the velocity-gauge factor exp(i A(T) z))."""
     a, p, g = classical(T, omega) if T > 0 else (0.0, 0.0, 0.0)
     x, w = leggauss(nquad)
     Pb = np.array([np.sqrt((2 * l + 1) / 2.0) * eval_legendre(l, x) for l in range(L)])
     psi = np.pi ** -0.75 * np.exp(-(r[None, :] ** 2 + a * a) / 2 - 1j * p * a + 1j * (g - T)
-                                 + (a + 1j * p) * r[None, :] * x[:, None])
+                                 + (a + 1j * (p + kick)) * r[None, :] * x[:, None])
     return np.sqrt(dr) * r[None, :] * (np.sqrt(2 * np.pi) * (Pb * w) @ psi)

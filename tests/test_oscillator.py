@@ -1,6 +1,6 @@
 """3-D harmonic oscillator in a time-dependent field (Sec. 4.3): the split-step
 propagator against the exact solution, with k~_n and with the corrected
-momenta k_nl of Sec. 3.
+momenta k_nl of Sec. 3, in the coordinate gauge and in the velocity gauge.
 
 The paper reports delta = |1 - <psi_exact|psi>| falling like r_max^-2 at fixed
 dr, and 4-5 times smaller with the corrected momenta.  Measured here (GPU and
@@ -17,7 +17,7 @@ import torch
 
 from oracle import tdse as otdse
 
-from _oscillator import classical, field, state
+from _oscillator import field, state, vector_potential, velocity_state
 
 OMEGA, L, DR, TAU, STEPS = 2.0, 16, 0.05, 0.005, 628
 
@@ -54,17 +54,41 @@ def test_oracle_oscillator_error_and_corrected_momenta():
     assert d_c < d_u / 3.5, (d_u, d_c)     # corrected momenta: several times smaller
 
 
-def gpu_delta(lib, r_max, kcorr):
+def delta_oracle_velocity(r_max, kcorr):
+    N = int(round(r_max / DR))
+    r = (np.arange(N) + 0.5) * DR
+    m = otdse.Model(N, r_max, L, TAU, V=0.5 * r * r, kcorr=kcorr)
+    x = m.to_eta(state(r, DR, L, 0.0, OMEGA))
+    for s in range(STEPS):
+        x = m.step_velocity(x, 0.0, vector_potential((s + 0.5) * TAU, OMEGA))
+    c = m.to_l(x)
+    return abs(1 - np.vdot(velocity_state(r, DR, L, STEPS * TAU, OMEGA), c)), c
+
+
+def test_oracle_oscillator_velocity_gauge():
+    d_u, _ = delta_oracle_velocity(12.8, False)
+    d_c, _ = delta_oracle_velocity(12.8, True)
+    assert 2e-4 < d_u < 3e-3, d_u
+    assert d_c < d_u / 2.5, (d_u, d_c)
+
+
+def gpu_delta(lib, r_max, kcorr, velocity=False):
     N = int(round(r_max / DR))
     r = (np.arange(N) + 0.5) * DR
     plan = lib.Plan(N, r_max, L - 1, tf32x3=False, kcorr=kcorr)
     td = lib.Tdse(plan, L, TAU)
     td.set_potential(0.5 * r * r)
     psi = torch.from_numpy(state(r, DR, L, 0.0, OMEGA)).cuda()
-    E = torch.tensor([field((s + 0.5) * TAU, OMEGA) for s in range(STEPS)], dtype=torch.float64)
-    td.propagate(psi, E, STEPS, 1)
+    if velocity:
+        A = torch.tensor([vector_potential((s + 0.5) * TAU, OMEGA) for s in range(STEPS)], dtype=torch.float64)
+        td.propagate_velocity(psi, A, STEPS, 1)
+        ref = velocity_state(r, DR, L, STEPS * TAU, OMEGA)
+    else:
+        E = torch.tensor([field((s + 0.5) * TAU, OMEGA) for s in range(STEPS)], dtype=torch.float64)
+        td.propagate(psi, E, STEPS, 1)
+        ref = state(r, DR, L, STEPS * TAU, OMEGA)
     c = psi.cpu().numpy()
-    d = abs(1 - np.vdot(state(r, DR, L, STEPS * TAU, OMEGA), c))
+    d = abs(1 - np.vdot(ref, c))
     td.close()
     plan.close()
     return d, c
@@ -85,3 +109,19 @@ def test_gpu_oscillator_matches_oracle_and_converges(lib):
     for a, b in ((12.8, 25.6), (25.6, 51.2)):
         assert 3.0 < d[a][0] / d[b][0] < 5.0, (a, b, d)             # k~_n: O(r_max^-2)
         assert d[a][1] / d[b][1] > 3.0, (a, b, d)                   # k_nl: at least as fast
+
+
+@pytest.mark.gpu
+def test_gpu_oscillator_velocity_gauge(lib):
+    """Velocity gauge (A(t) = -A0 sin(omega t) along z): GPU = oracle, delta
+    like r_max^-2 with k~_n (3.7e-4, 9.5e-5 at r_max = 12.8, 25.6) and several
+    times smaller with k_nl (6.9e-5, 1.3e-5)."""
+    du, cu = gpu_delta(lib, 12.8, False, velocity=True)
+    dc, cc = gpu_delta(lib, 12.8, True, velocity=True)
+    _, ou = delta_oracle_velocity(12.8, False)
+    _, oc = delta_oracle_velocity(12.8, True)
+    assert np.abs(cu - ou).max() < 1e-11 and np.abs(cc - oc).max() < 1e-11
+    du2 = gpu_delta(lib, 25.6, False, velocity=True)[0]
+    dc2 = gpu_delta(lib, 25.6, True, velocity=True)[0]
+    assert 3.0 < du / du2 < 5.0, (du, du2)
+    assert dc < du / 2.5 and dc2 < du2 / 2.5, (du, dc, du2, dc2)
