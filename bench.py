@@ -203,9 +203,7 @@ def oracle_sample(nchan=16, ls=(1, 2), seed=11):
         F = oracle.F_matrix(N, l)
         T = oracle.T_matrix(N, l)
         t_build += time.perf_counter() - t0
-        p = oracle.p_of(l)
-        n = np.arange(N) + p
-        kt = np.where(n == 0, N, n) * dk
+        kt = oracle.k_tilde(N, R_MAX, l)
         t0 = time.perf_counter()
         f = oracle.apply(F, x[c0:c0 + c])
         b = oracle.apply(T, f) * np.exp(-0.5j * kt * kt * TAU)
@@ -238,8 +236,7 @@ def run_reference(args, rank):
         it[0] += 1
         F, T = FT[l]
         xs = x[l - 1:l]
-        n = np.arange(N) + oracle.p_of(l)
-        kt = np.where(n == 0, N, n) * dk
+        kt = oracle.k_tilde(N, R_MAX, l)
         b = oracle.apply(T, oracle.apply(F, xs)) * np.exp(-0.5j * kt * kt * TAU)
         oracle.apply(F, oracle.apply(T, b, transpose=True), transpose=True)
         return 2

@@ -107,11 +107,11 @@ DSBT_API int dsbt_plan_get_T(const dsbt_plan* plan, int l, double* dst, void* st
 /*
  * Copy the N momenta that the kinetic phase of this plan uses for angular
  * momentum l (storage index s = n - p_l) into the HOST array host_out.
- * Without DSBT_PLAN_KCORR: k~_n = n dk (n = 0 of odd l -> N dk, Eq. (65)).
- * With it (Sec. 3, Eq. (kcorr)): on the regular rows n >= n0_l,
- * k_nl = x_m / r_max with x_m the m-th positive zero (m = n - floor(l/2)) of
- * chi_l(x) = x j_l(x) for even l, of chi_l'(x) for odd l; the completion rows
- * keep k~_n.  The table is computed on the host in FP64 at plan creation
+ * Regular rows n >= n0_l: without DSBT_PLAN_KCORR k~_n = n dk (Eq. (65));
+ * with it (Sec. 3, Eq. (kcorr)) k_nl = x_m / r_max with x_m the m-th positive
+ * zero (m = n - floor(l/2)) of chi_l(x) = x j_l(x) for even l, of chi_l'(x)
+ * for odd l.  Completion rows n < n0_l (n = 0 of odd l among them) take the
+ * largest grid momentum N dk in both cases.  The table is computed on the host in FP64 at plan creation
  * (relative accuracy ~1e-16).  Synchronous.
  */
 DSBT_API int dsbt_plan_get_k(const dsbt_plan* plan, int l, double* host_out);
@@ -150,8 +150,11 @@ DSBT_API int dsbt_inverse_grouped(const dsbt_plan* plan, const int* counts, int 
  * Free-particle kinetic step through the DSBT (the kinetic factor of the
  * split-operator scheme, Sec. 4.1, Eq. (81), with the momentum grid of
  * Eq. (65)): out = F^T T^T exp(-i K tau) T F in, per l group, where
- * K = diag(k~_n^2 / 2), k~_n = n dk for n >= 1 and, for odd l, the n = 0
- * coefficient takes k~_N = N dk.  Complex dtypes only (DSBT_C128, DSBT_C64).
+ * K = diag(k_n^2 / 2) with the plan's momenta (dsbt_plan_get_k): k~_n = n dk
+ * on the regular rows, N dk on the completion rows n < n0_l (which project
+ * onto non-regular high-frequency functions; with n0_l - p_l = 0 rows for
+ * l = 0 this is Eq. (65)'s rule that the n = 0 coefficient of odd l takes
+ * k~_N).  Complex dtypes only (DSBT_C128, DSBT_C64).
  * The phase is applied inside the forward contraction's epilogue.
  */
 DSBT_API int dsbt_kinetic_grouped(const dsbt_plan* plan, const int* counts, int dtype, double tau,

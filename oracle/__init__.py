@@ -20,6 +20,8 @@ import os
 import subprocess
 import threading
 
+import math
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -105,6 +107,16 @@ def p_of(l: int) -> int:
 
 
 # ------------------------------------------------------------------ matrices
+
+def k_tilde(N: int, r_max: float, l: int) -> np.ndarray:
+    """Momenta of the kinetic energy K = k^2/2 for storage index s = n - p_l
+    (Eq. (65) and the remark after it): k~_n = n pi / r_max on the regular
+    rows; the completion rows n < n0_l (Sec. 2.5; n = 0 of odd l among them)
+    project onto non-regular high-frequency functions and take the largest
+    grid momentum k~_N."""
+    n = np.arange(N) + p_of(l)
+    return np.where(n < n0(l), N, n) * (math.pi / r_max)
+
 
 def T_matrix(N: int, l: int) -> np.ndarray:
     """Full T_l (Sec. 2.4-2.5), [N][N], entry (n - p_l, m - p_l)."""

@@ -9,8 +9,8 @@ sin(k_n r - l pi/2) (even l) or its cosine partner (odd l), so the phase of
 chi_l must advance by the same number of half-waves; counting zeros from x = 0,
 coefficient n takes the m-th positive zero with m = n - floor(l/2).  That is
 m >= 1 exactly for the regular rows n >= n0_l = ceil((l+1)/2); the completion
-rows n < n0_l have no partner zero and keep k~_n of Eq. (65) (n = 0 of odd l
--> k~_N).  For large m the zeros approach the paper's estimate
+rows n < n0_l have no partner zero and keep the momentum they have without
+the correction (oracle.k_tilde: the largest grid momentum k~_N).  For large m the zeros approach the paper's estimate
 k_nl ~ k_n - l(l+1) dk^2 / (2 pi^2 k_n).
 
 Method: sign changes of chi_l (or chi_l') on a uniform scan from x = 0 with a
@@ -58,11 +58,10 @@ def zeros(l: int, count: int, derivative: bool, h: float = 0.02) -> np.ndarray:
 
 def k_table(N: int, r_max: float, l: int) -> np.ndarray:
     """Momentum of each storage index s = n - p_l (s = 0..N-1) for one l:
-    corrected k_nl on the regular rows, k~_n on the completion rows."""
-    dk = math.pi / r_max
+    corrected k_nl on the regular rows, k~_N on the completion rows."""
     p, n0 = oracle.p_of(l), oracle.n0(l)
     n = np.arange(N) + p
-    k = np.where(n == 0, N, n) * dk
+    k = oracle.k_tilde(N, r_max, l)
     half = l // 2
     reg = n >= n0
     m_last = int(n[-1]) - half

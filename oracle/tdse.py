@@ -54,8 +54,7 @@ class Model:
                 from oracle import kcorr as kc
                 self.kt.append(kc.k_table(N, r_max, l))
                 continue
-            n = np.arange(N) + oracle.p_of(l)
-            self.kt.append(np.where(n == 0, N, n) * dk)   # Eq. (65): n = 0 -> k~_N
+            self.kt.append(oracle.k_tilde(N, r_max, l))
 
     # l representation <-> angular grid (Y and Y^T)
     def to_l(self, psi_eta):

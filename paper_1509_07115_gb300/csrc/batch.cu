@@ -442,7 +442,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                     for (int j = 0; j < SEG; ++j)
                         if (j < nv) o[(size_t)j * N + row] = acc[ch * 32 + j];
                 } else {
-                    const float2 ph = T.phase[(size_t)(l & 1) * N + row];
+                    const float2 ph = T.phase[(size_t)(l & 1) * N + phase_entry(l, row, N)];
                     float* oh = T.b_hi + (size_t)(G.bline0 + c) * N;
                     float* ol = T.b_lo + (size_t)(G.bline0 + c) * N;
 #pragma unroll

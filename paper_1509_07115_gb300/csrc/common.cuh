@@ -38,6 +38,19 @@ __host__ __device__ inline int parity_p(int l) { return (l & 1) ? 0 : 1; }   // 
 __host__ __device__ inline int n0_of(int l) { return (l + 2) / 2; }           // ceil((l+1)/2)
 // Number of completion rows n in [p_l, n0_l - 1] (Sec. 2.5).
 __host__ __device__ inline int n_extra(int l) { return n0_of(l) - parity_p(l); }
+// Momentum of storage row s (row n = s + p_l) of T_l in units of dk for the
+// kinetic energy (Eq. (65) and the remark after it): n on the regular rows;
+// the completion rows n < n0_l (n = 0 of odd l among them) project onto
+// non-regular high-frequency functions and take the largest grid momentum N.
+__host__ __device__ inline int k_index(int l, int s, int N) {
+    const int n = s + parity_p(l);
+    return n < n0_of(l) ? N : n;
+}
+// Entry of the parity phase table (rows s = 0..N-1 with momentum n = s + p,
+// n = 0 -> N) that holds the phase of storage row s of T_l.
+__host__ __device__ inline int phase_entry(int l, int s, int N) {
+    return (s + parity_p(l) < n0_of(l)) ? ((l & 1) ? 0 : N - 1) : s;
+}
 
 inline bool is_complex(int dtype) { return dtype == DSBT_C128 || dtype == DSBT_C64; }
 inline bool is_fp64(int dtype) { return dtype == DSBT_F64 || dtype == DSBT_C128; }

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) k_contract64_tile(GroupTable g, const dou
             __syncthreads();
         }
     }
-    const int par = per_l ? l : (l & 1);   // phase row: per l, or by parity
+    const int par = per_l ? l : (l & 1);   // phase table row: per l, or by parity
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int r = r0 + ty * 4 + i;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) k_contract64_tile(GroupTable g, const dou
             const int c = c0 + tx * 4 + j;
             double re = acc[i][j], im = acc[i][j + 1];
             if (phase) {   // lines (c, c+1) are the real and imaginary parts of one channel
-                const double2 ph = phase[(size_t)par * N + r];
+                const double2 ph = phase[(size_t)par * N + (per_l ? r : phase_entry(l, r, N))];
                 const double t = re * ph.x - im * ph.y;
                 im = re * ph.y + im * ph.x;
                 re = t;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_contract64_rows(GroupTable g, const dou
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
     if (lane == 0) {
-        const double2 ph = phase ? phase[(size_t)(per_l ? l : (l & 1)) * N + r] : make_double2(1.0, 0.0);
+        const double2 ph = phase ? (per_l ? phase[(size_t)l * N + r] : phase[(size_t)(l & 1) * N + phase_entry(l, r, N)]) : make_double2(1.0, 0.0);
 #pragma unroll
         for (int j = 0; j < NLMAX; j += 2) {   // compile-time indices keep acc[] in registers
             if (j < nl) {

@@ -365,7 +365,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
             if (!ok) break;
             if (ncols <= 0) continue;
             float2 ph = make_float2(1.f, 0.f);
-            if (ep.phase) ph = ep.phase[(size_t)(ep.per_l ? l : (l & 1)) * N + row];
+            if (ep.phase) ph = ep.per_l ? ep.phase[(size_t)l * N + row] : ep.phase[(size_t)(l & 1) * N + phase_entry(l, row, N)];
             if (ep.mode == kOutUserC64) {
                 float2* o = reinterpret_cast<float2*>(ep.out0);
                 const size_t chan_base = (size_t)gt.chan0[tl.g] + (cbase >> 1);

@@ -7,7 +7,7 @@
 // n of a regular row (n >= n0_l) takes the m-th positive root, m = n -
 // floor(l/2): the basis function near r_max goes like sin(k_n r - l pi/2), so
 // it has made as many half-waves as chi_l at its m-th zero.  Completion rows
-// keep k~_n of Eq. (65).
+// take the largest grid momentum N dk, as in the uniform grid (k_index).
 //
 // Method (host, FP64).  Write chi_l = M sin(theta), -x y_l(x) = M cos(theta).
 // The phase theta(x) rises monotonically from 0 with theta' = 1/M^2 (the
@@ -142,10 +142,7 @@ double bracketed_newton(F f, double lo, double hi, double x0) {
 void fill_l(int N, double r_max, int l, double* out) {
     const double dk = M_PI / r_max;
     const int p = parity_p(l), n0 = n0_of(l), half = l / 2;
-    for (int s = 0; s < N; ++s) {
-        const int n = s + p;
-        out[s] = (n == 0 ? N : n) * dk;
-    }
+    for (int s = 0; s < N; ++s) out[s] = k_index(l, s, N) * dk;
     const int m_last = (N - 1 + p) - half;
     if (m_last < 1) return;
     // zeros of chi_l: theta(x) = m pi, m = 1..m_last
@@ -209,10 +206,6 @@ extern "C" int dsbt_plan_get_k(const dsbt_plan* plan, int l, double* host_out) {
         DSBT_CUDA_TRY(cudaMemcpy(host_out, plan->knl + (size_t)l * N, N * sizeof(double), cudaMemcpyDeviceToHost));
         return DSBT_OK;
     }
-    const int p = parity_p(l);
-    for (int s = 0; s < N; ++s) {
-        const int n = s + p;
-        host_out[s] = (n == 0 ? N : n) * plan->dk;
-    }
+    for (int s = 0; s < N; ++s) host_out[s] = k_index(l, s, N) * plan->dk;
     return DSBT_OK;
 }

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) k_tdse_velocity(double2* c, const double*
         double2 v = make_double2(0.0, 0.0);
         if (n <= N) {
             const int sidx = (l & 1) ? (n % N) : n - 1;
-            const double km = knl ? knl[(size_t)l * N + sidx] : n * dk;
+            const double km = knl ? knl[(size_t)l * N + sidx] : k_index(l, sidx, N) * dk;
             double sn, cs;
             sincos(-0.25 * km * km * tau, &sn, &cs);
             v = cmul2(c[(size_t)l * N + sidx], make_double2(cs, sn));
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256) k_tdse_velocity(double2* c, const double*
         }
         if (l & 1) s = make_double2(s.y, -s.x);   // times -i
         const int sidx = (l & 1) ? (n % N) : n - 1;
-        const double km = knl ? knl[(size_t)l * N + sidx] : n * dk;
+        const double km = knl ? knl[(size_t)l * N + sidx] : k_index(l, sidx, N) * dk;
         double sn, cs;
         sincos(-0.25 * km * km * tau, &sn, &cs);
         c[(size_t)l * N + sidx] = cmul2(s, make_double2(cs, sn));

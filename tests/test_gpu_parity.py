@@ -134,9 +134,7 @@ def test_kinetic_step_matches_oracle(plan256):
     ref = np.empty_like(x)
     c0 = 0
     for l, c in enumerate(counts):
-        p = oracle.p_of(l)
-        n = np.arange(256) + p
-        kt = np.where(n == 0, 256, n) * dk
+        kt = oracle.k_tilde(256, 25.6, l)
         b = oracle.forward(l, x[c0:c0 + c]) * np.exp(-0.5j * kt * kt * tau)
         ref[c0:c0 + c] = oracle.inverse(l, b)
         c0 += c

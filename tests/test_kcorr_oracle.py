@@ -5,7 +5,7 @@ reduce to elementary equations (sin x = 0; x cos x - sin x + x^2 sin x = 0;
 (3 - x^2) sin x - 3 x cos x = 0) whose roots are found here by a separate scan
 of those formulas; for large n the zeros approach the paper's estimate
 k_nl ~ k_n - l(l+1) dk^2 / (2 pi^2 k_n) with an error falling like n^-3; the
-completion rows keep k~_n; corrected momenta increase with n, lie below k_n
+completion rows take k~_N; corrected momenta increase with n, lie below k_n
 and their spacing tends to dk.
 """
 import math
@@ -69,6 +69,6 @@ def test_structure(l):
     n = np.arange(N) + oracle.p_of(l)
     kn = np.where(n == 0, N, n) * dk
     reg = n >= oracle.n0(l)
-    assert np.array_equal(k[~reg], kn[~reg])                     # completion rows unchanged
+    assert np.all(k[~reg] == N * dk)                             # completion rows: k~_N
     assert np.all(k[reg] < kn[reg]) and np.all(np.diff(k[reg]) > 0)
     assert abs(np.diff(k[reg])[-1] - dk) < 1e-3 * dk              # spacing -> dk
