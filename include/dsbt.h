@@ -215,6 +215,27 @@ DSBT_API int dsbt_kinetic_grouped_host(const dsbt_plan* plan, const int* counts,
 DSBT_API int dsbt_device_status(const dsbt_plan* plan, int reset, int* status_out);
 
 /* ---------------------------------------------------------------------------
+ * Bound states of one l channel (Sec. 4.4): imaginary-time evolution with the
+ * split propagator S = exp(-U tau/2) F^T T^T exp(-K tau) T F exp(-U tau/2)
+ * (K = k^2/2 with the plan's momenta, see dsbt_plan_get_k) and, after every
+ * step, modified Gram-Schmidt of each state against the lower ones.
+ * U: DEVICE array of N potential values U(r_i) (midpoint grid, spherical
+ * potential); psi: DEVICE array [nstates][N] of real FP64 radial states
+ * (psi(r_i) sqrt(dr)), in: a starting guess with a component along every
+ * wanted state, out: the normalised states after nsteps steps.  levels (HOST,
+ * nstates, may be NULL): -ln(R_ss)/tau with R_ss the norm of state s after one
+ * step and the projection (the levels of S that the states converge to);
+ * energies (HOST, may be NULL): <psi_s| F^T T^T K T F + U |psi_s> of the
+ * final states.  Plan built with DSBT_PLAN_FP64; 1 <= nstates <= 64;
+ * workspace: DEVICE, dsbt_radial_states_workspace_size bytes.  Synchronises
+ * the stream before returning (the outputs are on the host).
+ * ------------------------------------------------------------------------- */
+DSBT_API size_t dsbt_radial_states_workspace_size(const dsbt_plan* plan, int nstates);
+DSBT_API int dsbt_radial_states(const dsbt_plan* plan, int l, const double* U, int nstates, double tau,
+                                int nsteps, double* psi, double* levels, double* energies, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Split-operator TDSE through the DSBT (Sec. 4.1, Eq. (81)) for an axially
  * symmetric state (m = 0) in a linearly polarised field in the length gauge
  * (vector potential A = 0):  H = p^2/2 + V(r) + E(t) r cos(theta),

@@ -50,16 +50,25 @@ def levels(N: int, r_max: float, l: int, U: np.ndarray, count: int, corrected: b
     return np.linalg.eigvalsh(hamiltonian(N, r_max, l, U, corrected))[:count]
 
 
-def split_levels(N: int, r_max: float, l: int, U: np.ndarray, count: int, tau: float,
-                 corrected: bool = True) -> np.ndarray:
-    """-ln(lambda_s)/tau for the `count` largest eigenvalues lambda_s of the
-    imaginary-time split propagator S (symmetric)."""
+def split_states(N: int, r_max: float, l: int, U: np.ndarray, count: int, tau: float,
+                 corrected: bool = True):
+    """Levels -ln(lambda_s)/tau of the `count` largest eigenvalues lambda_s of
+    the imaginary-time split propagator S (symmetric), its eigenvectors
+    (columns) and their energies <v|H_l|v>."""
     B = oracle.T_matrix(N, l) @ oracle.F_matrix(N, l)
     k = momenta(N, r_max, l, corrected)
     h = np.exp(-0.5 * tau * U)
     S = h[:, None] * (B.T @ (np.exp(-0.5 * tau * k * k)[:, None] * B)) * h[None, :]
-    lam = np.linalg.eigvalsh(0.5 * (S + S.T))[::-1][:count]
-    return -np.log(lam) / tau
+    lam, V = np.linalg.eigh(0.5 * (S + S.T))
+    lam, V = lam[::-1][:count], V[:, ::-1][:, :count]
+    H = B.T @ ((0.5 * k * k)[:, None] * B) + np.diag(U)
+    E = np.einsum("is,ij,js->s", V, H, V)
+    return -np.log(lam) / tau, V, E
+
+
+def split_levels(N: int, r_max: float, l: int, U: np.ndarray, count: int, tau: float,
+                 corrected: bool = True) -> np.ndarray:
+    return split_states(N, r_max, l, U, count, tau, corrected)[0]
 
 
 def effective_potential(N: int, r_max: float, Z: float = 1.0) -> np.ndarray:

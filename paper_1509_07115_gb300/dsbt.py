@@ -46,6 +46,9 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_plan_info.argtypes = [vp, _c_int_p, _c_int_p, _c_int_p, ctypes.POINTER(d)]
         lib.dsbt_plan_get_T.argtypes = [vp, i, vp, vp]
         lib.dsbt_plan_get_k.argtypes = [vp, i, vp]
+        lib.dsbt_radial_states_workspace_size.restype = sz
+        lib.dsbt_radial_states_workspace_size.argtypes = [vp, i]
+        lib.dsbt_radial_states.argtypes = [vp, i, vp, i, d, i, vp, vp, vp, vp, sz, vp]
         lib.dsbt_workspace_size.argtypes = [vp, i, i]
         lib.dsbt_workspace_size.restype = sz
         for name in ("dsbt_forward", "dsbt_inverse"):
@@ -269,6 +272,24 @@ class Plan:
         k = np.empty(self.N)
         _check(load().dsbt_plan_get_k(self._h, int(l), k.ctypes.data_as(ctypes.c_void_p)), "dsbt_plan_get_k")
         return k
+
+    def radial_states(self, l: int, U, psi: torch.Tensor, tau: float, nsteps: int):
+        """Imaginary-time bound states of channel l (dsbt_radial_states): psi is a
+        float64 CUDA tensor [nstates][N] (start guess, overwritten with the
+        states); returns (levels of the split propagator, energies <H>)."""
+        import numpy as np
+        if psi.dtype != torch.float64 or not psi.is_cuda or psi.dim() != 2 or psi.shape[1] != self.N \
+                or not psi.is_contiguous():
+            raise ValueError("psi must be a contiguous float64 CUDA tensor [nstates][N]")
+        ns = psi.shape[0]
+        Ud = torch.as_tensor(np.asarray(U, dtype=np.float64)).to("cuda").contiguous()
+        nb = int(load().dsbt_radial_states_workspace_size(self._h, ns))
+        ws = torch.empty(max(nb, 256), dtype=torch.uint8, device="cuda")
+        lev, en = np.empty(ns), np.empty(ns)
+        _check(load().dsbt_radial_states(self._h, int(l), _ptr(Ud), ns, float(tau), int(nsteps), _ptr(psi),
+                                         lev.ctypes.data_as(ctypes.c_void_p), en.ctypes.data_as(ctypes.c_void_p),
+                                         _ptr(ws), ws.numel(), _stream()), "dsbt_radial_states")
+        return lev, en
 
     def device_status(self, reset: bool = True) -> int:
         s = ctypes.c_int()
