@@ -253,6 +253,17 @@ typedef struct dsbt_tdse dsbt_tdse;
  * the plan must outlive it.  Owns small device tables (P, V, r, eta). */
 DSBT_API int dsbt_tdse_create(const dsbt_plan* plan, int L, double tau, double Z, double a2,
                               dsbt_tdse** out);
+/* The same for a state of fixed magnetic quantum number m (an axially
+ * symmetric potential and a field along z conserve m): channels
+ * l = |m| .. |m| + L - 1 (the plan needs l_max >= |m| + L - 1), angular
+ * transform P[i][j] = the normalised associated Legendre functions
+ * Pbar_{|m|+i}^{|m|}(eta_j) sqrt(w_j), orthonormalised on the L-point
+ * Gauss-Legendre rule by Gram-Schmidt in order of l (Sec. 4.1: associated
+ * Legendre functions orthonormalised on the quadrature).  m = 0 is
+ * dsbt_tdse_create.  Every dsbt_tdse_* call then works on [L][N] states of
+ * those channels. */
+DSBT_API int dsbt_tdse_create_m(const dsbt_plan* plan, int L, int m, double tau, double Z, double a2,
+                                dsbt_tdse** out);
 DSBT_API int dsbt_tdse_destroy(dsbt_tdse* tdse);
 
 /*

@@ -21,16 +21,31 @@ from __future__ import annotations
 
 import numpy as np
 from numpy.polynomial.legendre import leggauss
-from scipy.special import eval_legendre
+from scipy.special import eval_legendre, gammaln, lpmv
 
 import oracle
 
 
-def angular(L: int):
-    """(eta, w, P) of the L-point Gauss-Legendre rule, P[l][j]."""
+def angular(L: int, m: int = 0):
+    """(eta, w, P) of the L-point Gauss-Legendre rule.  m = 0: P[l][j] =
+    sqrt((2l+1)/2) P_l(eta_j) sqrt(w_j), l < L (orthonormal on the rule).
+    m != 0 (Sec. 4.1: associated Legendre functions orthonormalised on the
+    quadrature): rows l = |m| .. |m|+L-1 of the normalised associated Legendre
+    functions (no Condon-Shortley sign) times sqrt(w_j), orthonormalised in
+    order of l (QR with a positive diagonal, i.e. Gram-Schmidt)."""
     eta, w = leggauss(L)
-    P = np.array([np.sqrt((2 * l + 1) / 2.0) * eval_legendre(l, eta) * np.sqrt(w) for l in range(L)])
-    return eta, w, P
+    if m == 0:
+        P = np.array([np.sqrt((2 * l + 1) / 2.0) * eval_legendre(l, eta) * np.sqrt(w) for l in range(L)])
+        return eta, w, P
+    m = abs(m)
+    rows = []
+    for l in range(m, m + L):
+        norm = np.sqrt((2 * l + 1) / 2.0 * np.exp(gammaln(l - m + 1) - gammaln(l + m + 1)))
+        rows.append((-1) ** m * norm * lpmv(m, l, eta) * np.sqrt(w))
+    A = np.array(rows)
+    Q, R = np.linalg.qr(A.T)                  # A^T = Q R: rows of Q^T orthonormal, same span in order
+    Q = Q * np.sign(np.diag(R))[None, :]
+    return eta, w, Q.T
 
 
 class Model:
@@ -39,17 +54,17 @@ class Model:
     potential on the grid (default the soft Coulomb -Z / sqrt(r^2 + a2))."""
 
     def __init__(self, N: int, r_max: float, L: int, tau: float, Z: float = 1.0, a2: float = 0.5,
-                 kcorr: bool = False, V=None):
+                 kcorr: bool = False, V=None, m: int = 0):
         self.N, self.r_max, self.L, self.tau = N, r_max, L, tau
         self.dr = r_max / N
         self.r = (np.arange(1, N + 1) - 0.5) * self.dr
         self.V = -Z / np.sqrt(self.r ** 2 + a2) if V is None else np.asarray(V, dtype=np.float64)
-        self.eta, self.w, self.P = angular(L)
-        self.F = [oracle.F_matrix(N, l) for l in range(L)]
-        self.T = [oracle.T_matrix(N, l) for l in range(L)]
-        dk = np.pi / r_max
+        self.eta, self.w, self.P = angular(L, m)
+        self.ls = [abs(m) + i for i in range(L)]          # angular momentum of each channel
+        self.F = [oracle.F_matrix(N, l) for l in self.ls]
+        self.T = [oracle.T_matrix(N, l) for l in self.ls]
         self.kt = []
-        for l in range(L):
+        for l in self.ls:
             if kcorr:
                 from oracle import kcorr as kc
                 self.kt.append(kc.k_table(N, r_max, l))
@@ -91,25 +106,25 @@ class Model:
         psi1 = self.potential_half(psi_eta, E, tau)
         c = self.to_l(psi1)
         coef = np.zeros((L, N), dtype=complex)        # [l][n - 1], n = 1..N
-        for l in range(L):
-            b = self.T[l] @ (self.F[l] @ c[l])
-            b = np.exp(-0.25j * self.kt[l] ** 2 * tau) * b
+        for i, l in enumerate(self.ls):
+            b = self.T[i] @ (self.F[i] @ c[i])
+            b = np.exp(-0.25j * self.kt[i] ** 2 * tau) * b
             s_l = (-1) ** ((l + 1) // 2)
             n = np.arange(N) + oracle.p_of(l)
             slot = np.where(n == 0, N, n) - 1
-            coef[l, slot] = s_l * b
+            coef[i, slot] = s_l * b
         kt = np.arange(1, N + 1) * np.pi / self.r_max
-        il = np.array([1j ** l for l in range(L)])
+        il = np.array([1j ** l for l in self.ls])
         phi = (np.conj(il)[:, None] * self.P).T @ coef                  # [j][n]
         phi = np.exp(1j * A * kt[None, :] * self.eta[:, None] * tau) * phi
         coef = (il[:, None] * self.P) @ phi                              # [l][n]
         c4 = np.empty_like(c)
-        for l in range(L):
+        for i, l in enumerate(self.ls):
             s_l = (-1) ** ((l + 1) // 2)
             n = np.arange(N) + oracle.p_of(l)
             slot = np.where(n == 0, N, n) - 1
-            b = np.exp(-0.25j * self.kt[l] ** 2 * tau) * (s_l * coef[l, slot])
-            c4[l] = self.F[l].T @ (self.T[l].T @ b)
+            b = np.exp(-0.25j * self.kt[i] ** 2 * tau) * (s_l * coef[i, slot])
+            c4[i] = self.F[i].T @ (self.T[i].T @ b)
         psi4 = self.to_eta(c4)
         return self.potential_half(psi4, E, tau)
 

@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "plan.cuh"
@@ -40,6 +41,7 @@ int kinetic_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtyp
 struct dsbt_tdse {
     const dsbt_plan* plan;
     int L, N;
+    int m0;         // |m|: channels are l = m0 .. m0 + L - 1
     double dr, tau, Z, a2;
     double* P;      // [L][L] angular transform
     double* V;      // [N] potential
@@ -108,6 +110,49 @@ void angular_matrix(int L, const std::vector<double>& x, const std::vector<doubl
             }
             P[(size_t)l * L + j] = sqrt((2.0 * l + 1.0) / 2.0) * pl * sqrt(w[j]);
         }
+    }
+}
+
+// m != 0: rows l = m .. m + L - 1 of the normalised associated Legendre
+// functions Pbar_l^m(eta_j) sqrt(w_j) (recurrence in l from Pbar_m^m), then
+// orthonormalised on the L-point rule by modified Gram-Schmidt in order of l
+// (the L-point rule integrates their products exactly only for m = 0).
+void angular_matrix_m(int L, int m, const std::vector<double>& x, const std::vector<double>& w,
+                      std::vector<double>& P) {
+    P.assign((size_t)L * L, 0.0);
+    for (int j = 0; j < L; ++j) {
+        const double z = x[j], sq = sqrt(std::max(0.0, 1.0 - z * z));
+        // Pbar_m^m = sqrt((2m+1)!! / (2 (2m)!!)) (1 - z^2)^(m/2) (Condon-Shortley sign dropped)
+        double pmm = sqrt(0.5);
+        for (int k = 1; k <= m; ++k) pmm *= sqrt((2.0 * k + 1.0) / (2.0 * k)) * sq;
+        double pa = pmm, pb = (L > 1) ? sqrt(2.0 * m + 3.0) * z * pmm : 0.0;   // Pbar_m^m, Pbar_{m+1}^m
+        for (int i = 0; i < L; ++i) {
+            const int l = m + i;
+            double pl;
+            if (i == 0) pl = pa;
+            else if (i == 1) pl = pb;
+            else {
+                const double a = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+                const double b = sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+                pl = a * (z * pb - b * pa);
+                pa = pb;
+                pb = pl;
+            }
+            P[(size_t)i * L + j] = pl * sqrt(w[j]);
+        }
+    }
+    for (int i = 0; i < L; ++i) {   // modified Gram-Schmidt of the rows
+        double* ri = P.data() + (size_t)i * L;
+        for (int k = 0; k < i; ++k) {
+            const double* rk = P.data() + (size_t)k * L;
+            double d = 0.0;
+            for (int j = 0; j < L; ++j) d += ri[j] * rk[j];
+            for (int j = 0; j < L; ++j) ri[j] -= d * rk[j];
+        }
+        double q = 0.0;
+        for (int j = 0; j < L; ++j) q += ri[j] * ri[j];
+        const double inv = 1.0 / sqrt(q);
+        for (int j = 0; j < L; ++j) ri[j] *= inv;
     }
 }
 
@@ -208,7 +253,7 @@ __global__ void __launch_bounds__(256) k_tdse_velocity(double2* c, const double*
                                                        const double* __restrict__ eta,
                                                        const double* __restrict__ knl, double dk, int L,
                                                        int N, const double* __restrict__ A, int aidx,
-                                                       double tau) {
+                                                       double tau, int m0) {
     extern __shared__ __align__(16) unsigned char sm[];
     double* Ps = reinterpret_cast<double*>(sm);                    // [L][L]
     double2* xs = reinterpret_cast<double2*>(Ps + kLMax * kLMax);  // [L][TI]
@@ -217,7 +262,7 @@ __global__ void __launch_bounds__(256) k_tdse_velocity(double2* c, const double*
     const int tid = threadIdx.x;
     for (int k = tid; k < L * L; k += blockDim.x) Ps[k] = P[k];
     for (int k = tid; k < L * TI; k += blockDim.x) {   // gather, half kinetic phase, (-i)^l s_l
-        const int l = k / TI, t = k % TI;
+        const int ch = k / TI, t = k % TI, l = m0 + ch;   // channel ch holds angular momentum l
         const int n = n0 + t;
         double2 v = make_double2(0.0, 0.0);
         if (n <= N) {
@@ -225,7 +270,7 @@ __global__ void __launch_bounds__(256) k_tdse_velocity(double2* c, const double*
             const double km = knl ? knl[(size_t)l * N + sidx] : k_index(l, sidx, N) * dk;
             double sn, cs;
             sincos(-0.25 * km * km * tau, &sn, &cs);
-            v = cmul2(c[(size_t)l * N + sidx], make_double2(cs, sn));
+            v = cmul2(c[(size_t)ch * N + sidx], make_double2(cs, sn));
             if (l & 1) v = make_double2(-v.y, v.x);   // times i
         }
         xs[k] = v;
@@ -251,12 +296,12 @@ __global__ void __launch_bounds__(256) k_tdse_velocity(double2* c, const double*
     }
     __syncthreads();
     for (int k = tid; k < L * TI; k += blockDim.x) {   // back to l, i^l s_l, half kinetic phase, scatter
-        const int l = k / TI, t = k % TI;
+        const int ch = k / TI, t = k % TI, l = m0 + ch;
         const int n = n0 + t;
         if (n > N) continue;
         double2 s = make_double2(0.0, 0.0);
         for (int j = 0; j < L; ++j) {
-            const double pl = Ps[l * L + j];
+            const double pl = Ps[ch * L + j];
             const double2 v = xe[j * TI + t];
             s.x = fma(pl, v.x, s.x);
             s.y = fma(pl, v.y, s.y);
@@ -266,7 +311,7 @@ __global__ void __launch_bounds__(256) k_tdse_velocity(double2* c, const double*
         const double km = knl ? knl[(size_t)l * N + sidx] : k_index(l, sidx, N) * dk;
         double sn, cs;
         sincos(-0.25 * km * km * tau, &sn, &cs);
-        c[(size_t)l * N + sidx] = cmul2(s, make_double2(cs, sn));
+        c[(size_t)ch * N + sidx] = cmul2(s, make_double2(cs, sn));
     }
 }
 
@@ -344,7 +389,7 @@ int step_velocity(const dsbt_tdse* t, const double2* in, double2* out, double2* 
         }
         ProfScope ps(kKTdseAng, st);
         k_tdse_velocity<<<(t->N + TI - 1) / TI, 256, smem, st>>>(c, t->P, t->eta, t->plan->knl, t->plan->dk,
-                                                                 t->L, t->N, A, idx, tau);
+                                                                 t->L, t->N, A, idx, tau, t->m0);
         DSBT_CUDA_TRY(cudaGetLastError());
     }
     rc = grouped_device_call(1, t->plan, counts, DSBT_C128, 0.0, c, out, kws, kws_b, st);
@@ -392,16 +437,23 @@ using namespace dsbt;
 
 extern "C" int dsbt_tdse_create(const dsbt_plan* plan, int L, double tau, double Z, double a2,
                                 dsbt_tdse** out) {
+    return dsbt_tdse_create_m(plan, L, 0, tau, Z, a2, out);
+}
+
+extern "C" int dsbt_tdse_create_m(const dsbt_plan* plan, int L, int m, double tau, double Z, double a2,
+                                  dsbt_tdse** out) {
     DSBT_CHECK_ARG(plan != nullptr && out != nullptr, "dsbt_tdse_create: NULL argument");
     *out = nullptr;
-    DSBT_CHECK_ARG(L >= 1 && L <= kLMax && L - 1 <= plan->l_max,
-                   "dsbt_tdse_create: L=%d must be in [1, min(64, l_max+1)]", L);
+    const int m0 = m < 0 ? -m : m;
+    DSBT_CHECK_ARG(L >= 1 && L <= kLMax && m0 + L - 1 <= plan->l_max,
+                   "dsbt_tdse_create: L=%d, |m|=%d need L <= 64 and |m| + L - 1 <= l_max", L, m0);
     DSBT_CHECK_ARG(plan->T64 != nullptr, "dsbt_tdse_create: the plan needs DSBT_PLAN_FP64");
     DSBT_CHECK_ARG(isfinite(tau) && isfinite(Z) && a2 > 0.0, "dsbt_tdse_create: bad tau/Z/a2");
     dsbt_tdse* t = new (std::nothrow) dsbt_tdse();
     if (!t) return DSBT_ERR_NOMEM;
     t->plan = plan;
     t->L = L;
+    t->m0 = m0;
     t->N = plan->N;
     t->dr = plan->r_max / plan->N;
     t->tau = tau;
@@ -409,7 +461,8 @@ extern "C" int dsbt_tdse_create(const dsbt_plan* plan, int L, double tau, double
     t->a2 = a2;
     gauss_legendre(L, t->eta_h, t->w_h);
     std::vector<double> Ph;
-    angular_matrix(L, t->eta_h, t->w_h, Ph);
+    if (m0 == 0) angular_matrix(L, t->eta_h, t->w_h, Ph);
+    else angular_matrix_m(L, m0, t->eta_h, t->w_h, Ph);
     std::vector<double> Vh(t->N), rh(t->N);
     for (int i = 0; i < t->N; ++i) {
         rh[i] = (i + 0.5) * t->dr;
@@ -488,7 +541,7 @@ extern "C" int dsbt_tdse_propagate(const dsbt_tdse* t, void* psi, const double* 
     TdseWs w;
     ws_layout(t, nsteps, 0, &w, workspace);
     std::vector<int> counts(t->plan->l_max + 1, 0);
-    for (int l = 0; l < t->L; ++l) counts[l] = 1;
+    for (int l = 0; l < t->L; ++l) counts[t->m0 + l] = 1;
     double2* x = (double2*)psi;
     const double tau = tau_sign * t->tau;
     for (int s = 0; s < nsteps; ++s) {
@@ -513,7 +566,7 @@ extern "C" int dsbt_tdse_propagate_velocity(const dsbt_tdse* t, void* psi, const
     TdseWs w;
     ws_layout(t, nsteps, 0, &w, workspace);
     std::vector<int> counts(t->plan->l_max + 1, 0);
-    for (int l = 0; l < t->L; ++l) counts[l] = 1;
+    for (int l = 0; l < t->L; ++l) counts[t->m0 + l] = 1;
     double2* x = (double2*)psi;
     const double tau = tau_sign * t->tau;
     for (int s = 0; s < nsteps; ++s) {
@@ -548,7 +601,7 @@ extern "C" int dsbt_tdse_gradient(const dsbt_tdse* t, const void* psi0, const do
     const size_t sb = state_bytes(t);
     const size_t sstride = a256(sb) / sizeof(double2);
     std::vector<int> counts(t->plan->l_max + 1, 0);
-    for (int l = 0; l < t->L; ++l) counts[l] = 1;
+    for (int l = 0; l < t->L; ++l) counts[t->m0 + l] = 1;
     const double tau = t->tau;
     // forward sweep with checkpoints every K steps
     DSBT_CUDA_TRY(cudaMemcpyAsync(w.ckpt, psi0, sb, cudaMemcpyDeviceToDevice, st));

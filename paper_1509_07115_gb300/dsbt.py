@@ -84,6 +84,7 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_tdse_destroy.argtypes = [vp]
         lib.dsbt_tdse_angular.argtypes = [vp, vp, vp, vp]
         lib.dsbt_tdse_set_potential.argtypes = [vp, vp, i]
+        lib.dsbt_tdse_create_m.argtypes = [vp, i, i, d, d, d, ctypes.POINTER(vp)]
         lib.dsbt_tdse_propagate_velocity.argtypes = [vp, vp, vp, vp, i, i, d, vp, sz, vp]
         lib.dsbt_tdse_workspace_size.argtypes = [vp, i, i]
         lib.dsbt_tdse_workspace_size.restype = sz
@@ -441,10 +442,10 @@ class Tdse:
     """Split-operator TDSE (m = 0, length gauge) through the DSBT: see
     dsbt_tdse_* in include/dsbt.h.  State: complex128 CUDA tensor [L][N]."""
 
-    def __init__(self, plan: Plan, L: int, tau: float, Z: float = 1.0, a2: float = 0.5):
+    def __init__(self, plan: Plan, L: int, tau: float, Z: float = 1.0, a2: float = 0.5, m: int = 0):
         h = ctypes.c_void_p()
-        _check(load().dsbt_tdse_create(plan.handle, int(L), float(tau), float(Z), float(a2), ctypes.byref(h)),
-               "dsbt_tdse_create")
+        _check(load().dsbt_tdse_create_m(plan.handle, int(L), int(m), float(tau), float(Z), float(a2),
+                                         ctypes.byref(h)), "dsbt_tdse_create_m")
         self._h, self.plan, self.L, self.N, self.tau = h, plan, int(L), plan.N, float(tau)
         self._ws = None
 

@@ -55,3 +55,19 @@ def state(r, dr, L, T, omega, nquad=200, kick=0.0):
     psi = np.pi ** -0.75 * np.exp(-(r[None, :] ** 2 + a * a) / 2 - 1j * p * a + 1j * (g - T)
                                  + (a + 1j * (p + kick)) * r[None, :] * x[:, None])
     return np.sqrt(dr) * r[None, :] * (np.sqrt(2 * np.pi) * (Pb * w) @ psi)
+
+
+def state_on_grid(r, dr, eta, w, T, omega, m):
+    """Exact length-gauge state at time T sampled on the DVR grid (eta_j, r_i):
+    psi[j][i] = R(r_i, eta_j) r_i sqrt(dr w_j) sqrt(2 pi), where Psi = R e^{i m phi}.
+    m = 0: the displaced ground state; m = 1: the displaced state
+    pi^{-3/4} (x + i y) exp(-(x^2 + y^2)/2) exp(-(z - a)^2/2 + ...), whose x, y
+    factor has energy 2 (phase exp(-2 i t))."""
+    a, p, g = classical(T, omega) if T > 0 else (0.0, 0.0, 0.0)
+    rr, ee = r[None, :], eta[:, None]
+    rho2 = rr * rr * (1 - ee * ee)
+    z = rr * ee
+    Rm = np.pi ** -0.75 * np.exp(-rho2 / 2 - (z - a) ** 2 / 2 + 1j * p * (z - a) + 1j * (g - (1 + m) * T))
+    if m == 1:
+        Rm = Rm * rr * np.sqrt(1 - ee * ee)
+    return Rm * rr * np.sqrt(dr * w[:, None]) * np.sqrt(2 * np.pi)

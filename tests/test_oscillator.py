@@ -17,7 +17,7 @@ import torch
 
 from oracle import tdse as otdse
 
-from _oscillator import field, state, vector_potential, velocity_state
+from _oscillator import field, state, state_on_grid, vector_potential, velocity_state
 
 OMEGA, L, DR, TAU, STEPS = 2.0, 16, 0.05, 0.005, 628
 
@@ -125,3 +125,55 @@ def test_gpu_oscillator_velocity_gauge(lib):
     dc2 = gpu_delta(lib, 25.6, True, velocity=True)[0]
     assert 3.0 < du / du2 < 5.0, (du, du2)
     assert dc < du / 2.5 and dc2 < du2 / 2.5, (du, dc, du2, dc2)
+
+
+def delta_oracle_m1(r_max, kcorr):
+    """m = 1 state (x + i y) exp(-(x^2+y^2)/2) times the displaced z factor."""
+    N = int(round(r_max / DR))
+    r = (np.arange(N) + 0.5) * DR
+    m = otdse.Model(N, r_max, L, TAU, V=0.5 * r * r, kcorr=kcorr, m=1)
+    x = state_on_grid(r, DR, m.eta, m.w, 0.0, OMEGA, 1)
+    for s in range(STEPS):
+        x = m.step(x, field((s + 0.5) * TAU, OMEGA))
+    c = m.to_l(x)
+    ex = m.to_l(state_on_grid(r, DR, m.eta, m.w, STEPS * TAU, OMEGA, 1))
+    return abs(1 - np.vdot(ex, c)), c, m
+
+
+def test_oracle_oscillator_m1():
+    """Channels l = 1..16 with the associated Legendre basis orthonormalised on
+    the rule: k~_n error ~1.7e-2 at r_max = 12.8, k_nl ~4.7x smaller."""
+    d_u, _, m = delta_oracle_m1(12.8, False)
+    d_c, _, _ = delta_oracle_m1(12.8, True)
+    assert np.abs(m.P @ m.P.T - np.eye(L)).max() < 1e-13
+    assert 5e-3 < d_u < 5e-2, d_u
+    assert d_c < d_u / 3.5, (d_u, d_c)
+
+
+@pytest.mark.gpu
+def test_gpu_oscillator_m1(lib):
+    out = {}
+    for r_max in (12.8, 25.6):
+        N = int(round(r_max / DR))
+        r = (np.arange(N) + 0.5) * DR
+        for kc in (False, True):
+            plan = lib.Plan(N, r_max, L, tf32x3=False, kcorr=kc)     # channels l = 1..16
+            td = lib.Tdse(plan, L, TAU, m=1)
+            td.set_potential(0.5 * r * r)
+            eta, w, P = td.angular()
+            o = np.argsort(eta)
+            psi = torch.from_numpy(P @ state_on_grid(r, DR, eta, w, 0.0, OMEGA, 1)).cuda()
+            E = torch.tensor([field((s + 0.5) * TAU, OMEGA) for s in range(STEPS)], dtype=torch.float64)
+            td.propagate(psi, E, STEPS, 1)
+            c = psi.cpu().numpy()
+            ex = P @ state_on_grid(r, DR, eta, w, STEPS * TAU, OMEGA, 1)
+            out[(r_max, kc)] = abs(1 - np.vdot(ex, c))
+            if r_max == 12.8:
+                d, oc, m = delta_oracle_m1(12.8, kc)
+                om = np.argsort(m.eta)
+                assert np.abs(P[:, o] - m.P[:, om]).max() < 1e-13          # same angular basis
+                assert np.abs(c - oc).max() < 1e-11
+            td.close()
+            plan.close()
+    assert 3.0 < out[(12.8, False)] / out[(25.6, False)] < 5.0, out
+    assert out[(12.8, True)] < out[(12.8, False)] / 3.5 and out[(25.6, True)] < out[(25.6, False)] / 3.5, out
