@@ -19,9 +19,13 @@
 // N/16 threads per line and several lines per CTA when N/16 < 256.  Shared
 // memory is padded by one element every 16, which makes every stage's loads
 // and stores free of bank conflicts.  Twiddles of a radix-16 butterfly come
-// from two table loads (w, w^4) and products of depth <= 3.  Global accesses
-// move two complex values per thread (16 or 32 bytes), the pair (x_{2j},
-// x_{2j+1}) that the reordering sends to v_j and v_{N-1-j}.
+// from two table loads (w, w^4) and products of depth <= 3.  The forward
+// transform's global loads move two complex values per thread (16 or 32
+// bytes), the pair (x_{2j}, x_{2j+1}) that the reordering sends to v_j and
+// v_{N-1-j}, through shared memory; the inverse runs its first radix-16 stage
+// on the V_k it has just formed in registers.  (Loading each thread's first
+// butterfly inputs straight from global memory in the forward transform made
+// it slower: the stride-2 loads cost more than the shared-memory pass.)
 #include "plan.cuh"
 
 namespace dsbt {
@@ -221,9 +225,8 @@ __device__ __forceinline__ void stockham_last_odd(C* s, const C* __restrict__ tw
 // stage for the rest of the power of two and, when Q > 1, one radix-Q stage
 // (sroot is a 32-entry shared scratch for its roots).
 template <int Q, typename C>
-__device__ __forceinline__ void fft_smem(C* s, const C* __restrict__ tw, C* sroot, int N, int lt, int T) {
-    int Ls = 1;
-    int rem = N;
+__device__ __forceinline__ void fft_stages(C* s, const C* __restrict__ tw, C* sroot, int N, int lt, int T, int Ls,
+                                           int rem) {
     while ((rem & 15) == 0) {
         stockham_stage<16>(s, tw, N, Ls, lt, T);
         Ls *= 16;
@@ -236,6 +239,22 @@ __device__ __forceinline__ void fft_smem(C* s, const C* __restrict__ tw, C* sroo
     for (int m = threadIdx.x; m < Q; m += blockDim.x) sroot[m] = tw[m * (N / Q)];   // W_Q^m
     __syncthreads();
     stockham_last_odd<(Q > 1 ? Q : 3)>(s, tw, sroot, N, lt, T);   // Ls = N / Q here
+}
+
+// Forward FFT of length N = 256 q whose input is already in registers:
+// x[r] = element lt + r T of the line (T = N/16), i.e. exactly the inputs of
+// butterfly lt of the first radix-16 Stockham stage (Ls = 1, no twiddles).
+// That stage runs on the registers and writes its outputs 16 lt + q to the
+// line's shared buffer s, then the remaining stages follow (fft_stages).
+// The caller must have finished every read of s before the call.
+template <int Q, typename C>
+__device__ __forceinline__ void fft_from_registers(C* s, C* x, const C* __restrict__ tw, C* sroot, int N, int lt,
+                                                   int T) {
+    dft16(x);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s[padi(16 * lt + q)] = x[q];
+    __syncthreads();
+    fft_stages<Q>(s, tw, sroot, N, lt, T, 16, N >> 4);
 }
 
 __device__ __forceinline__ int find_group(const GroupTable& g, int chan) {
@@ -328,7 +347,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
     }
     __syncthreads();
     __shared__ C sroot[32];
-    fft_smem<Q>(s, tw, sroot, N, lt, T);
+    fft_stages<Q>(s, tw, sroot, N, lt, T, 1, N);
     if (!live) return;
     const R sc1 = (R)sqrt(2.0 / (double)N), sc0 = (R)sqrt(1.0 / (double)N);
     const int line = g.line0[gi] + (cplx ? 2 * local : local);
@@ -441,12 +460,9 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_inv(GroupTa
         vk[u].x = v.x;
         vk[u].y = -v.y;
     }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 16; ++u) s[padi(lt + u * T)] = vk[u];
-    __syncthreads();
+    __syncthreads();   // every read of X from s is done
     __shared__ C sroot[32];
-    fft_smem<Q>(s, tw, sroot, N, lt, T);
+    fft_from_registers<Q>(s, vk, tw, sroot, N, lt, T);
     if (!live) return;
     const R invN = (R)(1.0 / (double)N);
     for (int j = lt; j < (N >> 1); j += T) {
