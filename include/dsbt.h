@@ -66,6 +66,15 @@ extern "C" {
 #define DSBT_PLAN_TF32X3 2 /* split-TF32 T_l and T_l^T (for DSBT_F32 / DSBT_C64)  */
 #define DSBT_PLAN_KCORR 4  /* kinetic phase with the corrected momenta k_nl (Sec. 3,
                               Eq. (kcorr)) instead of k~_n (see dsbt_plan_get_k) */
+#define DSBT_PLAN_FAST64 8 /* with DSBT_PLAN_FP64, N / 64 a power of two: FP64
+                              contractions on planar lines (the kinetic step, the
+                              TDSE) in O(N l log N) work instead of N^2/2: rows of
+                              T_l are polynomials in m left of the diagonal, applied
+                              through a tree of interval moments in orthonormal
+                              polynomial bases (stable counterpart of Sec. 2.6).
+                              Extra memory: 8 B x 64 x (l_max+1) x N x log2(N/64)
+                              of plan data; FP64 workspaces grow by about
+                              8 B x 128 x (N/64) per line. */
 
 /* element types of the caller's arrays */
 #define DSBT_F64 1  /* real double                 */

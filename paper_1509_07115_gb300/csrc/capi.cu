@@ -73,6 +73,7 @@ struct Workspace {
     double* f64a;
     double* f64b;
     double2* ph64;
+    double* fast;    // scratch of the DSBT_PLAN_FAST64 contraction (or nullptr)
     // TF32 path
     float* hi_a;
     float* lo_a;
@@ -92,7 +93,8 @@ size_t ws_bytes(const dsbt_plan* p, int total_channels, int dtype) {
     const int N = p->N;
     const size_t PR = (size_t)phase_rows(p) * N;
     if (is_fp64(dtype))
-        return align256(R * N * sizeof(double)) * 2 + align256(PR * sizeof(double2)) + 256;
+        return align256(R * N * sizeof(double)) * 2 + align256(PR * sizeof(double2)) +
+               align256(fast_scratch_bytes(p, (int)R)) + 256;
     return align256(R * N * sizeof(float)) * 4 + align256(PR * sizeof(float2)) + 256 + 256;
 }
 
@@ -107,6 +109,7 @@ Workspace carve(const dsbt_plan* pl, void* base, int total_channels, int dtype) 
         w.f64a = (double*)p;
         w.f64b = (double*)(p + b);
         w.ph64 = (double2*)(p + 2 * b);
+        w.fast = pl->fast ? (double*)(p + 2 * b + align256(PR * sizeof(double2))) : nullptr;
     } else {
         const size_t b = align256(R * N * sizeof(float));
         w.hi_a = (float*)p;
@@ -225,8 +228,8 @@ int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, 
         }
         DSBT_CUDA_TRY(cudaGetLastError());
         rc = dct_forward_f64(p, g, true, (const double*)in, w.f64a, st);
-        if (!rc) rc = contract_f64(p, g, +1, w.f64a, 0, w.f64b, 0, w.ph64, st);
-        if (!rc) rc = contract_f64(p, g, -1, w.f64b, 0, w.f64a, 0, nullptr, st);
+        if (!rc) rc = contract_f64(p, g, +1, w.f64a, 0, w.f64b, 0, w.ph64, st, w.fast);
+        if (!rc) rc = contract_f64(p, g, -1, w.f64b, 0, w.f64a, 0, nullptr, st, w.fast);
         if (!rc) rc = dct_inverse_f64(p, g, true, w.f64a, (double*)out, st);
         return rc;
     }

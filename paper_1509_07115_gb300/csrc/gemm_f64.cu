@@ -250,7 +250,7 @@ static void launch_rows(dim3 grid, cudaStream_t st, const GroupTable& g, const d
 }  // namespace
 
 int contract_f64(const dsbt_plan* p, const GroupTable& g, int dir, const double* in, int in_cplx,
-                 double* out, int out_cplx, const double2* phase, cudaStream_t st) {
+                 double* out, int out_cplx, const double2* phase, cudaStream_t st, double* fast_scratch) {
     if (!p->T64) {
         set_error("FP64 path needs a plan built with DSBT_PLAN_FP64");
         return DSBT_ERR_UNSUPPORTED;
@@ -259,6 +259,8 @@ int contract_f64(const dsbt_plan* p, const GroupTable& g, int dir, const double*
         set_error("contract_f64: phase only on the forward contraction");
         return DSBT_ERR_INVALID;
     }
+    if (p->fast && fast_scratch && !in_cplx && !out_cplx && g.ngroups > 0)   // planar lines: O(N l log N) path
+        return contract_f64_fast(p, g, dir, in, out, phase, fast_scratch, st);
     const int N = p->N;
     const int per_l = p->knl != nullptr;   // phase table rows per l (corrected momenta) or by parity
     int max_ct = 0, any_wide = 0, any_narrow = 0;

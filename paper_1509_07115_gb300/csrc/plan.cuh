@@ -7,6 +7,8 @@
 
 #include "common.cuh"
 
+namespace dsbt { struct FastData; }
+
 struct dsbt_plan {
     int N;
     int l_max;
@@ -36,6 +38,8 @@ struct dsbt_plan {
     // corrected momenta [(l_max+1)][N] of DSBT_PLAN_KCORR (else nullptr: the
     // kinetic phase uses k~_n = n dk by parity)
     double* knl;
+    // hierarchical FP64 data of DSBT_PLAN_FAST64 (fast64.cu), else nullptr
+    dsbt::FastData* fast;
     unsigned* status;          // device status word (kStatusOk / kStatusTimeout)
     double check_err;
     bool has_tmaps;
@@ -102,7 +106,15 @@ int dct_inverse_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const fl
 // phase: optional complex phase per coefficient applied to the result (kinetic
 // step), indexed [parity][N] as double2; nullptr for none.
 int contract_f64(const dsbt_plan* p, const GroupTable& g, int dir, const double* in, int in_cplx,
-                 double* out, int out_cplx, const double2* phase, cudaStream_t st);
+                 double* out, int out_cplx, const double2* phase, cudaStream_t st,
+                 double* fast_scratch = nullptr);
+// DSBT_PLAN_FAST64 (fast64.cu)
+bool fast_supported(int N);
+int fast_build(dsbt_plan* p, cudaStream_t st);
+void fast_free(dsbt_plan* p);
+size_t fast_scratch_bytes(const dsbt_plan* p, int lines);
+int contract_f64_fast(const dsbt_plan* p, const GroupTable& g, int dir, const double* in, double* out,
+                      const double2* phase, double* scratch, cudaStream_t st);
 
 // ---- split-TF32 tensor-core contraction (gemm_tf32x3.cu)
 // B operand: TF32 split lines [lines][N] (hi, lo).  `sched` is a device int
