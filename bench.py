@@ -306,11 +306,32 @@ def tdse_leg(dsbt, inputs, torch, dev):
     achieved = flop / (ms64 / n64 * 1e-3) / 1e12
     td.close()
     plan.close()
+    # the same propagation with the O(N l log N) FP64 contraction (DSBT_PLAN_FAST64)
+    fplan = dsbt.Plan(Nt, 204.8, L - 1, tf32x3=False, fast64=True)
+    ftd = dsbt.Tdse(fplan, L, tau)
+    psif = psi0.clone()
+    ftd.propagate(psif, E, 20, 2)
+    torch.cuda.synchronize()
+    psif = psi0.clone()
+    dsbt.profile_enable(True)
+    e0.record(st)
+    ftd.propagate(psif, E, steps, 2)
+    e1.record(st)
+    torch.cuda.synchronize()
+    fast_ms = e0.elapsed_time(e1)
+    fprof = dsbt.profile_read()
+    dsbt.profile_enable(False)
+    fast_dev = (psif - psi).abs().max().item()
+    ftd.close()
+    fplan.close()
     return {"config": "m=0, l=0..63, N=2048, dr=0.1, 400 steps of 0.05, soft-Coulomb -1/sqrt(r^2+0.5), "
                       "200 field samples held 2 steps, observable = norm beyond r=50, checkpoint every 20",
             "propagate_ms_per_step": prop_ms / steps, "gradient_ms_total": grad_ms,
             "norm_drift_400_steps": drift, "observable": O.item(),
             "kernels_ms_per_step": {k: v[1] / steps for k, v in prof.items()},
+            "fast64": {"propagate_ms_per_step": fast_ms / steps,
+                       "kernels_ms_per_step": {k: v[1] / steps for k, v in fprof.items()},
+                       "max_abs_diff_vs_dense": fast_dev},
             "roofline_contract_f64": {"bound": "fp64", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
                                       "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
                                       "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}}
