@@ -81,9 +81,11 @@ __global__ void k_fast_beta(const double* __restrict__ T64, const double* __rest
 
 struct FastArgs {
     const double* Q;       // all levels, [len_j][KM] at qoff[j]
+    const double* QT;      // all levels, [KM][len_j] at qoff[j]
     const size_t* qoff;
-    const double* A;       // [levels][2][KM][KM] (level 0 unused)
     const double* beta;    // [L][levels][N][KM]
+    const double* betaT;   // [L][levels][KM][N]
+    const double* nearT;   // [L][nleaf][FB][FB]: nearT[l][J][c][t] = T_l[J B + t][J B + c]
     const double* T64;
     int N, nleaf, levels, R;
 };
@@ -95,142 +97,213 @@ __device__ __forceinline__ size_t mpos(const FastArgs& a, int j, int i, int line
     return off + ((size_t)i * a.R + line) * KM + k;
 }
 
-// Leaf moments M_0[leaf][line][k] = sum_t Q_0[t][k] sqrt(w) f[line][leaf B + t].
-__global__ void k_fast_leaf_moments(FastArgs a, GroupTable g, const double* __restrict__ in, double* M) {
-    const int leaf = blockIdx.x, gi = blockIdx.y;
+// Groups are ordered by l, and the work of a block grows with l.  Projection
+// blocks take their group through this interleaving (0, n-1, 1, n-2, ...) so
+// that every run of consecutive blocks mixes light and heavy groups.
+__device__ __forceinline__ int interleave(int t, int n) { return (t & 1) ? n - 1 - (t >> 1) : (t >> 1); }
+
+constexpr int PROJ_THREADS = 256;
+
+// Interval i of level j is used when its right sibling exists (i even): the
+// rows of the sibling take it as a far interval.  Level j has nleaf >> (j+1)
+// used intervals, its rows are cut into nch_j <= 32 chunks, and a block takes
+// PROJ_THREADS / nch_j (line, k) pairs.  Blocks run over (level, tile, interval,
+// group), largest intervals first.
+__device__ __forceinline__ int proj_chunks(int j) { return min(32, 1 << j); }
+
+__device__ __forceinline__ bool proj_block(const FastArgs& a, int ngroups, int pmax, int b, int& j, int& gi,
+                                           int& i, int& tile) {
+    for (j = a.levels - 1; j >= 0; --j) {
+        const int used = a.nleaf >> (j + 1);
+        const int per = PROJ_THREADS / proj_chunks(j);
+        const int count = used * ngroups * ((pmax + per - 1) / per);
+        if (b < count) {
+            gi = interleave(b % ngroups, ngroups);
+            b /= ngroups;
+            i = 2 * (b % used);
+            tile = b / used;
+            return true;
+        }
+        b -= count;
+    }
+    return false;
+}
+
+// Projections onto the bases of the used intervals:
+//   forward (dir > 0): M_j[i][line][k] = sum_{t in I} Q_j[t][k] sqrt(w_t) f[line][t]
+//   inverse (dir < 0): W_j[i][line][k] = sum_{r in sibling} beta_{r,j}[k] b[line][r]
+// over the (line, k) pairs p = line K + k of a group (beta is zero on
+// completion rows, so those rows drop out).  Both operands are [row][KM].
+// Lane = (pair, chunk): a lane sums one chunk of len / nch rows, then the nch
+// lanes of a pair add their sums by shuffles.
+__global__ void __launch_bounds__(PROJ_THREADS) k_fast_project(FastArgs a, GroupTable g, int dir, int pmax,
+                                                               const double* __restrict__ in,
+                                                               double* __restrict__ out) {
+    int j, gi, i, tile;
+    if (!proj_block(a, g.ngroups, pmax, blockIdx.x, j, gi, i, tile)) return;
     const int l = g.l[gi], K = l, line0 = g.line0[gi], nl = g.line0[gi + 1] - line0;
-    const double* Q0 = a.Q + a.qoff[0];
-    for (int p = threadIdx.x; p < nl * K; p += blockDim.x) {
-        const int line = p / K, k = p % K;
-        const double* x = in + (size_t)(line0 + line) * a.N + leaf * FB;
-        double s = 0.0;
-        for (int t = 0; t < FB; ++t) s = fma(Q0[(size_t)t * KM + k], sqrt_w(l, leaf * FB + t) * x[t], s);
-        M[mpos(a, 0, leaf, line0 + line, k)] = s;
+    const int P = nl * K;
+    const int nch = proj_chunks(j), ppw = 32 / nch;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pw = (tile * (PROJ_THREADS / 32) + warp) * ppw;   // first pair of the warp
+    if (pw >= P) return;                                          // whole warp idle
+    const int q = lane & (nch - 1), pq = pw + lane / nch;
+    const int N = a.N, len = FB << j, clen = len / nch;
+    const int t0 = dir > 0 ? i * len : (i + 1) * len;
+    double acc = 0.0;
+    if (pq < P) {
+        const int line = pq / K, k = pq % K;
+        const double* x = in + (size_t)(line0 + line) * N + t0 + q * clen;
+        const double* o = (dir > 0 ? a.Q + a.qoff[j] : a.beta + (((size_t)l * a.levels + j) * N + t0) * KM) +
+                          (size_t)q * clen * KM + k;
+        const double x0 = (dir > 0 && t0 + q * clen == 0) ? sqrt_w(l, 0) * x[0] : x[0];
+        acc = o[0] * x0;
+#pragma unroll 8
+        for (int t = 1; t < clen; ++t) acc = fma(o[(size_t)t * KM], x[t], acc);
+    }
+    for (int s = nch >> 1; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+    if (q == 0 && pq < P) out[mpos(a, j, i, line0 + pq / K, pq % K)] = acc;
+}
+
+__device__ __forceinline__ void store_pair(double* out, size_t o0, int N, double s0, double s1, bool two,
+                                           const double2* phase, double2 ph) {
+    if (phase) {
+        out[o0] = s0 * ph.x - s1 * ph.y;
+        out[o0 + N] = s0 * ph.y + s1 * ph.x;
+    } else {
+        out[o0] = s0;
+        if (two) out[o0 + N] = s1;
     }
 }
 
-// Parent moments from children: M_j[i][k] = sum_k' (M_{j-1}[2i][k'] A0[k'][k] + M_{j-1}[2i+1][k'] A1[k'][k]).
-__global__ void k_fast_merge(FastArgs a, GroupTable g, int j, double* M) {
-    const int i = blockIdx.x, gi = blockIdx.y;
-    const int K = g.l[gi], line0 = g.line0[gi], nl = g.line0[gi + 1] - line0;
-    const double* A0 = a.A + ((size_t)j * 2 + 0) * KM * KM;
-    const double* A1 = a.A + ((size_t)j * 2 + 1) * KM * KM;
-    for (int p = threadIdx.x; p < nl * K; p += blockDim.x) {
-        const int line = line0 + p / K, k = p % K;
-        const double* c0 = M + mpos(a, j - 1, 2 * i, line, 0);
-        const double* c1 = M + mpos(a, j - 1, 2 * i + 1, line, 0);
-        double s = 0.0;
-        for (int q = 0; q < K; ++q) s = fma(c0[q], A0[(size_t)q * KM + k], fma(c1[q], A1[(size_t)q * KM + k], s));
-        M[mpos(a, j, i, line, k)] = s;
-    }
-}
-
-// b[line][r] = completion rows densely; regular rows: near field + far field;
-// optional kinetic phase on the (re, im) line pairs.  One thread per row.
-__global__ void __launch_bounds__(128) k_fast_eval(FastArgs a, GroupTable g, const double* __restrict__ in,
-                                                   const double* __restrict__ M, double* __restrict__ out,
-                                                   const double2* __restrict__ phase, int per_l) {
-    const int gi = blockIdx.y;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+// Forward output, lines in pairs (with a kinetic phase the pairs are the
+// (re, im) lines of a channel).  blockIdx.x < nleaf: leaf J, one thread per
+// regular row r = J B + t: near field sum_{c <= r in J} T_rc f_c from the
+// transposed leaf block, far field sum_j beta_{r,j} . M_j over the set bits j
+// of J.  blockIdx.x >= nleaf: completion rows, one warp per row (dense dot).
+__global__ void __launch_bounds__(FB) k_fast_eval(FastArgs a, GroupTable g, const double* __restrict__ in,
+                                                  const double* __restrict__ M, double* __restrict__ out,
+                                                  const double2* __restrict__ phase, int per_l) {
+    const int gi = gridDim.y - 1 - blockIdx.y, xb = blockIdx.x;   // largest l first
     const int l = g.l[gi], K = l, line0 = g.line0[gi], nl = g.line0[gi + 1] - line0;
-    const int N = a.N;
-    if (r >= N) return;
-    const double* Trow = a.T64 + ((size_t)l * N + r) * N;
-    const int J = r / FB, ne = n_extra(l);
+    const int N = a.N, ne = n_extra(l);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (xb >= a.nleaf) {
+        const int r = (xb - a.nleaf) * (FB / 32) + w;
+        if (r >= ne) return;
+        const double* Trow = a.T64 + ((size_t)l * N + r) * N;
+        double2 ph = make_double2(1.0, 0.0);
+        if (phase) ph = per_l ? phase[(size_t)l * N + r] : phase[(size_t)(l & 1) * N + phase_entry(l, r, N)];
+        for (int line = 0; line < nl; line += 2) {
+            const bool two = line + 1 < nl;
+            const double* x0 = in + (size_t)(line0 + line) * N;
+            const double* x1 = two ? x0 + N : x0;
+            double s0 = 0.0, s1 = 0.0;
+            for (int c = lane; c < N; c += 32) {
+                const double t = Trow[c];
+                s0 = fma(t, x0[c], s0);
+                s1 = fma(t, x1[c], s1);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            }
+            if (lane == 0) store_pair(out, (size_t)(line0 + line) * N + r, N, s0, s1, two, phase, ph);
+        }
+        return;
+    }
+    const int J = xb, r = J * FB + threadIdx.x;
+    if (J * FB + w * 32 + 31 < ne) return;   // the whole warp holds completion rows
+    const double* nt = a.nearT + (((size_t)l * a.nleaf + J) * FB) * FB + threadIdx.x;
+    const int cmax = (w + 1) * 32;           // T_rc = 0 for c > r
     double2 ph = make_double2(1.0, 0.0);
     if (phase) ph = per_l ? phase[(size_t)l * N + r] : phase[(size_t)(l & 1) * N + phase_entry(l, r, N)];
-    for (int line = 0; line < nl; line += (phase ? 2 : 1)) {
-        double acc[2] = {0.0, 0.0};
-        const int np = phase ? 2 : 1;
-        for (int h = 0; h < np; ++h) {
-            const double* x = in + (size_t)(line0 + line + h) * N;
-            double s = 0.0;
-            if (r < ne) {
-                for (int c = 0; c < N; ++c) s = fma(Trow[c], x[c], s);
-            } else {
-                for (int c = J * FB; c <= r; ++c) s = fma(Trow[c], x[c], s);
-                for (int j = 0; j < a.levels; ++j) {
-                    if (!((J >> j) & 1)) continue;
-                    const int i = (J >> j) - 1;
-                    const double* be = a.beta + (((size_t)l * a.levels + j) * N + r) * KM;
-                    const double* m = M + mpos(a, j, i, line0 + line + h, 0);
-                    for (int k = 0; k < K; ++k) s = fma(be[k], m[k], s);
-                }
+    for (int line = 0; line < nl; line += 2) {
+        const bool two = line + 1 < nl;
+        const double* x0 = in + (size_t)(line0 + line) * N + J * FB;
+        const double* x1 = two ? x0 + N : x0;
+        double s0 = 0.0, s1 = 0.0;
+        for (int c = 0; c < cmax; ++c) {
+            const double t = nt[(size_t)c * FB];
+            s0 = fma(t, x0[c], s0);
+            s1 = fma(t, x1[c], s1);
+        }
+        for (int j = 0; j < a.levels; ++j) {
+            if (!((J >> j) & 1)) continue;
+            const int i = (J >> j) - 1;
+            const double* be = a.betaT + (((size_t)l * a.levels + j) * KM) * N + r;
+            const double* m0 = M + mpos(a, j, i, line0 + line, 0);
+            const double* m1 = two ? m0 + KM : m0;
+            for (int k = 0; k < K; ++k) {
+                const double b = be[(size_t)k * N];
+                s0 = fma(b, m0[k], s0);
+                s1 = fma(b, m1[k], s1);
             }
-            acc[h] = s;
         }
-        if (phase) {
-            const double re = acc[0] * ph.x - acc[1] * ph.y, im = acc[0] * ph.y + acc[1] * ph.x;
-            out[(size_t)(line0 + line) * N + r] = re;
-            out[(size_t)(line0 + line + 1) * N + r] = im;
-        } else {
-            out[(size_t)(line0 + line) * N + r] = acc[0];
-        }
+        if (r >= ne) store_pair(out, (size_t)(line0 + line) * N + r, N, s0, s1, two, phase, ph);
     }
 }
 
-// W_j[i][line][k] = sum over the rows of interval i's right sibling (regular
-// rows only) of beta_{r,j}[k] b[line][r]; intervals whose sibling is missing
-// or that no row uses stay zero.  Grid (interval slot, group), all levels.
-__global__ void k_fast_w(FastArgs a, GroupTable g, const double* __restrict__ in, double* W) {
-    int slot = blockIdx.x, j = 0;
-    while (j < a.levels && slot >= (a.nleaf >> j)) { slot -= a.nleaf >> j; ++j; }
-    const int i = slot, gi = blockIdx.y;
+// Inverse output f = T^T b, one thread per column c of leaf J = blockIdx.x:
+// completion rows (dense), near field sum_{r >= c in J} T_rc b_r (T_rc = 0 for
+// r < c, so a warp starts at its first column), far field
+// sqrt(w_c) sum_j (Q_j W_j[i])_c over the levels j whose interval i holding c
+// is used.
+__global__ void __launch_bounds__(FB) k_fast_leaf_out(FastArgs a, GroupTable g, const double* __restrict__ in,
+                                                      const double* __restrict__ W, double* __restrict__ out) {
+    const int gi = gridDim.y - 1 - blockIdx.y, J = blockIdx.x;   // largest l first
     const int l = g.l[gi], K = l, line0 = g.line0[gi], nl = g.line0[gi + 1] - line0;
-    const int N = a.N, len = FB << j;
-    const bool used = (i & 1) == 0 && (i + 1) < (a.nleaf >> j);
-    const int r0 = max((i + 1) * len, n_extra(l)), r1 = min((i + 2) * len, N);
-    for (int p = threadIdx.x; p < nl * K; p += blockDim.x) {
-        const int line = line0 + p / K, k = p % K;
-        double s = 0.0;
-        if (used) {
-            const double* x = in + (size_t)line * N;
-            const double* be = a.beta + (((size_t)l * a.levels + j) * N) * KM + k;
-            for (int r = r0; r < r1; ++r) s = fma(be[(size_t)r * KM], x[r], s);
-        }
-        W[mpos(a, j, i, line, k)] = s;
-    }
-}
-
-// Push W from level j to level j-1: W_{j-1}[2i+h][k'] += sum_k A_h[k'][k] W_j[i][k].
-__global__ void k_fast_push(FastArgs a, GroupTable g, int j, double* W) {
-    const int i = blockIdx.x, gi = blockIdx.y;
-    const int K = g.l[gi], line0 = g.line0[gi], nl = g.line0[gi + 1] - line0;
-    for (int p = threadIdx.x; p < 2 * nl * K; p += blockDim.x) {
-        const int h = p / (nl * K), rest = p % (nl * K);
-        const int line = line0 + rest / K, kq = rest % K;
-        const double* Ah = a.A + ((size_t)j * 2 + h) * KM * KM + (size_t)kq * KM;
-        const double* w = W + mpos(a, j, i, line, 0);
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) s = fma(Ah[k], w[k], s);
-        W[mpos(a, j - 1, 2 * i + h, line, kq)] += s;
-    }
-}
-
-// f[line][c] = sqrt(w_c) (Q_0 W_leaf)_c + near field (rows of c's leaf at or
-// below the diagonal) + completion rows.  One thread per column.
-__global__ void __launch_bounds__(128) k_fast_leaf_out(FastArgs a, GroupTable g, const double* __restrict__ in,
-                                                       const double* __restrict__ W, double* __restrict__ out) {
-    const int gi = blockIdx.y;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int l = g.l[gi], K = l, line0 = g.line0[gi], nl = g.line0[gi + 1] - line0;
-    const int N = a.N;
-    if (c >= N) return;
-    const double* T = a.T64 + (size_t)l * N * N;
-    const int leaf = c / FB, ne = n_extra(l);
-    const double* Q0 = a.Q + a.qoff[0] + (size_t)(c - leaf * FB) * KM;
+    const int N = a.N, ne = n_extra(l);
+    const int c = J * FB + threadIdx.x, w = threadIdx.x >> 5;
+    const double* T = a.T64 + (size_t)l * N * N + c;
     const double sw = sqrt_w(l, c);
-    const int r_lo = max(c, ne), r_hi = min((leaf + 1) * FB, N);
-    for (int line = 0; line < nl; ++line) {
-        const double* x = in + (size_t)(line0 + line) * N;
-        double s = 0.0;
-        for (int r = 0; r < ne; ++r) s = fma(T[(size_t)r * N + c], x[r], s);
-        for (int r = r_lo; r < r_hi; ++r) s = fma(T[(size_t)r * N + c], x[r], s);
-        const double* w = W + mpos(a, 0, leaf, line0 + line, 0);
-        double f = 0.0;
-        for (int k = 0; k < K; ++k) f = fma(Q0[k], w[k], f);
-        out[(size_t)(line0 + line) * N + c] = s + sw * f;
+    const int r_lo = max(ne, J * FB + w * 32), r_hi = (J + 1) * FB;
+    for (int line = 0; line < nl; line += 2) {
+        const bool two = line + 1 < nl;
+        const double* x0 = in + (size_t)(line0 + line) * N;
+        const double* x1 = two ? x0 + N : x0;
+        double s0 = 0.0, s1 = 0.0;
+        for (int r = 0; r < ne; ++r) {
+            const double t = T[(size_t)r * N];
+            s0 = fma(t, x0[r], s0);
+            s1 = fma(t, x1[r], s1);
+        }
+        for (int r = r_lo; r < r_hi; ++r) {
+            const double t = T[(size_t)r * N];
+            s0 = fma(t, x0[r], s0);
+            s1 = fma(t, x1[r], s1);
+        }
+        double f0 = 0.0, f1 = 0.0;
+        for (int j = 0; j < a.levels; ++j) {
+            const int i = J >> j;
+            if ((i & 1) || i + 1 >= (a.nleaf >> j)) continue;
+            const int len = FB << j;
+            const double* qt = a.QT + a.qoff[j] + (c - i * len);
+            const double* w0 = W + mpos(a, j, i, line0 + line, 0);
+            const double* w1 = two ? w0 + KM : w0;
+            for (int k = 0; k < K; ++k) {
+                const double q = qt[(size_t)k * len];
+                f0 = fma(q, w0[k], f0);
+                f1 = fma(q, w1[k], f1);
+            }
+        }
+        out[(size_t)(line0 + line) * N + c] = fma(sw, f0, s0);
+        if (two) out[(size_t)(line0 + line + 1) * N + c] = fma(sw, f1, s1);
     }
+}
+
+// Build-time layouts: betaT[l][j][k][r] = beta[l][j][r][k] and the transposed
+// diagonal leaf blocks nearT[l][J][c][t] = T_l[J B + t][J B + c].
+__global__ void k_fast_transpose_beta(const double* __restrict__ beta, double* __restrict__ betaT, int N) {
+    const size_t lj = blockIdx.y;
+    const int r = blockIdx.x, k = threadIdx.x;
+    betaT[(lj * KM + k) * N + r] = beta[(lj * N + r) * KM + k];
+}
+
+__global__ void k_fast_near(const double* __restrict__ T64, double* __restrict__ nearT, int N, int nleaf) {
+    const int J = blockIdx.x, l = blockIdx.y, c = threadIdx.x;
+    for (int t = 0; t < FB; ++t)
+        nearT[(((size_t)l * nleaf + J) * FB + c) * FB + t] = T64[((size_t)l * N + J * FB + t) * N + J * FB + c];
 }
 
 }  // namespace
@@ -238,9 +311,11 @@ __global__ void __launch_bounds__(128) k_fast_leaf_out(FastArgs a, GroupTable g,
 struct FastData {
     int nleaf = 0, levels = 0;
     double* Q = nullptr;
+    double* QT = nullptr;
     size_t* qoff = nullptr;
-    double* A = nullptr;
     double* beta = nullptr;
+    double* betaT = nullptr;
+    double* nearT = nullptr;
 };
 
 bool fast_supported(int N) {
@@ -259,7 +334,7 @@ int fast_build(dsbt_plan* p, cudaStream_t st) {
     f->levels = 0;
     while ((1 << f->levels) < f->nleaf) ++f->levels;   // levels j = 0 .. levels-1, intervals up to N / 2
     const int levels = f->levels;
-    // bases (host, threads over levels) and transfer matrices
+    // orthonormal bases of the levels (host, one thread per level), both layouts
     std::vector<std::vector<double>> Qh(levels);
     std::vector<std::thread> pool;
     for (int j = 0; j < levels; ++j) pool.emplace_back([&, j]() { basis(FB << j, Qh[j]); });
@@ -270,33 +345,34 @@ int fast_build(dsbt_plan* p, cudaStream_t st) {
         qoff[j] = qtot;
         qtot += Qh[j].size();
     }
-    std::vector<double> Qall(qtot), Ah((size_t)levels * 2 * KM * KM, 0.0);
-    for (int j = 0; j < levels; ++j) std::copy(Qh[j].begin(), Qh[j].end(), Qall.begin() + qoff[j]);
-    for (int j = 1; j < levels; ++j) {
-        const int half = FB << (j - 1);
-        for (int h = 0; h < 2; ++h)
-            for (int q = 0; q < KM; ++q)
-                for (int k = 0; k < KM; ++k) {
-                    double s = 0.0;
-                    for (int t = 0; t < half; ++t) s += Qh[j - 1][(size_t)t * KM + q] * Qh[j][(size_t)(h * half + t) * KM + k];
-                    Ah[(((size_t)j * 2 + h) * KM + q) * KM + k] = s;
-                }
+    std::vector<double> Qall(qtot), QTall(qtot);
+    for (int j = 0; j < levels; ++j) {
+        const int len = FB << j;
+        for (int t = 0; t < len; ++t)
+            for (int k = 0; k < KM; ++k) {
+                Qall[qoff[j] + (size_t)t * KM + k] = Qh[j][(size_t)t * KM + k];
+                QTall[qoff[j] + (size_t)k * len + t] = Qh[j][(size_t)t * KM + k];
+            }
     }
     const size_t L = (size_t)p->l_max + 1;
+    const size_t nbeta = L * levels * N * KM;
     bool ok = cudaMalloc((void**)&f->Q, qtot * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void**)&f->QT, qtot * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void**)&f->qoff, levels * sizeof(size_t)) == cudaSuccess &&
-              cudaMalloc((void**)&f->A, Ah.size() * sizeof(double)) == cudaSuccess &&
-              cudaMalloc((void**)&f->beta, L * levels * N * KM * sizeof(double)) == cudaSuccess;
+              cudaMalloc((void**)&f->beta, nbeta * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void**)&f->betaT, nbeta * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void**)&f->nearT, L * N * FB * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMemcpy(f->Q, Qall.data(), qtot * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(f->qoff, qoff.data(), levels * sizeof(size_t), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(f->A, Ah.data(), Ah.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+         cudaMemcpy(f->QT, QTall.data(), qtot * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(f->qoff, qoff.data(), levels * sizeof(size_t), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         set_error("DSBT_PLAN_FAST64: device allocation or copy failed");
         return DSBT_ERR_NOMEM;
     }
-    dim3 grid(N, levels, (unsigned)L);
-    k_fast_beta<<<grid, KM, 0, st>>>(p->T64, f->Q, f->qoff, f->beta, N, levels);
+    k_fast_beta<<<dim3(N, levels, (unsigned)L), KM, 0, st>>>(p->T64, f->Q, f->qoff, f->beta, N, levels);
+    k_fast_transpose_beta<<<dim3(N, (unsigned)(L * levels)), KM, 0, st>>>(f->beta, f->betaT, N);
+    k_fast_near<<<dim3(f->nleaf, (unsigned)L), FB, 0, st>>>(p->T64, f->nearT, N, f->nleaf);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -304,9 +380,11 @@ int fast_build(dsbt_plan* p, cudaStream_t st) {
 void fast_free(dsbt_plan* p) {
     if (!p || !p->fast) return;
     cudaFree(p->fast->Q);
+    cudaFree(p->fast->QT);
     cudaFree(p->fast->qoff);
-    cudaFree(p->fast->A);
     cudaFree(p->fast->beta);
+    cudaFree(p->fast->betaT);
+    cudaFree(p->fast->nearT);
     delete p->fast;
     p->fast = nullptr;
 }
@@ -321,20 +399,27 @@ size_t fast_scratch_bytes(const dsbt_plan* p, int lines) {
 int contract_f64_fast(const dsbt_plan* p, const GroupTable& g, int dir, const double* in, double* out,
                       const double2* phase, double* scratch, cudaStream_t st) {
     const FastData* f = p->fast;
-    FastArgs a{f->Q, f->qoff, f->A, f->beta, p->T64, p->N, f->nleaf, f->levels, g.total_lines};
+    FastArgs a{f->Q, f->QT, f->qoff, f->beta, f->betaT, f->nearT, p->T64, p->N, f->nleaf, f->levels, g.total_lines};
     const int per_l = p->knl != nullptr;
-    const unsigned gy = (unsigned)g.ngroups;
+    int pmax = 0, lmax = 0;
+    for (int gi = 0; gi < g.ngroups; ++gi) {
+        pmax = std::max(pmax, (g.line0[gi + 1] - g.line0[gi]) * g.l[gi]);
+        lmax = std::max(lmax, g.l[gi]);
+    }
     ProfScope ps(kKContract64, st);
+    if (pmax > 0) {
+        long long blocks = 0;
+        for (int j = 0; j < f->levels; ++j) {
+            const int per = PROJ_THREADS / std::min(32, 1 << j);
+            blocks += (long long)(f->nleaf >> (j + 1)) * g.ngroups * ((pmax + per - 1) / per);
+        }
+        k_fast_project<<<(unsigned)blocks, PROJ_THREADS, 0, st>>>(a, g, dir, pmax, in, scratch);
+    }
     if (dir > 0) {
-        k_fast_leaf_moments<<<dim3(f->nleaf, gy), 256, 0, st>>>(a, g, in, scratch);
-        for (int j = 1; j < f->levels; ++j) k_fast_merge<<<dim3(f->nleaf >> j, gy), 256, 0, st>>>(a, g, j, scratch);
-        k_fast_eval<<<dim3((p->N + 127) / 128, gy), 128, 0, st>>>(a, g, in, scratch, out, phase, per_l);
+        const int ncomp = (n_extra(lmax) + FB / 32 - 1) / (FB / 32);
+        k_fast_eval<<<dim3(f->nleaf + ncomp, g.ngroups), FB, 0, st>>>(a, g, in, scratch, out, phase, per_l);
     } else {
-        int slots = 0;
-        for (int j = 0; j < f->levels; ++j) slots += f->nleaf >> j;
-        k_fast_w<<<dim3(slots, gy), 256, 0, st>>>(a, g, in, scratch);
-        for (int j = f->levels - 1; j >= 1; --j) k_fast_push<<<dim3(f->nleaf >> j, gy), 256, 0, st>>>(a, g, j, scratch);
-        k_fast_leaf_out<<<dim3((p->N + 127) / 128, gy), 128, 0, st>>>(a, g, in, scratch, out);
+        k_fast_leaf_out<<<dim3(f->nleaf, g.ngroups), FB, 0, st>>>(a, g, in, scratch, out);
     }
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
