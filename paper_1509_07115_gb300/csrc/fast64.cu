@@ -14,15 +14,21 @@
 // with Q_j an orthonormal basis [L_j][K] of the polynomials of degree < K on
 // the interval's points (K = the plan's l_max; the first l columns suffice for
 // T_l), beta_{r,j} = Q_j^T (T_{r,I} / sqrt(w_I)) computed from the FP64 T_l at
-// plan creation.  Forward: moments M_I = Q_j^T (sqrt(w) f)_I per line, leaves
-// first, then parents from children through the K x K transfer matrices
-// A_{j,h} = Q_{j-1}^T Q_j[half h] (the parent basis restricted to a child is a
-// polynomial of degree < K there); b_r = near + sum_j beta_{r,j} . M.
-// Inverse: W_I = sum_{r using I} beta_{r,j} b_r, pushed down the tree through
-// the same A, f_c = sqrt(w_c) (Q_0 W_leaf)_c + near + completion rows.  The
-// completion rows (n < n0_l) are dense and applied directly.  The bases are
-// built on the host by Arnoldi on the point grid with two Gram-Schmidt passes,
-// so every coefficient is a bounded projection (no monomial cancellation).
+// plan creation.  Forward: moments M_I = Q_j^T (sqrt(w) f)_I of every used
+// interval (one with a right sibling), projected directly from f, then
+// b_r = near + sum_j beta_{r,j} . M.  Inverse: W_I = sum_{r using I}
+// beta_{r,j} b_r, then f_c = sqrt(w_c) sum_j (Q_j W_{I_j(c)})_c + near, over
+// the used intervals I_j(c) holding c.  Direct projection costs about as many
+// multiply-adds as the leaf-to-root merge through K x K transfer matrices
+// would for K near 64, and has no chain of dependent levels.  The completion
+// rows (n < n0_l) are dense and applied directly.  The bases are built on the
+// host by Arnoldi on the point grid with two Gram-Schmidt passes, so every
+// coefficient is a bounded projection (no monomial cancellation).
+//
+// On this part FP64 multiply-adds are the bound (a few per clock per SM), so
+// the kernels keep every lane on useful multiply-adds: lanes run over rows or
+// columns with the basis index k in the loop, and the few reductions across
+// lanes are shuffles over row chunks.
 #include <math.h>
 
 #include <algorithm>
