@@ -1,7 +1,7 @@
 """FP64 contractions in O(N l log N) work (DSBT_PLAN_FAST64, csrc/fast64.cu):
 the kinetic step and the TDSE of a fast plan against the dense FP64 plan and
-the oracle.  The tree of interval moments reproduces T_l f and T_l^T b exactly
-up to rounding (oracle/fast.py pins the same algorithm on the CPU)."""
+the oracle.  Interval moments reproduce T_l f and T_l^T b exactly up to
+rounding (oracle/fast.py pins the scheme on the CPU)."""
 import ctypes
 
 import numpy as np

@@ -10,10 +10,11 @@ import pytest
 from oracle import fast
 
 
-@pytest.mark.parametrize("N, l", [(256, 0), (256, 1), (256, 2), (256, 7), (512, 10), (512, 33), (512, 63)])
-def test_fast_equals_dense(N, l):
+@pytest.mark.parametrize("N, l, B", [(256, 0, 64), (256, 1, 64), (256, 2, 64), (256, 7, 64), (512, 10, 64),
+                                     (512, 33, 64), (512, 63, 64), (256, 5, 32), (512, 20, 128)])
+def test_fast_equals_dense(N, l, B):
     rng = np.random.default_rng(l)
-    P = fast.Plan(N, l, B=64)
+    P = fast.Plan(N, l, B=B)
     f = rng.standard_normal(N)
     b = P.T @ f
     tol = 1e-14 if l < 40 else 1e-12
@@ -29,3 +30,28 @@ def test_work_grows_like_l_n_log_n():
         w = fast.work(4096, l)
         total = w["near"] + w["far"] + w["moments"] + w["completion"]
         assert w["dense"] / total > gain, (l, w)
+
+
+@pytest.mark.parametrize("l", [1, 2, 5, 12])
+def test_row_left_of_diagonal_has_degree_l_minus_1(l):
+    """The fact the scheme rests on (Eqs. (38)-(42)): on an interval of columns
+    left of a regular row, T_nm / sqrt(w_m) is a polynomial of degree exactly
+    l - 1 in m -- inside the span of the degree < l basis (residual at
+    rounding), outside the span of degree < l - 1 (the top coefficient is
+    small far from the row, but still orders of magnitude above rounding)."""
+    import oracle
+    N = 256
+    T = oracle.T_matrix(N, l)
+    sw = np.ones(N)
+    if l % 2 == 1:
+        sw[0] = np.sqrt(0.5)
+    r = 200
+    for lo, hi in ((0, 64), (64, 128), (128, 192)):
+        row = T[r, lo:hi] / sw[lo:hi]
+        Q = fast._basis(hi - lo, l)
+        res = row - Q @ (Q.T @ row)
+        assert np.abs(res).max() <= 1e-13 * np.abs(row).max(), (lo, np.abs(res).max())
+        if l >= 2:
+            Qs = fast._basis(hi - lo, l - 1)
+            res_s = row - Qs @ (Qs.T @ row)
+            assert np.abs(res_s).max() > 1e-11 * np.abs(row).max(), lo

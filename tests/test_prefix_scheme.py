@@ -1,7 +1,8 @@
 """The fast multiplication by T_l of Sec. 2.6 (monomial prefix sums,
 oracle/prefix.py) against the dense T_l: exact in structure (it agrees to
 rounding for small l) but its rounding error grows by orders of magnitude with
-l, which is why the library contracts with the dense T_l.  Measured (random
+l, which is why the library's fast FP64 path uses orthonormal polynomial bases
+on dyadic intervals instead (oracle/fast.py, DSBT_PLAN_FAST64).  Measured (random
 f, max |b_fast - b| / |f|): N = 256: 3e-17 (l = 2), 1e-15 (l = 8), 1e-12
 (l = 16); N = 1024: 6e-13 (l = 16), 1.4e-9 (l = 24), 1.2e-6 (l = 32)."""
 import numpy as np
