@@ -75,6 +75,15 @@ extern "C" {
                               Extra memory: 8 B x 64 x (l_max+1) x N x log2(N/64)
                               of plan data; FP64 workspaces grow by about
                               8 B x 128 x (N/64) per line. */
+#define DSBT_PLAN_FAST_TF32 16 /* with DSBT_PLAN_TF32X3, N / 128 a power of two:
+                              split-TF32 contractions (all DSBT_F32 / DSBT_C64
+                              calls) through the same interval scheme on the tensor
+                              cores: near band of T_l per 128-row leaf, far field
+                              through 64 basis functions per used dyadic interval.
+                              Needs l_max <= 64 (always true).  Extra memory:
+                              16 B x 128 x (l_max+1) x N x (N/128 - 1) of plan data
+                              (4.2 GB at N = 4096, l_max = 63) and 8 B x 64 x
+                              (N/128 - 1) per line of workspace. */
 
 /* element types of the caller's arrays */
 #define DSBT_F64 1  /* real double                 */

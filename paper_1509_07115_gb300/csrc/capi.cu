@@ -82,6 +82,7 @@ struct Workspace {
     float* planar;   // aliases hi_a
     float2* ph32;
     int* sched;      // tile-scheduler counter of the tensor-core contraction
+    float* ftc;      // augmented lines of the DSBT_PLAN_FAST_TF32 contraction (or nullptr)
 };
 
 size_t lines_of(int total_channels, int dtype) {
@@ -95,7 +96,8 @@ size_t ws_bytes(const dsbt_plan* p, int total_channels, int dtype) {
     if (is_fp64(dtype))
         return align256(R * N * sizeof(double)) * 2 + align256(PR * sizeof(double2)) +
                align256(fast_scratch_bytes(p, (int)R)) + 256;
-    return align256(R * N * sizeof(float)) * 4 + align256(PR * sizeof(float2)) + 256 + 256;
+    return align256(R * N * sizeof(float)) * 4 + align256(PR * sizeof(float2)) + 256 +
+           align256(ftc_scratch_bytes(p, R)) + 256;
 }
 
 Workspace carve(const dsbt_plan* pl, void* base, int total_channels, int dtype) {
@@ -119,6 +121,7 @@ Workspace carve(const dsbt_plan* pl, void* base, int total_channels, int dtype) 
         w.planar = w.hi_a;
         w.ph32 = (float2*)(p + 4 * b);
         w.sched = (int*)(p + 4 * b + align256(PR * sizeof(float2)));
+        w.ftc = pl->ftc ? (float*)(p + 4 * b + align256(PR * sizeof(float2)) + 256) : nullptr;
     }
     return w;
 }
@@ -183,7 +186,7 @@ int run_forward(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
     rc = dct_forward_f32(p, g, cplx, (const float*)in, w.hi_a, w.lo_a, st);
     if (rc) return rc;
     return contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, cplx ? kOutUserC64 : kOutUserF32, (float*)out,
-                           nullptr, nullptr, w.sched, st);
+                           nullptr, nullptr, w.sched, st, w.ftc);
 }
 
 int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* in, void* out,
@@ -209,7 +212,7 @@ int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
                                                                         total);
     }
     DSBT_CUDA_TRY(cudaGetLastError());
-    rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, w.sched, st);
+    rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, w.sched, st, w.ftc);
     if (rc) return rc;
     return dct_inverse_f32(p, g, cplx, w.planar, (float*)out, st);
 }
@@ -240,8 +243,9 @@ int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, 
     }
     DSBT_CUDA_TRY(cudaGetLastError());
     rc = dct_forward_f32(p, g, true, (const float*)in, w.hi_a, w.lo_a, st);
-    if (!rc) rc = contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, kOutPlanarSplit, w.hi_b, w.lo_b, w.ph32, w.sched, st);
-    if (!rc) rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, w.sched, st);
+    if (!rc) rc = contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, kOutPlanarSplit, w.hi_b, w.lo_b, w.ph32, w.sched, st, w.ftc);
+    if (!rc) rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, w.sched, st,
+                                  w.ftc);
     if (!rc) rc = dct_inverse_f32(p, g, true, w.planar, (float*)out, st);
     return rc;
 }

@@ -324,6 +324,8 @@ struct FastData {
     double* nearT = nullptr;
 };
 
+void poly_basis(int len, std::vector<double>& Q) { basis(len, Q); }
+
 bool fast_supported(int N) {
     const int nleaf = N / FB;
     return N % FB == 0 && nleaf >= 2 && (nleaf & (nleaf - 1)) == 0;

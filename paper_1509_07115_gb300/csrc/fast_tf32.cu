@@ -1,0 +1,749 @@
+// fast_tf32.cu -- split-TF32 tensor-core contractions with T_l and T_l^T in
+// O(N l log N) work, for plans built with DSBT_PLAN_FAST_TF32 (the stable
+// counterpart of the fast scheme of Sec. 2.6, on tcgen05).
+//
+// On a regular row n of T_l the entries left of the diagonal are
+// T_nm = alpha_n P'_l(n - m, 2n) sqrt(w_m): a polynomial of degree l - 1 in m
+// times sqrt(w_m) (Sec. 2.4, Eqs. (38)-(42)).  Columns are cut into leaves of
+// 128 (one output row tile) and a binary tree of intervals above them.  An
+// interval (j, i) of 128 * 2^j columns is "used" when i is even and its right
+// sibling i + 1 exists: the rows of that sibling take it as a far interval, and
+// every row r of leaf J takes exactly the used intervals ((J >> j) - 1) for the
+// set bits j of J.  On a used interval the row is sqrt(w) (Q_j beta_{r,j}) with
+// Q_j an orthonormal basis [len][64] of the polynomials of degree < 64 on the
+// interval's points.  Used intervals are numbered (slots s, level-major); the
+// augmented index (s, k), k < 64, spans NA = 64 (nleaf - 1) columns.
+//
+// Every step is then the dense contraction kernel of gemm_tf32x3.cu with other
+// operands and K ranges:
+//   forward   MOMENTS  M[line][(s,k)]  = sum_t QT[(s,k)][t] f[line][t]          (t in interval s)
+//             EVAL     b[line][r]      = sum_c T[r][c] f[line][c]  (near band: c in r's leaf;
+//                                                                   leaf 0: all c)
+//                                      + sum_(s,k) B[r][(s,k)] M[line][(s,k)]  (far slots of r)
+//   inverse   WEIGHTS  W[line][(s,k)]  = sum_r BT[(s,k)][r] b[line][r]          (r in sibling of s)
+//             LEAFOUT  f[line][c]      = sum_r T^T[c][r] b[line][r] (completion rows and near band)
+//                                      + sum_(s,k) QA[c][(s,k)] W[line][(s,k)]  (used slots holding c)
+// with B[r][(s,k)] = beta_{r,j}[k] (zero unless s is a far slot of r), BT its
+// transpose, QT[(s,k)][t] = Q_j[t - i len][k] sqrt(w_t) and QA its transpose,
+// all split into TF32 pairs.  MOMENTS and WEIGHTS tiles hold one slot (64 of
+// the 128 TMEM lanes carry results; the A box is 64 rows and the other half of
+// the A tile is ignored).  K blocks of a tile come from up to two operand
+// sources (near: T / T^T against the lines; far: B / QA against M / W), listed
+// per tile by segments.
+//
+// Work per line (N = 4096, l = 63): near 0.5 M, far 0.7 M, moments 1.3 M (half
+// of it on the ignored lanes), leaf 0 0.5 M multiply-adds, against 8.7 M for the
+// dense tiles: about 3x fewer tensor operations.
+#include <math.h>
+
+#include <algorithm>
+#include <thread>
+#include <vector>
+
+#include "plan.cuh"
+#include "tc_ptx.cuh"
+
+namespace dsbt {
+
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128;
+constexpr int BK = 32;
+constexpr int BN_MAX = 256;
+constexpr int BBOX = 64;                           // rows per B TMA box
+constexpr int STAGES = 2;
+constexpr int KC = 4;                              // K blocks per main-accumulator chunk
+constexpr int EPI_WARPS = 8;
+constexpr int QS = 4;                              // tile-queue slots
+constexpr int A_BYTES = BM * BK * 4;               // 16 KiB
+constexpr int B_BYTES = BN_MAX * BK * 4;           // 32 KiB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
+constexpr int FL = 128;                            // leaf = output row tile
+constexpr int KP = 64;                             // basis functions per interval (>= l_max)
+constexpr int MAX_LEVELS = 10;                     // N / 128 <= 2^10
+constexpr int MAX_SEGS = MAX_LEVELS + 3;
+
+enum Mode { kMoments = 0, kEval = 1, kWeights = 2, kLeafOut = 3 };
+
+struct FtcSpace {
+    int mode;
+    int RT;                        // row tiles of this launch
+    int KB;                        // K blocks of N
+    int nleaf, levels, nslots;
+    int slot_off[MAX_LEVELS + 1];  // first slot of level j
+    int total;                     // tiles
+    int order[kMaxGroups];         // group visited at position i
+    int t0[kMaxGroups + 1];        // first tile of position i
+    int ct[kMaxGroups];            // column tiles of the group at position i (0: group skipped)
+};
+
+struct Tile {
+    int g, rt, ct, nmma;
+};
+
+__device__ __forceinline__ Tile decode(const FtcSpace& fs, const GroupTable& gt, int t) {
+    Tile tl;
+    int i = 0;
+    while (fs.t0[i + 1] <= t) ++i;
+    const int g = fs.order[i];
+    const int local = t - fs.t0[i];
+    const int q = local / fs.ct[i];
+    tl.g = g;
+    tl.ct = local - q * fs.ct[i];
+    if (fs.mode == kMoments || fs.mode == kWeights) tl.rt = fs.RT - 1 - q;   // longest slots first
+    else if (fs.mode == kEval) tl.rt = (q == 0) ? 0 : fs.RT - q;            // dense leaf 0 first
+    else tl.rt = q;
+    const int nl = gt.line0[g + 1] - gt.line0[g];
+    int left = nl - tl.ct * BN_MAX;
+    if (left > BN_MAX) left = BN_MAX;
+    tl.nmma = (left + 15) & ~15;
+    return tl;
+}
+
+// slot s -> (level j, interval i)
+__device__ __forceinline__ void slot_ji(const FtcSpace& fs, int s, int& j, int& i) {
+    j = 0;
+    while (j + 1 < fs.levels && fs.slot_off[j + 1] <= s) ++j;
+    i = 2 * (s - fs.slot_off[j]);
+}
+
+// K blocks of one tile: segments [k0, k1) of operand source src (1 near, 2 far).
+struct Segs {
+    int n;
+    int src[MAX_SEGS], k0[MAX_SEGS], k1[MAX_SEGS];
+    __device__ __forceinline__ void add(int s, int a, int b) {
+        if (b > a) {
+            src[n] = s;
+            k0[n] = a;
+            k1[n] = b;
+            ++n;
+        }
+    }
+    __device__ __forceinline__ int count() const {
+        int c = 0;
+        for (int q = 0; q < n; ++q) c += k1[q] - k0[q];
+        return c;
+    }
+    __device__ __forceinline__ void at(int i, int& s, int& kb) const {
+        for (int q = 0; q < n; ++q) {
+            const int len = k1[q] - k0[q];
+            if (i < len) {
+                s = src[q];
+                kb = k0[q] + i;
+                return;
+            }
+            i -= len;
+        }
+        s = 1;
+        kb = 0;
+    }
+};
+
+__device__ __forceinline__ Segs segments(const FtcSpace& fs, int l, int rt) {
+    Segs sg;
+    sg.n = 0;
+    const int nx = n_extra(l);
+    const int nf = (l + BK - 1) / BK;   // far K blocks per slot (basis functions k < l)
+    if (fs.mode == kMoments || fs.mode == kWeights) {
+        int j, i;
+        slot_ji(fs, rt, j, i);
+        const int lb = (FL << j) / BK;   // K blocks of the interval
+        const int first = (fs.mode == kMoments) ? i * lb : (i + 1) * lb;
+        sg.add(1, first, first + lb);
+    } else if (fs.mode == kEval) {
+        if (rt == 0) {
+            sg.add(1, 0, nx > 0 ? fs.KB : FL / BK);
+        } else {
+            for (int j = 0; j < fs.levels; ++j)
+                if ((rt >> j) & 1) {
+                    const int s = fs.slot_off[j] + (((rt >> j) - 1) >> 1);
+                    sg.add(2, s * (KP / BK), s * (KP / BK) + nf);
+                }
+            sg.add(1, rt * (FL / BK), (rt + 1) * (FL / BK));
+        }
+    } else {   // kLeafOut
+        if (rt > 0 && nx > 0) sg.add(1, 0, 1);   // completion rows n < n0_l (storage rows < 32)
+        sg.add(1, rt * (FL / BK), (rt + 1) * (FL / BK));
+        for (int j = 0; j < fs.levels; ++j) {
+            const int i = rt >> j;
+            if ((i & 1) == 0 && i + 1 < (fs.nleaf >> j)) {
+                const int s = fs.slot_off[j] + (i >> 1);
+                sg.add(2, s * (KP / BK), s * (KP / BK) + nf);
+            }
+        }
+    }
+    return sg;
+}
+
+// Number of K blocks of a tile (what segments(...).count() gives), without
+// building the list.
+__device__ __forceinline__ int seg_count(const FtcSpace& fs, int l, int rt) {
+    const int nx = n_extra(l);
+    const int nf = (l + BK - 1) / BK;
+    if (fs.mode == kMoments || fs.mode == kWeights) {
+        int j, i;
+        slot_ji(fs, rt, j, i);
+        return (FL << j) / BK;
+    }
+    if (fs.mode == kEval) return rt == 0 ? (nx > 0 ? fs.KB : FL / BK) : __popc(rt) * nf + FL / BK;
+    int c = ((rt > 0 && nx > 0) ? 1 : 0) + FL / BK;
+    for (int j = 0; j < fs.levels; ++j) {
+        const int i = rt >> j;
+        if ((i & 1) == 0 && i + 1 < (fs.nleaf >> j)) c += nf;
+    }
+    return c;
+}
+
+struct EpiArgs {
+    int mode;              // OutMode, or kOutAugSplit for MOMENTS / WEIGHTS
+    float* out0;
+    float* out1;
+    const float2* phase;
+    int per_l;
+    int stride;            // output row stride (N, or NA for the augmented lines)
+};
+constexpr int kOutAugSplit = 16;
+
+// The kernel: roles, TMEM layout, chunked main accumulator and bounded waits
+// as in gemm_tf32x3.cu; what differs is where each K block comes from.
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constant__ CUtensorMap tmA1_lo,
+               const __grid_constant__ CUtensorMap tmB1_hi, const __grid_constant__ CUtensorMap tmB1_lo,
+               const __grid_constant__ CUtensorMap tmA2_hi, const __grid_constant__ CUtensorMap tmA2_lo,
+               const __grid_constant__ CUtensorMap tmB2_hi, const __grid_constant__ CUtensorMap tmB2_lo,
+               GroupTable gt, FtcSpace fs, int N, EpiArgs ep, unsigned* status, int* sched) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* stage_base = smem;
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* main_full = empty + STAGES;
+    uint64_t* main_empty = main_full + 1;
+    uint64_t* tq_full = main_empty + 1;
+    uint64_t* tq_empty = tq_full + QS;
+    int* tile_q = (int*)(tq_empty + QS);
+    uint32_t* tmem_slot = (uint32_t*)(tile_q + QS);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool aug = fs.mode == kMoments || fs.mode == kWeights;   // one slot per tile, 64-row A
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(main_full, 1);
+        mbar_init(main_empty, EPI_WARPS);
+        for (int q = 0; q < QS; ++q) {
+            mbar_init(&tq_full[q], 1);
+            mbar_init(&tq_empty[q], 1 + EPI_WARPS);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            const uint64_t pol_b = policy_evict_last();
+            int qslot = 0;
+            uint32_t qphase = 0;
+            const uint32_t a_bytes = (aug ? 64u : 128u) * BK * 4u;
+            while (ok) {
+                if (!mbar_wait(&tq_empty[qslot], qphase ^ 1, abort_flag, status)) { ok = false; break; }
+                int t = atomicAdd(sched, 1);
+                if (t >= fs.total) t = -1;
+                tile_q[qslot] = t;
+                mbar_arrive(&tq_full[qslot]);
+                if (++qslot == QS) { qslot = 0; qphase ^= 1; }
+                if (t < 0) break;
+                const Tile tl = decode(fs, gt, t);
+                const int l = gt.l[tl.g];
+                const Segs sg = segments(fs, l, tl.rt);
+                const int nbox = (tl.nmma + BBOX - 1) / BBOX;
+                const uint32_t bytes = 2 * a_bytes + 2 * nbox * BBOX * BK * 4;
+                int arow1, arow2 = 0;
+                if (fs.mode == kMoments) arow1 = ((l & 1) * fs.nslots + tl.rt) * KP;
+                else if (fs.mode == kWeights) arow1 = (l * fs.nslots + tl.rt) * KP;
+                else {
+                    arow1 = l * N + tl.rt * BM;
+                    arow2 = (fs.mode == kEval ? l : (l & 1)) * N + tl.rt * BM;
+                }
+                const int brow = gt.line0[tl.g] + tl.ct * BN_MAX;
+                const int nkb = sg.count();
+                for (int i = 0; i < nkb; ++i) {
+                    int src, kb;
+                    sg.at(i, src, kb);
+                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status)) { ok = false; break; }
+                    unsigned char* sb = stage_base + stage * STAGE_BYTES;
+                    mbar_expect_tx(&full[stage], bytes);
+                    const CUtensorMap* ah = src == 1 ? &tmA1_hi : &tmA2_hi;
+                    const CUtensorMap* al = src == 1 ? &tmA1_lo : &tmA2_lo;
+                    const CUtensorMap* bh = src == 1 ? &tmB1_hi : &tmB2_hi;
+                    const CUtensorMap* bl = src == 1 ? &tmB1_lo : &tmB2_lo;
+                    const int arow = src == 1 ? arow1 : arow2;
+                    tma_load_2d(sb, ah, &full[stage], kb * BK, arow);
+                    tma_load_2d(sb + A_BYTES, al, &full[stage], kb * BK, arow);
+                    for (int b = 0; b < nbox; ++b) {
+                        tma_load_2d_hint(sb + 2 * A_BYTES + b * BBOX * 128, bh, &full[stage], kb * BK,
+                                         brow + b * BBOX, pol_b);
+                        tma_load_2d_hint(sb + 2 * A_BYTES + B_BYTES + b * BBOX * 128, bl, &full[stage],
+                                         kb * BK, brow + b * BBOX, pol_b);
+                    }
+                    if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t mphase = 0;
+            bool ok = true;
+            const uint32_t d_main = tmem_base, d_corr = tmem_base + 256;
+            int qslot = 0;
+            uint32_t qphase = 0;
+            while (ok) {
+                if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status)) break;
+                const int t = ((volatile int*)tile_q)[qslot];
+                mbar_arrive(&tq_empty[qslot]);
+                if (++qslot == QS) { qslot = 0; qphase ^= 1; }
+                if (t < 0) break;
+                const Tile tl = decode(fs, gt, t);
+                const int l = gt.l[tl.g];
+                const int nkb = seg_count(fs, l, tl.rt);
+                const uint32_t idesc = idesc_tf32(BM, tl.nmma);
+                uint32_t acc_corr = 0;
+                for (int c0 = 0; c0 < nkb && ok; c0 += KC) {
+                    const int c1 = min(nkb, c0 + KC);
+                    const bool pre = c0 > 0;
+                    if (pre) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
+                        const uint32_t sb_hi = sa + 2 * A_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < BK / 8; ++ks) {
+                            const uint32_t off = ks * 32;
+                            const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa + A_BYTES + off);
+                            const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_hi + B_BYTES + off);
+                            mma_tf32(d_corr, dah, dbl, idesc, 1);
+                            mma_tf32(d_corr, dal, dbh, idesc, 1);
+                        }
+                    }
+                    if (!mbar_wait(main_empty, mphase ^ 1, abort_flag, status)) { ok = false; break; }
+                    mphase ^= 1;
+                    tc_fence_after();
+                    uint32_t acc_main = 0;
+                    for (int i = c0; i < c1; ++i) {
+                        const bool early = pre && i == c0;
+                        if (!early) {
+                            if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                            tc_fence_after();
+                        }
+                        const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
+                        const uint32_t sa_lo = sa + A_BYTES;
+                        const uint32_t sb_hi = sa + 2 * A_BYTES;
+                        const uint32_t sb_lo = sb_hi + B_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < BK / 8; ++ks) {
+                            const uint32_t off = ks * 32;
+                            const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa_lo + off);
+                            const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_lo + off);
+                            mma_tf32(d_main, dah, dbh, idesc, acc_main);
+                            if (!early) {
+                                mma_tf32(d_corr, dah, dbl, idesc, acc_corr);
+                                mma_tf32(d_corr, dal, dbh, idesc, 1);
+                            }
+                            acc_main = 1;
+                            acc_corr = 1;
+                        }
+                        mma_commit(&empty[stage]);
+                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                    }
+                    if (!ok) break;
+                    mma_commit(main_full);
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue (EPI_WARPS warps)
+        const int ew = warp - 2;
+        const int quarter = warp & 3;
+        const int half = ew >> 2;
+        uint32_t mphase = 0;
+        int qslot = 0;
+        uint32_t qphase = 0;
+        while (true) {
+            if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status)) break;
+            const int t = ((volatile int*)tile_q)[qslot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tq_empty[qslot]);
+            if (++qslot == QS) { qslot = 0; qphase ^= 1; }
+            if (t < 0) break;
+            const Tile tl = decode(fs, gt, t);
+            const int l = gt.l[tl.g];
+            const int nkb = seg_count(fs, l, tl.rt);
+            const int nl = gt.line0[tl.g + 1] - gt.line0[tl.g];
+            const int trow = quarter * 32 + lane;                 // TMEM lane = A row of the tile
+            const int row = aug ? tl.rt * KP + trow : tl.rt * BM + trow;
+            const bool store_row = !aug || trow < KP;
+            const int cbase = tl.ct * BN_MAX + half * 128;
+            const int ncols = min(128, nl - cbase);
+            const int nch = (tl.nmma > half * 128) ? ((min(tl.nmma - half * 128, 128) + 31) >> 5) : 0;
+            const uint32_t tl_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+            float acc[128];
+#pragma unroll
+            for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+            bool ok = true;
+            for (int c0 = 0; c0 < nkb; c0 += KC) {
+                if (!mbar_wait(main_full, mphase, abort_flag, status)) { ok = false; break; }
+                mphase ^= 1;
+                tc_fence_after();
+                const bool last = c0 + KC >= nkb;
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    if (ch < nch) {
+                        float v[32];
+                        tmem_ld32(tl_addr + ch * 32, v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[ch * 32 + j] += v[j];
+                        if (last) {
+                            tmem_ld32(tl_addr + 256 + ch * 32, v);
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) acc[ch * 32 + j] += v[j];
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(main_empty);
+            }
+            if (!ok) break;
+            if (ncols <= 0 || !store_row) continue;
+            const int S = ep.stride;
+            if (ep.mode == kOutAugSplit) {
+                const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+#pragma unroll
+                for (int j = 0; j < 128; ++j) {
+                    if (j < ncols) {
+                        const float h = round_tf32(acc[j]);
+                        const size_t o = (line_base + j) * S + row;
+                        ep.out0[o] = h;
+                        ep.out1[o] = round_tf32(acc[j] - h);
+                    }
+                }
+                continue;
+            }
+            float2 ph = make_float2(1.f, 0.f);
+            if (ep.phase) ph = ep.per_l ? ep.phase[(size_t)l * N + row] : ep.phase[(size_t)(l & 1) * N + phase_entry(l, row, N)];
+            if (ep.mode == kOutUserC64) {
+                float2* o = reinterpret_cast<float2*>(ep.out0);
+                const size_t chan_base = (size_t)gt.chan0[tl.g] + (cbase >> 1);
+#pragma unroll
+                for (int j = 0; j < 128; j += 2)
+                    if (j < ncols) o[(chan_base + (j >> 1)) * N + row] = make_float2(acc[j], acc[j + 1]);
+            } else if (ep.mode == kOutUserF32) {
+                const size_t chan_base = (size_t)gt.chan0[tl.g] + cbase;
+#pragma unroll
+                for (int j = 0; j < 128; ++j)
+                    if (j < ncols) ep.out0[(chan_base + j) * N + row] = acc[j];
+            } else if (ep.mode == kOutPlanarF32) {
+                const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+#pragma unroll
+                for (int j = 0; j < 128; ++j)
+                    if (j < ncols) ep.out0[(line_base + j) * N + row] = acc[j];
+            } else {   // kOutPlanarSplit: complex pairs with optional phase, TF32 split
+                const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+#pragma unroll
+                for (int j = 0; j < 128; j += 2) {
+                    if (j < ncols) {
+                        const float re = acc[j] * ph.x - acc[j + 1] * ph.y;
+                        const float im = acc[j] * ph.y + acc[j + 1] * ph.x;
+                        const float hr = round_tf32(re), hi = round_tf32(im);
+                        const size_t o = (line_base + j) * N + row;
+                        ep.out0[o] = hr;
+                        ep.out1[o] = round_tf32(re - hr);
+                        ep.out0[o + N] = hi;
+                        ep.out1[o + N] = round_tf32(im - hi);
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 512);
+    }
+}
+
+// ------------------------------------------------------------ plan data
+
+// beta_{r,j}[k] of every row r of the used slot s = (j, i) it takes (the rows
+// of the sibling interval i + 1), from the FP64 T_l:
+//   beta = sum_t Q_j[t][k] T_l[r][i len + t] / sqrt(w_{i len + t}),
+// zero on completion rows and for k >= l; written as TF32 pairs to
+// B[l][r][(s,k)] and BT[l][(s,k)][r].  Block (position, l), KP threads (k).
+__global__ void k_ftc_beta(const double* __restrict__ T64, const double* __restrict__ Q,
+                           const size_t* __restrict__ qoff, FtcSpace fs, int N, float* bA_hi, float* bA_lo,
+                           float* bT_hi, float* bT_lo) {
+    const int half = N / 2;
+    const int j = blockIdx.x / half, q = blockIdx.x % half, l = blockIdx.y, k = threadIdx.x;
+    const int len = FL << j;
+    const int s = fs.slot_off[j] + q / len, i = 2 * (q / len);
+    const int r = (i + 1) * len + q % len;
+    const int NA = fs.nslots * KP;
+    double b = 0.0;
+    if (r >= n_extra(l) && k < l) {
+        const double* row = T64 + ((size_t)l * N + r) * N + (size_t)i * len;
+        const double* Qj = Q + qoff[j];
+        for (int t = 0; t < len; ++t) {
+            const double w = ((l & 1) && i == 0 && t == 0) ? 0.70710678118654752440 : 1.0;
+            b = fma(row[t] / w, Qj[(size_t)t * KP + k], b);
+        }
+    }
+    const float h = round_tf32((float)b), lo = round_tf32((float)(b - (double)h));
+    const size_t oa = ((size_t)l * N + r) * NA + (size_t)s * KP + k;
+    const size_t ot = (((size_t)l * fs.nslots + s) * KP + k) * N + r;
+    bA_hi[oa] = h;
+    bA_lo[oa] = lo;
+    bT_hi[ot] = h;
+    bT_lo[ot] = lo;
+}
+
+// QT[p][(s,k)][c] = QA[p][c][(s,k)] = Q_j[c - i len][k] sqrt(w_c) for the
+// columns c of used slot s = (j, i); parity p = 1 (odd l) carries
+// sqrt(w_0) = 1/sqrt(2).  Block (position, p), KP threads (k).
+__global__ void k_ftc_q(const double* __restrict__ Q, const size_t* __restrict__ qoff, FtcSpace fs, int N,
+                        float* qT_hi, float* qT_lo, float* qA_hi, float* qA_lo) {
+    const int half = N / 2;
+    const int j = blockIdx.x / half, q = blockIdx.x % half, p = blockIdx.y, k = threadIdx.x;
+    const int len = FL << j;
+    const int s = fs.slot_off[j] + q / len, i = 2 * (q / len), t = q % len;
+    const int c = i * len + t;
+    const int NA = fs.nslots * KP;
+    const double v = Q[qoff[j] + (size_t)t * KP + k] * ((p == 1 && c == 0) ? 0.70710678118654752440 : 1.0);
+    const float h = round_tf32((float)v), lo = round_tf32((float)(v - (double)h));
+    const size_t ot = (((size_t)p * fs.nslots + s) * KP + k) * N + c;
+    const size_t oa = ((size_t)p * N + c) * NA + (size_t)s * KP + k;
+    qT_hi[ot] = h;
+    qT_lo[ot] = lo;
+    qA_hi[oa] = h;
+    qA_lo[oa] = lo;
+}
+
+}  // namespace
+
+struct FtcData {
+    FtcSpace base{};   // nleaf, levels, nslots, slot_off
+    int NA = 0;
+    float* bA_hi = nullptr;
+    float* bA_lo = nullptr;
+    float* bT_hi = nullptr;
+    float* bT_lo = nullptr;
+    float* qT_hi = nullptr;
+    float* qT_lo = nullptr;
+    float* qA_hi = nullptr;
+    float* qA_lo = nullptr;
+    CUtensorMap tm_bA_hi, tm_bA_lo, tm_bT_hi, tm_bT_lo, tm_qT_hi, tm_qT_lo, tm_qA_hi, tm_qA_lo;
+};
+
+bool ftc_supported(int N) {
+    const int nleaf = N / FL;
+    return N % FL == 0 && nleaf >= 2 && nleaf <= (1 << MAX_LEVELS) && (nleaf & (nleaf - 1)) == 0;
+}
+
+int ftc_build(dsbt_plan* p, cudaStream_t st) {
+    const int N = p->N;
+    DSBT_CHECK_ARG(ftc_supported(N), "DSBT_PLAN_FAST_TF32 needs N / 128 a power of two (N = %d)", N);
+    DSBT_CHECK_ARG(p->T64 != nullptr, "DSBT_PLAN_FAST_TF32: FP64 factors missing at build");
+    FtcData* f = new (std::nothrow) FtcData();
+    if (!f) return DSBT_ERR_NOMEM;
+    p->ftc = f;
+    FtcSpace& b = f->base;
+    b.nleaf = N / FL;
+    b.levels = 0;
+    while ((1 << b.levels) < b.nleaf) ++b.levels;
+    b.slot_off[0] = 0;
+    for (int j = 0; j < b.levels; ++j) b.slot_off[j + 1] = b.slot_off[j] + (b.nleaf >> (j + 1));
+    b.nslots = b.slot_off[b.levels];
+    b.KB = N / BK;
+    f->NA = b.nslots * KP;
+    const int levels = b.levels, NA = f->NA;
+    // orthonormal polynomial bases of the levels (host, one thread per level)
+    std::vector<std::vector<double>> Qh(levels);
+    std::vector<std::thread> pool;
+    for (int j = 0; j < levels; ++j) pool.emplace_back([&, j]() { poly_basis(FL << j, Qh[j]); });
+    for (auto& t : pool) t.join();
+    std::vector<size_t> qoff(levels);
+    size_t qtot = 0;
+    for (int j = 0; j < levels; ++j) {
+        qoff[j] = qtot;
+        qtot += Qh[j].size();
+    }
+    std::vector<double> Qall(qtot);
+    for (int j = 0; j < levels; ++j) std::copy(Qh[j].begin(), Qh[j].end(), Qall.begin() + qoff[j]);
+    const size_t L = (size_t)p->l_max + 1;
+    const size_t nbA = L * N * NA, nq = 2 * (size_t)N * NA;
+    double* Qd = nullptr;
+    size_t* qoffd = nullptr;
+    bool ok = cudaMalloc((void**)&f->bA_hi, nbA * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->bA_lo, nbA * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->bT_hi, nbA * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->bT_lo, nbA * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->qT_hi, nq * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->qT_lo, nq * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->qA_hi, nq * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->qA_lo, nq * 4) == cudaSuccess &&
+              cudaMalloc((void**)&Qd, qtot * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void**)&qoffd, levels * sizeof(size_t)) == cudaSuccess;
+    ok = ok && cudaMemcpy(Qd, Qall.data(), qtot * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(qoffd, qoff.data(), levels * sizeof(size_t), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(Qd);
+        cudaFree(qoffd);
+        set_error("DSBT_PLAN_FAST_TF32: device allocation or copy failed");
+        return DSBT_ERR_NOMEM;
+    }
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->bA_hi, 0, nbA * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->bA_lo, 0, nbA * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->bT_hi, 0, nbA * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->bT_lo, 0, nbA * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->qT_hi, 0, nq * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->qT_lo, 0, nq * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->qA_hi, 0, nq * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->qA_lo, 0, nq * 4, st));
+    {
+        ProfScope ps(kKPlan, st);
+        k_ftc_beta<<<dim3(levels * (N / 2), (unsigned)L), KP, 0, st>>>(p->T64, Qd, qoffd, b, N, f->bA_hi, f->bA_lo,
+                                                                       f->bT_hi, f->bT_lo);
+        k_ftc_q<<<dim3(levels * (N / 2), 2), KP, 0, st>>>(Qd, qoffd, b, N, f->qT_hi, f->qT_lo, f->qA_hi, f->qA_lo);
+    }
+    DSBT_CUDA_TRY(cudaGetLastError());
+    DSBT_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(Qd);
+    cudaFree(qoffd);
+    int rc = encode_tmap_f32_sw128(&f->tm_bA_hi, f->bA_hi, L * N, NA, 128, 32);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_bA_lo, f->bA_lo, L * N, NA, 128, 32);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_bT_hi, f->bT_hi, L * NA, N, 64, 32);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_bT_lo, f->bT_lo, L * NA, N, 64, 32);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qT_hi, f->qT_hi, 2 * (uint64_t)NA, N, 64, 32);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qT_lo, f->qT_lo, 2 * (uint64_t)NA, N, 64, 32);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qA_hi, f->qA_hi, 2 * (uint64_t)N, NA, 128, 32);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qA_lo, f->qA_lo, 2 * (uint64_t)N, NA, 128, 32);
+    return rc;
+}
+
+void ftc_free(dsbt_plan* p) {
+    if (!p || !p->ftc) return;
+    FtcData* f = p->ftc;
+    cudaFree(f->bA_hi);
+    cudaFree(f->bA_lo);
+    cudaFree(f->bT_hi);
+    cudaFree(f->bT_lo);
+    cudaFree(f->qT_hi);
+    cudaFree(f->qT_lo);
+    cudaFree(f->qA_hi);
+    cudaFree(f->qA_lo);
+    delete f;
+    p->ftc = nullptr;
+}
+
+size_t ftc_scratch_bytes(const dsbt_plan* p, size_t lines) {
+    return p->ftc ? 2 * lines * (size_t)p->ftc->NA * sizeof(float) : 0;
+}
+
+namespace {
+
+// One launch of the segmented kernel over the groups (largest l first).
+int launch_ftc(const dsbt_plan* p, const GroupTable& g, int mode, const CUtensorMap& a1h, const CUtensorMap& a1l,
+               const CUtensorMap& b1h, const CUtensorMap& b1l, const CUtensorMap& a2h, const CUtensorMap& a2l,
+               const CUtensorMap& b2h, const CUtensorMap& b2l, const EpiArgs& ep, int* sched, cudaStream_t st) {
+    FtcSpace fs = p->ftc->base;
+    fs.mode = mode;
+    const bool aug = mode == kMoments || mode == kWeights;
+    fs.RT = aug ? fs.nslots : p->N / BM;
+    fs.t0[0] = 0;
+    for (int i = 0; i < g.ngroups; ++i) {
+        const int gi = g.ngroups - 1 - i;
+        const int nl = g.line0[gi + 1] - g.line0[gi];
+        fs.order[i] = gi;
+        fs.ct[i] = (aug && g.l[gi] == 0) ? 0 : (nl + BN_MAX - 1) / BN_MAX;
+        fs.t0[i + 1] = fs.t0[i] + fs.RT * fs.ct[i];
+    }
+    fs.total = fs.t0[g.ngroups];
+    if (fs.total == 0) return DSBT_OK;
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+    static bool attr_done = false;
+    if (!attr_done) {
+        DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_ftc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_done = true;
+    }
+    int dev = 0, nsm = 0;
+    DSBT_CUDA_TRY(cudaGetDevice(&dev));
+    DSBT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = fs.total < nsm ? fs.total : nsm;
+    DSBT_CUDA_TRY(cudaMemsetAsync(sched, 0, sizeof(int), st));
+    ProfScope ps(kKContractTF32, st);
+    k_contract_ftc<<<grid, NTHREADS, smem, st>>>(a1h, a1l, b1h, b1l, a2h, a2l, b2h, b2l, g, fs, p->N, ep, p->status,
+                                                 sched);
+    DSBT_CUDA_TRY(cudaGetLastError());
+    return DSBT_OK;
+}
+
+}  // namespace
+
+int contract_tf32_fast(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi, const float* in_lo,
+                       int out_mode, float* out0, float* out1, const float2* phase, int* sched, float* scratch,
+                       cudaStream_t st) {
+    const FtcData* f = p->ftc;
+    const int N = p->N, NA = f->NA;
+    const size_t R = (size_t)g.total_lines;
+    float* aug_hi = scratch;
+    float* aug_lo = scratch + R * NA;
+    CUtensorMap in_h, in_l, aug_h, aug_l;
+    int rc = encode_tmap_f32_sw128(&in_h, in_hi, R, N, BBOX, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&in_l, in_lo, R, N, BBOX, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&aug_h, aug_hi, R, NA, BBOX, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&aug_l, aug_lo, R, NA, BBOX, BK);
+    if (rc != DSBT_OK) return rc;
+    const EpiArgs ep_aug{kOutAugSplit, aug_hi, aug_lo, nullptr, 0, NA};
+    const EpiArgs ep_out{out_mode, out0, out1, phase, p->knl != nullptr, N};
+    if (dir > 0) {
+        rc = launch_ftc(p, g, kMoments, f->tm_qT_hi, f->tm_qT_lo, in_h, in_l, f->tm_qT_hi, f->tm_qT_lo, in_h, in_l,
+                        ep_aug, sched, st);
+        if (rc == DSBT_OK)
+            rc = launch_ftc(p, g, kEval, p->tm_T_hi, p->tm_T_lo, in_h, in_l, f->tm_bA_hi, f->tm_bA_lo, aug_h, aug_l,
+                            ep_out, sched, st);
+    } else {
+        rc = launch_ftc(p, g, kWeights, f->tm_bT_hi, f->tm_bT_lo, in_h, in_l, f->tm_bT_hi, f->tm_bT_lo, in_h, in_l,
+                        ep_aug, sched, st);
+        if (rc == DSBT_OK)
+            rc = launch_ftc(p, g, kLeafOut, p->tm_Tt_hi, p->tm_Tt_lo, in_h, in_l, f->tm_qA_hi, f->tm_qA_lo, aug_h,
+                            aug_l, ep_out, sched, st);
+    }
+    return rc;
+}
+
+}  // namespace dsbt

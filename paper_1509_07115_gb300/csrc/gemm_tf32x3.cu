@@ -413,10 +413,21 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
 
 int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi,
                     const float* in_lo, int out_mode, float* out0, float* out1, const float2* phase,
-                    int* sched, cudaStream_t st) {
+                    int* sched, cudaStream_t st, float* fast_scratch) {
     if (!p->has_tmaps) {
         set_error("split-TF32 path needs a plan built with DSBT_PLAN_TF32X3");
         return DSBT_ERR_UNSUPPORTED;
+    }
+    if (p->ftc && fast_scratch && g.total_lines > 0) {
+        if (out_mode == kOutPlanarSplit || out_mode == kOutUserC64) {
+            for (int i = 0; i < g.ngroups; ++i) {
+                if ((g.line0[i] & 1) || ((g.line0[i + 1] - g.line0[i]) & 1)) {
+                    set_error("complex output needs whole channels per group");
+                    return DSBT_ERR_INVALID;
+                }
+            }
+        }
+        return contract_tf32_fast(p, g, dir, in_hi, in_lo, out_mode, out0, out1, phase, sched, fast_scratch, st);
     }
     const int N = p->N;
     TileSpace ts;

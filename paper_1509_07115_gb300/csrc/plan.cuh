@@ -7,7 +7,7 @@
 
 #include "common.cuh"
 
-namespace dsbt { struct FastData; }
+namespace dsbt { struct FastData; struct FtcData; }
 
 struct dsbt_plan {
     int N;
@@ -40,6 +40,8 @@ struct dsbt_plan {
     double* knl;
     // hierarchical FP64 data of DSBT_PLAN_FAST64 (fast64.cu), else nullptr
     dsbt::FastData* fast;
+    // interval bases and projections of DSBT_PLAN_FAST_TF32 (fast_tf32.cu), else nullptr
+    dsbt::FtcData* ftc;
     unsigned* status;          // device status word (kStatusOk / kStatusTimeout)
     double check_err;
     bool has_tmaps;
@@ -115,13 +117,26 @@ void fast_free(dsbt_plan* p);
 size_t fast_scratch_bytes(const dsbt_plan* p, int lines);
 int contract_f64_fast(const dsbt_plan* p, const GroupTable& g, int dir, const double* in, double* out,
                       const double2* phase, double* scratch, cudaStream_t st);
+// Orthonormal basis [len][64] of the polynomials of degree < min(64, len) on
+// the points x_t = (2t+1)/len - 1 (Arnoldi with two Gram-Schmidt passes).
+void poly_basis(int len, std::vector<double>& Q);
+// DSBT_PLAN_FAST_TF32 (fast_tf32.cu)
+bool ftc_supported(int N);
+int ftc_build(dsbt_plan* p, cudaStream_t st);
+void ftc_free(dsbt_plan* p);
+size_t ftc_scratch_bytes(const dsbt_plan* p, size_t lines);
+int contract_tf32_fast(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi, const float* in_lo,
+                       int out_mode, float* out0, float* out1, const float2* phase, int* sched, float* scratch,
+                       cudaStream_t st);
 
 // ---- split-TF32 tensor-core contraction (gemm_tf32x3.cu)
 // B operand: TF32 split lines [lines][N] (hi, lo).  `sched` is a device int
 // (zeroed here before the launch) for the dynamic tile scheduler.  Output modes:
 enum OutMode { kOutUserC64 = 0, kOutUserF32 = 1, kOutPlanarF32 = 2, kOutPlanarSplit = 3 };
+// With a DSBT_PLAN_FAST_TF32 plan and `fast_scratch` (ftc_scratch_bytes of
+// the call's lines) the contraction runs the interval scheme of fast_tf32.cu.
 int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi,
                     const float* in_lo, int out_mode, float* out0, float* out1,
-                    const float2* phase, int* sched, cudaStream_t st);
+                    const float2* phase, int* sched, cudaStream_t st, float* fast_scratch = nullptr);
 
 }  // namespace dsbt

@@ -1,0 +1,76 @@
+"""Split-TF32 tensor-core contractions through the interval scheme
+(DSBT_PLAN_FAST_TF32, csrc/fast_tf32.cu): the near band of T_l per 128-row
+leaf plus the far field through 64 basis functions per used dyadic interval.
+Same results as the FP64 contraction with the dense T_l within the split-TF32
+bar (1e-6 of the channel norm), for every l (odd l carries the m = 0 weight)
+and grids of 2 to 32 leaves."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1509_07115_gb300 import dsbt, inputs
+
+
+def test_fast_tf32_flag_rules():
+    lib = dsbt.load()
+    h = ctypes.c_void_p()
+    assert lib.dsbt_plan_create(1024, 102.4, 4, dsbt.DSBT_PLAN_FAST_TF32 | dsbt.DSBT_PLAN_FP64, None,
+                                ctypes.byref(h)) == -1          # needs the split-TF32 factors
+    assert lib.dsbt_plan_create(768, 76.8, 4, dsbt.DSBT_PLAN_FAST_TF32 | dsbt.DSBT_PLAN_TF32X3, None,
+                                ctypes.byref(h)) == -1          # N / 128 = 6, not a power of two
+
+
+def rel(a, b, nrm):
+    return (np.abs(a - b).max(axis=1) / nrm).max()
+
+
+def counts_for(lmax):
+    c = [1] * (lmax + 1)
+    for l in (0, 1, 2, 3, 31, 32, 33, lmax - 1, lmax):
+        c[l] = 3
+    return c
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("N", [256, 1024, 4096])
+def test_fast_tf32_matches_fp64(lib, N):
+    r_max, lmax, tau = N * 0.1, 63, 0.05
+    counts = counts_for(lmax)
+    x = inputs.gaussian_sum(70 + N, N, r_max / N, counts)
+    nrm = np.linalg.norm(x, axis=1)
+    plan = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, fast_tf32=True)
+    x128 = torch.from_numpy(x).cuda()
+    x64 = x128.to(torch.complex64)
+    ref_b = plan.forward_grouped(counts, x128).cpu().numpy()
+    b = plan.forward_grouped(counts, x64).cpu().numpy()
+    assert rel(b, ref_b, nrm) < 1e-6
+    ref_f = plan.inverse_grouped(counts, torch.from_numpy(ref_b).cuda()).cpu().numpy()
+    f = plan.inverse_grouped(counts, torch.from_numpy(ref_b).cuda().to(torch.complex64)).cpu().numpy()
+    assert rel(f, ref_f, nrm) < 1e-6
+    assert rel(ref_f, x, nrm) < 1e-12                            # the FP64 reference round trip
+    ref_k = plan.kinetic_grouped(counts, x128, tau).cpu().numpy()
+    k = plan.kinetic_grouped(counts, x64, tau).cpu().numpy()
+    assert rel(k, ref_k, nrm) < 1e-6
+    plan.close()
+
+
+@pytest.mark.gpu
+def test_fast_tf32_error_close_to_dense_tf32(lib):
+    """The interval scheme adds no error of its own beyond the split-TF32
+    rounding: its deviation from FP64 stays within 2x of the dense split-TF32
+    contraction's on the same input."""
+    N, r_max, lmax = 2048, 204.8, 63
+    counts = counts_for(lmax)
+    x = inputs.gaussian_sum(91, N, r_max / N, counts)
+    nrm = np.linalg.norm(x, axis=1)
+    x128 = torch.from_numpy(x).cuda()
+    fast = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, fast_tf32=True)
+    dense = lib.Plan(N, r_max, lmax, fp64=False, tf32x3=True)
+    ref = fast.forward_grouped(counts, x128).cpu().numpy()
+    e_fast = rel(fast.forward_grouped(counts, x128.to(torch.complex64)).cpu().numpy(), ref, nrm)
+    e_dense = rel(dense.forward_grouped(counts, x128.to(torch.complex64)).cpu().numpy(), ref, nrm)
+    fast.close()
+    dense.close()
+    assert e_fast < max(2.0 * e_dense, 2e-7), (e_fast, e_dense)
