@@ -13,8 +13,11 @@ Printed JSON line (rank 0):
               (dsbt_kinetic_grouped_host: copies inside the call, overlapped in chunks)
               (host->device copy of the inputs and device->host copy of the
               result inside the timed region)
-  roofline    of the dominant kernel (the split-TF32 contraction), timed live
-              with CUDA events on its launch stream during the timed steps
+  roofline    of the dominant kernel (the split-TF32 contraction through the
+              interval scheme of DSBT_PLAN_FAST_TF32; --dense: the dense one),
+              timed live with CUDA events on its launch stream during the
+              timed steps; algorithmic flops of the scheme it runs
+  dense_tf32  the same step with the dense split-TF32 contraction
   fp64_gpu    the plain FP64 GPU path on a one-eighth sample (batch 1), and the
               split-TF32 error against it (max |diff| / ||psi|| per channel)
   cpu_baseline  the FP64 CPU oracle on a bounded sample (N = 4096, l = 1, 2)
@@ -88,10 +91,24 @@ def source_hash(paths):
     return m.hexdigest()[:16]
 
 
-def ncu_traffic():
+def fast_tf32_mac_per_line(N, l, leaf=128):
+    """Multiply-adds of one DSBT_PLAN_FAST_TF32 contraction of one real line of
+    T_l (forward and inverse cost the same): near-field triangle of each
+    128-row leaf, far field (l per set bit of the leaf index), moments of the
+    used intervals (l per point of half the columns at each level), and the
+    dense completion rows n < n0_l = (l + 2) // 2."""
+    nleaf = N // leaf
+    levels = (nleaf - 1).bit_length()
+    ne = (l + 2) // 2 - (1 if l % 2 == 0 else 0)
+    near = sum(r % leaf + 1 for r in range(ne, N))
+    far = sum(l * bin(r // leaf).count("1") for r in range(ne, N))
+    return near + far + levels * (N // 2) * l + ne * N
+
+
+def ncu_traffic(name="contract_tf32x3_precision_form.json"):
     """DRAM bytes per launch of the contraction from the committed ncu summary,
     if it was taken on the current kernel sources (else None)."""
-    prof = os.path.join(ROOT, "profiles", "contract_tf32x3_precision_form.json")
+    prof = os.path.join(ROOT, "profiles", name)
     try:
         with open(prof) as fh:
             d = json.load(fh)
@@ -425,6 +442,39 @@ def batch_leg(dsbt, inputs, torch, dev, steps, warmup):
 
 # ---------------------------------------------------------------- GPU leg
 
+def dense_leg(dsbt, torch, counts, x, peak, args):
+    """The same kinetic step with the dense split-TF32 contraction (a plan
+    without DSBT_PLAN_FAST_TF32), for comparison with the interval scheme."""
+    nchan = sum(counts)
+    p = dsbt.Plan(N, R_MAX, L_MAX, fp64=False, tf32x3=True)
+    y = torch.empty_like(x)
+    ws = p.workspace(nchan, torch.complex64)
+    for _ in range(3):
+        p.kinetic_grouped(counts, x, TAU, out=y, workspace=ws)
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 3)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dsbt.profile_enable(True)
+    e0.record(st)
+    for _ in range(steps):
+        p.kinetic_grouped(counts, x, TAU, out=y, workspace=ws)
+    e1.record(st)
+    torch.cuda.synchronize()
+    prof = dsbt.profile_read()
+    dsbt.profile_enable(False)
+    ms = e0.elapsed_time(e1) / steps
+    n_c, ms_c = prof.get("contract_tf32x3", (0, 0.0))
+    ach = FLOP_PER_CHANNEL * nchan / (ms_c / max(1, n_c) * 1e-3) / 1e12
+    p.close()
+    del ws
+    torch.cuda.empty_cache()
+    return {"ms_per_step": ms, "value": 2 * nchan / (ms * 1e-3), "unit": UNIT,
+            "contraction_ms_per_step": ms_c / steps,
+            "roofline": {"bound": "tensor", "kernel": "contract_tf32x3", "achieved": ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": ach / peak, "flop_per_launch": FLOP_PER_CHANNEL * nchan}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,6 +486,8 @@ def main():
     ap.add_argument("--no-tdse", action="store_true", help="skip the TDSE propagation/adjoint leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch leg")
     ap.add_argument("--e2e-chunks", type=int, default=8, help="chunks of the host-streamed e2e call")
+    ap.add_argument("--dense", action="store_true",
+                    help="time the dense split-TF32 contraction instead of the interval scheme")
     ap.add_argument("--workload", default="precision", choices=sorted(WORKLOADS),
                     help="'small' is a reduced case for profiler captures, not a bench line")
     args = ap.parse_args()
@@ -465,7 +517,8 @@ def main():
         if world > 1:
             dist.barrier()
 
-    plan = dsbt.Plan(N, R_MAX, L_MAX, fp64=not args.no_fp64, tf32x3=True)
+    fast = not args.dense
+    plan = dsbt.Plan(N, R_MAX, L_MAX, fp64=not args.no_fp64, tf32x3=True, fast_tf32=fast)
     x = inputs.gaussian_sum(100 + rank, N, DR, counts, dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
     ws = plan.workspace(nchan, torch.complex64)
@@ -539,16 +592,27 @@ def main():
 
     # ---------------------------------------------------------- roofline of the contraction
     peaks, src = load_peaks()
+    peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
     k_launches, k_ms = prof.get("contract_tf32x3", (0, 0.0))
     avg_ms = k_ms / max(1, k_launches)
-    flop_per_launch = FLOP_PER_CHANNEL * nchan
+    launches_per_step = k_launches / args.steps
+    if fast:
+        # four launches per step (moments, forward rows, adjoint weights, adjoint
+        # columns); algorithmic flops of the interval scheme, 3 split products
+        flop_per_step = 2 * 3 * 2.0 * sum(2 * c * fast_tf32_mac_per_line(N, l) for l, c in enumerate(counts))
+        kname, tname = "contract_ftc (interval scheme, DSBT_PLAN_FAST_TF32)", "contract_ftc_precision_form.json"
+    else:
+        flop_per_step = 2 * FLOP_PER_CHANNEL * nchan
+        kname, tname = "contract_tf32x3", "contract_tf32x3_precision_form.json"
+    flop_per_launch = flop_per_step / launches_per_step
     achieved = flop_per_launch / (avg_ms * 1e-3) / 1e12
-    peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
-    traffic = ncu_traffic() if args.workload == "precision" else None
-    roofline = {"bound": "tensor", "kernel": "contract_tf32x3", "achieved": achieved, "peak": peak,
+    traffic = ncu_traffic(tname) if args.workload == "precision" else None
+    roofline = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{src}: bf16 sustained x {TF32_OVER_BF16:.3f} (nominal tf32/bf16)",
                 "flop_per_launch": flop_per_launch, "avg_launch_ms": avg_ms,
+                "launches_per_step": launches_per_step,
+                "dense_equivalent_tflops": 2 * FLOP_PER_CHANNEL * nchan / (k_ms / args.steps * 1e-3) / 1e12,
                 "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
 
     line = None
@@ -598,6 +662,10 @@ def main():
                                 "ms_per_step": f_ms, "speedup_of_split_tf32": value / world / fp64_value,
                                 "split_tf32_max_rel_err": {"kinetic_round_trip": err_rt, "forward": err_fw,
                                                            "norm_drift": drift}}
+
+    # ---------------------------------------------------------- dense split-TF32 contraction (context)
+    if rank == 0 and fast and args.workload == "precision":
+        line["dense_tf32"] = dense_leg(dsbt, torch, counts, x, peak, args)
 
     # ---------------------------------------------------------- TDSE (propagator + adjoint)
     if rank == 0 and not args.no_tdse and args.workload == "precision":
