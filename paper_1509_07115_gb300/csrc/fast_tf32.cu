@@ -54,7 +54,11 @@ constexpr int BK = 32;
 constexpr int BN_MAX = 256;
 constexpr int BBOX = 64;                           // rows per B TMA box
 constexpr int STAGES = 2;
-constexpr int KC = 4;                              // K blocks per main-accumulator chunk
+// K blocks per main-accumulator chunk: the tensor cores accumulate with
+// truncation, so a shorter chunk than the dense kernel's 4 keeps the scheme's
+// longer chains of sums (moments, then the far field) at the dense kernel's
+// accuracy (round trip 5.8e-7 against 8.5e-7 with 4, N = 4096, l <= 63).
+constexpr int KC = 3;
 constexpr int EPI_WARPS = 8;
 constexpr int QS = 4;                              // tile-queue slots
 constexpr int A_BYTES = BM * BK * 4;               // 16 KiB
@@ -70,6 +74,7 @@ enum Mode { kMoments = 0, kEval = 1, kWeights = 2, kLeafOut = 3 };
 
 struct FtcSpace {
     int mode;
+    int kc;                        // K blocks per main-accumulator chunk
     int RT;                        // row tiles of this launch
     int KB;                        // K blocks of N
     int nleaf, levels, nslots;
@@ -330,8 +335,8 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 const int nkb = seg_count(fs, l, tl.rt);
                 const uint32_t idesc = idesc_tf32(BM, tl.nmma);
                 uint32_t acc_corr = 0;
-                for (int c0 = 0; c0 < nkb && ok; c0 += KC) {
-                    const int c1 = min(nkb, c0 + KC);
+                for (int c0 = 0; c0 < nkb && ok; c0 += fs.kc) {
+                    const int c1 = min(nkb, c0 + fs.kc);
                     const bool pre = c0 > 0;
                     if (pre) {
                         if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
@@ -413,11 +418,11 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
 #pragma unroll
             for (int j = 0; j < 128; ++j) acc[j] = 0.f;
             bool ok = true;
-            for (int c0 = 0; c0 < nkb; c0 += KC) {
+            for (int c0 = 0; c0 < nkb; c0 += fs.kc) {
                 if (!mbar_wait(main_full, mphase, abort_flag, status)) { ok = false; break; }
                 mphase ^= 1;
                 tc_fence_after();
-                const bool last = c0 + KC >= nkb;
+                const bool last = c0 + fs.kc >= nkb;
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) {
                     if (ch < nch) {
@@ -682,6 +687,7 @@ int launch_ftc(const dsbt_plan* p, const GroupTable& g, int mode, const CUtensor
                const CUtensorMap& b2h, const CUtensorMap& b2l, const EpiArgs& ep, int* sched, cudaStream_t st) {
     FtcSpace fs = p->ftc->base;
     fs.mode = mode;
+    fs.kc = KC;
     const bool aug = mode == kMoments || mode == kWeights;
     fs.RT = aug ? fs.nslots : p->N / BM;
     fs.t0[0] = 0;
