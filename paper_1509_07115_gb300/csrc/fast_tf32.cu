@@ -25,9 +25,9 @@
 //                                      + sum_(s,k) QA[c][(s,k)] W[line][(s,k)]  (used slots holding c)
 // with B[r][(s,k)] = beta_{r,j}[k] (zero unless s is a far slot of r), BT its
 // transpose, QT[(s,k)][t] = Q_j[t - i len][k] sqrt(w_t) and QA its transpose,
-// all split into TF32 pairs.  MOMENTS and WEIGHTS tiles hold one slot (64 of
-// the 128 TMEM lanes carry results; the A box is 64 rows and the other half of
-// the A tile is ignored).  K blocks of a tile come from up to two operand
+// all split into TF32 pairs.  MOMENTS and WEIGHTS tiles hold two slots (64
+// rows of QT / BT each; a slot of odd level with the child slot whose range it
+// contains, else two slots of similar length).  K blocks of a tile come from up to two operand
 // sources (near: T / T^T against the lines; far: B / QA against M / W), listed
 // per tile by segments.
 //
@@ -67,7 +67,8 @@ constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr int FL = 128;                            // leaf = output row tile
 constexpr int KP = 64;                             // basis functions per interval (>= l_max)
-constexpr int MAX_LEVELS = 10;                     // N / 128 <= 2^10
+constexpr int MAX_LEVELS = 6;                      // N / 128 <= 64 (plans have N <= 8192)
+constexpr int MAX_SLOTS = (1 << MAX_LEVELS) - 1;
 constexpr int MAX_SEGS = MAX_LEVELS + 3;
 
 enum Mode { kMoments = 0, kEval = 1, kWeights = 2, kLeafOut = 3 };
@@ -79,6 +80,8 @@ struct FtcSpace {
     int KB;                        // K blocks of N
     int nleaf, levels, nslots;
     int slot_off[MAX_LEVELS + 1];  // first slot of level j
+    int npairs;                    // MOMENTS / WEIGHTS tiles: slot pairs (b = -1: single slot)
+    int pair_a[MAX_SLOTS], pair_b[MAX_SLOTS];
     int total;                     // tiles
     int order[kMaxGroups];         // group visited at position i
     int t0[kMaxGroups + 1];        // first tile of position i
@@ -98,7 +101,7 @@ __device__ __forceinline__ Tile decode(const FtcSpace& fs, const GroupTable& gt,
     const int q = local / fs.ct[i];
     tl.g = g;
     tl.ct = local - q * fs.ct[i];
-    if (fs.mode == kMoments || fs.mode == kWeights) tl.rt = fs.RT - 1 - q;   // longest slots first
+    if (fs.mode == kMoments || fs.mode == kWeights) tl.rt = q;   // pairs are sorted longest first
     else if (fs.mode == kEval) tl.rt = (q == 0) ? 0 : fs.RT - q;            // dense leaf 0 first
     else tl.rt = q;
     const int nl = gt.line0[g + 1] - gt.line0[g];
@@ -113,6 +116,16 @@ __device__ __forceinline__ void slot_ji(const FtcSpace& fs, int s, int& j, int& 
     j = 0;
     while (j + 1 < fs.levels && fs.slot_off[j + 1] <= s) ++j;
     i = 2 * (s - fs.slot_off[j]);
+}
+
+// K blocks [k0, k1) a MOMENTS (the interval's columns) or WEIGHTS (its
+// sibling's rows) slot contracts over.
+__device__ __forceinline__ void aug_range(const FtcSpace& fs, int s, int& k0, int& k1) {
+    int j, i;
+    slot_ji(fs, s, j, i);
+    const int lb = (FL << j) / BK;
+    k0 = (fs.mode == kMoments) ? i * lb : (i + 1) * lb;
+    k1 = k0 + lb;
 }
 
 // K blocks of one tile: segments [k0, k1) of operand source src (1 near, 2 far).
@@ -153,11 +166,19 @@ __device__ __forceinline__ Segs segments(const FtcSpace& fs, int l, int rt) {
     const int nx = n_extra(l);
     const int nf = (l + BK - 1) / BK;   // far K blocks per slot (basis functions k < l)
     if (fs.mode == kMoments || fs.mode == kWeights) {
-        int j, i;
-        slot_ji(fs, rt, j, i);
-        const int lb = (FL << j) / BK;   // K blocks of the interval
-        const int first = (fs.mode == kMoments) ? i * lb : (i + 1) * lb;
-        sg.add(1, first, first + lb);
+        // the K ranges of the tile's two slots are dyadic intervals: nested
+        // (one segment, the larger) or disjoint (two segments)
+        int a0, a1, b0 = 0, b1 = 0;
+        aug_range(fs, fs.pair_a[rt], a0, a1);
+        if (fs.pair_b[rt] >= 0) aug_range(fs, fs.pair_b[rt], b0, b1);
+        if (b1 <= b0 || (b0 >= a0 && b1 <= a1)) {
+            sg.add(1, a0, a1);
+        } else if (a0 >= b0 && a1 <= b1) {
+            sg.add(1, b0, b1);
+        } else {
+            sg.add(1, a0, a1);
+            sg.add(1, b0, b1);
+        }
     } else if (fs.mode == kEval) {
         if (rt == 0) {
             sg.add(1, 0, nx > 0 ? fs.KB : FL / BK);
@@ -189,9 +210,12 @@ __device__ __forceinline__ int seg_count(const FtcSpace& fs, int l, int rt) {
     const int nx = n_extra(l);
     const int nf = (l + BK - 1) / BK;
     if (fs.mode == kMoments || fs.mode == kWeights) {
-        int j, i;
-        slot_ji(fs, rt, j, i);
-        return (FL << j) / BK;
+        int a0, a1, b0 = 0, b1 = 0;
+        aug_range(fs, fs.pair_a[rt], a0, a1);
+        if (fs.pair_b[rt] >= 0) aug_range(fs, fs.pair_b[rt], b0, b1);
+        if (b1 <= b0 || (b0 >= a0 && b1 <= a1)) return a1 - a0;
+        if (a0 >= b0 && a1 <= b1) return b1 - b0;
+        return (a1 - a0) + (b1 - b0);
     }
     if (fs.mode == kEval) return rt == 0 ? (nx > 0 ? fs.KB : FL / BK) : __popc(rt) * nf + FL / BK;
     int c = ((rt > 0 && nx > 0) ? 1 : 0) + FL / BK;
@@ -281,11 +305,16 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 const int l = gt.l[tl.g];
                 const Segs sg = segments(fs, l, tl.rt);
                 const int nbox = (tl.nmma + BBOX - 1) / BBOX;
-                const uint32_t bytes = 2 * a_bytes + 2 * nbox * BBOX * BK * 4;
+                const bool pair = aug && fs.pair_b[tl.rt] >= 0;
+                const uint32_t bytes = 2 * a_bytes * (pair ? 2 : 1) + 2 * nbox * BBOX * BK * 4;
                 int arow1, arow2 = 0;
-                if (fs.mode == kMoments) arow1 = ((l & 1) * fs.nslots + tl.rt) * KP;
-                else if (fs.mode == kWeights) arow1 = (l * fs.nslots + tl.rt) * KP;
-                else {
+                if (fs.mode == kMoments) {
+                    arow1 = ((l & 1) * fs.nslots + fs.pair_a[tl.rt]) * KP;
+                    if (pair) arow2 = ((l & 1) * fs.nslots + fs.pair_b[tl.rt]) * KP;
+                } else if (fs.mode == kWeights) {
+                    arow1 = (l * fs.nslots + fs.pair_a[tl.rt]) * KP;
+                    if (pair) arow2 = (l * fs.nslots + fs.pair_b[tl.rt]) * KP;
+                } else {
                     arow1 = l * N + tl.rt * BM;
                     arow2 = (fs.mode == kEval ? l : (l & 1)) * N + tl.rt * BM;
                 }
@@ -301,9 +330,18 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                     const CUtensorMap* al = src == 1 ? &tmA1_lo : &tmA2_lo;
                     const CUtensorMap* bh = src == 1 ? &tmB1_hi : &tmB2_hi;
                     const CUtensorMap* bl = src == 1 ? &tmB1_lo : &tmB2_lo;
-                    const int arow = src == 1 ? arow1 : arow2;
-                    tma_load_2d(sb, ah, &full[stage], kb * BK, arow);
-                    tma_load_2d(sb + A_BYTES, al, &full[stage], kb * BK, arow);
+                    if (aug) {   // slot a -> A rows 0..63, slot b -> rows 64..127
+                        tma_load_2d(sb, ah, &full[stage], kb * BK, arow1);
+                        tma_load_2d(sb + A_BYTES, al, &full[stage], kb * BK, arow1);
+                        if (pair) {
+                            tma_load_2d(sb + KP * 128, ah, &full[stage], kb * BK, arow2);
+                            tma_load_2d(sb + A_BYTES + KP * 128, al, &full[stage], kb * BK, arow2);
+                        }
+                    } else {
+                        const int arow = src == 1 ? arow1 : arow2;
+                        tma_load_2d(sb, ah, &full[stage], kb * BK, arow);
+                        tma_load_2d(sb + A_BYTES, al, &full[stage], kb * BK, arow);
+                    }
                     for (int b = 0; b < nbox; ++b) {
                         tma_load_2d_hint(sb + 2 * A_BYTES + b * BBOX * 128, bh, &full[stage], kb * BK,
                                          brow + b * BBOX, pol_b);
@@ -408,8 +446,13 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             const int nkb = seg_count(fs, l, tl.rt);
             const int nl = gt.line0[tl.g + 1] - gt.line0[tl.g];
             const int trow = quarter * 32 + lane;                 // TMEM lane = A row of the tile
-            const int row = aug ? tl.rt * KP + trow : tl.rt * BM + trow;
-            const bool store_row = !aug || trow < KP;
+            int row = tl.rt * BM + trow;
+            bool store_row = true;
+            if (aug) {   // lanes 0..63: slot a, 64..127: slot b
+                const int slot = trow < KP ? fs.pair_a[tl.rt] : fs.pair_b[tl.rt];
+                store_row = slot >= 0;
+                row = slot * KP + (trow & (KP - 1));
+            }
             const int cbase = tl.ct * BN_MAX + half * 128;
             const int ncols = min(128, nl - cbase);
             const int nch = (tl.nmma > half * 128) ? ((min(tl.nmma - half * 128, 128) + 31) >> 5) : 0;
@@ -561,6 +604,8 @@ __global__ void k_ftc_q(const double* __restrict__ Q, const size_t* __restrict__
 
 struct FtcData {
     FtcSpace base{};   // nleaf, levels, nslots, slot_off
+    int np_m = 0, np_w = 0;                        // slot pairs of the MOMENTS / WEIGHTS tiles
+    int pa_m[MAX_SLOTS], pb_m[MAX_SLOTS], pa_w[MAX_SLOTS], pb_w[MAX_SLOTS];
     int NA = 0;
     float* bA_hi = nullptr;
     float* bA_lo = nullptr;
@@ -572,6 +617,42 @@ struct FtcData {
     float* qA_lo = nullptr;
     CUtensorMap tm_bA_hi, tm_bA_lo, tm_bT_hi, tm_bT_lo, tm_qT_hi, tm_qT_lo, tm_qA_hi, tm_qA_lo;
 };
+
+// MOMENTS / WEIGHTS tiles hold two slots.  Each slot (j, i) of an odd level j
+// takes the child slot whose range lies inside its own: (j - 1, 2i) for the
+// moments (the interval's columns), (j - 1, 2i + 2) for the adjoint weights
+// (the sibling's rows), so the child adds no K blocks; the other slots go two
+// by two in order of decreasing length.  Tiles are sorted longest first.
+static void build_pairs(const FtcSpace& b, int child, int& npairs, int* pa, int* pb) {
+    std::vector<int> used(b.nslots, 0);
+    std::vector<std::pair<int, int>> pairs;
+    auto slot = [&](int j, int i) { return b.slot_off[j] + i / 2; };
+    for (int j = 1; j < b.levels; j += 2)
+        for (int i = 0; i + 1 < (b.nleaf >> j); i += 2) {
+            const int c = 2 * i + child;
+            pairs.push_back({slot(j, i), slot(j - 1, c)});
+            used[slot(j, i)] = used[slot(j - 1, c)] = 1;
+        }
+    std::vector<int> rest;
+    for (int j = b.levels - 1; j >= 0; --j)
+        for (int i = 0; i + 1 < (b.nleaf >> j); i += 2)
+            if (!used[slot(j, i)]) rest.push_back(slot(j, i));
+    for (size_t q = 0; q < rest.size(); q += 2)
+        pairs.push_back({rest[q], q + 1 < rest.size() ? rest[q + 1] : -1});
+    auto level_of = [&](int s) {
+        int j = 0;
+        while (j + 1 < b.levels && b.slot_off[j + 1] <= s) ++j;
+        return j;
+    };
+    std::stable_sort(pairs.begin(), pairs.end(), [&](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+        return level_of(x.first) > level_of(y.first);
+    });
+    npairs = (int)pairs.size();
+    for (int q = 0; q < npairs; ++q) {
+        pa[q] = pairs[q].first;
+        pb[q] = pairs[q].second;
+    }
+}
 
 bool ftc_supported(int N) {
     const int nleaf = N / FL;
@@ -594,6 +675,8 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
     b.nslots = b.slot_off[b.levels];
     b.KB = N / BK;
     f->NA = b.nslots * KP;
+    build_pairs(b, 0, f->np_m, f->pa_m, f->pb_m);
+    build_pairs(b, 2, f->np_w, f->pa_w, f->pb_w);
     const int levels = b.levels, NA = f->NA;
     // orthonormal polynomial bases of the levels (host, one thread per level)
     std::vector<std::vector<double>> Qh(levels);
@@ -689,7 +772,16 @@ int launch_ftc(const dsbt_plan* p, const GroupTable& g, int mode, const CUtensor
     fs.mode = mode;
     fs.kc = KC;
     const bool aug = mode == kMoments || mode == kWeights;
-    fs.RT = aug ? fs.nslots : p->N / BM;
+    if (aug) {
+        const FtcData* f = p->ftc;
+        const bool m = mode == kMoments;
+        fs.npairs = m ? f->np_m : f->np_w;
+        for (int q = 0; q < fs.npairs; ++q) {
+            fs.pair_a[q] = m ? f->pa_m[q] : f->pa_w[q];
+            fs.pair_b[q] = m ? f->pb_m[q] : f->pb_w[q];
+        }
+    }
+    fs.RT = aug ? fs.npairs : p->N / BM;
     fs.t0[0] = 0;
     for (int i = 0; i < g.ngroups; ++i) {
         const int gi = g.ngroups - 1 - i;
