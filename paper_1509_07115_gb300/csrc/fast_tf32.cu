@@ -17,13 +17,15 @@
 // Every step is then the dense contraction kernel of gemm_tf32x3.cu with other
 // operands and K ranges:
 //   forward   MOMENTS  M[line][(s,k)]  = sum_t QT[(s,k)][t] f[line][t]          (t in interval s)
-//             EVAL     b[line][r]      = sum_c T[r][c] f[line][c]  (near band: c in r's leaf;
-//                                                                   leaf 0: all c)
+//             EVAL     b[line][r]      = sum_c T[r][c] f[line][c]  (near band: c in r's leaf)
 //                                      + sum_(s,k) B[r][(s,k)] M[line][(s,k)]  (far slots of r)
 //   inverse   WEIGHTS  W[line][(s,k)]  = sum_r BT[(s,k)][r] b[line][r]          (r in sibling of s)
 //             LEAFOUT  f[line][c]      = sum_r T^T[c][r] b[line][r] (completion rows and near band)
 //                                      + sum_(s,k) QA[c][(s,k)] W[line][(s,k)]  (used slots holding c)
-// with B[r][(s,k)] = beta_{r,j}[k] (zero unless s is a far slot of r), BT its
+// The completion rows n < n0_l (Sec. 2.5) are polynomials of degree < l in m
+// too, so the forward gives them the columns right of leaf 0 through extra
+// "right" slots: the intervals (j, 1), j = 0 .. levels - 1.
+// With B[r][(s,k)] = beta_{r,j}[k] (zero unless s is a far slot of r), BT its
 // transpose, QT[(s,k)][t] = Q_j[t - i len][k] sqrt(w_t) and QA its transpose,
 // all split into TF32 pairs.  MOMENTS and WEIGHTS tiles hold two slots (64
 // rows of QT / BT each; a slot of odd level with the child slot whose range it
@@ -79,6 +81,7 @@ struct FtcSpace {
     int RT;                        // row tiles of this launch
     int KB;                        // K blocks of N
     int nleaf, levels, nslots;
+    int nslots_f;                  // forward slots: the used ones, then the right intervals (j, 1)
     int slot_off[MAX_LEVELS + 1];  // first slot of level j
     int npairs;                    // MOMENTS / WEIGHTS tiles: slot pairs (b = -1: single slot)
     int pair_a[MAX_SLOTS], pair_b[MAX_SLOTS];
@@ -111,8 +114,15 @@ __device__ __forceinline__ Tile decode(const FtcSpace& fs, const GroupTable& gt,
     return tl;
 }
 
-// slot s -> (level j, interval i)
-__device__ __forceinline__ void slot_ji(const FtcSpace& fs, int s, int& j, int& i) {
+// slot s -> (level j, interval i); slots s >= nslots (forward only) are the
+// right intervals (j, 1), j = s - nslots, that cover the columns right of
+// leaf 0 for the completion rows.
+__host__ __device__ inline void slot_ji(const FtcSpace& fs, int s, int& j, int& i) {
+    if (s >= fs.nslots) {
+        j = s - fs.nslots;
+        i = 1;
+        return;
+    }
     j = 0;
     while (j + 1 < fs.levels && fs.slot_off[j + 1] <= s) ++j;
     i = 2 * (s - fs.slot_off[j]);
@@ -181,7 +191,14 @@ __device__ __forceinline__ Segs segments(const FtcSpace& fs, int l, int rt) {
         }
     } else if (fs.mode == kEval) {
         if (rt == 0) {
-            sg.add(1, 0, nx > 0 ? fs.KB : FL / BK);
+            // leaf 0: near band; the completion rows (polynomials of degree < l
+            // in m as well) take the columns right of it through the right slots
+            sg.add(1, 0, FL / BK);
+            if (nx > 0)
+                for (int j = 0; j < fs.levels; ++j) {
+                    const int s = fs.nslots + j;
+                    sg.add(2, s * (KP / BK), s * (KP / BK) + nf);
+                }
         } else {
             for (int j = 0; j < fs.levels; ++j)
                 if ((rt >> j) & 1) {
@@ -217,7 +234,7 @@ __device__ __forceinline__ int seg_count(const FtcSpace& fs, int l, int rt) {
         if (a0 >= b0 && a1 <= b1) return b1 - b0;
         return (a1 - a0) + (b1 - b0);
     }
-    if (fs.mode == kEval) return rt == 0 ? (nx > 0 ? fs.KB : FL / BK) : __popc(rt) * nf + FL / BK;
+    if (fs.mode == kEval) return rt == 0 ? FL / BK + (nx > 0 ? fs.levels * nf : 0) : __popc(rt) * nf + FL / BK;
     int c = ((rt > 0 && nx > 0) ? 1 : 0) + FL / BK;
     for (int j = 0; j < fs.levels; ++j) {
         const int i = rt >> j;
@@ -309,8 +326,8 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 const uint32_t bytes = 2 * a_bytes * (pair ? 2 : 1) + 2 * nbox * BBOX * BK * 4;
                 int arow1, arow2 = 0;
                 if (fs.mode == kMoments) {
-                    arow1 = ((l & 1) * fs.nslots + fs.pair_a[tl.rt]) * KP;
-                    if (pair) arow2 = ((l & 1) * fs.nslots + fs.pair_b[tl.rt]) * KP;
+                    arow1 = ((l & 1) * fs.nslots_f + fs.pair_a[tl.rt]) * KP;
+                    if (pair) arow2 = ((l & 1) * fs.nslots_f + fs.pair_b[tl.rt]) * KP;
                 } else if (fs.mode == kWeights) {
                     arow1 = (l * fs.nslots + fs.pair_a[tl.rt]) * KP;
                     if (pair) arow2 = (l * fs.nslots + fs.pair_b[tl.rt]) * KP;
@@ -560,7 +577,7 @@ __global__ void k_ftc_beta(const double* __restrict__ T64, const double* __restr
     const int len = FL << j;
     const int s = fs.slot_off[j] + q / len, i = 2 * (q / len);
     const int r = (i + 1) * len + q % len;
-    const int NA = fs.nslots * KP;
+    const int NA = fs.nslots * KP, NAF = fs.nslots_f * KP;
     double b = 0.0;
     if (r >= n_extra(l) && k < l) {
         const double* row = T64 + ((size_t)l * N + r) * N + (size_t)i * len;
@@ -571,8 +588,9 @@ __global__ void k_ftc_beta(const double* __restrict__ T64, const double* __restr
         }
     }
     const float h = round_tf32((float)b), lo = round_tf32((float)(b - (double)h));
-    const size_t oa = ((size_t)l * N + r) * NA + (size_t)s * KP + k;
+    const size_t oa = ((size_t)l * N + r) * NAF + (size_t)s * KP + k;
     const size_t ot = (((size_t)l * fs.nslots + s) * KP + k) * N + r;
+    (void)NA;
     bA_hi[oa] = h;
     bA_lo[oa] = lo;
     bT_hi[ot] = h;
@@ -592,12 +610,50 @@ __global__ void k_ftc_q(const double* __restrict__ Q, const size_t* __restrict__
     const int NA = fs.nslots * KP;
     const double v = Q[qoff[j] + (size_t)t * KP + k] * ((p == 1 && c == 0) ? 0.70710678118654752440 : 1.0);
     const float h = round_tf32((float)v), lo = round_tf32((float)(v - (double)h));
-    const size_t ot = (((size_t)p * fs.nslots + s) * KP + k) * N + c;
+    const size_t ot = (((size_t)p * fs.nslots_f + s) * KP + k) * N + c;
     const size_t oa = ((size_t)p * N + c) * NA + (size_t)s * KP + k;
     qT_hi[ot] = h;
     qT_lo[ot] = lo;
     qA_hi[oa] = h;
     qA_lo[oa] = lo;
+}
+
+// Right slots (j, 1): beta of the completion rows r < n0_l - p_l on the
+// columns [len_j, 2 len_j) into B[l][r][(nslots + j, k)].  Block (j, l), KP
+// threads (k).
+__global__ void k_ftc_beta_right(const double* __restrict__ T64, const double* __restrict__ Q,
+                                 const size_t* __restrict__ qoff, FtcSpace fs, int N, float* bA_hi, float* bA_lo) {
+    const int j = blockIdx.x, l = blockIdx.y, k = threadIdx.x;
+    const int len = FL << j, NAF = fs.nslots_f * KP;
+    const double* Qj = Q + qoff[j];
+    for (int r = 0; r < n_extra(l); ++r) {
+        double b = 0.0;
+        if (k < l) {
+            const double* row = T64 + ((size_t)l * N + r) * N + len;
+            for (int t = 0; t < len; ++t) b = fma(row[t], Qj[(size_t)t * KP + k], b);
+        }
+        const float h = round_tf32((float)b), lo = round_tf32((float)(b - (double)h));
+        const size_t oa = ((size_t)l * N + r) * NAF + (size_t)(fs.nslots + j) * KP + k;
+        bA_hi[oa] = h;
+        bA_lo[oa] = lo;
+    }
+}
+
+// QT rows of the right slots: QT[p][(nslots + j, k)][len_j + t] = Q_j[t][k]
+// (columns >= 128 carry weight 1).  Block (position over all j, p), KP threads.
+__global__ void k_ftc_q_right(const double* __restrict__ Q, const size_t* __restrict__ qoff, FtcSpace fs, int N,
+                              float* qT_hi, float* qT_lo) {
+    int t = blockIdx.x, j = 0;
+    while (t >= (FL << j)) {
+        t -= FL << j;
+        ++j;
+    }
+    const int p = blockIdx.y, k = threadIdx.x, c = (FL << j) + t;
+    const double v = Q[qoff[j] + (size_t)t * KP + k];
+    const float h = round_tf32((float)v), lo = round_tf32((float)(v - (double)h));
+    const size_t ot = (((size_t)p * fs.nslots_f + fs.nslots + j) * KP + k) * N + c;
+    qT_hi[ot] = h;
+    qT_lo[ot] = lo;
 }
 
 }  // namespace
@@ -606,7 +662,7 @@ struct FtcData {
     FtcSpace base{};   // nleaf, levels, nslots, slot_off
     int np_m = 0, np_w = 0;                        // slot pairs of the MOMENTS / WEIGHTS tiles
     int pa_m[MAX_SLOTS], pb_m[MAX_SLOTS], pa_w[MAX_SLOTS], pb_w[MAX_SLOTS];
-    int NA = 0;
+    int NA = 0, NAF = 0;   // augmented widths: adjoint (used slots), forward (+ right slots)
     float* bA_hi = nullptr;
     float* bA_lo = nullptr;
     float* bT_hi = nullptr;
@@ -623,8 +679,9 @@ struct FtcData {
 // moments (the interval's columns), (j - 1, 2i + 2) for the adjoint weights
 // (the sibling's rows), so the child adds no K blocks; the other slots go two
 // by two in order of decreasing length.  Tiles are sorted longest first.
-static void build_pairs(const FtcSpace& b, int child, int& npairs, int* pa, int* pb) {
-    std::vector<int> used(b.nslots, 0);
+static void build_pairs(const FtcSpace& b, int child, bool right, int& npairs, int* pa, int* pb) {
+    const int ns = right ? b.nslots_f : b.nslots;
+    std::vector<int> used(ns, 0);
     std::vector<std::pair<int, int>> pairs;
     auto slot = [&](int j, int i) { return b.slot_off[j] + i / 2; };
     for (int j = 1; j < b.levels; j += 2)
@@ -633,17 +690,23 @@ static void build_pairs(const FtcSpace& b, int child, int& npairs, int* pa, int*
             pairs.push_back({slot(j, i), slot(j - 1, c)});
             used[slot(j, i)] = used[slot(j - 1, c)] = 1;
         }
-    std::vector<int> rest;
-    for (int j = b.levels - 1; j >= 0; --j)
-        for (int i = 0; i + 1 < (b.nleaf >> j); i += 2)
-            if (!used[slot(j, i)]) rest.push_back(slot(j, i));
-    for (size_t q = 0; q < rest.size(); q += 2)
-        pairs.push_back({rest[q], q + 1 < rest.size() ? rest[q + 1] : -1});
+    if (right)   // right slot (j, 1) contains the used slot (j - 1, 2)
+        for (int j = 1; j < b.levels; ++j)
+            if (3 < (b.nleaf >> (j - 1)) && !used[slot(j - 1, 2)]) {
+                pairs.push_back({b.nslots + j, slot(j - 1, 2)});
+                used[b.nslots + j] = used[slot(j - 1, 2)] = 1;
+            }
     auto level_of = [&](int s) {
-        int j = 0;
-        while (j + 1 < b.levels && b.slot_off[j + 1] <= s) ++j;
+        int j, i;
+        slot_ji(b, s, j, i);
         return j;
     };
+    std::vector<int> rest;
+    for (int s = 0; s < ns; ++s)
+        if (!used[s]) rest.push_back(s);
+    std::stable_sort(rest.begin(), rest.end(), [&](int x, int y) { return level_of(x) > level_of(y); });
+    for (size_t q = 0; q < rest.size(); q += 2)
+        pairs.push_back({rest[q], q + 1 < rest.size() ? rest[q + 1] : -1});
     std::stable_sort(pairs.begin(), pairs.end(), [&](const std::pair<int, int>& x, const std::pair<int, int>& y) {
         return level_of(x.first) > level_of(y.first);
     });
@@ -673,11 +736,13 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
     b.slot_off[0] = 0;
     for (int j = 0; j < b.levels; ++j) b.slot_off[j + 1] = b.slot_off[j] + (b.nleaf >> (j + 1));
     b.nslots = b.slot_off[b.levels];
+    b.nslots_f = b.nslots + b.levels;
     b.KB = N / BK;
     f->NA = b.nslots * KP;
-    build_pairs(b, 0, f->np_m, f->pa_m, f->pb_m);
-    build_pairs(b, 2, f->np_w, f->pa_w, f->pb_w);
-    const int levels = b.levels, NA = f->NA;
+    f->NAF = b.nslots_f * KP;
+    build_pairs(b, 0, true, f->np_m, f->pa_m, f->pb_m);
+    build_pairs(b, 2, false, f->np_w, f->pa_w, f->pb_w);
+    const int levels = b.levels, NA = f->NA, NAF = f->NAF;
     // orthonormal polynomial bases of the levels (host, one thread per level)
     std::vector<std::vector<double>> Qh(levels);
     std::vector<std::thread> pool;
@@ -692,15 +757,15 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
     std::vector<double> Qall(qtot);
     for (int j = 0; j < levels; ++j) std::copy(Qh[j].begin(), Qh[j].end(), Qall.begin() + qoff[j]);
     const size_t L = (size_t)p->l_max + 1;
-    const size_t nbA = L * N * NA, nq = 2 * (size_t)N * NA;
+    const size_t nbA = L * N * NAF, nbT = L * N * NA, nqT = 2 * (size_t)N * NAF, nq = 2 * (size_t)N * NA;
     double* Qd = nullptr;
     size_t* qoffd = nullptr;
     bool ok = cudaMalloc((void**)&f->bA_hi, nbA * 4) == cudaSuccess &&
               cudaMalloc((void**)&f->bA_lo, nbA * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->bT_hi, nbA * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->bT_lo, nbA * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->qT_hi, nq * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->qT_lo, nq * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->bT_hi, nbT * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->bT_lo, nbT * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->qT_hi, nqT * 4) == cudaSuccess &&
+              cudaMalloc((void**)&f->qT_lo, nqT * 4) == cudaSuccess &&
               cudaMalloc((void**)&f->qA_hi, nq * 4) == cudaSuccess &&
               cudaMalloc((void**)&f->qA_lo, nq * 4) == cudaSuccess &&
               cudaMalloc((void**)&Qd, qtot * sizeof(double)) == cudaSuccess &&
@@ -716,10 +781,10 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
     }
     DSBT_CUDA_TRY(cudaMemsetAsync(f->bA_hi, 0, nbA * 4, st));
     DSBT_CUDA_TRY(cudaMemsetAsync(f->bA_lo, 0, nbA * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->bT_hi, 0, nbA * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->bT_lo, 0, nbA * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->qT_hi, 0, nq * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->qT_lo, 0, nq * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->bT_hi, 0, nbT * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->bT_lo, 0, nbT * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->qT_hi, 0, nqT * 4, st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(f->qT_lo, 0, nqT * 4, st));
     DSBT_CUDA_TRY(cudaMemsetAsync(f->qA_hi, 0, nq * 4, st));
     DSBT_CUDA_TRY(cudaMemsetAsync(f->qA_lo, 0, nq * 4, st));
     {
@@ -727,17 +792,19 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
         k_ftc_beta<<<dim3(levels * (N / 2), (unsigned)L), KP, 0, st>>>(p->T64, Qd, qoffd, b, N, f->bA_hi, f->bA_lo,
                                                                        f->bT_hi, f->bT_lo);
         k_ftc_q<<<dim3(levels * (N / 2), 2), KP, 0, st>>>(Qd, qoffd, b, N, f->qT_hi, f->qT_lo, f->qA_hi, f->qA_lo);
+        k_ftc_beta_right<<<dim3(levels, (unsigned)L), KP, 0, st>>>(p->T64, Qd, qoffd, b, N, f->bA_hi, f->bA_lo);
+        k_ftc_q_right<<<dim3(N - FL, 2), KP, 0, st>>>(Qd, qoffd, b, N, f->qT_hi, f->qT_lo);
     }
     DSBT_CUDA_TRY(cudaGetLastError());
     DSBT_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(Qd);
     cudaFree(qoffd);
-    int rc = encode_tmap_f32_sw128(&f->tm_bA_hi, f->bA_hi, L * N, NA, 128, 32);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_bA_lo, f->bA_lo, L * N, NA, 128, 32);
+    int rc = encode_tmap_f32_sw128(&f->tm_bA_hi, f->bA_hi, L * N, NAF, 128, 32);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_bA_lo, f->bA_lo, L * N, NAF, 128, 32);
     if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_bT_hi, f->bT_hi, L * NA, N, 64, 32);
     if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_bT_lo, f->bT_lo, L * NA, N, 64, 32);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qT_hi, f->qT_hi, 2 * (uint64_t)NA, N, 64, 32);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qT_lo, f->qT_lo, 2 * (uint64_t)NA, N, 64, 32);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qT_hi, f->qT_hi, 2 * (uint64_t)NAF, N, 64, 32);
+    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qT_lo, f->qT_lo, 2 * (uint64_t)NAF, N, 64, 32);
     if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qA_hi, f->qA_hi, 2 * (uint64_t)N, NA, 128, 32);
     if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qA_lo, f->qA_lo, 2 * (uint64_t)N, NA, 128, 32);
     return rc;
@@ -759,7 +826,7 @@ void ftc_free(dsbt_plan* p) {
 }
 
 size_t ftc_scratch_bytes(const dsbt_plan* p, size_t lines) {
-    return p->ftc ? 2 * lines * (size_t)p->ftc->NA * sizeof(float) : 0;
+    return p->ftc ? 2 * lines * (size_t)p->ftc->NAF * sizeof(float) : 0;
 }
 
 namespace {
@@ -816,7 +883,7 @@ int contract_tf32_fast(const dsbt_plan* p, const GroupTable& g, int dir, const f
                        int out_mode, float* out0, float* out1, const float2* phase, int* sched, float* scratch,
                        cudaStream_t st) {
     const FtcData* f = p->ftc;
-    const int N = p->N, NA = f->NA;
+    const int N = p->N, NA = dir > 0 ? f->NAF : f->NA;   // augmented width of this direction
     const size_t R = (size_t)g.total_lines;
     float* aug_hi = scratch;
     float* aug_lo = scratch + R * NA;

@@ -55,3 +55,21 @@ def test_row_left_of_diagonal_has_degree_l_minus_1(l):
             Qs = fast._basis(hi - lo, l - 1)
             res_s = row - Qs @ (Qs.T @ row)
             assert np.abs(res_s).max() > 1e-11 * np.abs(row).max(), lo
+
+
+@pytest.mark.parametrize("l", [1, 2, 5, 20, 63])
+def test_completion_rows_are_polynomials_of_degree_below_l(l):
+    """Sec. 2.5: the completion rows n < n0_l come from P_{2n-p}(N_l - m, 2N_l),
+    a polynomial in m of degree 2n - p_l <= l - 1.  The split-TF32 interval
+    scheme applies them right of leaf 0 through the same degree < l bases:
+    on such an interval the row lies in the span of degree < l to rounding."""
+    import oracle
+    N = 1024
+    T = oracle.T_matrix(N, l)
+    ne = oracle.n0(l) - oracle.p_of(l)
+    for r in range(ne):
+        for lo, hi in ((128, 256), (256, 512), (512, 1024)):
+            row = T[r, lo:hi]
+            Q = fast._basis(hi - lo, l)
+            res = row - Q @ (Q.T @ row)
+            assert np.abs(res).max() <= 1e-12 * max(np.abs(row).max(), 1e-300), (r, lo)
