@@ -74,3 +74,38 @@ def test_fast_tf32_error_close_to_dense_tf32(lib):
     fast.close()
     dense.close()
     assert e_fast < max(2.0 * e_dense, 2e-7), (e_fast, e_dense)
+
+
+@pytest.mark.gpu
+def test_fast_tf32_real_lines_and_edges(lib):
+    """Real (DSBT_F32) channels, l_max = 64 (the largest: right slots of the
+    completion rows at degree 63) and the largest grid N = 8192 (64 leaves,
+    six levels) against the FP64 path of the same plan."""
+    for N, lmax, counts in ((8192, 8, [2, 1, 1, 1, 1, 1, 1, 1, 2]),
+                            (512, 64, [1] * 60 + [2, 1, 1, 2, 3])):
+        r_max = N * 0.1
+        plan = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, fast_tf32=True)
+        x = inputs.gaussian_sum(5 + N, N, r_max / N, counts).real.copy()
+        nrm = np.linalg.norm(x, axis=1)
+        ref = plan.forward_grouped(counts, torch.from_numpy(x).cuda()).cpu().numpy()
+        b = plan.forward_grouped(counts, torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
+        assert rel(b, ref, nrm) < 1e-6, (N, lmax)
+        f = plan.inverse_grouped(counts, torch.from_numpy(ref.astype(np.float32)).cuda()).cpu().numpy()
+        assert rel(f, x, nrm) < 1e-6, (N, lmax)
+        plan.close()
+
+
+@pytest.mark.gpu
+def test_fast_tf32_host_streamed_matches_device(lib):
+    """The host-streamed kinetic step (chunks that cut l groups) runs the
+    interval scheme on every chunk: identical to the device call."""
+    N, r_max, lmax = 1024, 102.4, 20
+    counts = [3] * (lmax + 1)
+    x = inputs.gaussian_sum(17, N, r_max / N, counts).astype(np.complex64)
+    plan = lib.Plan(N, r_max, lmax, fp64=False, tf32x3=True, fast_tf32=True)
+    dev = plan.kinetic_grouped(counts, torch.from_numpy(x).cuda(), 0.05).cpu().numpy()
+    xh = torch.from_numpy(x).pin_memory()
+    out = plan.kinetic_grouped_host(counts, xh, 0.05, chunks=5)
+    torch.cuda.synchronize()
+    plan.close()
+    assert np.array_equal(out.numpy(), dev)
