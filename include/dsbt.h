@@ -340,6 +340,40 @@ DSBT_API int dsbt_tdse_gradient(const dsbt_tdse* tdse, const void* psi0, const d
                                 double* dOdE, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * The full DSBT-DVR step (Sec. 4.1): all magnetic quantum numbers at once, for
+ * potentials and fields without axial symmetry.  Channels (l, m) with
+ * m = -M .. M and, for each m, l = |m| .. |m| + L - 1 (the fixed-m ranges of
+ * dsbt_tdse_create_m, so the angular transform is square per m), stored
+ * l-major as psi[c][i] (complex128, i = 0..N-1); dsbt_tdse3d_channels lists
+ * (l, m) per channel c.  Angular grid: L Gauss-Legendre nodes eta_j = cos(theta_j)
+ * times NM = 2M + 1 angles phi_q = 2 pi q / NM; Y = P Phi with P^m as in
+ * dsbt_tdse_create_m and Phi[m][q] = exp(i m phi_q) / sqrt(NM) (Sec. 4.1, the
+ * DFT over phi), unitary on the channel space.  One step of length tau:
+ *   psi <- Q Kin Q psi,  Q = Y^H diag(exp(-i [V(r) + r F.n] tau/2)) Y,
+ *   n = (sin theta cos phi, sin theta sin phi, cos theta),
+ *   Kin = the kinetic step of dsbt_kinetic_grouped (each channel with its l),
+ * with F = (F[3s'], F[3s'+1], F[3s'+2]), s' = s / hold, the field sample of step
+ * s (a DEVICE array; NULL: no field).  V defaults to 0.  A field along z couples
+ * no m and reproduces dsbt_tdse_create_m for every m.
+ * ------------------------------------------------------------------------- */
+typedef struct dsbt_tdse3d dsbt_tdse3d;
+
+/* Plan built with DSBT_PLAN_FP64 and l_max >= M + L - 1; 1 <= L <= 32,
+ * 0 <= M <= 12.  The plan must outlive the propagator.  Errors: -1 on bad
+ * arguments (or too much shared memory for L, M), -3 out of memory. */
+DSBT_API int dsbt_tdse3d_create(const dsbt_plan* plan, int L, int M, double tau, dsbt_tdse3d** out);
+DSBT_API int dsbt_tdse3d_destroy(dsbt_tdse3d* tdse);
+/* *nchan and, per channel c, l_of[c] and m_of[c] (HOST arrays of nchan ints, may be NULL). */
+DSBT_API int dsbt_tdse3d_channels(const dsbt_tdse3d* tdse, int* nchan, int* l_of, int* m_of);
+/* The radial potential V(r_i) from n = N HOST values on the midpoint grid.  Synchronous. */
+DSBT_API int dsbt_tdse3d_set_potential(dsbt_tdse3d* tdse, const double* V, int n);
+/* Device workspace: one state plus one DSBT workspace. */
+DSBT_API size_t dsbt_tdse3d_workspace_size(const dsbt_tdse3d* tdse);
+/* Propagate psi (device, in place) by nsteps steps, asynchronous on stream. */
+DSBT_API int dsbt_tdse3d_propagate(const dsbt_tdse3d* tdse, void* psi, const double* F, int nsteps, int hold,
+                                   void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Batch of uneven transforms (different grids and l_max) sharing one factor
  * set.  The regular rows of T_l (Sec. 2.4) do not depend on the grid size N;
  * only the completion rows (Sec. 2.5, Eq. (43)) do.  A batch builds the

@@ -129,6 +129,14 @@ int contract_tf32_fast(const dsbt_plan* p, const GroupTable& g, int dir, const f
                        int out_mode, float* out0, float* out1, const float2* phase, int* sched, float* scratch,
                        cudaStream_t st);
 
+// ---- angular rule of the TDSE (tdse.cu), shared with tdse3d.cu
+// L-point Gauss-Legendre nodes x (cos theta) and weights w.
+void tdse_gauss_legendre(int L, std::vector<double>& x, std::vector<double>& w);
+// P[i][j], i < L: rows l = m + i of the normalised associated Legendre functions
+// times sqrt(w_j), orthonormalised on the rule (an orthogonal L x L matrix).
+void tdse_angular_rows(int L, int m, const std::vector<double>& x, const std::vector<double>& w,
+                       std::vector<double>& P);
+
 // ---- split-TF32 tensor-core contraction (gemm_tf32x3.cu)
 // B operand: TF32 split lines [lines][N] (hi, lo).  `sched` is a device int
 // (zeroed here before the launch) for the dynamic tile scheduler.  Output modes:

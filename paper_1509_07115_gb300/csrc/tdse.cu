@@ -335,6 +335,16 @@ __global__ void k_tdse_observable(const double2* __restrict__ x, double2* __rest
 
 size_t state_bytes(const dsbt_tdse* t) { return (size_t)t->L * t->N * sizeof(double2); }
 
+}  // namespace
+
+void tdse_gauss_legendre(int L, std::vector<double>& x, std::vector<double>& w) { gauss_legendre(L, x, w); }
+void tdse_angular_rows(int L, int m, const std::vector<double>& x, const std::vector<double>& w,
+                       std::vector<double>& P) {
+    angular_matrix_m(L, m, x, w, P);
+}
+
+namespace {
+
 inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int potential(const dsbt_tdse* t, const double2* x, double2* y, const double* E, int eidx, double ht,

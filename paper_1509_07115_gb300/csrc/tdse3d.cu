@@ -1,0 +1,285 @@
+// tdse3d.cu -- the full DSBT-DVR split-operator step (Sec. 4.1): all m at once,
+// angular transform Y = P Phi over a (theta, phi) grid, length gauge with a
+// field of any direction.
+//
+// Channels (l, m): m = -M .. M and, for each m, l = |m| .. |m| + L - 1 (the
+// per-m range of the fixed-m propagator, so every P^m below is square),
+// stored l-major as the DSBT's grouped calls want them (channel c -> line c).
+// Angular grid: the L-point Gauss-Legendre nodes eta_j = cos(theta_j) and
+// NM = 2M + 1 uniform angles phi_q = 2 pi q / NM.  The transform of Sec. 4.1
+// in two factors:
+//     G_m(eta_j)      = sum_l P^m[l - |m|][j] psi_lm          (P^m: Pbar_l^|m| sqrt(w_j),
+//                                                               orthonormalised on the rule)
+//     g(eta_j, phi_q) = sum_m Phi[m][q] G_m(eta_j),   Phi[m][q] = exp(i m phi_q) / sqrt(NM)
+// Both factors are orthogonal / unitary, so Y is unitary on the channel space.
+// One step of length tau (vector potential 0, the kinetic half steps merged):
+//     psi <- Q Kin Q psi,   Q = Y^H diag exp(-i [V(r) + r F.n(theta, phi)] tau/2) Y,
+//     Kin = the grouped DSBT kinetic step (each channel with its own l),
+// with n = (sin theta cos phi, sin theta sin phi, cos theta) and F the field
+// sample of the step (three components).  A field along z couples no m, and the
+// step then equals the fixed-m propagator's for every m.
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "plan.cuh"
+
+namespace dsbt {
+int kinetic_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtype, double tau,
+                                 const void* in, void* out, void* scratch, size_t scratch_bytes,
+                                 cudaStream_t st);
+}
+
+struct dsbt_tdse3d {
+    const dsbt_plan* plan;
+    int L, M, NM, N, nchan;
+    double tau;
+    double* P;        // [NM][L][L]: P^m (row i = l - |m|, column j), m = mi - M
+    int* map;         // [NM][L]: channel of (l = |m| + i, m)
+    double* V;        // [N]
+    double* rr;       // [N]
+    double* eta;      // [L]
+    std::vector<int> counts;            // channels per l, l = 0 .. plan l_max
+    std::vector<int> chan_l, chan_m;    // per channel
+};
+
+namespace dsbt {
+namespace {
+
+constexpr int TI3 = 4;   // radial points per block of the angular kernel
+
+// y = Q x on TI3 radial points per block (x and y may alias): to the
+// (theta, phi) grid, the phase exp(-i [V + r F.n] ht), back.  Shared memory:
+// the channel values, G[m][j] and the grid values, each [.][TI3].
+__global__ void __launch_bounds__(256) k_tdse3d_potential(const double2* x, double2* y, const double* __restrict__ P,
+                                                          const int* __restrict__ map, const double* __restrict__ V,
+                                                          const double* __restrict__ rr,
+                                                          const double* __restrict__ eta, int L, int M, int N,
+                                                          int nchan, const double* __restrict__ F, int fidx,
+                                                          double ht) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int NM = 2 * M + 1;
+    double2* xs = reinterpret_cast<double2*>(sm);   // [nchan][TI3]
+    double2* G = xs + (size_t)nchan * TI3;          // [NM][L][TI3]
+    double2* g = G + (size_t)NM * L * TI3;          // [L][NM][TI3]
+    double2* ph = g + (size_t)NM * L * TI3;         // [NM][NM]: Phi[m][q]
+    const int i0 = blockIdx.x * TI3, tid = threadIdx.x;
+    const double inv = rsqrt((double)NM);
+    for (int k = tid; k < NM * NM; k += blockDim.x) {
+        const int mi = k / NM, q = k % NM;
+        double sn, cs;
+        sincospi(2.0 * (double)((mi - M) * q) / NM, &sn, &cs);
+        ph[k] = make_double2(cs * inv, sn * inv);
+    }
+    for (int k = tid; k < nchan * TI3; k += blockDim.x) {
+        const int c = k / TI3, t = k % TI3, i = i0 + t;
+        xs[k] = (i < N) ? x[(size_t)c * N + i] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int k = tid; k < NM * L * TI3; k += blockDim.x) {   // G_m(eta_j) = sum_l P^m x_lm
+        const int mi = k / (L * TI3), j = (k / TI3) % L, t = k % TI3;
+        const double* Pm = P + (size_t)mi * L * L;
+        double2 s = make_double2(0.0, 0.0);
+        for (int ii = 0; ii < L; ++ii) {
+            const double p = Pm[ii * L + j];
+            const double2 v = xs[map[mi * L + ii] * TI3 + t];
+            s.x = fma(p, v.x, s.x);
+            s.y = fma(p, v.y, s.y);
+        }
+        G[k] = s;
+    }
+    __syncthreads();
+    const double Fx = F ? F[3 * fidx] : 0.0, Fy = F ? F[3 * fidx + 1] : 0.0, Fz = F ? F[3 * fidx + 2] : 0.0;
+    for (int k = tid; k < L * NM * TI3; k += blockDim.x) {   // grid values times the phase
+        const int j = k / (NM * TI3), q = (k / TI3) % NM, t = k % TI3, i = i0 + t;
+        double2 s = make_double2(0.0, 0.0);
+        for (int mi = 0; mi < NM; ++mi) {
+            const double2 a = ph[mi * NM + q], v = G[(mi * L + j) * TI3 + t];
+            s.x = fma(a.x, v.x, fma(-a.y, v.y, s.x));
+            s.y = fma(a.x, v.y, fma(a.y, v.x, s.y));
+        }
+        if (i < N) {
+            const double ct = eta[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+            double sp, cp;
+            sincospi(2.0 * (double)q / NM, &sp, &cp);
+            const double u = V[i] + rr[i] * (Fx * st * cp + Fy * st * sp + Fz * ct);
+            double sn, cs;
+            sincos(-u * ht, &sn, &cs);
+            s = make_double2(s.x * cs - s.y * sn, s.x * sn + s.y * cs);
+        }
+        g[k] = s;
+    }
+    __syncthreads();
+    for (int k = tid; k < NM * L * TI3; k += blockDim.x) {   // back over phi: sum_q conj(Phi[m][q]) g
+        const int mi = k / (L * TI3), j = (k / TI3) % L, t = k % TI3;
+        double2 s = make_double2(0.0, 0.0);
+        for (int q = 0; q < NM; ++q) {
+            const double2 a = ph[mi * NM + q], v = g[(j * NM + q) * TI3 + t];
+            s.x = fma(a.x, v.x, fma(a.y, v.y, s.x));
+            s.y = fma(a.x, v.y, fma(-a.y, v.x, s.y));
+        }
+        G[k] = s;
+    }
+    __syncthreads();
+    for (int k = tid; k < NM * L * TI3; k += blockDim.x) {   // back over theta: psi_lm = sum_j P^m G_m
+        const int mi = k / (L * TI3), ii = (k / TI3) % L, t = k % TI3, i = i0 + t;
+        const double* Pm = P + (size_t)mi * L * L + (size_t)ii * L;
+        double2 s = make_double2(0.0, 0.0);
+        for (int j = 0; j < L; ++j) {
+            const double p = Pm[j];
+            const double2 v = G[(mi * L + j) * TI3 + t];
+            s.x = fma(p, v.x, s.x);
+            s.y = fma(p, v.y, s.y);
+        }
+        if (i < N) y[(size_t)map[mi * L + ii] * N + i] = s;
+    }
+}
+
+size_t smem3d(const dsbt_tdse3d* t) {
+    return ((size_t)t->nchan * TI3 + 2 * (size_t)t->NM * t->L * TI3 + (size_t)t->NM * t->NM) * sizeof(double2);
+}
+
+int potential3d(const dsbt_tdse3d* t, const double2* x, double2* y, const double* F, int fidx, double ht,
+                cudaStream_t st) {
+    const size_t smem = smem3d(t);
+    if (smem > 48 * 1024)
+        DSBT_CUDA_TRY(cudaFuncSetAttribute(k_tdse3d_potential, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps(kKTdsePot, st);
+    k_tdse3d_potential<<<(t->N + TI3 - 1) / TI3, 256, smem, st>>>(x, y, t->P, t->map, t->V, t->rr, t->eta, t->L,
+                                                                  t->M, t->N, t->nchan, F, fidx, ht);
+    DSBT_CUDA_TRY(cudaGetLastError());
+    return DSBT_OK;
+}
+
+inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace dsbt
+
+using namespace dsbt;
+
+extern "C" int dsbt_tdse3d_create(const dsbt_plan* plan, int L, int M, double tau, dsbt_tdse3d** out) {
+    DSBT_CHECK_ARG(out != nullptr && plan != nullptr, "dsbt_tdse3d_create: NULL argument");
+    *out = nullptr;
+    DSBT_CHECK_ARG(plan->T64 != nullptr, "dsbt_tdse3d_create: the plan needs DSBT_PLAN_FP64");
+    DSBT_CHECK_ARG(L >= 1 && L <= 32, "dsbt_tdse3d_create: L=%d not in 1..32", L);
+    DSBT_CHECK_ARG(M >= 0 && M <= 12, "dsbt_tdse3d_create: M=%d not in 0..12", M);
+    DSBT_CHECK_ARG(M + L - 1 <= plan->l_max, "dsbt_tdse3d_create: channels up to l=%d, plan l_max=%d", M + L - 1,
+                   plan->l_max);
+    DSBT_CHECK_ARG(isfinite(tau), "dsbt_tdse3d_create: tau must be finite");
+    dsbt_tdse3d* t = new (std::nothrow) dsbt_tdse3d();
+    if (!t) return DSBT_ERR_NOMEM;
+    t->plan = plan;
+    t->L = L;
+    t->M = M;
+    t->NM = 2 * M + 1;
+    t->N = plan->N;
+    t->tau = tau;
+    // channels, l-major
+    std::vector<int> map((size_t)t->NM * L, -1);
+    t->counts.assign(plan->l_max + 1, 0);
+    for (int l = 0; l <= M + L - 1; ++l)
+        for (int mi = 0; mi < t->NM; ++mi) {
+            const int m = mi - M, am = m < 0 ? -m : m;
+            if (l < am || l > am + L - 1) continue;
+            map[(size_t)mi * L + (l - am)] = (int)t->chan_l.size();
+            t->chan_l.push_back(l);
+            t->chan_m.push_back(m);
+            ++t->counts[l];
+        }
+    t->nchan = (int)t->chan_l.size();
+    std::vector<double> x, w, Pm, Pall((size_t)t->NM * L * L), rr(t->N);
+    tdse_gauss_legendre(L, x, w);
+    for (int mi = 0; mi < t->NM; ++mi) {
+        const int am = std::abs(mi - M);
+        tdse_angular_rows(L, am, x, w, Pm);
+        std::copy(Pm.begin(), Pm.end(), Pall.begin() + (size_t)mi * L * L);
+    }
+    const double dr = plan->r_max / plan->N;
+    for (int i = 0; i < t->N; ++i) rr[i] = (i + 0.5) * dr;
+    bool ok = cudaMalloc((void**)&t->P, Pall.size() * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void**)&t->map, map.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void**)&t->V, t->N * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void**)&t->rr, t->N * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void**)&t->eta, L * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMemcpy(t->P, Pall.data(), Pall.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(t->map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(t->V, 0, t->N * sizeof(double)) == cudaSuccess &&
+         cudaMemcpy(t->rr, rr.data(), t->N * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(t->eta, x.data(), L * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(t->P); cudaFree(t->map); cudaFree(t->V); cudaFree(t->rr); cudaFree(t->eta);
+        delete t;
+        set_error("dsbt_tdse3d_create: device allocation or copy failed");
+        return DSBT_ERR_NOMEM;
+    }
+    if (smem3d(t) > 200 * 1024) {
+        cudaFree(t->P); cudaFree(t->map); cudaFree(t->V); cudaFree(t->rr); cudaFree(t->eta);
+        delete t;
+        set_error("dsbt_tdse3d_create: L=%d, M=%d need too much shared memory", L, M);
+        return DSBT_ERR_INVALID;
+    }
+    *out = t;
+    return DSBT_OK;
+}
+
+extern "C" int dsbt_tdse3d_destroy(dsbt_tdse3d* t) {
+    if (!t) return DSBT_OK;
+    cudaDeviceSynchronize();
+    cudaFree(t->P);
+    cudaFree(t->map);
+    cudaFree(t->V);
+    cudaFree(t->rr);
+    cudaFree(t->eta);
+    delete t;
+    return DSBT_OK;
+}
+
+extern "C" int dsbt_tdse3d_channels(const dsbt_tdse3d* t, int* nchan, int* l_of, int* m_of) {
+    DSBT_CHECK_ARG(t != nullptr, "dsbt_tdse3d_channels: NULL handle");
+    if (nchan) *nchan = t->nchan;
+    for (int c = 0; c < t->nchan; ++c) {
+        if (l_of) l_of[c] = t->chan_l[c];
+        if (m_of) m_of[c] = t->chan_m[c];
+    }
+    return DSBT_OK;
+}
+
+extern "C" int dsbt_tdse3d_set_potential(dsbt_tdse3d* t, const double* V, int n) {
+    DSBT_CHECK_ARG(t != nullptr && V != nullptr, "dsbt_tdse3d_set_potential: NULL argument");
+    DSBT_CHECK_ARG(n == t->N, "dsbt_tdse3d_set_potential: n=%d, grid has N=%d", n, t->N);
+    DSBT_CUDA_TRY(cudaMemcpy(t->V, V, t->N * sizeof(double), cudaMemcpyHostToDevice));
+    return DSBT_OK;
+}
+
+extern "C" size_t dsbt_tdse3d_workspace_size(const dsbt_tdse3d* t) {
+    if (!t) return 0;
+    return a256((size_t)t->nchan * t->N * sizeof(double2)) +
+           dsbt_workspace_size(t->plan, t->nchan, DSBT_C128) + 512;
+}
+
+extern "C" int dsbt_tdse3d_propagate(const dsbt_tdse3d* t, void* psi, const double* F, int nsteps, int hold,
+                                     void* workspace, size_t workspace_bytes, void* stream) {
+    DSBT_CHECK_ARG(t != nullptr && psi != nullptr, "dsbt_tdse3d_propagate: NULL argument");
+    DSBT_CHECK_ARG(nsteps >= 0 && hold >= 1, "dsbt_tdse3d_propagate: nsteps >= 0 and hold >= 1 required");
+    const size_t need = dsbt_tdse3d_workspace_size(t);
+    DSBT_CHECK_ARG(workspace != nullptr && workspace_bytes >= need,
+                   "dsbt_tdse3d_propagate: workspace too small (need %zu bytes)", need);
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* base = (unsigned char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    double2* tmp = (double2*)base;
+    void* kws = base + a256((size_t)t->nchan * t->N * sizeof(double2));
+    const size_t kws_b = dsbt_workspace_size(t->plan, t->nchan, DSBT_C128);
+    double2* x = (double2*)psi;
+    for (int s = 0; s < nsteps; ++s) {
+        const int fidx = s / hold;
+        int rc = potential3d(t, x, tmp, F, fidx, 0.5 * t->tau, st);
+        if (!rc) rc = kinetic_grouped_with_scratch(t->plan, t->counts.data(), DSBT_C128, t->tau, tmp, x, kws, kws_b, st);
+        if (!rc) rc = potential3d(t, x, x, F, fidx, 0.5 * t->tau, st);
+        if (rc) return rc;
+    }
+    return DSBT_OK;
+}

@@ -87,6 +87,13 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_tdse_angular.argtypes = [vp, vp, vp, vp]
         lib.dsbt_tdse_set_potential.argtypes = [vp, vp, i]
         lib.dsbt_tdse_create_m.argtypes = [vp, i, i, d, d, d, ctypes.POINTER(vp)]
+        lib.dsbt_tdse3d_create.argtypes = [vp, i, i, d, ctypes.POINTER(vp)]
+        lib.dsbt_tdse3d_destroy.argtypes = [vp]
+        lib.dsbt_tdse3d_channels.argtypes = [vp, _c_int_p, vp, vp]
+        lib.dsbt_tdse3d_set_potential.argtypes = [vp, vp, i]
+        lib.dsbt_tdse3d_workspace_size.argtypes = [vp]
+        lib.dsbt_tdse3d_workspace_size.restype = sz
+        lib.dsbt_tdse3d_propagate.argtypes = [vp, vp, vp, i, i, vp, sz, vp]
         lib.dsbt_tdse_propagate_velocity.argtypes = [vp, vp, vp, vp, i, i, d, vp, sz, vp]
         lib.dsbt_tdse_workspace_size.argtypes = [vp, i, i]
         lib.dsbt_tdse_workspace_size.restype = sz
@@ -440,6 +447,59 @@ class Batch:
 
 
 # ------------------------------------------------------------------ TDSE
+
+class Tdse3d:
+    """The full DSBT-DVR step with all m (dsbt_tdse3d_* in include/dsbt.h).
+    State: complex128 CUDA tensor [nchan][N], channels l-major; ``channels``
+    gives (l, m) per row.  Field samples F: [nsamples][3] (x, y, z)."""
+
+    def __init__(self, plan: Plan, L: int, M: int, tau: float):
+        import numpy as np
+        h = ctypes.c_void_p()
+        _check(load().dsbt_tdse3d_create(plan.handle, int(L), int(M), float(tau), ctypes.byref(h)),
+               "dsbt_tdse3d_create")
+        self._h, self.plan, self.L, self.M, self.N, self.tau = h, plan, int(L), int(M), plan.N, float(tau)
+        n = ctypes.c_int()
+        _check(load().dsbt_tdse3d_channels(h, ctypes.byref(n), None, None), "dsbt_tdse3d_channels")
+        ls = np.empty(n.value, dtype=np.int32)
+        ms = np.empty(n.value, dtype=np.int32)
+        _check(load().dsbt_tdse3d_channels(h, ctypes.byref(n), ls.ctypes.data_as(ctypes.c_void_p),
+                                           ms.ctypes.data_as(ctypes.c_void_p)), "dsbt_tdse3d_channels")
+        self.nchan = n.value
+        self.channels = list(zip(ls.tolist(), ms.tolist()))
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dsbt_tdse3d_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_potential(self, V):
+        import numpy as np
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        _check(load().dsbt_tdse3d_set_potential(self._h, V.ctypes.data_as(ctypes.c_void_p), int(V.size)),
+               "dsbt_tdse3d_set_potential")
+
+    def propagate(self, psi: torch.Tensor, F, nsteps: int, hold: int = 1) -> torch.Tensor:
+        """In-place propagation by nsteps steps; F: [nsamples][3] field samples (or None)."""
+        if psi.dtype != torch.complex128 or not psi.is_cuda or tuple(psi.shape) != (self.nchan, self.N) \
+                or not psi.is_contiguous():
+            raise ValueError(f"state must be a contiguous complex128 CUDA tensor of shape ({self.nchan}, {self.N})")
+        Fp = None if F is None else torch.as_tensor(F).to(device="cuda", dtype=torch.float64).contiguous()
+        nb = int(load().dsbt_tdse3d_workspace_size(self._h))
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        _check(load().dsbt_tdse3d_propagate(self._h, _ptr(psi), None if Fp is None else _ptr(Fp), int(nsteps),
+                                            int(hold), _ptr(self._ws), self._ws.numel(), _stream()),
+               "dsbt_tdse3d_propagate")
+        return psi
+
 
 class Tdse:
     """Split-operator TDSE (m = 0, length gauge) through the DSBT: see
