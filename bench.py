@@ -357,11 +357,39 @@ def tdse_leg(dsbt, inputs, torch, dev):
     fast_achieved = fast_flop / (fprof["contract_f64"][1] / steps * 1e-3) / 1e12
     ftd.close()
     fplan.close()
+    # all m (Y = P Phi): 32 x 17 = 544 channels, field along x
+    p3 = dsbt.Plan(Nt, 204.8, 40, tf32x3=False)
+    t3 = dsbt.Tdse3d(p3, 32, 8, tau)
+    r3 = (np.arange(Nt) + 0.5) * 0.1
+    t3.set_potential(-1.0 / np.sqrt(r3 * r3 + 0.5))
+    c3 = np.zeros((t3.nchan, Nt), dtype=np.complex128)
+    c3[t3.channels.index((0, 0))] = f / np.linalg.norm(f)
+    F3 = torch.zeros((200, 3), dtype=torch.float64, device=dev)
+    F3[:, 0] = E[:200]
+    psi3 = torch.from_numpy(c3).to(dev)
+    t3.propagate(psi3, F3, 10, 2)
+    torch.cuda.synchronize()
+    steps3 = 100
+    dsbt.profile_enable(True)
+    e0.record(st)
+    t3.propagate(psi3, F3, steps3, 2)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms3 = e0.elapsed_time(e1)
+    prof3 = dsbt.profile_read()
+    dsbt.profile_enable(False)
+    norm3 = torch.linalg.vector_norm(psi3).item()
+    t3.close()
+    p3.close()
     return {"config": "m=0, l=0..63, N=2048, dr=0.1, 400 steps of 0.05, soft-Coulomb -1/sqrt(r^2+0.5), "
                       "200 field samples held 2 steps, observable = norm beyond r=50, checkpoint every 20",
             "propagate_ms_per_step": prop_ms / steps, "gradient_ms_total": grad_ms,
             "norm_drift_400_steps": drift, "observable": O.item(),
             "kernels_ms_per_step": {k: v[1] / steps for k, v in prof.items()},
+            "all_m": {"config": "N=2048, L=32 per m, M=8 (544 channels, l <= 39), field along x, "
+                                "100 steps of 0.05", "propagate_ms_per_step": ms3 / steps3,
+                      "kernels_ms_per_step": {k: v[1] / steps3 for k, v in prof3.items()},
+                      "norm_after": norm3},
             "fast64": {"propagate_ms_per_step": fast_ms / steps,
                        "kernels_ms_per_step": {k: v[1] / steps for k, v in fprof.items()},
                        "max_abs_diff_vs_dense": fast_dev,
