@@ -73,3 +73,16 @@ def test_batch_tile_planning_on_host():
     assert lib.dsbt_batch_tiles(1, one(256), one(0), one(1), 4, 256, None, None, None) == -1
     assert lib.dsbt_batch_tiles(1, one(256), one(0), one(1), 0, 100, None, None, None) == -1
     assert lib.dsbt_batch_tiles(1, one(300), one(0), one(1), 0, 256, None, None, None) == -1
+
+
+def test_tdse3d_argument_checks():
+    """dsbt_tdse3d_create rejects bad arguments before touching the GPU."""
+    import ctypes
+    from paper_1509_07115_gb300 import dsbt
+    lib = dsbt.load()
+    h = ctypes.c_void_p()
+    assert lib.dsbt_tdse3d_create(None, 8, 2, 0.05, ctypes.byref(h)) == -1
+    assert lib.dsbt_tdse3d_channels(None, None, None, None) == -1
+    assert lib.dsbt_tdse3d_propagate(None, None, None, 1, 1, None, 0, None) == -1
+    assert lib.dsbt_tdse3d_workspace_size(None) == 0
+    assert lib.dsbt_tdse3d_destroy(None) == 0

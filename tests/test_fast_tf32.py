@@ -109,3 +109,19 @@ def test_fast_tf32_host_streamed_matches_device(lib):
     torch.cuda.synchronize()
     plan.close()
     assert np.array_equal(out.numpy(), dev)
+
+
+@pytest.mark.gpu
+def test_fast_tf32_kinetic_with_corrected_momenta(lib):
+    """DSBT_PLAN_KCORR with the interval scheme: the kinetic phase per (l, n)
+    (the corrected momenta of Sec. 3) in the forward-rows epilogue, against the
+    FP64 path of the same plan."""
+    N, r_max, lmax, tau = 1024, 102.4, 40, 0.05
+    counts = [2] * (lmax + 1)
+    x = inputs.gaussian_sum(23, N, r_max / N, counts)
+    nrm = np.linalg.norm(x, axis=1)
+    plan = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, kcorr=True, fast_tf32=True)
+    ref = plan.kinetic_grouped(counts, torch.from_numpy(x).cuda(), tau).cpu().numpy()
+    k = plan.kinetic_grouped(counts, torch.from_numpy(x.astype(np.complex64)).cuda(), tau).cpu().numpy()
+    plan.close()
+    assert rel(k, ref, nrm) < 1e-6
