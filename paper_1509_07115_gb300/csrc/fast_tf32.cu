@@ -14,8 +14,11 @@
 // interval's points.  Used intervals are numbered (slots s, level-major); the
 // augmented index (s, k), k < 64, spans NA = 64 (nleaf - 1) columns.
 //
-// Every step is then the dense contraction kernel of gemm_tf32x3.cu with other
-// operands and K ranges:
+// Every step is then the contraction of gemm_tf32x3.cu with other operands and
+// K ranges.  Tiles are short (4-16 K blocks), so the TMEM accumulator is split
+// into two 256-column buffers used by alternate chunks of KC K blocks (all three
+// split products of a chunk into one buffer): the MMAs of the next chunk, also
+// across tiles, run while the epilogue drains the previous one.
 //   forward   MOMENTS  M[line][(s,k)]  = sum_t QT[(s,k)][t] f[line][t]          (t in interval s)
 //             EVAL     b[line][r]      = sum_c T[r][c] f[line][c]  (near band: c in r's leaf)
 //                                      + sum_(s,k) B[r][(s,k)] M[line][(s,k)]  (far slots of r)
@@ -56,11 +59,12 @@ constexpr int BK = 32;
 constexpr int BN_MAX = 256;
 constexpr int BBOX = 64;                           // rows per B TMA box
 constexpr int STAGES = 2;
-// K blocks per main-accumulator chunk: the tensor cores accumulate with
-// truncation, so a shorter chunk than the dense kernel's 4 keeps the scheme's
-// longer chains of sums (moments, then the far field) at the dense kernel's
-// accuracy (round trip 5.8e-7 against 8.5e-7 with 4, N = 4096, l <= 63).
-constexpr int KC = 3;
+// K blocks per chunk.  The tensor cores accumulate with truncation, and all
+// three split products of a chunk go into one buffer, so the chunk is one K
+// block: the round-trip error at N = 4096, l <= 63 is then 5.6e-7, the dense
+// kernel's (2 blocks: 8.3e-7; a separate correction accumulator, as in the
+// dense kernel, leaves no TMEM columns for a second buffer).
+constexpr int KC = 1;
 constexpr int EPI_WARPS = 8;
 constexpr int QS = 4;                              // tile-queue slots
 constexpr int A_BYTES = BM * BK * 4;               // 16 KiB
@@ -266,9 +270,9 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
     unsigned char* stage_base = smem;
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* main_full = empty + STAGES;
-    uint64_t* main_empty = main_full + 1;
-    uint64_t* tq_full = main_empty + 1;
+    uint64_t* acc_full = empty + STAGES;    // [2]: a chunk's sum is in TMEM buffer b
+    uint64_t* acc_empty = acc_full + 2;     // [2]: buffer b drained by the epilogue
+    uint64_t* tq_full = acc_empty + 2;
     uint64_t* tq_empty = tq_full + QS;
     int* tile_q = (int*)(tq_empty + QS);
     uint32_t* tmem_slot = (uint32_t*)(tile_q + QS);
@@ -282,8 +286,10 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(main_full, 1);
-        mbar_init(main_empty, EPI_WARPS);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], EPI_WARPS);
+        }
         for (int q = 0; q < QS; ++q) {
             mbar_init(&tq_full[q], 1);
             mbar_init(&tq_empty[q], 1 + EPI_WARPS);
@@ -374,9 +380,8 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t mphase = 0;
+            uint32_t gch = 0;   // chunks issued so far: buffer gch & 1, round gch >> 1
             bool ok = true;
-            const uint32_t d_main = tmem_base, d_corr = tmem_base + 256;
             int qslot = 0;
             uint32_t qphase = 0;
             while (ok) {
@@ -389,34 +394,18 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 const int l = gt.l[tl.g];
                 const int nkb = seg_count(fs, l, tl.rt);
                 const uint32_t idesc = idesc_tf32(BM, tl.nmma);
-                uint32_t acc_corr = 0;
                 for (int c0 = 0; c0 < nkb && ok; c0 += fs.kc) {
                     const int c1 = min(nkb, c0 + fs.kc);
-                    const bool pre = c0 > 0;
-                    if (pre) {
+                    const int buf = gch & 1;
+                    // the epilogue drained this buffer's previous chunk; the other
+                    // buffer may still be draining while these MMAs run
+                    if (!mbar_wait(&acc_empty[buf], ((gch >> 1) & 1) ^ 1, abort_flag, status)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + (uint32_t)buf * 256;
+                    uint32_t accf = 0;
+                    for (int i = c0; i < c1; ++i) {
                         if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
-                        const uint32_t sb_hi = sa + 2 * A_BYTES;
-#pragma unroll
-                        for (int ks = 0; ks < BK / 8; ++ks) {
-                            const uint32_t off = ks * 32;
-                            const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa + A_BYTES + off);
-                            const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_hi + B_BYTES + off);
-                            mma_tf32(d_corr, dah, dbl, idesc, 1);
-                            mma_tf32(d_corr, dal, dbh, idesc, 1);
-                        }
-                    }
-                    if (!mbar_wait(main_empty, mphase ^ 1, abort_flag, status)) { ok = false; break; }
-                    mphase ^= 1;
-                    tc_fence_after();
-                    uint32_t acc_main = 0;
-                    for (int i = c0; i < c1; ++i) {
-                        const bool early = pre && i == c0;
-                        if (!early) {
-                            if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
-                            tc_fence_after();
-                        }
                         const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
                         const uint32_t sa_lo = sa + A_BYTES;
                         const uint32_t sb_hi = sa + 2 * A_BYTES;
@@ -426,19 +415,17 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                             const uint32_t off = ks * 32;
                             const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa_lo + off);
                             const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_lo + off);
-                            mma_tf32(d_main, dah, dbh, idesc, acc_main);
-                            if (!early) {
-                                mma_tf32(d_corr, dah, dbl, idesc, acc_corr);
-                                mma_tf32(d_corr, dal, dbh, idesc, 1);
-                            }
-                            acc_main = 1;
-                            acc_corr = 1;
+                            mma_tf32(d, dah, dbh, idesc, accf);
+                            mma_tf32(d, dah, dbl, idesc, 1);
+                            mma_tf32(d, dal, dbh, idesc, 1);
+                            accf = 1;
                         }
                         mma_commit(&empty[stage]);
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                     if (!ok) break;
-                    mma_commit(main_full);
+                    mma_commit(&acc_full[buf]);
+                    ++gch;
                 }
             }
         }
@@ -448,7 +435,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
         const int ew = warp - 2;
         const int quarter = warp & 3;
         const int half = ew >> 2;
-        uint32_t mphase = 0;
+        uint32_t gch = 0;   // chunks drained so far (same order as the MMA issuer)
         int qslot = 0;
         uint32_t qphase = 0;
         while (true) {
@@ -479,27 +466,22 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             for (int j = 0; j < 128; ++j) acc[j] = 0.f;
             bool ok = true;
             for (int c0 = 0; c0 < nkb; c0 += fs.kc) {
-                if (!mbar_wait(main_full, mphase, abort_flag, status)) { ok = false; break; }
-                mphase ^= 1;
+                const int buf = gch & 1;
+                if (!mbar_wait(&acc_full[buf], (gch >> 1) & 1, abort_flag, status)) { ok = false; break; }
                 tc_fence_after();
-                const bool last = c0 + fs.kc >= nkb;
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) {
                     if (ch < nch) {
                         float v[32];
-                        tmem_ld32(tl_addr + ch * 32, v);
+                        tmem_ld32(tl_addr + (uint32_t)buf * 256 + ch * 32, v);
 #pragma unroll
                         for (int j = 0; j < 32; ++j) acc[ch * 32 + j] += v[j];
-                        if (last) {
-                            tmem_ld32(tl_addr + 256 + ch * 32, v);
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) acc[ch * 32 + j] += v[j];
-                        }
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(main_empty);
+                if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                ++gch;
             }
             if (!ok) break;
             if (ncols <= 0 || !store_row) continue;
