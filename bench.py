@@ -358,7 +358,7 @@ def tdse_leg(dsbt, inputs, torch, dev):
     ftd.close()
     fplan.close()
     # all m (Y = P Phi): 32 x 17 = 544 channels, field along x
-    p3 = dsbt.Plan(Nt, 204.8, 40, tf32x3=False)
+    p3 = dsbt.Plan(Nt, 204.8, 40, tf32x3=False, fast64=True)
     t3 = dsbt.Tdse3d(p3, 32, 8, tau)
     r3 = (np.arange(Nt) + 0.5) * 0.1
     t3.set_potential(-1.0 / np.sqrt(r3 * r3 + 0.5))
@@ -387,7 +387,7 @@ def tdse_leg(dsbt, inputs, torch, dev):
             "norm_drift_400_steps": drift, "observable": O.item(),
             "kernels_ms_per_step": {k: v[1] / steps for k, v in prof.items()},
             "all_m": {"config": "N=2048, L=32 per m, M=8 (544 channels, l <= 39), field along x, "
-                                "100 steps of 0.05", "propagate_ms_per_step": ms3 / steps3,
+                                "100 steps of 0.05, DSBT_PLAN_FAST64 plan", "propagate_ms_per_step": ms3 / steps3,
                       "kernels_ms_per_step": {k: v[1] / steps3 for k, v in prof3.items()},
                       "norm_after": norm3},
             "fast64": {"propagate_ms_per_step": fast_ms / steps,

@@ -100,3 +100,25 @@ def test_oscillator_along_x_matches_analytic(lib):
     print(f"oscillator delta: field along x {delta[0]:.3e}, along z {delta[2]:.3e}")
     assert delta[0] < 1.2e-3, delta
     assert abs(delta[0] - delta[2]) < 0.05 * delta[2], delta
+
+
+@pytest.mark.gpu
+def test_fast64_plan_gives_the_same_steps(lib):
+    """The all-m propagator over a DSBT_PLAN_FAST64 plan (O(N l log N) FP64
+    contractions) equals the dense FP64 plan's steps."""
+    N, r_max, L, M, tau = 1024, 102.4, 8, 3, 0.05
+    rng = np.random.default_rng(13)
+    F = rng.standard_normal((4, 3)) * 0.03
+    out = []
+    for fast in (False, True):
+        plan = lib.Plan(N, r_max, M + L - 1, tf32x3=False, fast64=fast)
+        t3 = lib.Tdse3d(plan, L, M, tau)
+        r = (np.arange(N) + 0.5) * (r_max / N)
+        t3.set_potential(-1.0 / np.sqrt(r ** 2 + 0.5))
+        psi = np.zeros((t3.nchan, N), dtype=complex)
+        f = r * np.exp(-0.5 * r * r)
+        psi[t3.channels.index((0, 0))] = f / np.linalg.norm(f)
+        out.append(t3.propagate(torch.from_numpy(psi).cuda(), torch.from_numpy(F), 8, hold=2).cpu().numpy())
+        t3.close()
+        plan.close()
+    assert np.abs(out[0] - out[1]).max() < 1e-12
