@@ -257,8 +257,8 @@ struct EpiArgs {
 };
 constexpr int kOutAugSplit = 16;
 
-// The kernel: roles, TMEM layout, chunked main accumulator and bounded waits
-// as in gemm_tf32x3.cu; what differs is where each K block comes from.
+// The kernel: roles and bounded waits as in gemm_tf32x3.cu; what differs is
+// where each K block comes from and the two alternating accumulator buffers.
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constant__ CUtensorMap tmA1_lo,
                const __grid_constant__ CUtensorMap tmB1_hi, const __grid_constant__ CUtensorMap tmB1_lo,
