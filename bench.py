@@ -232,6 +232,26 @@ def oracle_sample(nchan=16, ls=(1, 2), seed=11):
     return ntr, t_xform, t_build
 
 
+def rank_seed(rank: int, base: int = 100) -> int:
+    """Seed of a rank's synthetic batch: every rank transforms its own batch of
+    the workload (weak scaling, no data-path collective)."""
+    return base + rank
+
+
+def job_ms(ms_local: float, world: int, dist, device) -> float:
+    """Duration of the timed region for the whole job: the max over ranks."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank_step: float, world: int, steps: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return units_per_rank_step * world * steps / (ms_max * 1e-3)
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -547,7 +567,7 @@ def main():
 
     fast = not args.dense
     plan = dsbt.Plan(N, R_MAX, L_MAX, fp64=not args.no_fp64, tf32x3=True, fast_tf32=fast)
-    x = inputs.gaussian_sum(100 + rank, N, DR, counts, dtype=torch.complex64, device=dev)
+    x = inputs.gaussian_sum(rank_seed(rank), N, DR, counts, dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
     ws = plan.workspace(nchan, torch.complex64)
     stream = torch.cuda.current_stream()
@@ -587,12 +607,8 @@ def main():
     if status != 0:
         raise RuntimeError(f"device status {status} after the timed region")
 
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
-    transforms_per_step = 2 * nchan * world
-    value = transforms_per_step * args.steps / (ms_max * 1e-3)
+    ms_max = job_ms(ms, world, dist, dev)
+    value = job_value(2 * nchan, world, args.steps, ms_max)
 
     # ---------------------------------------------------------- e2e via host buffers
     # dsbt_kinetic_grouped_host: pinned host input and output, the library streams
@@ -611,10 +627,7 @@ def main():
         plan.kinetic_grouped_host(counts, xh, TAU, out=yh, chunks=args.e2e_chunks, workspace=hws)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_value = transforms_per_step * e2e_steps / (float(e2e_ms.item()) * 1e-3)
+    e2e_value = job_value(2 * nchan, world, e2e_steps, job_ms(e0.elapsed_time(e1), world, dist, dev))
     nbytes = x.numel() * x.element_size()
     del hws
 
