@@ -367,11 +367,21 @@ DSBT_API int dsbt_tdse3d_destroy(dsbt_tdse3d* tdse);
 DSBT_API int dsbt_tdse3d_channels(const dsbt_tdse3d* tdse, int* nchan, int* l_of, int* m_of);
 /* The radial potential V(r_i) from n = N HOST values on the midpoint grid.  Synchronous. */
 DSBT_API int dsbt_tdse3d_set_potential(dsbt_tdse3d* tdse, const double* V, int n);
-/* Device workspace: one state plus one DSBT workspace. */
+/* Device workspace: two states plus one DSBT workspace. */
 DSBT_API size_t dsbt_tdse3d_workspace_size(const dsbt_tdse3d* tdse);
 /* Propagate psi (device, in place) by nsteps steps, asynchronous on stream. */
 DSBT_API int dsbt_tdse3d_propagate(const dsbt_tdse3d* tdse, void* psi, const double* F, int nsteps, int hold,
                                    void* workspace, size_t workspace_bytes, void* stream);
+/* Velocity-gauge steps (Eq. (81)) with the vector potential A of any direction:
+ * psi <- exp(-iU tau/2) Y^H B^T exp(-iK tau/2) Ytilde exp(i k~_n (A.n) tau)
+ *        Ytilde^H exp(-iK tau/2) B Y exp(-iU tau/2) psi,
+ * U = V(r) + r F.n (F may be NULL), A = (A[3s'], A[3s'+1], A[3s'+2]), s' = s / hold
+ * (DEVICE array, NULL: A = 0), Ytilde = Y with the factors i^l of the modified
+ * harmonics on the momentum grid k~_n = n dk; the kinetic half phases use the
+ * plan's momenta.  Same workspace as dsbt_tdse3d_propagate. */
+DSBT_API int dsbt_tdse3d_propagate_velocity(const dsbt_tdse3d* tdse, void* psi, const double* F, const double* A,
+                                            int nsteps, int hold, void* workspace, size_t workspace_bytes,
+                                            void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batch of uneven transforms (different grids and l_max) sharing one factor

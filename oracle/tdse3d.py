@@ -75,6 +75,39 @@ class Model3d:
         x = self.kinetic(x, tau)
         return self.potential_half(x, Fv, tau)
 
+    def step_velocity(self, psi, Fv, Av, tau=None):
+        """Eq. (81) with a vector potential A of any direction: between the two
+        kinetic half steps, phi = Ytilde^H c on the momentum grid k~_n = n dk
+        (Ytilde = Y with the factors i^l of the modified harmonics), phi *=
+        exp(i k~_n (A . n) tau), c = Ytilde phi.  The spherical-wave
+        coefficients are s_l = (-1)^ceil(l/2) times this library's, so the
+        factor on c is (-i)^l s_l going in and i^l s_l coming out.  Momentum
+        slot n holds storage n - 1 (even l) or n (odd l, slot N at storage 0)."""
+        tau = self.tau if tau is None else tau
+        N = self.N
+        x = self.potential_half(psi, Fv, tau)
+        coef = np.zeros((len(self.channels), N), dtype=complex)       # [ch][n - 1]
+        slots = []
+        for c, (l, _) in enumerate(self.channels):
+            b = self.T[l] @ (self.F[l] @ x[c])
+            b = np.exp(-0.25j * self.kt[l] ** 2 * tau) * b
+            n = np.arange(N) + oracle.p_of(l)
+            slot = np.where(n == 0, N, n) - 1
+            slots.append(slot)
+            s_l = (-1) ** ((l + 1) // 2)
+            coef[c, slot] = (-1j) ** l * s_l * b
+        kt = np.arange(1, N + 1) * np.pi / self.r_max
+        phi = self.Y @ coef                                             # [(j, q)][n]
+        phi = np.exp(1j * (np.asarray(Av, dtype=np.float64) @ self.n)[:, None] * kt[None, :] * tau) * phi
+        coef = self.Y.conj().T @ phi
+        out = np.empty_like(x)
+        for c, (l, _) in enumerate(self.channels):
+            s_l = (-1) ** ((l + 1) // 2)
+            b = (1j) ** l * s_l * coef[c, slots[c]]
+            b = np.exp(-0.25j * self.kt[l] ** 2 * tau) * b
+            out[c] = self.F[l].T @ (self.T[l].T @ b)
+        return self.potential_half(out, Fv, tau)
+
     def run(self, psi, F_samples, nsteps: int, hold: int = 1):
         x = psi.copy()
         for s in range(nsteps):

@@ -27,6 +27,8 @@
 #include "plan.cuh"
 
 namespace dsbt {
+int grouped_device_call(int which, const dsbt_plan* p, const int* counts, int dtype, double tau,
+                        const void* in, void* out, void* ws, size_t ws_b, cudaStream_t st);
 int kinetic_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtype, double tau,
                                  const void* in, void* out, void* scratch, size_t scratch_bytes,
                                  cudaStream_t st);
@@ -38,6 +40,7 @@ struct dsbt_tdse3d {
     double tau;
     double* P;        // [NM][L][L]: P^m (row i = l - |m|, column j), m = mi - M
     int* map;         // [NM][L]: channel of (l = |m| + i, m)
+    int* lch;         // [nchan]: l of each channel
     double* V;        // [N]
     double* rr;       // [N]
     double* eta;      // [L]
@@ -137,6 +140,115 @@ __global__ void __launch_bounds__(256) k_tdse3d_potential(const double2* x, doub
     }
 }
 
+// The momentum-space middle of the velocity-gauge step (Eq. (81)) with all m,
+// in place on the DSBT coefficients c[ch][s] at TI3 momentum slots
+// n = 1..N per block (k~_n = n dk; storage s = n - 1 for even l, s = n for odd
+// l with n = N at s = 0): the half kinetic phase exp(-i k^2 tau/4) with the
+// plan's momentum of (l, s); phi = Ytilde^H c with the factors (-i)^l s_l = 1
+// (even l) or i (odd l) of the modified harmonics (s_l: this library's
+// sine/cosine signs); phi *= exp(i k~_n (A . n) tau) on the (theta, phi) grid;
+// c = Ytilde phi with i^l s_l = 1 or -i; the half kinetic phase again.
+__global__ void __launch_bounds__(256) k_tdse3d_velocity(double2* c, const double* __restrict__ P,
+                                                         const int* __restrict__ map, const int* __restrict__ lch,
+                                                         const double* __restrict__ eta,
+                                                         const double* __restrict__ knl, double dk, int L, int M,
+                                                         int N, int nchan, const double* __restrict__ A, int aidx,
+                                                         double tau) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int NM = 2 * M + 1;
+    double2* xs = reinterpret_cast<double2*>(sm);   // [nchan][TI3]
+    double2* G = xs + (size_t)nchan * TI3;          // [NM][L][TI3]
+    double2* g = G + (size_t)NM * L * TI3;          // [L][NM][TI3]
+    double2* ph = g + (size_t)NM * L * TI3;         // [NM][NM]
+    const int n0 = 1 + blockIdx.x * TI3, tid = threadIdx.x;
+    const double inv = rsqrt((double)NM);
+    for (int k = tid; k < NM * NM; k += blockDim.x) {
+        const int mi = k / NM, q = k % NM;
+        double sn, cs;
+        sincospi(2.0 * (double)((mi - M) * q) / NM, &sn, &cs);
+        ph[k] = make_double2(cs * inv, sn * inv);
+    }
+    for (int k = tid; k < nchan * TI3; k += blockDim.x) {   // gather, half kinetic phase, (-i)^l s_l
+        const int ch = k / TI3, t = k % TI3, n = n0 + t, l = lch[ch];
+        double2 v = make_double2(0.0, 0.0);
+        if (n <= N) {
+            const int sidx = (l & 1) ? (n % N) : n - 1;
+            const double km = knl ? knl[(size_t)l * N + sidx] : k_index(l, sidx, N) * dk;
+            double sn, cs;
+            sincos(-0.25 * km * km * tau, &sn, &cs);
+            const double2 a = c[(size_t)ch * N + sidx];
+            v = make_double2(a.x * cs - a.y * sn, a.x * sn + a.y * cs);
+            if (l & 1) v = make_double2(-v.y, v.x);   // times i
+        }
+        xs[k] = v;
+    }
+    __syncthreads();
+    for (int k = tid; k < NM * L * TI3; k += blockDim.x) {
+        const int mi = k / (L * TI3), j = (k / TI3) % L, t = k % TI3;
+        const double* Pm = P + (size_t)mi * L * L;
+        double2 s = make_double2(0.0, 0.0);
+        for (int ii = 0; ii < L; ++ii) {
+            const double p = Pm[ii * L + j];
+            const double2 v = xs[map[mi * L + ii] * TI3 + t];
+            s.x = fma(p, v.x, s.x);
+            s.y = fma(p, v.y, s.y);
+        }
+        G[k] = s;
+    }
+    __syncthreads();
+    const double Ax = A ? A[3 * aidx] : 0.0, Ay = A ? A[3 * aidx + 1] : 0.0, Az = A ? A[3 * aidx + 2] : 0.0;
+    for (int k = tid; k < L * NM * TI3; k += blockDim.x) {   // A . p phase on the momentum grid
+        const int j = k / (NM * TI3), q = (k / TI3) % NM, t = k % TI3, n = n0 + t;
+        double2 s = make_double2(0.0, 0.0);
+        for (int mi = 0; mi < NM; ++mi) {
+            const double2 a = ph[mi * NM + q], v = G[(mi * L + j) * TI3 + t];
+            s.x = fma(a.x, v.x, fma(-a.y, v.y, s.x));
+            s.y = fma(a.x, v.y, fma(a.y, v.x, s.y));
+        }
+        if (n <= N) {
+            const double ct = eta[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+            double sp, cp;
+            sincospi(2.0 * (double)q / NM, &sp, &cp);
+            const double an = Ax * st * cp + Ay * st * sp + Az * ct;
+            double sn, cs;
+            sincos(an * (n * dk) * tau, &sn, &cs);
+            s = make_double2(s.x * cs - s.y * sn, s.x * sn + s.y * cs);
+        }
+        g[k] = s;
+    }
+    __syncthreads();
+    for (int k = tid; k < NM * L * TI3; k += blockDim.x) {
+        const int mi = k / (L * TI3), j = (k / TI3) % L, t = k % TI3;
+        double2 s = make_double2(0.0, 0.0);
+        for (int q = 0; q < NM; ++q) {
+            const double2 a = ph[mi * NM + q], v = g[(j * NM + q) * TI3 + t];
+            s.x = fma(a.x, v.x, fma(a.y, v.y, s.x));
+            s.y = fma(a.x, v.y, fma(-a.y, v.x, s.y));
+        }
+        G[k] = s;
+    }
+    __syncthreads();
+    for (int k = tid; k < NM * L * TI3; k += blockDim.x) {   // back to (l, m), i^l s_l, half phase, scatter
+        const int mi = k / (L * TI3), ii = (k / TI3) % L, t = k % TI3, n = n0 + t;
+        if (n > N) continue;
+        const double* Pm = P + (size_t)mi * L * L + (size_t)ii * L;
+        double2 s = make_double2(0.0, 0.0);
+        for (int j = 0; j < L; ++j) {
+            const double p = Pm[j];
+            const double2 v = G[(mi * L + j) * TI3 + t];
+            s.x = fma(p, v.x, s.x);
+            s.y = fma(p, v.y, s.y);
+        }
+        const int ch = map[mi * L + ii], l = lch[ch];
+        if (l & 1) s = make_double2(s.y, -s.x);   // times -i
+        const int sidx = (l & 1) ? (n % N) : n - 1;
+        const double km = knl ? knl[(size_t)l * N + sidx] : k_index(l, sidx, N) * dk;
+        double sn, cs;
+        sincos(-0.25 * km * km * tau, &sn, &cs);
+        c[(size_t)ch * N + sidx] = make_double2(s.x * cs - s.y * sn, s.x * sn + s.y * cs);
+    }
+}
+
 size_t smem3d(const dsbt_tdse3d* t) {
     return ((size_t)t->nchan * TI3 + 2 * (size_t)t->NM * t->L * TI3 + (size_t)t->NM * t->NM) * sizeof(double2);
 }
@@ -149,6 +261,18 @@ int potential3d(const dsbt_tdse3d* t, const double2* x, double2* y, const double
     ProfScope ps(kKTdsePot, st);
     k_tdse3d_potential<<<(t->N + TI3 - 1) / TI3, 256, smem, st>>>(x, y, t->P, t->map, t->V, t->rr, t->eta, t->L,
                                                                   t->M, t->N, t->nchan, F, fidx, ht);
+    DSBT_CUDA_TRY(cudaGetLastError());
+    return DSBT_OK;
+}
+
+int velocity3d(const dsbt_tdse3d* t, double2* c, const double* A, int aidx, cudaStream_t st) {
+    const size_t smem = smem3d(t);
+    if (smem > 48 * 1024)
+        DSBT_CUDA_TRY(cudaFuncSetAttribute(k_tdse3d_velocity, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps(kKTdseAng, st);
+    k_tdse3d_velocity<<<(t->N + TI3 - 1) / TI3, 256, smem, st>>>(c, t->P, t->map, t->lch, t->eta, t->plan->knl,
+                                                                 t->plan->dk, t->L, t->M, t->N, t->nchan, A, aidx,
+                                                                 t->tau);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -201,23 +325,25 @@ extern "C" int dsbt_tdse3d_create(const dsbt_plan* plan, int L, int M, double ta
     for (int i = 0; i < t->N; ++i) rr[i] = (i + 0.5) * dr;
     bool ok = cudaMalloc((void**)&t->P, Pall.size() * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void**)&t->map, map.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void**)&t->lch, t->nchan * sizeof(int)) == cudaSuccess &&
               cudaMalloc((void**)&t->V, t->N * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void**)&t->rr, t->N * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void**)&t->eta, L * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMemcpy(t->P, Pall.data(), Pall.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(t->map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(t->lch, t->chan_l.data(), t->nchan * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(t->V, 0, t->N * sizeof(double)) == cudaSuccess &&
          cudaMemcpy(t->rr, rr.data(), t->N * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(t->eta, x.data(), L * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
-        cudaFree(t->P); cudaFree(t->map); cudaFree(t->V); cudaFree(t->rr); cudaFree(t->eta);
+        cudaFree(t->P); cudaFree(t->map); cudaFree(t->lch); cudaFree(t->V); cudaFree(t->rr); cudaFree(t->eta);
         delete t;
         set_error("dsbt_tdse3d_create: device allocation or copy failed");
         return DSBT_ERR_NOMEM;
     }
     if (smem3d(t) > 200 * 1024) {
-        cudaFree(t->P); cudaFree(t->map); cudaFree(t->V); cudaFree(t->rr); cudaFree(t->eta);
+        cudaFree(t->P); cudaFree(t->map); cudaFree(t->lch); cudaFree(t->V); cudaFree(t->rr); cudaFree(t->eta);
         delete t;
         set_error("dsbt_tdse3d_create: L=%d, M=%d need too much shared memory", L, M);
         return DSBT_ERR_INVALID;
@@ -231,6 +357,7 @@ extern "C" int dsbt_tdse3d_destroy(dsbt_tdse3d* t) {
     cudaDeviceSynchronize();
     cudaFree(t->P);
     cudaFree(t->map);
+    cudaFree(t->lch);
     cudaFree(t->V);
     cudaFree(t->rr);
     cudaFree(t->eta);
@@ -257,7 +384,7 @@ extern "C" int dsbt_tdse3d_set_potential(dsbt_tdse3d* t, const double* V, int n)
 
 extern "C" size_t dsbt_tdse3d_workspace_size(const dsbt_tdse3d* t) {
     if (!t) return 0;
-    return a256((size_t)t->nchan * t->N * sizeof(double2)) +
+    return 2 * a256((size_t)t->nchan * t->N * sizeof(double2)) +
            dsbt_workspace_size(t->plan, t->nchan, DSBT_C128) + 512;
 }
 
@@ -271,7 +398,7 @@ extern "C" int dsbt_tdse3d_propagate(const dsbt_tdse3d* t, void* psi, const doub
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* base = (unsigned char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
     double2* tmp = (double2*)base;
-    void* kws = base + a256((size_t)t->nchan * t->N * sizeof(double2));
+    void* kws = base + 2 * a256((size_t)t->nchan * t->N * sizeof(double2));
     const size_t kws_b = dsbt_workspace_size(t->plan, t->nchan, DSBT_C128);
     double2* x = (double2*)psi;
     for (int s = 0; s < nsteps; ++s) {
@@ -279,6 +406,34 @@ extern "C" int dsbt_tdse3d_propagate(const dsbt_tdse3d* t, void* psi, const doub
         int rc = potential3d(t, x, tmp, F, fidx, 0.5 * t->tau, st);
         if (!rc) rc = kinetic_grouped_with_scratch(t->plan, t->counts.data(), DSBT_C128, t->tau, tmp, x, kws, kws_b, st);
         if (!rc) rc = potential3d(t, x, x, F, fidx, 0.5 * t->tau, st);
+        if (rc) return rc;
+    }
+    return DSBT_OK;
+}
+
+extern "C" int dsbt_tdse3d_propagate_velocity(const dsbt_tdse3d* t, void* psi, const double* F, const double* A,
+                                              int nsteps, int hold, void* workspace, size_t workspace_bytes,
+                                              void* stream) {
+    DSBT_CHECK_ARG(t != nullptr && psi != nullptr, "dsbt_tdse3d_propagate_velocity: NULL argument");
+    DSBT_CHECK_ARG(nsteps >= 0 && hold >= 1, "dsbt_tdse3d_propagate_velocity: nsteps >= 0 and hold >= 1 required");
+    const size_t need = dsbt_tdse3d_workspace_size(t);
+    DSBT_CHECK_ARG(workspace != nullptr && workspace_bytes >= need,
+                   "dsbt_tdse3d_propagate_velocity: workspace too small (need %zu bytes)", need);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t sb = a256((size_t)t->nchan * t->N * sizeof(double2));
+    unsigned char* base = (unsigned char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    double2* tmp = (double2*)base;
+    double2* c = (double2*)(base + sb);
+    void* kws = base + 2 * sb;
+    const size_t kws_b = dsbt_workspace_size(t->plan, t->nchan, DSBT_C128);
+    double2* x = (double2*)psi;
+    for (int s = 0; s < nsteps; ++s) {
+        const int idx = s / hold;
+        int rc = potential3d(t, x, tmp, F, idx, 0.5 * t->tau, st);
+        if (!rc) rc = grouped_device_call(0, t->plan, t->counts.data(), DSBT_C128, 0.0, tmp, c, kws, kws_b, st);
+        if (!rc) rc = velocity3d(t, c, A, idx, st);
+        if (!rc) rc = grouped_device_call(1, t->plan, t->counts.data(), DSBT_C128, 0.0, c, x, kws, kws_b, st);
+        if (!rc) rc = potential3d(t, x, x, F, idx, 0.5 * t->tau, st);
         if (rc) return rc;
     }
     return DSBT_OK;

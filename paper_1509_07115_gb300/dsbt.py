@@ -94,6 +94,7 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_tdse3d_workspace_size.argtypes = [vp]
         lib.dsbt_tdse3d_workspace_size.restype = sz
         lib.dsbt_tdse3d_propagate.argtypes = [vp, vp, vp, i, i, vp, sz, vp]
+        lib.dsbt_tdse3d_propagate_velocity.argtypes = [vp, vp, vp, vp, i, i, vp, sz, vp]
         lib.dsbt_tdse_propagate_velocity.argtypes = [vp, vp, vp, vp, i, i, d, vp, sz, vp]
         lib.dsbt_tdse_workspace_size.argtypes = [vp, i, i]
         lib.dsbt_tdse_workspace_size.restype = sz
@@ -498,6 +499,21 @@ class Tdse3d:
         _check(load().dsbt_tdse3d_propagate(self._h, _ptr(psi), None if Fp is None else _ptr(Fp), int(nsteps),
                                             int(hold), _ptr(self._ws), self._ws.numel(), _stream()),
                "dsbt_tdse3d_propagate")
+        return psi
+
+    def propagate_velocity(self, psi: torch.Tensor, A, nsteps: int, hold: int = 1, F=None) -> torch.Tensor:
+        """In-place velocity-gauge propagation; A (and optionally F): [nsamples][3]."""
+        if psi.dtype != torch.complex128 or not psi.is_cuda or tuple(psi.shape) != (self.nchan, self.N) \
+                or not psi.is_contiguous():
+            raise ValueError(f"state must be a contiguous complex128 CUDA tensor of shape ({self.nchan}, {self.N})")
+        Ap = torch.as_tensor(A).to(device="cuda", dtype=torch.float64).contiguous()
+        Fp = None if F is None else torch.as_tensor(F).to(device="cuda", dtype=torch.float64).contiguous()
+        nb = int(load().dsbt_tdse3d_workspace_size(self._h))
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        _check(load().dsbt_tdse3d_propagate_velocity(self._h, _ptr(psi), None if Fp is None else _ptr(Fp), _ptr(Ap),
+                                                     int(nsteps), int(hold), _ptr(self._ws), self._ws.numel(),
+                                                     _stream()), "dsbt_tdse3d_propagate_velocity")
         return psi
 
 

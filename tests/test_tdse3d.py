@@ -58,15 +58,18 @@ def test_field_along_z_equals_fixed_m_propagator(lib):
     plan.close()
 
 
-def grid_state(m3, T, omega, axis):
+def grid_state(m3, T, omega, axis, kick=0.0, phase=0.0):
     """Exact oscillator state (field along `axis`) as channel coefficients:
-    Y^H of r Psi sqrt(dr w_j 2 pi / NM) on the (theta_j, phi_q) grid."""
+    Y^H of r Psi sqrt(dr w_j 2 pi / NM) on the (theta_j, phi_q) grid; kick
+    multiplies Psi by exp(i kick s) (s the coordinate along the axis) and phase
+    by exp(i phase) (the velocity-gauge factors)."""
     a, p, g = osc.classical(T, omega) if T > 0 else (0.0, 0.0, 0.0)
     st = np.sqrt(1 - m3.eta ** 2)
     n = {0: np.outer(st, np.cos(m3.phi)), 1: np.outer(st, np.sin(m3.phi)), 2: np.outer(m3.eta, np.ones(m3.NM))}[axis]
     s = n.reshape(-1)[:, None] * m3.r[None, :]                    # coordinate along the field
     rr = m3.r[None, :]
-    Psi = np.pi ** -0.75 * np.exp(-(rr ** 2 - s ** 2) / 2 - (s - a) ** 2 / 2 + 1j * p * (s - a) + 1j * (g - T))
+    Psi = np.pi ** -0.75 * np.exp(-(rr ** 2 - s ** 2) / 2 - (s - a) ** 2 / 2 + 1j * p * (s - a) + 1j * (g - T)
+                                  + 1j * kick * s + 1j * phase)
     wq = np.repeat(m3.w, m3.NM) * (2 * np.pi / m3.NM)
     gr = Psi * rr * np.sqrt(m3.dr * wq)[:, None]
     return m3.Y.conj().T @ gr
@@ -122,3 +125,56 @@ def test_fast64_plan_gives_the_same_steps(lib):
         t3.close()
         plan.close()
     assert np.abs(out[0] - out[1]).max() < 1e-12
+
+
+@pytest.mark.gpu
+def test_velocity_gauge_matches_oracle(lib):
+    N, r_max, L, M, tau = 256, 25.6, 4, 2, 0.05
+    plan = lib.Plan(N, r_max, M + L - 1, tf32x3=False)
+    t = lib.Tdse3d(plan, L, M, tau)
+    r = (np.arange(N) + 0.5) * (r_max / N)
+    V = 0.5 * r * r
+    t.set_potential(V)
+    m3 = tdse3d.Model3d(N, r_max, L, M, tau, V=V)
+    rng = np.random.default_rng(21)
+    psi = (rng.standard_normal((t.nchan, N)) + 1j * rng.standard_normal((t.nchan, N))) * 0.05
+    A = rng.standard_normal((3, 3)) * 0.2
+    F = rng.standard_normal((3, 3)) * 0.02
+    ref = psi.copy()
+    for s in range(6):
+        ref = m3.step_velocity(ref, F[s // 2], A[s // 2])
+    out = t.propagate_velocity(torch.from_numpy(psi).cuda(), torch.from_numpy(A), 6, hold=2,
+                               F=torch.from_numpy(F)).cpu().numpy()
+    t.close()
+    plan.close()
+    assert np.abs(out - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.gpu
+def test_velocity_gauge_oscillator_along_x_matches_analytic(lib):
+    """Velocity gauge, A(t) = -A0 sin(omega t) along x: the exact state is
+    exp(i int A^2/2) exp(i A(T) x) times the length-gauge one (Sec. 4.3)."""
+    N, r_max, L, M, omega = 256, 12.8, 12, 6, 2.0
+    tau, steps = 0.005, 628
+    T = tau * steps
+    plan = lib.Plan(N, r_max, M + L - 1, tf32x3=False)
+    t3 = lib.Tdse3d(plan, L, M, tau)
+    r = (np.arange(N) + 0.5) * (r_max / N)
+    t3.set_potential(0.5 * r ** 2)
+    m3 = tdse3d.Model3d(N, r_max, L, M, tau)
+    phase = 0.5 * osc.A0 ** 2 * (T / 2 - math.sin(2 * omega * T) / (4 * omega))
+    delta = {}
+    for axis in (0, 2):
+        c0 = grid_state(m3, 0.0, omega, axis)
+        c0 = c0 / np.linalg.norm(c0)
+        A = np.zeros((steps, 3))
+        A[:, axis] = [osc.vector_potential((s + 0.5) * tau, omega) for s in range(steps)]
+        out = t3.propagate_velocity(torch.from_numpy(c0).cuda(), torch.from_numpy(A), steps).cpu().numpy()
+        ex = grid_state(m3, T, omega, axis, kick=osc.vector_potential(T, omega), phase=phase)
+        ex = ex / np.linalg.norm(ex)
+        delta[axis] = abs(1 - np.vdot(ex, out))
+    t3.close()
+    plan.close()
+    print(f"velocity-gauge oscillator delta: along x {delta[0]:.3e}, along z {delta[2]:.3e}")
+    assert delta[0] < 6e-4, delta
+    assert abs(delta[0] - delta[2]) < 0.05 * delta[2], delta

@@ -60,3 +60,39 @@ def test_rotation_invariance_of_an_s_state():
     assert np.abs(dx - dz).max() < 1e-9 and np.abs(dy - dz).max() < 1e-9
     assert np.abs(dz.sum() - 1.0) < 1e-12                      # unitary
     assert np.sum(np.abs(ax[[c for c, (l, m) in enumerate(m3.channels) if m != 0]]) ** 2) > 1e-6   # m mixing
+
+
+def test_velocity_gauge_along_z_is_the_fixed_m_model():
+    """A vector potential along z couples no m: every m block of the all-m
+    velocity step equals the fixed-m oracle's velocity step."""
+    N, r_max, L, M, tau = 128, 12.8, 4, 2, 0.05
+    r = (np.arange(N) + 0.5) * (r_max / N)
+    V = 0.5 * r * r
+    m3 = tdse3d.Model3d(N, r_max, L, M, tau, V=V)
+    rng = np.random.default_rng(9)
+    psi = rng.standard_normal((len(m3.channels), N)) + 1j * rng.standard_normal((len(m3.channels), N))
+    out = m3.step_velocity(psi, (0.0, 0.0, 0.01), (0.0, 0.0, 0.2))
+    for mm in range(-M, M + 1):
+        fm = tdse1.Model(N, r_max, L, tau, V=V, m=mm)
+        idx = [m3.index(abs(mm) + i, mm) for i in range(L)]
+        ref = fm.to_l(fm.step_velocity(fm.to_eta(psi[idx]), 0.01, 0.2))
+        assert np.abs(out[idx] - ref).max() < 1e-12 * np.abs(ref).max(), mm
+
+
+def test_velocity_gauge_rotation_invariance_and_unitarity():
+    N, r_max, L, M, tau, S = 128, 12.8, 8, 6, 0.05, 10
+    m3 = tdse3d.Model3d(N, r_max, L, M, tau)
+    psi = np.zeros((len(m3.channels), N), dtype=complex)
+    f = m3.r * np.exp(-0.5 * m3.r ** 2)
+    psi[m3.index(0, 0)] = f / np.linalg.norm(f)
+    out = {}
+    for ax in (0, 2):
+        A = [0.0, 0.0, 0.0]
+        A[ax] = 0.3
+        x = psi.copy()
+        for _ in range(S):
+            x = m3.step_velocity(x, (0.0, 0.0, 0.0), A)
+        out[ax] = x
+    dx, dz = (np.sum(np.abs(a) ** 2, axis=0) for a in (out[0], out[2]))
+    assert abs(dz.sum() - 1.0) < 1e-12
+    assert np.abs(dx - dz).max() < 1e-9
