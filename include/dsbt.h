@@ -81,9 +81,10 @@ extern "C" {
                               cores: near band of T_l per 128-row leaf, far field
                               through 64 basis functions per used dyadic interval.
                               Needs l_max <= 64 (always true).  Extra memory:
-                              16 B x 128 x (l_max+1) x N x (N/128 - 1) of plan data
-                              (4.2 GB at N = 4096, l_max = 63) and 8 B x 64 x
-                              (N/128 - 1) per line of workspace. */
+                              about 16 B x 64 x (l_max+1) x N x (N/128 - 1) of plan
+                              data (8.4 GB at N = 4096, l_max = 63) and
+                              8 B x 64 x (N/128 - 1 + log2(N/128)) per line of
+                              workspace. */
 
 /* element types of the caller's arrays */
 #define DSBT_F64 1  /* real double                 */
