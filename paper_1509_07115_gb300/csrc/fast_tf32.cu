@@ -279,7 +279,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool aug = fs.mode == kMoments || fs.mode == kWeights;   // one slot per tile, 64-row A
+    const bool aug = fs.mode == kMoments || fs.mode == kWeights;   // two slots per tile, 64 A rows each
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
