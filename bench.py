@@ -93,16 +93,19 @@ def source_hash(paths):
 
 def fast_tf32_mac_per_line(N, l, leaf=128):
     """Multiply-adds of one DSBT_PLAN_FAST_TF32 contraction of one real line of
-    T_l (forward and inverse cost the same): near-field triangle of each
-    128-row leaf, far field (l per set bit of the leaf index), moments of the
-    used intervals (l per point of half the columns at each level), and the
-    dense completion rows n < n0_l = (l + 2) // 2."""
+    T_l as the scheme runs it: near-field triangle of each 128-row leaf, far
+    field (l per set bit of the leaf index), moments of the used intervals
+    (l per point of half the columns at each level) and of the right intervals
+    (l per column right of leaf 0), and the completion rows n < n0_l =
+    (l + 2) // 2 (leaf 0's columns plus l per right interval)."""
     nleaf = N // leaf
     levels = (nleaf - 1).bit_length()
     ne = (l + 2) // 2 - (1 if l % 2 == 0 else 0)
     near = sum(r % leaf + 1 for r in range(ne, N))
     far = sum(l * bin(r // leaf).count("1") for r in range(ne, N))
-    return near + far + levels * (N // 2) * l + ne * N
+    moments = levels * (N // 2) * l + ((N - leaf) * l if ne else 0)
+    completion = ne * (leaf + levels * l)
+    return near + far + moments + completion
 
 
 def ncu_traffic(name="contract_tf32x3_precision_form.json"):
