@@ -40,7 +40,12 @@ def _basis(length: int, K: int) -> np.ndarray:
 
 
 class Plan:
-    def __init__(self, N: int, l: int, B: int = 64):
+    """right=True: the completion rows n < n0_l (polynomials of degree < l in m
+    as well, Sec. 2.5) take the columns right of leaf 0 through the right
+    intervals (j, 1) = [B 2^j, B 2^(j+1)) instead of densely (forward only), as
+    the split-TF32 interval scheme does."""
+
+    def __init__(self, N: int, l: int, B: int = 64, right: bool = False):
         if N % B or (N // B) & (N // B - 1):
             raise ValueError("N / B must be a power of two")
         self.N, self.l, self.B = N, l, B
@@ -62,6 +67,15 @@ class Plan:
             half = B << (j - 1)
             Qp, Qc = self.Q[j], self.Q[j - 1]
             self.A.append([Qc.T @ Qp[:half], Qc.T @ Qp[half:]])
+        self.right = right
+        # completion rows on the right intervals (j, 1): moments there come from
+        # the level bases directly (columns >= B carry weight 1)
+        self.beta_right = {}
+        if right:
+            for r in range(self.ne):
+                for j in range(self.levels):
+                    lo, hi = B << j, B << (j + 1)
+                    self.beta_right[(r, j)] = self.Q[j].T @ self.T[r, lo:hi]
         # beta[r][j] = Q^T T[r, I_j(r)] for every far interval of row r
         self.beta = {}
         for r in range(self.ne, N):
@@ -84,7 +98,15 @@ class Plan:
         N, B, K = self.N, self.B, self.K
         T = self.T
         b = np.zeros(N)
-        b[:self.ne] = T[:self.ne] @ f                                  # completion rows
+        if self.right and K > 0:                                       # completion rows
+            for r in range(self.ne):
+                s = T[r, :B] @ f[:B]
+                for j in range(self.levels):
+                    lo, hi = B << j, B << (j + 1)
+                    s += self.beta_right[(r, j)] @ (self.Q[j].T @ f[lo:hi])
+                b[r] = s
+        else:
+            b[:self.ne] = T[:self.ne] @ f
         if K == 0:
             b[self.ne:] = np.diag(T)[self.ne:] * f[self.ne:]
             return b

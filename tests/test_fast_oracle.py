@@ -73,3 +73,16 @@ def test_completion_rows_are_polynomials_of_degree_below_l(l):
             Q = fast._basis(hi - lo, l)
             res = row - Q @ (Q.T @ row)
             assert np.abs(res).max() <= 1e-12 * max(np.abs(row).max(), 1e-300), (r, lo)
+
+
+@pytest.mark.parametrize("N, l", [(256, 1), (512, 6), (1024, 33), (1024, 63)])
+def test_completion_rows_through_right_intervals(N, l):
+    """The split-TF32 interval scheme's completion rows: leaf 0's columns densely,
+    the columns right of it through the right intervals (j, 1) and the level
+    bases.  Equals the dense product to rounding (leaves of 128)."""
+    rng = np.random.default_rng(100 + l)
+    P = fast.Plan(N, l, B=128, right=True)
+    f = rng.standard_normal(N)
+    b = P.T @ f
+    tol = 1e-14 if l < 40 else 1e-12
+    assert np.abs(P.forward(f) - b).max() <= tol * np.linalg.norm(f)
