@@ -49,6 +49,7 @@ class Plan:
         if N % B or (N // B) & (N // B - 1):
             raise ValueError("N / B must be a power of two")
         self.N, self.l, self.B = N, l, B
+        self.right = right
         self.T = oracle.T_matrix(N, l)
         self.ne = oracle.n0(l) - oracle.p_of(l)           # completion rows (storage 0..ne-1)
         self.sw = np.ones(N)                               # sqrt(w_m): 1/sqrt(2) at m = 0 (odd l)
@@ -67,7 +68,6 @@ class Plan:
             half = B << (j - 1)
             Qp, Qc = self.Q[j], self.Q[j - 1]
             self.A.append([Qc.T @ Qp[:half], Qc.T @ Qp[half:]])
-        self.right = right
         # completion rows on the right intervals (j, 1): moments there come from
         # the level bases directly (columns >= B carry weight 1)
         self.beta_right = {}
