@@ -5,7 +5,8 @@ transform is orthogonal and reproduces the cos(theta) coupling of the l basis,
 the step is unitary and palindromic, and with V = 0, E = 0 it reduces to the
 closed-form free evolution exp(-i k~^2 t / 2) in the DSBT basis.  GPU tests
 compare the CUDA propagator with the oracle and check the adjoint gradient
-against central finite differences (the paper has no gradient).
+against central finite differences (the paper gives no gradient, so finite
+differences are its reference).
 """
 import numpy as np
 import pytest
