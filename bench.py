@@ -13,14 +13,20 @@ Printed JSON line (rank 0):
               (dsbt_kinetic_grouped_host: copies inside the call, overlapped in chunks)
               (host->device copy of the inputs and device->host copy of the
               result inside the timed region)
-  roofline    of the dominant kernel (the split-TF32 contraction through the
+  roofline    of the dominant kernel (the split contraction through the
               interval scheme of DSBT_PLAN_FAST_TF32; --dense: the dense one),
               timed live with CUDA events on its launch stream during the
-              timed steps; algorithmic flops of the scheme it runs
+              timed steps; HBM-bound, algorithmic bytes 16 N B per complex64
+              channel-transform (its share per launch), with the whole-step
+              fraction and the kernel's tensor rate (algorithmic flops of the
+              scheme it runs) against the measured matmul rate beside it
+  measured_peaks  FP64 / TF32 / FP16 matmul rates and pinned copy bandwidth
+              measured in this run (the denominators MEASURED_PEAKS.json lacks)
   dense_tf32  the same step with the dense split-TF32 contraction
   fp64_gpu    the plain FP64 GPU path on a one-eighth sample (batch 1), and the
               split-TF32 error against it (max |diff| / ||psi|| per channel)
-  cpu_baseline  the FP64 CPU oracle on a bounded sample (N = 4096, l = 1, 2)
+  cpu_baseline  the FP64 CPU oracle on a bounded sample (N = 4096, l = 1, 2),
+              one channel per call over all host cores
 
 --impl reference runs the FP64 CPU oracle (the only reference this project
 has) on the same workload, a bounded sample per step.
@@ -61,7 +67,6 @@ TAU = 0.05
 N, R_MAX, L_MAX, BATCH = 4096, 409.6, 63, 8
 DR = R_MAX / N
 WORKLOAD = WORKLOADS["precision"]["desc"]
-TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rate ratio
 FLOP_PER_CHANNEL = 6.0 * N * N   # split-TF32 contraction, one direction, per complex channel
 
 
@@ -120,6 +125,51 @@ def ncu_traffic(name="contract_tf32x3_precision_form.json"):
         return d.get("dram_bytes_per_launch_full_size")
     except Exception:
         return None
+
+
+def probe_peaks(torch, dev):
+    """Measured denominators that MEASURED_PEAKS.json lacks, on this GPU:
+    dense FP64, TF32 and FP16 matmul rates (torch.matmul, 8192^3, 2 N^3 flop,
+    best of several, CUDA events; burst figures) and the pinned host<->device
+    copy bandwidth (1 GiB, best of 5)."""
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def best_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    out = {}
+    n = 8192
+    old_tf32 = torch.backends.cuda.matmul.allow_tf32
+    for name, dt, reps, tf32 in (("fp64", torch.float64, 3, False), ("tf32", torch.float32, 10, True),
+                                 ("fp16", torch.float16, 10, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device=dev, dtype=torch.float32).to(dt)
+        b = torch.randn(n, n, device=dev, dtype=torch.float32).to(dt)
+        c = torch.empty(n, n, device=dev, dtype=dt)
+        ms = best_ms(lambda: torch.matmul(a, b, out=c), reps)
+        out[f"{name}_tflops"] = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = old_tf32
+    nb = 1 << 30
+    h = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nb, dtype=torch.uint8, device=dev)
+    out["h2d_gbs"] = nb / (best_ms(lambda: d.copy_(h, non_blocking=True), 5) * 1e-3) / 1e9
+    out["d2h_gbs"] = nb / (best_ms(lambda: h.copy_(d, non_blocking=True), 5) * 1e-3) / 1e9
+    del h, d
+    torch.cuda.empty_cache()
+    out["how"] = ("torch.matmul 8192^3 (2 N^3 flop), best of 3 (fp64) / 10 (tf32 with allow_tf32, fp16), "
+                  "CUDA events; pinned 1 GiB copies best of 5")
+    return out
 
 
 class ClockSampler:
@@ -197,42 +247,53 @@ def bad_clocks(c):
 
 # ---------------------------------------------------------------- CPU oracle leg
 
-def oracle_sample(nchan=16, ls=(1, 2), seed=11):
-    """Times the FP64 oracle as it stands (single thread) on a bounded sample:
-    for each l in ls, nchan channels of the workload's Gaussian-sum inputs;
-    factor build (binary128 DLOP rows, explicit F_l) timed separately from the
-    transforms (naive O(N^2) sums in C).  Returns (transforms, seconds, build_s)."""
+def oracle_threads():
+    return max(1, os.cpu_count() or 1)
+
+
+def oracle_sample(per_thread=2, ls=(1, 2), seed=11):
+    """Times the FP64 oracle as it stands on a bounded sample, one channel per
+    call of its C routines spread over all host cores by a thread pool (the C
+    routines release the GIL; the oracle's arithmetic is untouched): for each l
+    in ls, per_thread x cores channels of the workload's Gaussian-sum inputs,
+    kinetic round trip by naive O(N^2) sums.  The cost per channel does not
+    depend on l (dense sums), so the sample stands for every l group; the
+    factor build (binary128 DLOP rows, explicit F_l), which does depend on l,
+    is timed separately and excluded.  Returns (transforms, seconds, build_s,
+    threads)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import numpy as np
 
     import oracle
     from paper_1509_07115_gb300 import inputs
+    nt = oracle_threads()
+    nchan = per_thread * nt
     counts = [0] * (max(ls) + 1)
     for l in ls:
         counts[l] = nchan
     x = inputs.gaussian_sum(seed, N, DR, counts)
-    t_build = 0.0
-    t_xform = 0.0
-    ntr = 0
+    t0 = time.perf_counter()
+    FT = {l: (oracle.F_matrix(N, l), oracle.T_matrix(N, l)) for l in ls}
+    t_build = time.perf_counter() - t0
+    jobs = []
     c0 = 0
-    dk = math.pi / R_MAX
     for l in range(max(ls) + 1):
-        c = counts[l]
-        if not c:
-            continue
-        t0 = time.perf_counter()
-        F = oracle.F_matrix(N, l)
-        T = oracle.T_matrix(N, l)
-        t_build += time.perf_counter() - t0
+        for c in range(counts[l]):
+            jobs.append((l, c0 + c))
+        c0 += counts[l]
+
+    def one(job):
+        l, c = job
+        F, T = FT[l]
         kt = oracle.k_tilde(N, R_MAX, l)
-        t0 = time.perf_counter()
-        f = oracle.apply(F, x[c0:c0 + c])
-        b = oracle.apply(T, f) * np.exp(-0.5j * kt * kt * TAU)
-        f2 = oracle.apply(T, b, transpose=True)
-        oracle.apply(F, f2, transpose=True)
-        t_xform += time.perf_counter() - t0
-        ntr += 2 * c
-        c0 += c
-    return ntr, t_xform, t_build
+        b = oracle.apply(T, oracle.apply(F, x[c:c + 1])) * np.exp(-0.5j * kt * kt * TAU)
+        oracle.apply(F, oracle.apply(T, b, transpose=True), transpose=True)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(nt) as ex:
+        list(ex.map(one, jobs))
+    t_xform = time.perf_counter() - t0
+    return 2 * len(jobs), t_xform, t_build, nt
 
 
 def rank_seed(rank: int, base: int = 100) -> int:
@@ -258,28 +319,34 @@ def job_value(units_per_rank_step: float, world: int, steps: int, ms_max: float)
 def run_reference(args, rank):
     if rank != 0:
         return
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle
     oracle.build()
     import numpy as np
     from paper_1509_07115_gb300 import inputs
     # factors for the sampled l, built once (binary128 recurrences); each step
-    # then runs the kinetic round trip of one channel, alternating l = 1 and 2
+    # then runs the kinetic round trip of one channel per host core (threads,
+    # alternating l = 1 and 2); the dense sums cost the same for every l
+    nt = oracle_threads()
     t0 = time.perf_counter()
     FT = {1: (oracle.F_matrix(N, 1), oracle.T_matrix(N, 1)), 2: (oracle.F_matrix(N, 2), oracle.T_matrix(N, 2))}
     t_build = time.perf_counter() - t0
-    x = inputs.gaussian_sum(13, N, DR, [0, 1, 1])
-    dk = math.pi / R_MAX
-    it = [0]
+    x = inputs.gaussian_sum(13, N, DR, [0, nt, nt])
 
-    def step():
-        l = 1 + (it[0] % 2)
-        it[0] += 1
+    def one(c):
+        l = 1 + (c % 2)
         F, T = FT[l]
-        xs = x[l - 1:l]
+        xs = x[(l - 1) * nt + c // 2:(l - 1) * nt + c // 2 + 1]
         kt = oracle.k_tilde(N, R_MAX, l)
         b = oracle.apply(T, oracle.apply(F, xs)) * np.exp(-0.5j * kt * kt * TAU)
         oracle.apply(F, oracle.apply(T, b, transpose=True), transpose=True)
-        return 2
+
+    ex = ThreadPoolExecutor(nt)
+
+    def step():
+        list(ex.map(one, range(nt)))
+        return 2 * nt
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
@@ -287,24 +354,24 @@ def run_reference(args, rank):
     for _ in range(args.steps):
         ntr += step()
     dt = time.perf_counter() - t0
+    ex.shutdown()
     value = ntr / dt
-    sample = (f"one complex channel per step (alternating l=1 and l=2) of the N=4096 workload, kinetic "
-              f"round trip by naive O(N^2) sums, single thread; factor build for l=1,2 took "
-              f"{t_build:.1f} s (excluded)")
+    sample = (f"{nt} complex channels per step (one per host thread, alternating l=1 and l=2) of the N=4096 "
+              f"workload, kinetic round trip by naive O(N^2) sums (cost independent of l); factor build for "
+              f"l=1,2 took {t_build:.1f} s (excluded)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Gaussian-sum radial functions)",
             "config": {"workload": WORKLOAD, "N": N, "l_max": L_MAX, "channels": sum(2 * l + 1 for l in range(L_MAX + 1)) * BATCH,
                        "reference": "FP64 CPU oracle (plain C, binary128 DLOP rows), bounded sample"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- TDSE leg
 
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (nominal; not in the measured peaks)
 
 
 def fast64_fma_per_line(N, l, B=64):
@@ -321,10 +388,10 @@ def fast64_fma_per_line(N, l, B=64):
     return near + far + levels * (N // 2) * l + ne * N
 
 
-def tdse_leg(dsbt, inputs, torch, dev):
+def tdse_leg(dsbt, inputs, torch, dev, fp64_peak):
     """m = 0, l = 0..63, N = 2048, dr = 0.1, soft-Coulomb, 400 steps of 0.05 with
     200 field samples (held 2 steps): propagation and adjoint-gradient timings,
-    and the FP64 contraction's rate against the nominal FP64 peak."""
+    and the FP64 contraction's rate against the measured FP64 matmul rate."""
     import numpy as np
     Nt, L, tau, steps = 2048, 64, 0.05, 400
     plan = dsbt.Plan(Nt, 204.8, L - 1, tf32x3=False)
@@ -417,18 +484,18 @@ def tdse_leg(dsbt, inputs, torch, dev):
                        "kernels_ms_per_step": {k: v[1] / steps for k, v in fprof.items()},
                        "max_abs_diff_vs_dense": fast_dev,
                        "roofline_contract": {"bound": "fp64", "achieved": fast_achieved,
-                                             "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                                             "frac": fast_achieved / FP64_NOMINAL_TFLOPS,
+                                             "peak": fp64_peak, "unit": "TFLOP/s",
+                                             "frac": fast_achieved / fp64_peak,
                                              "flop_per_step": fast_flop,
-                                             "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}},
-            "roofline_contract_f64": {"bound": "fp64", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-                                      "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
-                                      "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}}
+                                             "peak_source": "measured fp64 matmul (burst, this run)"}},
+            "roofline_contract_f64": {"bound": "fp64", "achieved": achieved, "peak": fp64_peak,
+                                      "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                                      "peak_source": "measured fp64 matmul (burst, this run)"}}
 
 
 # ---------------------------------------------------------------- uneven batch leg
 
-def batch_leg(dsbt, inputs, torch, dev, steps, warmup):
+def batch_leg(dsbt, inputs, torch, dev, steps, warmup, peak):
     """64 transforms, N ~ U{512..8192 step 256}, l_max ~ U{8..64} (seed 0), 2l+1
     complex64 Gaussian-sum channels per l; one kinetic step of the whole batch
     per graph replay (factors shared across grids, one persistent contraction
@@ -466,8 +533,6 @@ def batch_leg(dsbt, inputs, torch, dev, steps, warmup):
     nchan = sum(sum(c) for _, _, c in trs)
     flop = sum(6.0 * N * N * sum(c) for N, _, c in trs)   # per contraction launch (one direction)
     n_c, ms_c = prof.get("contract_tf32x3", (1, 0.0))
-    peaks, src = load_peaks()
-    peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
     ach = flop / (ms_c / n_c * 1e-3) / 1e12
     info = b.info()
     # sampled parity: one mid-size transform against the single-plan path
@@ -487,7 +552,13 @@ def batch_leg(dsbt, inputs, torch, dev, steps, warmup):
             "steps": steps, "build_s": build_s, "autotune": info,
             "kernels_ms_direct_call": {kk: v[1] for kk, v in prof.items()},
             "roofline_contract": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": ach / peak, "flop_per_launch": flop},
+                                  "frac": ach / peak, "flop_per_launch": flop,
+                                  "note": "dense N^2 flops of the contraction this batch runs (the interval "
+                                          "scheme's count would be several times lower)",
+                                  "peak_source": "measured tf32 matmul (burst, this run)"},
+            "hbm": {"algorithmic_bytes_per_step": 2 * 16.0 * sum(N * sum(c) for N, _, c in trs),
+                    "frac_whole_step": 2 * 16.0 * sum(N * sum(c) for N, _, c in trs) / (ms * 1e-3) / 1e9
+                    / load_peaks()[0]["hbm_gbs"]},
             "max_rel_err_vs_single_plan": err}
 
 
@@ -630,16 +701,29 @@ def main():
         plan.kinetic_grouped_host(counts, xh, TAU, out=yh, chunks=args.e2e_chunks, workspace=hws)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_value = job_value(2 * nchan, world, e2e_steps, job_ms(e0.elapsed_time(e1), world, dist, dev))
+    job_ms_e2e = job_ms(e0.elapsed_time(e1), world, dist, dev)
+    e2e_value = job_value(2 * nchan, world, e2e_steps, job_ms_e2e)
     nbytes = x.numel() * x.element_size()
     del hws
 
-    # ---------------------------------------------------------- roofline of the contraction
+    # ---------------------------------------------------------- measured peaks (after the timed region)
     peaks, src = load_peaks()
-    peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+    probes = probe_peaks(torch, dev)
+    hbm = peaks["hbm_gbs"]
+
+    # ---------------------------------------------------------- roofline of the contraction
+    # The method's algorithmic work is HBM-bound: 16 N bytes per complex64
+    # channel-transform (one read and one write of the channel), i.e.
+    # 2 x 16 N x channels bytes per kinetic step.  A launch of the dominant
+    # kernel is credited with its share of the step's bytes (step bytes over the
+    # contraction launches per step); its tensor rate against the measured dense
+    # rate of its operand type is reported beside it.
     k_launches, k_ms = prof.get("contract_tf32x3", (0, 0.0))
     avg_ms = k_ms / max(1, k_launches)
     launches_per_step = k_launches / args.steps
+    bytes_step = 2 * 16.0 * N * nchan
+    bytes_launch = bytes_step / launches_per_step
+    achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
     if fast:
         # four launches per step (moments, forward rows, adjoint weights, adjoint
         # columns); algorithmic flops of the interval scheme, 3 split products
@@ -649,14 +733,24 @@ def main():
         flop_per_step = 2 * FLOP_PER_CHANNEL * nchan
         kname, tname = "contract_tf32x3", "contract_tf32x3_precision_form.json"
     flop_per_launch = flop_per_step / launches_per_step
-    achieved = flop_per_launch / (avg_ms * 1e-3) / 1e12
+    tflops = flop_per_launch / (avg_ms * 1e-3) / 1e12
+    tpeak = probes["tf32_tflops"]
     traffic = ncu_traffic(tname) if args.workload == "precision" else None
-    roofline = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": f"{src}: bf16 sustained x {TF32_OVER_BF16:.3f} (nominal tf32/bf16)",
-                "flop_per_launch": flop_per_launch, "avg_launch_ms": avg_ms,
-                "launches_per_step": launches_per_step,
-                "dense_equivalent_tflops": 2 * FLOP_PER_CHANNEL * nchan / (k_ms / args.steps * 1e-3) / 1e12,
+    step_ms = ms / args.steps
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic,
+                "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
+                "algorithmic_bytes_per_launch": bytes_launch,
+                "algorithmic_bytes_rule": "16 N B per complex64 channel-transform, 2 per channel per step, "
+                                          "shared over the contraction launches of the step",
+                "traffic_ratio": (traffic / bytes_launch) if traffic else None,
+                "avg_launch_ms": avg_ms, "launches_per_step": launches_per_step,
+                "whole_step": {"achieved": bytes_step / (step_ms * 1e-3) / 1e9, "frac": bytes_step / (step_ms * 1e-3) / 1e9 / hbm,
+                               "ms": step_ms},
+                "tensor": {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
+                           "flop_per_launch": flop_per_launch,
+                           "peak_source": "measured tf32 matmul (burst, this run)",
+                           "dense_equivalent_tflops": 2 * FLOP_PER_CHANNEL * nchan / (k_ms / args.steps * 1e-3) / 1e12},
                 "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
 
     line = None
@@ -671,7 +765,13 @@ def main():
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                         "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
                         "api": f"dsbt_kinetic_grouped_host, pinned host buffers, {args.e2e_chunks} chunks"},
-                "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+                "gpu_launches": launches, "roofline": roofline, "clocks": clocks,
+                "measured_peaks": dict(probes, hbm_gbs=hbm, bf16_tflops=peaks.get("bf16_tflops"),
+                                       bf16_tflops_sustained=peaks.get("bf16_tflops_sustained"))}
+        line["e2e"]["copy_bound"] = {
+            "h2d_gbs_achieved": nbytes / (1e-3 * job_ms_e2e / e2e_steps) / 1e9,
+            "h2d_gbs_pinned_peak": probes["h2d_gbs"], "d2h_gbs_pinned_peak": probes["d2h_gbs"],
+            "note": "each step copies the batch in and out; copies run both ways at once, overlapped with compute"}
 
     # ---------------------------------------------------------- FP64 GPU path (sample) + error
     if not args.no_fp64:
@@ -709,25 +809,28 @@ def main():
 
     # ---------------------------------------------------------- dense split-TF32 contraction (context)
     if rank == 0 and fast and args.workload == "precision":
-        line["dense_tf32"] = dense_leg(dsbt, torch, counts, x, peak, args)
+        line["dense_tf32"] = dense_leg(dsbt, torch, counts, x, tpeak, args)
 
     # ---------------------------------------------------------- TDSE (propagator + adjoint)
     if rank == 0 and not args.no_tdse and args.workload == "precision":
-        line["tdse"] = tdse_leg(dsbt, inputs, torch, dev)
+        line["tdse"] = tdse_leg(dsbt, inputs, torch, dev, probes["fp64_tflops"])
 
     # ---------------------------------------------------------- uneven batch (one launch, graph)
     if rank == 0 and not args.no_batch and args.workload == "precision":
         plan.close()
         torch.cuda.empty_cache()
-        line["uneven_batch"] = batch_leg(dsbt, inputs, torch, dev, max(3, args.steps // 3), 2)
+        line["uneven_batch"] = batch_leg(dsbt, inputs, torch, dev, max(3, args.steps // 3), 2, tpeak)
 
     # ---------------------------------------------------------- CPU oracle baseline
     if rank == 0 and world == 1 and not args.no_cpu:
-        ntr, t_x, t_b = oracle_sample()
-        line["cpu_baseline"] = {"value": ntr / t_x, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": (f"{ntr} channel-transforms (16 complex channels each of l=1 and l=2, "
-                                           f"N=4096, kinetic round trip by naive O(N^2) sums, single thread); "
-                                           f"factor build {t_b:.1f} s excluded")}
+        ntr, t_x, t_b, nt = oracle_sample()
+        line["cpu_baseline"] = {"value": ntr / t_x, "unit": UNIT, "cores": nt, "kind": "oracle",
+                                "sample": (f"{ntr} channel-transforms ({ntr // 4} complex channels each of l=1 and "
+                                           f"l=2, N=4096, kinetic round trip by naive O(N^2) sums, {nt} threads, "
+                                           f"one channel per call; the cost per channel is the same for every l, "
+                                           f"so the rate stands for the whole workload); factor build for l=1,2 "
+                                           f"{t_b:.1f} s excluded"),
+                                "build_s_l12": t_b}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()   # idempotent

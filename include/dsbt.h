@@ -190,9 +190,11 @@ DSBT_API int dsbt_kinetic_grouped(const dsbt_plan* plan, const int* counts, int 
  * loading this library reserves until the process exits; a call whose
  * dsbt_workspace_size exceeds 64 MiB (roughly sum(counts) * N > 2^21 complex
  * samples) is rejected with DSBT_ERR_INVALID before any launch.  The call
- * allocates nothing: the first call on a device looks up the array's device
- * address with cudaGetSymbolAddress (so make that first call before any stream
- * capture).  All calls on a device share the one array, so calls that may
+ * allocates nothing: every call looks up the array's device address with
+ * cudaGetSymbolAddress on the current device (no cached address, so the call
+ * stays valid after cudaDeviceReset); the first call on a device may load the
+ * library's device code there, so make that first call before any stream
+ * capture.  All calls on a device share the one array, so calls that may
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  The plan must belong to the current device.
  */
@@ -228,10 +230,33 @@ DSBT_API int dsbt_kinetic_grouped_host(const dsbt_plan* plan, const int* counts,
 /*
  * Read the plan's device status word (synchronous: waits for the device).
  * 0 = OK; 1 = a device-side wait in a tensor-core contraction gave up after its
- * iteration limit (the kernel then skipped its remaining work).  reset != 0
+ * iteration limit (the kernel then skipped its remaining work, after letting
+ * its own TMA copies and MMAs already in flight finish; the results of that
+ * call are undefined, the context and the plan stay usable).  reset != 0
  * clears the word afterwards.
  */
 DSBT_API int dsbt_device_status(const dsbt_plan* plan, int reset, int* status_out);
+
+/*
+ * Re-run the plan's orthogonality probe (Eq. (25), T^{-1} = T^T) on its FP64
+ * factors: max |T^T (T x) - x| over two pseudo-random x per l into *err_out
+ * (may be NULL); DSBT_ERR_PLAN_CHECK above 1e-12, DSBT_ERR_UNSUPPORTED for a
+ * plan without DSBT_PLAN_FP64.  Synchronous on `stream`.
+ */
+DSBT_API int dsbt_plan_check(dsbt_plan* plan, double* err_out, void* stream);
+
+/*
+ * Testing hooks for the failure paths (no counterpart in the paper).
+ * dsbt_plan_set_spin_limit: polls of each bounded mbarrier wait in this plan's
+ * tensor-core kernels (0 restores the default, 2^25); a small value makes
+ * waits give up, which a later dsbt_device_status reports.
+ * dsbt_plan_perturb_T: adds delta to entry (row, col) of the FP64 T_l (not to
+ * the split copies), so that dsbt_plan_check sees a corrupt factor.
+ * Both change a plan that is otherwise immutable: no call may be in flight on
+ * it.  Synchronous.
+ */
+DSBT_API int dsbt_plan_set_spin_limit(dsbt_plan* plan, unsigned polls);
+DSBT_API int dsbt_plan_perturb_T(dsbt_plan* plan, int l, int row, int col, double delta, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Bound states of one l channel (Sec. 4.4): imaginary-time evolution with the

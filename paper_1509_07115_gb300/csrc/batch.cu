@@ -180,7 +180,8 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                  const __grid_constant__ CUtensorMap tI_hi, const __grid_constant__ CUtensorMap tI_lo,
                  const PTile* __restrict__ tiles, int total, const BGroup* __restrict__ groups,
                  const BTrans* __restrict__ trans, const TMaps* __restrict__ tmaps, const BMaps* __restrict__ cmaps,
-                 int Nmax, int dir, int mode, float2* __restrict__ out_user, unsigned* status, int* sched) {
+                 int Nmax, int dir, int mode, float2* __restrict__ out_user, unsigned* status, uint32_t spin,
+                 int* sched) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage_base = smem;
@@ -190,7 +191,8 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
     uint64_t* main_empty = main_full + 1;
     uint64_t* tq_full = main_empty + 1;
     uint64_t* tq_empty = tq_full + QS;
-    int* tile_q = (int*)(tq_empty + QS);
+    uint64_t* drain_bar = tq_empty + QS;    // the MMA issuer's exit drain
+    int* tile_q = (int*)(drain_bar + 1);
     uint32_t* tmem_slot = (uint32_t*)(tile_q + QS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -206,6 +208,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
             mbar_init(&tq_full[q], 1);
             mbar_init(&tq_empty[q], 1 + EPI_WARPS);
         }
+        mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -227,10 +230,11 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
+            StageLedger led;
             int qslot = 0;
             uint32_t qphase = 0;
             while (ok) {
-                if (!mbar_wait(&tq_empty[qslot], qphase ^ 1, abort_flag, status)) { ok = false; break; }
+                if (!mbar_wait(&tq_empty[qslot], qphase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                 int t = atomicAdd(sched, 1);
                 if (t >= total) t = -1;
                 tile_q[qslot] = t;
@@ -252,9 +256,10 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                     const int kb = sp.kb(i);
                     int s0, s1;
                     step_segments(dir, tl, sp, i, &s0, &s1);
-                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                     unsigned char* sb = stage_base + stage * STAGE_BYTES;
                     mbar_expect_tx(&full[stage], 2 * A_BYTES + 2 * (s1 - s0) * SEG * BK * 4);
+                    led.arm(stage, phase);
                     if (dir > 0) {
                         if (rt == 0) {   // rows 0..31 from the per-N table, 32..127 shared
                             const int cidx = tl.cidx;
@@ -289,6 +294,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
             }
+            led.drain(full, STAGES, status);   // copies still in flight after an abort
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
@@ -301,7 +307,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
             int qslot = 0;
             uint32_t qphase = 0;
             while (ok) {
-                if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status)) break;
+                if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status, spin)) break;
                 const int t = ((volatile int*)tile_q)[qslot];
                 mbar_arrive(&tq_empty[qslot]);
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
@@ -316,7 +322,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                     // epilogue to drain the main accumulator.
                     const bool pre = c0 > 0;
                     if (pre) {
-                        if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                        if (!mbar_wait(&full[stage], phase, abort_flag, status, spin)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
                         const uint32_t sb_hi = sa + 2 * A_BYTES;
@@ -329,7 +335,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                             mma_tf32(d_corr, dal, dbh, idesc_all, 1);
                         }
                     }
-                    if (!mbar_wait(main_empty, mphase ^ 1, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(main_empty, mphase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                     mphase ^= 1;
                     tc_fence_after();
                     for (int i = c0; i < c1; ++i) {
@@ -343,7 +349,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                         const uint32_t idesc = sub ? idesc_tf32(BM, (s1 - s0) * SEG) : idesc_all;
                         const uint32_t col0 = (uint32_t)(s0 * SEG);
                         if (!early) {
-                            if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                            if (!mbar_wait(&full[stage], phase, abort_flag, status, spin)) { ok = false; break; }
                             tc_fence_after();
                         }
                         const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
@@ -369,6 +375,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
                     c0 = c1;
                 }
             }
+            mma_drain(drain_bar, status);   // every MMA issued has finished
         }
         __syncwarp();
     } else {
@@ -380,7 +387,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
         int qslot = 0;
         uint32_t qphase = 0;
         while (true) {
-            if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status)) break;
+            if (!warp_all(mbar_wait(&tq_full[qslot], qphase, abort_flag, status, spin))) break;
             const int t = ((volatile int*)tile_q)[qslot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&tq_empty[qslot]);
@@ -398,7 +405,7 @@ k_contract_batch(const __grid_constant__ CUtensorMap tF_hi, const __grid_constan
             bool ok = true;
             for (int c0 = 0; c0 < sp.nsteps;) {
                 const int c1 = sp.chunk_end(c0);
-                if (!mbar_wait(main_full, mphase, abort_flag, status)) { ok = false; break; }
+                if (!warp_all(mbar_wait(main_full, mphase, abort_flag, status, spin))) { ok = false; break; }
                 mphase ^= 1;
                 tc_fence_after();
                 const bool last = c1 == sp.nsteps;
@@ -773,12 +780,8 @@ int launch_contract(const dsbt_batch* b, int order, int ci, int dir, int mode, f
         return DSBT_ERR_INVALID;
     }
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    static bool attr = false;
-    if (!attr) {
-        DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        attr = true;
-    }
+    // set before every launch: the limit belongs to the current device
+    DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, nsm = 0;
     DSBT_CUDA_TRY(cudaGetDevice(&dev));
     DSBT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -789,7 +792,8 @@ int launch_contract(const dsbt_batch* b, int order, int ci, int dir, int mode, f
     ProfScope ps(kKContractTF32, st);
     k_contract_batch<<<grid, NTHREADS, smem, st>>>(s->tm_T_hi, s->tm_T_lo, b->tF96_hi, b->tF96_lo, s->tm_Tt_hi,
                                                    s->tm_Tt_lo, ts.d[d], total, b->groups_d, b->trans_d, b->tmaps_d,
-                                                   b->cmaps_d, b->Nmax, dir, mode, out_user, s->status, b->sched);
+                                                   b->cmaps_d, b->Nmax, dir, mode, out_user, s->status, s->spin_limit,
+                                                   b->sched);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }

@@ -264,7 +264,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                const __grid_constant__ CUtensorMap tmB1_hi, const __grid_constant__ CUtensorMap tmB1_lo,
                const __grid_constant__ CUtensorMap tmA2_hi, const __grid_constant__ CUtensorMap tmA2_lo,
                const __grid_constant__ CUtensorMap tmB2_hi, const __grid_constant__ CUtensorMap tmB2_lo,
-               GroupTable gt, FtcSpace fs, int N, EpiArgs ep, unsigned* status, int* sched) {
+               GroupTable gt, FtcSpace fs, int N, EpiArgs ep, unsigned* status, uint32_t spin, int* sched) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage_base = smem;
@@ -274,7 +274,8 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
     uint64_t* acc_empty = acc_full + 2;     // [2]: buffer b drained by the epilogue
     uint64_t* tq_full = acc_empty + 2;
     uint64_t* tq_empty = tq_full + QS;
-    int* tile_q = (int*)(tq_empty + QS);
+    uint64_t* drain_bar = tq_empty + QS;    // the MMA issuer's exit drain
+    int* tile_q = (int*)(drain_bar + 1);
     uint32_t* tmem_slot = (uint32_t*)(tile_q + QS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -294,6 +295,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             mbar_init(&tq_full[q], 1);
             mbar_init(&tq_empty[q], 1 + EPI_WARPS);
         }
+        mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -312,12 +314,13 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
+            StageLedger led;
             const uint64_t pol_b = policy_evict_last();
             int qslot = 0;
             uint32_t qphase = 0;
             const uint32_t a_bytes = (aug ? 64u : 128u) * BK * 4u;
             while (ok) {
-                if (!mbar_wait(&tq_empty[qslot], qphase ^ 1, abort_flag, status)) { ok = false; break; }
+                if (!mbar_wait(&tq_empty[qslot], qphase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                 int t = atomicAdd(sched, 1);
                 if (t >= fs.total) t = -1;
                 tile_q[qslot] = t;
@@ -346,9 +349,10 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 for (int i = 0; i < nkb; ++i) {
                     int src, kb;
                     sg.at(i, src, kb);
-                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                     unsigned char* sb = stage_base + stage * STAGE_BYTES;
                     mbar_expect_tx(&full[stage], bytes);
+                    led.arm(stage, phase);
                     const CUtensorMap* ah = src == 1 ? &tmA1_hi : &tmA2_hi;
                     const CUtensorMap* al = src == 1 ? &tmA1_lo : &tmA2_lo;
                     const CUtensorMap* bh = src == 1 ? &tmB1_hi : &tmB2_hi;
@@ -374,6 +378,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
             }
+            led.drain(full, STAGES, status);   // copies still in flight after an abort
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
@@ -385,7 +390,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             int qslot = 0;
             uint32_t qphase = 0;
             while (ok) {
-                if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status)) break;
+                if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status, spin)) break;
                 const int t = ((volatile int*)tile_q)[qslot];
                 mbar_arrive(&tq_empty[qslot]);
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
@@ -399,12 +404,12 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                     const int buf = gch & 1;
                     // the epilogue drained this buffer's previous chunk; the other
                     // buffer may still be draining while these MMAs run
-                    if (!mbar_wait(&acc_empty[buf], ((gch >> 1) & 1) ^ 1, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(&acc_empty[buf], ((gch >> 1) & 1) ^ 1, abort_flag, status, spin)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d = tmem_base + (uint32_t)buf * 256;
                     uint32_t accf = 0;
                     for (int i = c0; i < c1; ++i) {
-                        if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                        if (!mbar_wait(&full[stage], phase, abort_flag, status, spin)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
                         const uint32_t sa_lo = sa + A_BYTES;
@@ -428,6 +433,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                     ++gch;
                 }
             }
+            mma_drain(drain_bar, status);   // every MMA issued has finished
         }
         __syncwarp();
     } else {
@@ -439,7 +445,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
         int qslot = 0;
         uint32_t qphase = 0;
         while (true) {
-            if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status)) break;
+            if (!warp_all(mbar_wait(&tq_full[qslot], qphase, abort_flag, status, spin))) break;
             const int t = ((volatile int*)tile_q)[qslot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&tq_empty[qslot]);
@@ -467,7 +473,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             bool ok = true;
             for (int c0 = 0; c0 < nkb; c0 += fs.kc) {
                 const int buf = gch & 1;
-                if (!mbar_wait(&acc_full[buf], (gch >> 1) & 1, abort_flag, status)) { ok = false; break; }
+                if (!warp_all(mbar_wait(&acc_full[buf], (gch >> 1) & 1, abort_flag, status, spin))) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) {
@@ -842,11 +848,8 @@ int launch_ftc(const dsbt_plan* p, const GroupTable& g, int mode, const CUtensor
     fs.total = fs.t0[g.ngroups];
     if (fs.total == 0) return DSBT_OK;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    static bool attr_done = false;
-    if (!attr_done) {
-        DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_ftc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_done = true;
-    }
+    // set before every launch: the limit belongs to the current device
+    DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_ftc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, nsm = 0;
     DSBT_CUDA_TRY(cudaGetDevice(&dev));
     DSBT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -854,7 +857,7 @@ int launch_ftc(const dsbt_plan* p, const GroupTable& g, int mode, const CUtensor
     DSBT_CUDA_TRY(cudaMemsetAsync(sched, 0, sizeof(int), st));
     ProfScope ps(kKContractTF32, st);
     k_contract_ftc<<<grid, NTHREADS, smem, st>>>(a1h, a1l, b1h, b1l, a2h, a2l, b2h, b2l, g, fs, p->N, ep, p->status,
-                                                 sched);
+                                                 p->spin_limit, sched);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                   const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
                   GroupTable gt, TileSpace ts, int N, int dir, EpiArgs ep, unsigned* status,
-                  int* sched) {
+                  uint32_t spin, int* sched) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage_base = smem;
@@ -145,7 +145,8 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
     uint64_t* main_empty = main_full + 1;
     uint64_t* tq_full = main_empty + 1;
     uint64_t* tq_empty = tq_full + QS;
-    int* tile_q = (int*)(tq_empty + QS);
+    uint64_t* drain_bar = tq_empty + QS;    // the MMA issuer's exit drain
+    int* tile_q = (int*)(drain_bar + 1);
     uint32_t* tmem_slot = (uint32_t*)(tile_q + QS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -162,6 +163,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
             mbar_init(&tq_full[q], 1);
             mbar_init(&tq_empty[q], 1 + EPI_WARPS);
         }
+        mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -180,6 +182,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
+            StageLedger led;
 #if DSBT_B_EVICT_LAST
             const uint64_t pol_b = policy_evict_last();
 #endif
@@ -189,7 +192,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
                 // dynamic tile scheduler: the next tile of the ordered list goes to
                 // whichever CTA asks first, so the tiles in flight always form one
                 // contiguous window of the list (at most two groups' B lines live in L2)
-                if (!mbar_wait(&tq_empty[qslot], qphase ^ 1, abort_flag, status)) { ok = false; break; }
+                if (!mbar_wait(&tq_empty[qslot], qphase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                 int t = atomicAdd(sched, 1);
                 if (t >= ts.total) t = -1;
                 tile_q[qslot] = t;
@@ -206,9 +209,10 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
                 const int nkb = kr.count();
                 for (int i = 0; i < nkb; ++i) {
                     const int kb = kr.at(i);
-                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                     unsigned char* sb = stage_base + stage * STAGE_BYTES;
                     mbar_expect_tx(&full[stage], bytes);
+                    led.arm(stage, phase);
                     tma_load_2d(sb, &tmA_hi, &full[stage], kb * BK, arow);
                     tma_load_2d(sb + A_BYTES, &tmA_lo, &full[stage], kb * BK, arow);
                     for (int b = 0; b < nbox; ++b) {
@@ -227,6 +231,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
             }
+            led.drain(full, STAGES, status);   // copies still in flight after an abort
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
@@ -239,7 +244,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
             int qslot = 0;
             uint32_t qphase = 0;
             while (ok) {
-                if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status)) break;
+                if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status, spin)) break;
                 const int t = ((volatile int*)tile_q)[qslot];
                 mbar_arrive(&tq_empty[qslot]);
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
@@ -259,7 +264,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
                     // reading the previous tile's correction sum, so nothing goes early.
                     const bool pre = c0 > 0;
                     if (pre) {
-                        if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                        if (!mbar_wait(&full[stage], phase, abort_flag, status, spin)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
                         const uint32_t sb_hi = sa + 2 * A_BYTES;
@@ -274,14 +279,14 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
                     }
                     // the epilogue must have drained the previous chunk (and, at a
                     // tile start, read the previous tile's correction sum)
-                    if (!mbar_wait(main_empty, mphase ^ 1, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(main_empty, mphase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                     mphase ^= 1;
                     tc_fence_after();
                     uint32_t acc_main = 0;
                     for (int i = c0; i < c1; ++i) {
                         const bool early = pre && i == c0;   // correction products already issued
                         if (!early) {
-                            if (!mbar_wait(&full[stage], phase, abort_flag, status)) { ok = false; break; }
+                            if (!mbar_wait(&full[stage], phase, abort_flag, status, spin)) { ok = false; break; }
                             tc_fence_after();
                         }
                         const uint32_t sa = smem_u32(stage_base + stage * STAGE_BYTES);
@@ -308,6 +313,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
                     mma_commit(main_full);
                 }
             }
+            mma_drain(drain_bar, status);   // every MMA issued has finished
         }
         __syncwarp();
     } else {
@@ -319,7 +325,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
         int qslot = 0;
         uint32_t qphase = 0;
         while (true) {
-            if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status)) break;
+            if (!warp_all(mbar_wait(&tq_full[qslot], qphase, abort_flag, status, spin))) break;
             const int t = ((volatile int*)tile_q)[qslot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&tq_empty[qslot]);
@@ -340,7 +346,7 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
             for (int j = 0; j < 128; ++j) acc[j] = 0.f;
             bool ok = true;
             for (int c0 = 0; c0 < nkb; c0 += KC) {
-                if (!mbar_wait(main_full, mphase, abort_flag, status)) { ok = false; break; }
+                if (!warp_all(mbar_wait(main_full, mphase, abort_flag, status, spin))) { ok = false; break; }
                 mphase ^= 1;
                 tc_fence_after();
                 const bool last = c0 + KC >= nkb;
@@ -411,6 +417,8 @@ k_contract_tf32x3(const __grid_constant__ CUtensorMap tmA_hi, const __grid_const
 
 }  // namespace
 
+unsigned tc_default_spin_limit() { return tc::kSpinLimit; }
+
 int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi,
                     const float* in_lo, int out_mode, float* out0, float* out1, const float2* phase,
                     int* sched, cudaStream_t st, float* fast_scratch) {
@@ -456,12 +464,8 @@ int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const floa
     if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&tb_lo, in_lo, (uint64_t)g.total_lines, N, BBOX, BK);
     if (rc != DSBT_OK) return rc;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    static bool attr_done = false;
-    if (!attr_done) {
-        DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        attr_done = true;
-    }
+    // set before every launch: the limit belongs to the current device
+    DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, nsm = 0;
     DSBT_CUDA_TRY(cudaGetDevice(&dev));
     DSBT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -472,7 +476,7 @@ int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const floa
     DSBT_CUDA_TRY(cudaMemsetAsync(sched, 0, sizeof(int), st));
     ProfScope ps(kKContractTF32, st);
     k_contract_tf32x3<<<grid, NTHREADS, smem, st>>>(ahi, alo, tb_hi, tb_lo, g, ts, N, dir, ep, p->status,
-                                                    sched);
+                                                    p->spin_limit, sched);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }

@@ -10,11 +10,11 @@
 // file-scope device array of fixed size instead of a caller workspace.
 //
 // The array is reserved on every GPU that loads this library, for the life of
-// the process.  Host code cannot use its name as a device address, so the
-// first call on each device looks the address up with cudaGetSymbolAddress
-// (with that device current) and caches it.
-#include <mutex>
-
+// the process.  Host code cannot use its name as a device address, so every
+// call looks the address up with cudaGetSymbolAddress, with the plan's device
+// current.  The lookup allocates nothing and is cheap; doing it per call (no
+// cache) keeps the address right after a cudaDeviceReset, which reloads the
+// module at a new address.
 #include "plan.cuh"
 
 namespace dsbt {
@@ -25,21 +25,14 @@ int forward_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtyp
 namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)64 << 20;   // 64 MiB per device
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices];
-
-int static_scratch(int dev, void** out) {
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* ptr = nullptr;
-        DSBT_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_static_scratch));
-        g_scratch_addr[dev] = ptr;
-    }
-    *out = g_scratch_addr[dev];
+// Device address of the array on the current device.
+int static_scratch(void** out) {
+    void* ptr = nullptr;
+    DSBT_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_static_scratch));
+    *out = ptr;
     return DSBT_OK;
 }
 
@@ -65,10 +58,9 @@ extern "C" int dsbt_forward_grouped_noalloc(const dsbt_plan* plan, const int* co
                    need, kStaticScratchBytes);
     int dev = 0;
     DSBT_CUDA_TRY(cudaGetDevice(&dev));
-    DSBT_CHECK_ARG(dev >= 0 && dev < kMaxDevices, "device %d out of range", dev);
     DSBT_CHECK_ARG(dev == plan->device, "current device %d is not the plan's device %d", dev, plan->device);
     void* scratch = nullptr;
-    int rc = static_scratch(dev, &scratch);
+    int rc = static_scratch(&scratch);
     if (rc) return rc;
     return forward_grouped_with_scratch(plan, counts, dtype, in, out, scratch, kStaticScratchBytes,
                                         (cudaStream_t)stream);

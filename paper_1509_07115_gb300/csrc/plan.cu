@@ -213,25 +213,11 @@ int build_first_rows(double* dst, int N, int lmax, int R, cudaStream_t st) {
     return DSBT_OK;
 }
 
-int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
+// Orthogonality probe of the FP64 factors (Eq. (25), T^{-1} = T^T): two
+// pseudo-random vectors x per l, max |T^T (T x) - x| into p->check_err;
+// DSBT_ERR_PLAN_CHECK above 1e-12.
+int plan_probe(dsbt_plan* p, cudaStream_t st) {
     const int N = p->N, L = p->l_max + 1;
-    const size_t bytes64 = (size_t)L * p->nn * sizeof(double);
-    DSBT_CUDA_TRY(cudaMemsetAsync(p->T64, 0, bytes64, st));
-    {
-        const long long threads = (long long)L * N;
-        const int bs = 128;
-        ProfScope ps(kKPlan, st);
-        k_build_rows<<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(p->T64, N, p->l_max, N);
-        DSBT_CUDA_TRY(cudaGetLastError());
-    }
-    {
-        const int nthreads = 256;
-        ProfScope ps(kKPlan, st);
-        k_twiddles<<<(N + nthreads - 1) / nthreads, nthreads, 0, st>>>(p->tw64, p->post64, p->tw32,
-                                                                       p->post32, N);
-        DSBT_CUDA_TRY(cudaGetLastError());
-    }
-    // orthogonality probe: two random vectors per l
     double* y = nullptr;
     unsigned long long* err = nullptr;
     DSBT_CUDA_TRY(cudaMallocAsync((void**)&y, (size_t)L * N * sizeof(double), st));
@@ -257,6 +243,29 @@ int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
         set_error("plan check failed: max |T^T T x - x| = %.3e", e);
         return DSBT_ERR_PLAN_CHECK;
     }
+    return DSBT_OK;
+}
+
+int plan_build_factors(dsbt_plan* p, cudaStream_t st) {
+    const int N = p->N, L = p->l_max + 1;
+    const size_t bytes64 = (size_t)L * p->nn * sizeof(double);
+    DSBT_CUDA_TRY(cudaMemsetAsync(p->T64, 0, bytes64, st));
+    {
+        const long long threads = (long long)L * N;
+        const int bs = 128;
+        ProfScope ps(kKPlan, st);
+        k_build_rows<<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(p->T64, N, p->l_max, N);
+        DSBT_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        const int nthreads = 256;
+        ProfScope ps(kKPlan, st);
+        k_twiddles<<<(N + nthreads - 1) / nthreads, nthreads, 0, st>>>(p->tw64, p->post64, p->tw32,
+                                                                       p->post32, N);
+        DSBT_CUDA_TRY(cudaGetLastError());
+    }
+    int rc = plan_probe(p, st);
+    if (rc) return rc;
     if (p->flags & DSBT_PLAN_FP64) {
         dim3 grid(N / 32, N / 32, L), block(32, 8);
         ProfScope ps(kKPlan, st);
@@ -282,6 +291,7 @@ int plan_twiddles_only(int N, double r_max, cudaStream_t st, dsbt_plan** out) {
     p->r_max = r_max;
     p->dk = M_PI / r_max;
     p->nn = (size_t)N * N;
+    p->spin_limit = tc_default_spin_limit();
     cudaGetDevice(&p->device);
     bool ok = cudaMalloc((void**)&p->tw64, N * sizeof(double2)) == cudaSuccess &&
               cudaMalloc((void**)&p->post64, N * sizeof(double2)) == cudaSuccess &&
@@ -357,6 +367,7 @@ extern "C" int dsbt_plan_create(int N, double r_max, int l_max, int flags, void*
     p->r_max = r_max;
     p->dk = M_PI / r_max;
     p->nn = (size_t)N * N;
+    p->spin_limit = tc_default_spin_limit();
     cudaGetDevice(&p->device);
     const size_t L = (size_t)l_max + 1;
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
@@ -450,5 +461,40 @@ extern "C" int dsbt_plan_get_T(const dsbt_plan* plan, int l, double* dst, void* 
     }
     DSBT_CUDA_TRY(cudaMemcpyAsync(dst, plan->T64 + (size_t)l * plan->nn, plan->nn * sizeof(double),
                                   cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return DSBT_OK;
+}
+
+extern "C" int dsbt_plan_check(dsbt_plan* plan, double* err_out, void* stream) {
+    DSBT_CHECK_ARG(plan != nullptr, "dsbt_plan_check: plan is NULL");
+    if (!plan->T64) {
+        set_error("dsbt_plan_check: plan was built without DSBT_PLAN_FP64");
+        return DSBT_ERR_UNSUPPORTED;
+    }
+    const int rc = plan_probe(plan, (cudaStream_t)stream);
+    if (err_out) *err_out = plan->check_err;
+    return rc;
+}
+
+extern "C" int dsbt_plan_set_spin_limit(dsbt_plan* plan, unsigned polls) {
+    DSBT_CHECK_ARG(plan != nullptr, "dsbt_plan_set_spin_limit: plan is NULL");
+    plan->spin_limit = polls ? polls : tc_default_spin_limit();
+    return DSBT_OK;
+}
+
+extern "C" int dsbt_plan_perturb_T(dsbt_plan* plan, int l, int row, int col, double delta, void* stream) {
+    DSBT_CHECK_ARG(plan != nullptr, "dsbt_plan_perturb_T: plan is NULL");
+    DSBT_CHECK_ARG(l >= 0 && l <= plan->l_max && row >= 0 && row < plan->N && col >= 0 && col < plan->N,
+                   "dsbt_plan_perturb_T: index out of range");
+    if (!plan->T64) {
+        set_error("dsbt_plan_perturb_T: plan was built without DSBT_PLAN_FP64");
+        return DSBT_ERR_UNSUPPORTED;
+    }
+    double* e = plan->T64 + (size_t)l * plan->nn + (size_t)row * plan->N + col;
+    double v = 0.0;
+    DSBT_CUDA_TRY(cudaMemcpyAsync(&v, e, sizeof(v), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    DSBT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    v += delta;
+    DSBT_CUDA_TRY(cudaMemcpyAsync(e, &v, sizeof(v), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    DSBT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     return DSBT_OK;
 }

@@ -43,6 +43,7 @@ struct dsbt_plan {
     // interval bases and projections of DSBT_PLAN_FAST_TF32 (fast_tf32.cu), else nullptr
     dsbt::FtcData* ftc;
     unsigned* status;          // device status word (kStatusOk / kStatusTimeout)
+    unsigned spin_limit;       // polls of a bounded mbarrier wait in the tensor-core kernels
     double check_err;
     bool has_tmaps;
     CUtensorMap tm_T_hi, tm_T_lo, tm_Tt_hi, tm_Tt_lo;
@@ -75,6 +76,9 @@ int profile_set_enabled(int on);
 
 // ---- plan build (plan.cu)
 int plan_build_factors(dsbt_plan* p, cudaStream_t st);
+int plan_probe(dsbt_plan* p, cudaStream_t st);
+// Default polls of a bounded mbarrier wait (tc_ptx.cuh kSpinLimit).
+unsigned tc_default_spin_limit();
 int build_first_rows(double* dst, int N, int lmax, int R, cudaStream_t st);
 int plan_twiddles_only(int N, double r_max, cudaStream_t st, dsbt_plan** out);
 void plan_release(dsbt_plan* p);

@@ -10,7 +10,11 @@
 namespace dsbt {
 namespace tc {
 
+// Default iteration limit of a bounded mbarrier wait (a plan may set another,
+// see dsbt_plan_set_spin_limit), and the fixed limit of the waits that let an
+// aborting CTA's own copies and MMAs finish before it frees TMEM and exits.
 constexpr uint32_t kSpinLimit = 1u << 25;
+constexpr uint32_t kDrainLimit = 1u << 25;
 
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -43,10 +47,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; false on timeout or when another role aborted.
+// Bounded wait of at most `spin` polls; false on timeout (which raises the
+// CTA's abort flag and records kStatusTimeout) or when another role aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          unsigned* status) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+                                          unsigned* status, uint32_t spin) {
+    for (uint32_t it = 0; it < spin; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
     }
@@ -54,6 +59,39 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     atomicExch(status, (unsigned)kStatusTimeout);
     return false;
 }
+
+// Warp-uniform verdict of a wait that every lane of a warp ran: lanes may see
+// the barrier complete at different polls, or one may time out while another
+// succeeds; the warp then goes on only if all lanes succeeded, so the
+// .sync.aligned TMEM loads that follow never run divergent.
+__device__ __forceinline__ bool warp_all(bool ok) { return __all_sync(0xffffffffu, ok); }
+
+// Wait that ignores the abort flag, for the drain at a CTA's exit: TMA copies
+// and MMAs already issued complete on their own, so this wait ends unless the
+// hardware misbehaves; after kDrainLimit polls it records kStatusTimeout and
+// gives up anyway.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, unsigned* status) {
+    for (uint32_t it = 0; it < kDrainLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return;
+    atomicExch(status, (unsigned)kStatusTimeout);
+}
+
+// The producer's record of the stages it armed (expect_tx + TMA loads) and the
+// phase each arming completes, so that the copies still in flight when a CTA
+// leaves its loops early can be waited out before the CTA exits.
+struct StageLedger {
+    uint32_t armed = 0, par = 0;
+    __device__ __forceinline__ void arm(int stage, uint32_t phase) {
+        armed |= 1u << stage;
+        par = (par & ~(1u << stage)) | (phase << stage);
+    }
+    // Every armed stage's last copy has landed (immediate on a normal exit:
+    // the MMA issuer waited for each of them already).
+    __device__ __forceinline__ void drain(uint64_t* full, int stages, unsigned* status) const {
+        for (int s = 0; s < stages; ++s)
+            if ((armed >> s) & 1u) mbar_drain(&full[s], (par >> s) & 1u, status);
+    }
+};
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
                                             int y) {
@@ -117,6 +155,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
+}
+
+// At the MMA issuer's exit: one more commit tracks every tcgen05 operation this
+// thread issued; waiting for it means no MMA still reads shared memory or
+// writes TMEM when the CTA frees TMEM and exits.  `bar` is a barrier of count 1
+// used only here.
+__device__ __forceinline__ void mma_drain(uint64_t* bar, unsigned* status) {
+    mma_commit(bar);
+    mbar_drain(bar, 0, status);
 }
 
 // 32 lanes x 32 consecutive FP32 columns from TMEM.

@@ -64,6 +64,9 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
             getattr(lib, name).argtypes = [vp, _c_int_p, i, vp, vp, i, vp, sz, vp]
         lib.dsbt_kinetic_grouped_host.argtypes = [vp, _c_int_p, i, d, vp, vp, i, vp, sz, vp]
         lib.dsbt_device_status.argtypes = [vp, i, _c_int_p]
+        lib.dsbt_plan_check.argtypes = [vp, ctypes.POINTER(d), vp]
+        lib.dsbt_plan_set_spin_limit.argtypes = [vp, ctypes.c_uint]
+        lib.dsbt_plan_perturb_T.argtypes = [vp, i, i, i, d, vp]
         lib.dsbt_last_error.restype = ctypes.c_char_p
         lib.dsbt_launch_count.restype = ctypes.c_longlong
         lib.dsbt_profile_enable.argtypes = [i]
@@ -302,6 +305,22 @@ class Plan:
                                          lev.ctypes.data_as(ctypes.c_void_p), en.ctypes.data_as(ctypes.c_void_p),
                                          _ptr(ws), ws.numel(), _stream()), "dsbt_radial_states")
         return lev, en
+
+    def check(self) -> float:
+        """Re-run the orthogonality probe on the FP64 factors; raises
+        DSBTError (code -3) when max |T^T T x - x| exceeds 1e-12."""
+        err = ctypes.c_double()
+        _check(load().dsbt_plan_check(self._h, ctypes.byref(err), _stream()), "dsbt_plan_check")
+        return err.value
+
+    def set_spin_limit(self, polls: int):
+        """Testing hook: polls of each bounded device-side wait (0 = default)."""
+        _check(load().dsbt_plan_set_spin_limit(self._h, int(polls)), "dsbt_plan_set_spin_limit")
+
+    def perturb_T(self, l: int, row: int, col: int, delta: float):
+        """Testing hook: add delta to one entry of the FP64 T_l."""
+        _check(load().dsbt_plan_perturb_T(self._h, int(l), int(row), int(col), float(delta), _stream()),
+               "dsbt_plan_perturb_T")
 
     def device_status(self, reset: bool = True) -> int:
         s = ctypes.c_int()

@@ -128,3 +128,13 @@ def grouped_workload(seed: int, ntransforms: int = 64):
     Ns = 256 * rng.integers(2, 33, size=ntransforms)
     lmaxs = rng.integers(8, 65, size=ntransforms)
     return [(int(n), int(l)) for n, l in zip(Ns, lmaxs)]
+
+
+def sparse_coefficient_values(seed: int, nchan: int, nrows: int) -> np.ndarray:
+    """Values [nchan][nrows] ~ CN(0, 1), each channel scaled to unit 2-norm:
+    the nonzero entries of coefficient vectors that vanish outside nrows chosen
+    storage indices.  Such vectors are inputs of the inverse transform whose
+    exact result needs only those rows of T_l (full-size checks)."""
+    rng = np.random.default_rng(seed)
+    v = (rng.standard_normal((nchan, nrows)) + 1j * rng.standard_normal((nchan, nrows))) / math.sqrt(2)
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
