@@ -608,6 +608,8 @@ def main():
     ap.add_argument("--no-tdse", action="store_true", help="skip the TDSE propagation/adjoint leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch leg")
     ap.add_argument("--e2e-chunks", type=int, default=8, help="chunks of the host-streamed e2e call")
+    ap.add_argument("--no-probe", action="store_true",
+                    help="skip the matmul / copy probes (profiler runs); fractions then use nominal ratios")
     ap.add_argument("--dense", action="store_true",
                     help="time the dense split-TF32 contraction instead of the interval scheme")
     ap.add_argument("--workload", default="precision", choices=sorted(WORKLOADS),
@@ -640,7 +642,7 @@ def main():
             dist.barrier()
 
     fast = not args.dense
-    plan = dsbt.Plan(N, R_MAX, L_MAX, fp64=not args.no_fp64, tf32x3=True, fast_tf32=fast)
+    plan = dsbt.Plan(N, R_MAX, L_MAX, fp64=not args.no_fp64, tf32x3=not fast, fast_split=fast)
     x = inputs.gaussian_sum(rank_seed(rank), N, DR, counts, dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
     ws = plan.workspace(nchan, torch.complex64)
@@ -708,7 +710,12 @@ def main():
 
     # ---------------------------------------------------------- measured peaks (after the timed region)
     peaks, src = load_peaks()
-    probes = probe_peaks(torch, dev)
+    if args.no_probe:   # nominal ratios to the measured BF16 rate; no copy figures
+        bf = peaks["bf16_tflops"]
+        probes = {"fp64_tflops": bf * 1.25 / 2250, "tf32_tflops": bf * 1.1 / 2.25, "fp16_tflops": bf,
+                  "h2d_gbs": None, "d2h_gbs": None, "how": "not probed: nominal ratios to bf16_tflops"}
+    else:
+        probes = probe_peaks(torch, dev)
     hbm = peaks["hbm_gbs"]
 
     # ---------------------------------------------------------- roofline of the contraction
@@ -734,7 +741,9 @@ def main():
         kname, tname = "contract_tf32x3", "contract_tf32x3_precision_form.json"
     flop_per_launch = flop_per_step / launches_per_step
     tflops = flop_per_launch / (avg_ms * 1e-3) / 1e12
-    tpeak = probes["tf32_tflops"]
+    # the interval scheme multiplies FP16 pairs, the dense kernel TF32 pairs
+    tpeak = probes["fp16_tflops"] if fast else probes["tf32_tflops"]
+    tpeak_src = "measured fp16 matmul (burst, this run)" if fast else "measured tf32 matmul (burst, this run)"
     traffic = ncu_traffic(tname) if args.workload == "precision" else None
     step_ms = ms / args.steps
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -749,7 +758,7 @@ def main():
                                "ms": step_ms},
                 "tensor": {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
                            "flop_per_launch": flop_per_launch,
-                           "peak_source": "measured tf32 matmul (burst, this run)",
+                           "peak_source": tpeak_src,
                            "dense_equivalent_tflops": 2 * FLOP_PER_CHANNEL * nchan / (k_ms / args.steps * 1e-3) / 1e12},
                 "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
 
@@ -757,7 +766,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (split-tf32 contraction, fp32 accumulate)",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (split-fp16 interval-scheme contraction, fp32 accumulate)" if fast else "f32 (split-tf32 contraction, fp32 accumulate)",
                 "data": "synthetic (seeded Gaussian-sum radial functions r sum_j c_j r^l exp(-a_j r^2))",
                 "config": {"workload": WORKLOAD, "N": N, "r_max": R_MAX, "l_max": L_MAX, "batch": BATCH,
                            "channels_per_gpu": nchan, "tau": TAU,
@@ -768,10 +777,11 @@ def main():
                 "gpu_launches": launches, "roofline": roofline, "clocks": clocks,
                 "measured_peaks": dict(probes, hbm_gbs=hbm, bf16_tflops=peaks.get("bf16_tflops"),
                                        bf16_tflops_sustained=peaks.get("bf16_tflops_sustained"))}
-        line["e2e"]["copy_bound"] = {
-            "h2d_gbs_achieved": nbytes / (1e-3 * job_ms_e2e / e2e_steps) / 1e9,
-            "h2d_gbs_pinned_peak": probes["h2d_gbs"], "d2h_gbs_pinned_peak": probes["d2h_gbs"],
-            "note": "each step copies the batch in and out; copies run both ways at once, overlapped with compute"}
+        if probes["h2d_gbs"]:
+            line["e2e"]["copy_bound"] = {
+                "h2d_gbs_achieved": nbytes / (1e-3 * job_ms_e2e / e2e_steps) / 1e9,
+                "h2d_gbs_pinned_peak": probes["h2d_gbs"], "d2h_gbs_pinned_peak": probes["d2h_gbs"],
+                "note": "each step copies the batch in and out; copies run both ways at once, overlapped with compute"}
 
     # ---------------------------------------------------------- FP64 GPU path (sample) + error
     if not args.no_fp64:
@@ -809,7 +819,7 @@ def main():
 
     # ---------------------------------------------------------- dense split-TF32 contraction (context)
     if rank == 0 and fast and args.workload == "precision":
-        line["dense_tf32"] = dense_leg(dsbt, torch, counts, x, tpeak, args)
+        line["dense_tf32"] = dense_leg(dsbt, torch, counts, x, probes["tf32_tflops"], args)
 
     # ---------------------------------------------------------- TDSE (propagator + adjoint)
     if rank == 0 and not args.no_tdse and args.workload == "precision":
@@ -819,7 +829,7 @@ def main():
     if rank == 0 and not args.no_batch and args.workload == "precision":
         plan.close()
         torch.cuda.empty_cache()
-        line["uneven_batch"] = batch_leg(dsbt, inputs, torch, dev, max(3, args.steps // 3), 2, tpeak)
+        line["uneven_batch"] = batch_leg(dsbt, inputs, torch, dev, max(3, args.steps // 3), 2, probes["tf32_tflops"])
 
     # ---------------------------------------------------------- CPU oracle baseline
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -26,8 +26,14 @@
  *   - DSBT_F64 / DSBT_C128: everything in FP64 (sine/cosine transform by an
  *     FP64 FFT, T_l contraction by FP64 FMA).
  *   - DSBT_F32 / DSBT_C64: FP32 FFT, T_l contraction on the tcgen05 tensor
- *     cores as compensated split-TF32 (T = T_hi + T_lo, x = x_hi + x_lo,
- *     T x ~ T_hi x_hi + T_hi x_lo + T_lo x_hi, FP32 accumulation in TMEM).
+ *     cores as a compensated split product (T = T_hi + T_lo, x = x_hi + x_lo,
+ *     T x ~ T_hi x_hi + T_hi x_lo + T_lo x_hi, FP32 accumulation in TMEM):
+ *     TF32 pairs for the dense factors (DSBT_PLAN_TF32X3); FP16 pairs (same
+ *     11 significant bits, twice the tensor rate, half the bytes) for the
+ *     interval scheme (DSBT_PLAN_FAST_SPLIT), with T_l scaled by 2^14 and each
+ *     channel by a power of two 2^e, ||2^e psi|| in [2^12, 2^13), so that no
+ *     intermediate leaves the FP16 range; scales are exact and removed before
+ *     any FP32 output.
  *
  * Errors: every entry point returns an int status (DSBT_OK = 0, negative on
  * failure) and never throws; dsbt_last_error() returns a thread-local message
@@ -75,16 +81,21 @@ extern "C" {
                               Extra memory: 8 B x 64 x (l_max+1) x N x log2(N/64)
                               of plan data; FP64 workspaces grow by about
                               8 B x 128 x (N/64) per line. */
-#define DSBT_PLAN_FAST_TF32 16 /* with DSBT_PLAN_TF32X3, N / 128 a power of two:
-                              split-TF32 contractions (all DSBT_F32 / DSBT_C64
-                              calls) through the same interval scheme on the tensor
-                              cores: near band of T_l per 128-row leaf, far field
-                              through 64 basis functions per used dyadic interval.
-                              Needs l_max <= 64 (always true).  Extra memory:
-                              about 16 B x 64 x (l_max+1) x N x (N/128 - 1) of plan
-                              data (8.4 GB at N = 4096, l_max = 63) and
-                              8 B x 64 x (N/128 - 1 + log2(N/128)) per line of
+#define DSBT_PLAN_FAST_SPLIT 16 /* N / 128 a power of two: split-precision
+                              contractions (all DSBT_F32 / DSBT_C64 calls) in
+                              O(N l log N) work on the tensor cores: near band of
+                              T_l per 128-row leaf (diagonal blocks), far field
+                              through 64 basis functions per used dyadic interval
+                              (the rows of T_l are polynomials of degree l - 1 in m
+                              left of the diagonal, Eqs. (38)-(42)), operands as
+                              FP16 pairs.  Needs l_max <= 64 (always true); with
+                              or without DSBT_PLAN_TF32X3 (whose dense copies it
+                              does not use).  Extra memory: about
+                              8 B x 64 x (l_max+1) x N x (N/128 - 1) of plan data
+                              (4.2 GB at N = 4096, l_max = 63) and
+                              4 B x 64 x (N/128 - 1 + log2(N/128)) per line of
                               workspace. */
+#define DSBT_PLAN_FAST_TF32 DSBT_PLAN_FAST_SPLIT /* earlier name of the same flag */
 
 /* element types of the caller's arrays */
 #define DSBT_F64 1  /* real double                 */

@@ -780,8 +780,7 @@ int launch_contract(const dsbt_batch* b, int order, int ci, int dir, int mode, f
         return DSBT_ERR_INVALID;
     }
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    // set before every launch: the limit belongs to the current device
-    DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (int rc0 = ensure_smem((const void*)k_contract_batch, smem)) return rc0;
     int dev = 0, nsm = 0;
     DSBT_CUDA_TRY(cudaGetDevice(&dev));
     DSBT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

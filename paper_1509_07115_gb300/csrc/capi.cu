@@ -38,6 +38,44 @@ __global__ void k_split_lines_c(const float2* __restrict__ in, float* __restrict
     lo[o + N] = round_tf32(v.y - hi_);
 }
 
+// FP16 pair of caller data for the interval-scheme contraction: one CTA per
+// channel (N values, or N complex values = two lines) computes ||psi||, picks
+// 2^e with ||2^e psi|| in [2^12, 2^13) and writes hi = fp16(2^e x),
+// lo = fp16(2^e x - hi) to the channel's planar lines and 2^-e to scale[line].
+__global__ void k_split_f16(const float* __restrict__ in, int cplx, int N, __half* __restrict__ hi,
+                            __half* __restrict__ lo, float* __restrict__ scale) {
+    const long long c = blockIdx.x;
+    const int per = cplx ? 2 : 1;
+    const float* x = in + c * (long long)N * per;
+    float part = 0.f;
+    for (int i = threadIdx.x; i < N * per; i += blockDim.x) part += x[i] * x[i];
+    __shared__ float red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    const float nrm = sqrtf(red[0]);
+    const int e = (nrm > 0.f && isfinite(nrm)) ? 12 - ilogbf(nrm) : 0;
+    const float fs = ldexpf(1.f, e);
+    const long long line = c * per;
+    if (threadIdx.x < per) scale[line + threadIdx.x] = ldexpf(1.f, -e);
+    for (int i = threadIdx.x; i < N * per; i += blockDim.x) {
+        const int part_ = cplx ? (i & 1) : 0, n = cplx ? (i >> 1) : i;
+        const float v = x[i] * fs;
+        const __half h = __float2half_rn(v);
+        const size_t o = (size_t)(line + part_) * N + n;
+        hi[o] = h;
+        lo[o] = __float2half_rn(v - __half2float(h));
+    }
+}
+
 // exp(-i k~_n^2 tau / 2) on the unified momentum grid (Eq. (65)): storage index
 // k of parity class par (0: even l, n = k + 1; 1: odd l, n = k) maps to
 // k~ = n dk, except the odd-l coefficient n = 0, which takes k~_N = N dk.
@@ -82,7 +120,15 @@ struct Workspace {
     float* planar;   // aliases hi_a
     float2* ph32;
     int* sched;      // tile-scheduler counter of the tensor-core contraction
-    float* ftc;      // augmented lines of the DSBT_PLAN_FAST_TF32 contraction (or nullptr)
+    // interval-scheme path (plans with DSBT_PLAN_FAST_SPLIT): FP16 pairs of the
+    // lines before (a) and between (b) the contractions, per-line unscale
+    // factors, the augmented lines; planar aliases the a pair
+    __half* h_hi_a;
+    __half* h_lo_a;
+    __half* h_hi_b;
+    __half* h_lo_b;
+    float* scale;
+    void* ftc;
 };
 
 size_t lines_of(int total_channels, int dtype) {
@@ -96,8 +142,10 @@ size_t ws_bytes(const dsbt_plan* p, int total_channels, int dtype) {
     if (is_fp64(dtype))
         return align256(R * N * sizeof(double)) * 2 + align256(PR * sizeof(double2)) +
                align256(fast_scratch_bytes(p, (int)R)) + 256;
-    return align256(R * N * sizeof(float)) * 4 + align256(PR * sizeof(float2)) + 256 +
-           align256(ftc_scratch_bytes(p, R)) + 256;
+    if (p->ftc)   // FP16 pairs a, b (4 B per value each), scale, phase, counter, augmented lines
+        return align256(R * N * 4) * 2 + align256(R * sizeof(float)) + align256(PR * sizeof(float2)) + 256 +
+               align256(ftc_scratch_bytes(p, R)) + 256;
+    return align256(R * N * sizeof(float)) * 4 + align256(PR * sizeof(float2)) + 256 + 256;
 }
 
 Workspace carve(const dsbt_plan* pl, void* base, int total_channels, int dtype) {
@@ -112,6 +160,18 @@ Workspace carve(const dsbt_plan* pl, void* base, int total_channels, int dtype) 
         w.f64b = (double*)(p + b);
         w.ph64 = (double2*)(p + 2 * b);
         w.fast = pl->fast ? (double*)(p + 2 * b + align256(PR * sizeof(double2))) : nullptr;
+    } else if (pl->ftc) {
+        const size_t b = align256(R * N * 4);   // one FP16 pair of every line
+        w.h_hi_a = (__half*)p;
+        w.h_lo_a = w.h_hi_a + R * N;
+        w.planar = (float*)p;                   // FP32 lines after the last contraction
+        w.h_hi_b = (__half*)(p + b);
+        w.h_lo_b = w.h_hi_b + R * N;
+        w.scale = (float*)(p + 2 * b);
+        unsigned char* q = p + 2 * b + align256(R * sizeof(float));
+        w.ph32 = (float2*)q;
+        w.sched = (int*)(q + align256(PR * sizeof(float2)));
+        w.ftc = q + align256(PR * sizeof(float2)) + 256;
     } else {
         const size_t b = align256(R * N * sizeof(float));
         w.hi_a = (float*)p;
@@ -121,7 +181,6 @@ Workspace carve(const dsbt_plan* pl, void* base, int total_channels, int dtype) 
         w.planar = w.hi_a;
         w.ph32 = (float2*)(p + 4 * b);
         w.sched = (int*)(p + 4 * b + align256(PR * sizeof(float2)));
-        w.ftc = pl->ftc ? (float*)(p + 4 * b + align256(PR * sizeof(float2)) + 256) : nullptr;
     }
     return w;
 }
@@ -165,8 +224,8 @@ int check_common(const dsbt_plan* p, int dtype, const void* in, void* out, void*
         set_error("FP64 dtype needs a plan built with DSBT_PLAN_FP64");
         return DSBT_ERR_UNSUPPORTED;
     }
-    if (!is_fp64(dtype) && !p->has_tmaps) {
-        set_error("FP32 dtype needs a plan built with DSBT_PLAN_TF32X3");
+    if (!is_fp64(dtype) && !p->has_tmaps && !p->ftc) {
+        set_error("FP32 dtype needs a plan built with DSBT_PLAN_TF32X3 or DSBT_PLAN_FAST_SPLIT");
         return DSBT_ERR_UNSUPPORTED;
     }
     return DSBT_OK;
@@ -183,10 +242,16 @@ int run_forward(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
         if (rc) return rc;
         return contract_f64(p, g, +1, w.f64a, 0, (double*)out, cplx ? 1 : 0, nullptr, st);
     }
+    if (p->ftc) {   // interval scheme on FP16 pairs
+        rc = dct_forward_f16(p, g, cplx, (const float*)in, w.h_hi_a, w.h_lo_a, w.scale, st);
+        if (rc) return rc;
+        return contract_split_fast(p, g, +1, w.h_hi_a, w.h_lo_a, w.scale, cplx ? kOutUserC64 : kOutUserF32, out,
+                                   nullptr, nullptr, w.sched, w.ftc, st);
+    }
     rc = dct_forward_f32(p, g, cplx, (const float*)in, w.hi_a, w.lo_a, st);
     if (rc) return rc;
     return contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, cplx ? kOutUserC64 : kOutUserF32, (float*)out,
-                           nullptr, nullptr, w.sched, st, w.ftc);
+                           nullptr, nullptr, w.sched, st);
 }
 
 int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* in, void* out,
@@ -200,6 +265,18 @@ int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
         if (rc) return rc;
         return dct_inverse_f64(p, g, cplx, w.f64a, (double*)out, st);
     }
+    if (p->ftc) {   // interval scheme on FP16 pairs
+        {
+            ProfScope ps(kKSplit, st);
+            k_split_f16<<<(unsigned)g.chan0[g.ngroups], 256, 0, st>>>((const float*)in, cplx ? 1 : 0, p->N,
+                                                                       w.h_hi_b, w.h_lo_b, w.scale);
+        }
+        DSBT_CUDA_TRY(cudaGetLastError());
+        rc = contract_split_fast(p, g, -1, w.h_hi_b, w.h_lo_b, w.scale, kOutPlanarF32, w.planar, nullptr, nullptr,
+                                 w.sched, w.ftc, st);
+        if (rc) return rc;
+        return dct_inverse_f32(p, g, cplx, w.planar, (float*)out, st);
+    }
     const long long total = (long long)g.chan0[g.ngroups] * p->N;
     const int bs = 256;
     {
@@ -212,7 +289,7 @@ int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
                                                                         total);
     }
     DSBT_CUDA_TRY(cudaGetLastError());
-    rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, w.sched, st, w.ftc);
+    rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, w.sched, st);
     if (rc) return rc;
     return dct_inverse_f32(p, g, cplx, w.planar, (float*)out, st);
 }
@@ -242,10 +319,20 @@ int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, 
         k_phase<<<(rows * N + 255) / 256, 256, 0, st>>>(nullptr, w.ph32, N, p->dk, tau, p->knl, rows);
     }
     DSBT_CUDA_TRY(cudaGetLastError());
+    if (p->ftc) {   // interval scheme on FP16 pairs; the lines stay scaled until the last contraction
+        rc = dct_forward_f16(p, g, true, (const float*)in, w.h_hi_a, w.h_lo_a, w.scale, st);
+        if (!rc)
+            rc = contract_split_fast(p, g, +1, w.h_hi_a, w.h_lo_a, w.scale, kOutPlanarSplit, w.h_hi_b, w.h_lo_b,
+                                     w.ph32, w.sched, w.ftc, st);
+        if (!rc)
+            rc = contract_split_fast(p, g, -1, w.h_hi_b, w.h_lo_b, w.scale, kOutPlanarF32, w.planar, nullptr,
+                                     nullptr, w.sched, w.ftc, st);
+        if (!rc) rc = dct_inverse_f32(p, g, true, w.planar, (float*)out, st);
+        return rc;
+    }
     rc = dct_forward_f32(p, g, true, (const float*)in, w.hi_a, w.lo_a, st);
-    if (!rc) rc = contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, kOutPlanarSplit, w.hi_b, w.lo_b, w.ph32, w.sched, st, w.ftc);
-    if (!rc) rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, w.sched, st,
-                                  w.ftc);
+    if (!rc) rc = contract_tf32x3(p, g, +1, w.hi_a, w.lo_a, kOutPlanarSplit, w.hi_b, w.lo_b, w.ph32, w.sched, st);
+    if (!rc) rc = contract_tf32x3(p, g, -1, w.hi_b, w.lo_b, kOutPlanarF32, w.planar, nullptr, nullptr, w.sched, st);
     if (!rc) rc = dct_inverse_f32(p, g, true, w.planar, (float*)out, st);
     return rc;
 }

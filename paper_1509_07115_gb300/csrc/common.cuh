@@ -32,6 +32,15 @@ void set_error(const char* fmt, ...);
         }                                                                              \
     } while (0)
 
+// ----------------------------------------------------------------- launch attributes
+
+// Raises the dynamic shared-memory limit of kernel `fn` on the current device
+// to `bytes` the first time it is needed there (profile.cu).  The limit is a
+// per-device attribute of each kernel; setting it before every launch would be
+// correct but can wait for the device, which stalls a host that queues work
+// ahead on several streams.  Thread-safe.
+int ensure_smem(const void* fn, size_t bytes);
+
 // ----------------------------------------------------------------- index helpers
 
 __host__ __device__ inline int parity_p(int l) { return (l & 1) ? 0 : 1; }   // p_l

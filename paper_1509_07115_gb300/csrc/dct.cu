@@ -26,6 +26,8 @@
 // on the V_k it has just formed in registers.  (Loading each thread's first
 // butterfly inputs straight from global memory in the forward transform made
 // it slower: the stride-2 loads cost more than the shared-memory pass.)
+#include <cuda_fp16.h>
+
 #include "plan.cuh"
 
 namespace dsbt {
@@ -299,16 +301,32 @@ template <> __device__ __forceinline__ void st_pair<double2>(double2* p, double2
 // line of up to 512 threads when N/16 > 256).
 __host__ __device__ inline int lines_per_cta(int N) { return (N / 16 >= 256) ? 1 : 256 / (N / 16); }
 
-// Forward transform.  Output: planar lines.  SPLIT: write the TF32 hi/lo pair.
-// FP32 kernels: at most 64 registers, so two CTAs of
+// Output modes of the forward transform (planar lines, storage index n - p_l):
+// kPlain: R values; kSplitTF32: the TF32 pair hi + lo as two FP32 lines;
+// kSplitF16: the channel scaled by a power of two 2^e with ||2^e psi|| in
+// [2^12, 2^13), then the FP16 pair hi = fp16(v), lo = fp16(v - hi), and the
+// unscale factor 2^-e per line in `scale`.  FP16 keeps 11 significant bits
+// like TF32; the scale keeps every value of the orthogonal transforms that
+// follow far below the FP16 range (|v| <= ||v|| < 2^13.5) and puts the FP16
+// subnormal step (2^-24) 2^-36 below the channel norm.
+enum : int { kPlain = 0, kSplitTF32 = 1, kSplitF16 = 2 };
+
+// Power-of-two exponent e with x 2^e in [2^12, 2^13) (0 for 0, inf, nan).
+__device__ __forceinline__ int scale_exp(float nrm) {
+    return (nrm > 0.f && isfinite(nrm)) ? 12 - ilogbf(nrm) : 0;
+}
+
+// Forward transform.  FP32 kernels: at most 64 registers, so two CTAs of
 // up to 512 threads (one line of N/16 threads each) fit on an SM.
-template <typename R, bool SPLIT, int Q>
+template <typename R, int MODE, int Q>
 __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTable g, int N, int cplx, const R* __restrict__ in,
-                                                 R* __restrict__ out0, R* __restrict__ out1,
+                                                 void* __restrict__ out0, void* __restrict__ out1,
+                                                 float* __restrict__ scale,
                                                  const typename Cx<R>::T* __restrict__ tw,
                                                  const typename Cx<R>::T* __restrict__ post) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float spart[32];   // per 16 threads (<= 512 threads): partial sums of |psi_i|^2
     const int T = N >> 4;
     const int G = lines_per_cta(N);
     const int grp = threadIdx.x / T, lt = threadIdx.x % T;
@@ -338,6 +356,12 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
             a[u].y = b[u].y = (R)0;
         }
     }
+    float part = 0.f;
+    if (MODE == kSplitF16) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            part += (float)(a[u].x * a[u].x + a[u].y * a[u].y) + (float)(b[u].x * b[u].x + b[u].y * b[u].y);
+    }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int j = lt + u * T;
@@ -346,13 +370,33 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
         s[padi(N - 1 - j)] = b[u];
     }
     __syncthreads();
+    if (MODE == kSplitF16) {
+        // sum over the line's T threads (T a multiple of 16) in a fixed order, so
+        // that the scale never depends on timing: 16-lane groups by shuffles, one
+        // shared slot per group, summed in slot order below (the FFT's barriers
+        // order the slots before those reads).  blockDim is a multiple of 16, so
+        // a warp is 32 or (the last one) 16 threads.
+        const unsigned mask = (blockDim.x - (threadIdx.x & ~31u)) >= 32 ? 0xffffffffu : 0x0000ffffu;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(mask, part, o);
+        if ((threadIdx.x & 15) == 0) spart[threadIdx.x >> 4] = part;
+    }
     __shared__ C sroot[32];
     fft_stages<Q>(s, tw, sroot, N, lt, T, 1, N);
     if (!live) return;
     const R sc1 = (R)sqrt(2.0 / (double)N), sc0 = (R)sqrt(1.0 / (double)N);
     const int line = g.line0[gi] + (cplx ? 2 * local : local);
-    R* o0 = out0 + (size_t)line * N;
-    R* o1 = SPLIT ? out1 + (size_t)line * N : nullptr;
+    float fs = 1.f;
+    if (MODE == kSplitF16) {
+        float nrm2 = 0.f;
+        for (int q = grp * (T >> 4); q < (grp + 1) * (T >> 4); ++q) nrm2 += spart[q];
+        const int e = scale_exp(sqrtf(nrm2));
+        fs = ldexpf(1.f, e);
+        if (lt == 0) {
+            scale[line] = ldexpf(1.f, -e);
+            if (cplx) scale[line + 1] = ldexpf(1.f, -e);
+        }
+    }
     for (int m = lt; m < (N >> 1); m += T) {
         C X[2];
 #pragma unroll
@@ -371,7 +415,9 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
         // storage index of k: odd l -> k; even l -> N-1-k (pairs stay adjacent, order flips)
         const int idx = even ? (N - 2 - 2 * m) : 2 * m;
         const C lo_e = even ? X[1] : X[0], hi_e = even ? X[0] : X[1];   // elements at idx, idx+1
-        if (SPLIT) {
+        if (MODE == kSplitTF32) {
+            float* o0 = reinterpret_cast<float*>(out0) + (size_t)line * N;
+            float* o1 = reinterpret_cast<float*>(out1) + (size_t)line * N;
             const float r0 = round_tf32((float)lo_e.x), r1 = round_tf32((float)hi_e.x);
             *reinterpret_cast<float2*>(o0 + idx) = make_float2(r0, r1);
             *reinterpret_cast<float2*>(o1 + idx) =
@@ -382,7 +428,23 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
                 *reinterpret_cast<float2*>(o1 + N + idx) =
                     make_float2(round_tf32((float)lo_e.y - i0), round_tf32((float)hi_e.y - i1));
             }
+        } else if (MODE == kSplitF16) {
+            __half* o0 = reinterpret_cast<__half*>(out0) + (size_t)line * N;
+            __half* o1 = reinterpret_cast<__half*>(out1) + (size_t)line * N;
+            const float2 vr = make_float2((float)lo_e.x * fs, (float)hi_e.x * fs);
+            const __half2 hr = __float22half2_rn(vr);
+            *reinterpret_cast<__half2*>(o0 + idx) = hr;
+            *reinterpret_cast<__half2*>(o1 + idx) = __float22half2_rn(
+                make_float2(vr.x - __low2float(hr), vr.y - __high2float(hr)));
+            if (cplx) {
+                const float2 vi = make_float2((float)lo_e.y * fs, (float)hi_e.y * fs);
+                const __half2 hi2 = __float22half2_rn(vi);
+                *reinterpret_cast<__half2*>(o0 + N + idx) = hi2;
+                *reinterpret_cast<__half2*>(o1 + N + idx) = __float22half2_rn(
+                    make_float2(vi.x - __low2float(hi2), vi.y - __high2float(hi2)));
+            }
         } else {
+            R* o0 = reinterpret_cast<R*>(out0) + (size_t)line * N;
             o0[idx] = lo_e.x;
             o0[idx + 1] = hi_e.x;
             if (cplx) {
@@ -484,13 +546,7 @@ static int launch_cfg(K kernel, int N, size_t elem, unsigned& threads, size_t& s
     const int G = lines_per_cta(N);
     threads = (unsigned)(G * (N / 16));
     smem = (size_t)G * (N + N / 16) * elem;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) {
-            set_error("dct: cannot opt in %zu bytes of shared memory: %s", smem, cudaGetErrorString(e));
-            return DSBT_ERR_CUDA;
-        }
-    }
+    if (smem > 48 * 1024) return ensure_smem((const void*)kernel, smem);
     return DSBT_OK;
 }
 
@@ -510,15 +566,16 @@ static int odd_part(int N) {
 #define DSBT_DCT_Q_CASES(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21) X(23) X(25) X(27) X(29) X(31)
 
 template <typename R>
-using FwdKernel = void (*)(GroupTable, int, int, const R*, R*, R*, const typename Cx<R>::T*, const typename Cx<R>::T*);
+using FwdKernel = void (*)(GroupTable, int, int, const R*, void*, void*, float*, const typename Cx<R>::T*,
+                           const typename Cx<R>::T*);
 template <typename R>
 using InvKernel = void (*)(GroupTable, int, int, const R*, R*, const typename Cx<R>::T*, const typename Cx<R>::T*);
 
-template <typename R, bool SPLIT>
+template <typename R, int MODE>
 static FwdKernel<R> fwd_kernel(int N) {
     switch (odd_part(N)) {
 #define DSBT_CASE(q) \
-    case q: return k_dct_fwd<R, SPLIT, q>;
+    case q: return k_dct_fwd<R, MODE, q>;
         DSBT_DCT_Q_CASES(DSBT_CASE)
 #undef DSBT_CASE
     }
@@ -540,12 +597,12 @@ int dct_forward_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const do
                     double* out, cudaStream_t st) {
     if (nchannels(g) == 0) return DSBT_OK;
     unsigned th; size_t sm;
-    FwdKernel<double> k = fwd_kernel<double, false>(p->N);
+    FwdKernel<double> k = fwd_kernel<double, kPlain>(p->N);
     DSBT_CHECK_ARG(k != nullptr, "dct: N=%d not of the form 256 q, q <= 32", p->N);
     int rc = launch_cfg(k, p->N, sizeof(double2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctFwd, st);
-    k<<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, nullptr, p->tw64, p->post64);
+    k<<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out, nullptr, nullptr, p->tw64, p->post64);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -554,12 +611,26 @@ int dct_forward_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const fl
                     float* out_hi, float* out_lo, cudaStream_t st) {
     if (nchannels(g) == 0) return DSBT_OK;
     unsigned th; size_t sm;
-    FwdKernel<float> k = fwd_kernel<float, true>(p->N);
+    FwdKernel<float> k = fwd_kernel<float, kSplitTF32>(p->N);
     DSBT_CHECK_ARG(k != nullptr, "dct: N=%d not of the form 256 q, q <= 32", p->N);
     int rc = launch_cfg(k, p->N, sizeof(float2), th, sm);
     if (rc) return rc;
     ProfScope ps(kKDctFwd, st);
-    k<<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out_hi, out_lo, p->tw32, p->post32);
+    k<<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out_hi, out_lo, nullptr, p->tw32, p->post32);
+    DSBT_CUDA_TRY(cudaGetLastError());
+    return DSBT_OK;
+}
+
+int dct_forward_f16(const dsbt_plan* p, const GroupTable& g, bool cplx, const float* in, __half* out_hi,
+                    __half* out_lo, float* scale, cudaStream_t st) {
+    if (nchannels(g) == 0) return DSBT_OK;
+    unsigned th; size_t sm;
+    FwdKernel<float> k = fwd_kernel<float, kSplitF16>(p->N);
+    DSBT_CHECK_ARG(k != nullptr, "dct: N=%d not of the form 256 q, q <= 32", p->N);
+    int rc = launch_cfg(k, p->N, sizeof(float2), th, sm);
+    if (rc) return rc;
+    ProfScope ps(kKDctFwd, st);
+    k<<<nblocks(g, p->N), th, sm, st>>>(g, p->N, cplx ? 1 : 0, in, out_hi, out_lo, scale, p->tw32, p->post32);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }

@@ -1,6 +1,16 @@
-// fast_tf32.cu -- split-TF32 tensor-core contractions with T_l and T_l^T in
-// O(N l log N) work, for plans built with DSBT_PLAN_FAST_TF32 (the stable
+// fast_split.cu -- split-precision tensor-core contractions with T_l and T_l^T
+// in O(N l log N) work, for plans built with DSBT_PLAN_FAST_SPLIT (the stable
 // counterpart of the fast scheme of Sec. 2.6, on tcgen05).
+//
+// Operands are FP16 pairs hi + lo (11 significant bits each, as TF32, at twice
+// the TF32 tensor rate and half the bytes): plan factors scaled by 2^14 (rows of
+// an orthogonal matrix, |entries| <= 1), lines scaled per channel by a power of
+// two 2^e with ||2^e psi|| < 2^13 (set by the sine/cosine kernel or the input
+// split), so every intermediate of the orthogonal maps stays far inside the
+// FP16 range and the FP16 subnormal step lies 2^-36 below the channel norm.
+// Each K step issues hi*hi + hi*lo + lo*hi into one FP32 TMEM accumulator
+// (lo*lo, 2^-22 relative, dropped); epilogues remove 2^14 (and 2^e where the
+// output leaves the scaled domain) by exact power-of-two products.
 //
 // On a regular row n of T_l the entries left of the diagonal are
 // T_nm = alpha_n P'_l(n - m, 2n) sqrt(w_m): a polynomial of degree l - 1 in m
@@ -45,6 +55,8 @@
 #include <thread>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "plan.cuh"
 #include "tc_ptx.cuh"
 
@@ -55,7 +67,7 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128;
-constexpr int BK = 32;
+constexpr int BK = 64;                             // K elements per block: one 128-byte swizzle row of FP16
 constexpr int BN_MAX = 256;
 constexpr int BBOX = 64;                           // rows per B TMA box
 constexpr int STAGES = 2;
@@ -67,8 +79,10 @@ constexpr int STAGES = 2;
 constexpr int KC = 1;
 constexpr int EPI_WARPS = 8;
 constexpr int QS = 4;                              // tile-queue slots
-constexpr int A_BYTES = BM * BK * 4;               // 16 KiB
-constexpr int B_BYTES = BN_MAX * BK * 4;           // 32 KiB
+constexpr int A_BYTES = BM * BK * 2;               // 16 KiB
+constexpr int B_BYTES = BN_MAX * BK * 2;           // 32 KiB
+constexpr float kFacScale = 16384.f;               // plan factors are stored times 2^14
+constexpr float kFacUnscale = 1.f / 16384.f;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr int FL = 128;                            // leaf = output row tile
@@ -142,7 +156,10 @@ __device__ __forceinline__ void aug_range(const FtcSpace& fs, int s, int& k0, in
     k1 = k0 + lb;
 }
 
-// K blocks of one tile: segments [k0, k1) of operand source src (1 near, 2 far).
+// K blocks of one tile: segments [k0, k1) of operand source src (1 near: the
+// lines against a diagonal 128 x 128 block of T_l / T_l^T or, for MOMENTS and
+// WEIGHTS, the basis rows; 2 far: the augmented lines against B / QA; 3: the
+// completion block, T_l rows < 64 transposed, against the lines' K block 0).
 struct Segs {
     int n;
     int src[MAX_SEGS], k0[MAX_SEGS], k1[MAX_SEGS];
@@ -212,7 +229,7 @@ __device__ __forceinline__ Segs segments(const FtcSpace& fs, int l, int rt) {
             sg.add(1, rt * (FL / BK), (rt + 1) * (FL / BK));
         }
     } else {   // kLeafOut
-        if (rt > 0 && nx > 0) sg.add(1, 0, 1);   // completion rows n < n0_l (storage rows < 32)
+        if (rt > 0 && nx > 0) sg.add(3, 0, 1);   // completion rows n < n0_l (storage rows < 64)
         sg.add(1, rt * (FL / BK), (rt + 1) * (FL / BK));
         for (int j = 0; j < fs.levels; ++j) {
             const int i = rt >> j;
@@ -249,12 +266,19 @@ __device__ __forceinline__ int seg_count(const FtcSpace& fs, int l, int rt) {
 
 struct EpiArgs {
     int mode;              // OutMode, or kOutAugSplit for MOMENTS / WEIGHTS
-    float* out0;
-    float* out1;
+    void* out0;            // FP16 pair (kOutAugSplit, kOutPlanarSplit) or FP32 values
+    void* out1;
     const float2* phase;
     int per_l;
     int stride;            // output row stride (N, or NA for the augmented lines)
+    const float* scale;    // per line: 2^-e, the factor that leaves the scaled domain
 };
+
+// FP16 pair of v: hi = fp16(v), lo = fp16(v - hi).
+__device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
+    hi = __float2half_rn(v);
+    lo = __float2half_rn(v - __half2float(hi));
+}
 constexpr int kOutAugSplit = 16;
 
 // The kernel: roles and bounded waits as in gemm_tf32x3.cu; what differs is
@@ -264,6 +288,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                const __grid_constant__ CUtensorMap tmB1_hi, const __grid_constant__ CUtensorMap tmB1_lo,
                const __grid_constant__ CUtensorMap tmA2_hi, const __grid_constant__ CUtensorMap tmA2_lo,
                const __grid_constant__ CUtensorMap tmB2_hi, const __grid_constant__ CUtensorMap tmB2_lo,
+               const __grid_constant__ CUtensorMap tmA3_hi, const __grid_constant__ CUtensorMap tmA3_lo,
                GroupTable gt, FtcSpace fs, int N, EpiArgs ep, unsigned* status, uint32_t spin, int* sched) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -318,7 +343,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             const uint64_t pol_b = policy_evict_last();
             int qslot = 0;
             uint32_t qphase = 0;
-            const uint32_t a_bytes = (aug ? 64u : 128u) * BK * 4u;
+            const uint32_t a_bytes = (aug ? 64u : 128u) * BK * 2u;
             while (ok) {
                 if (!mbar_wait(&tq_empty[qslot], qphase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                 int t = atomicAdd(sched, 1);
@@ -332,7 +357,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 const Segs sg = segments(fs, l, tl.rt);
                 const int nbox = (tl.nmma + BBOX - 1) / BBOX;
                 const bool pair = aug && fs.pair_b[tl.rt] >= 0;
-                const uint32_t bytes = 2 * a_bytes * (pair ? 2 : 1) + 2 * nbox * BBOX * BK * 4;
+                const uint32_t bytes = 2 * a_bytes * (pair ? 2 : 1) + 2 * nbox * BBOX * BK * 2;
                 int arow1, arow2 = 0;
                 if (fs.mode == kMoments) {
                     arow1 = ((l & 1) * fs.nslots_f + fs.pair_a[tl.rt]) * KP;
@@ -341,7 +366,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                     arow1 = (l * fs.nslots + fs.pair_a[tl.rt]) * KP;
                     if (pair) arow2 = (l * fs.nslots + fs.pair_b[tl.rt]) * KP;
                 } else {
-                    arow1 = l * N + tl.rt * BM;
+                    arow1 = (l * fs.nleaf + tl.rt) * BM;   // diagonal block of leaf rt
                     arow2 = (fs.mode == kEval ? l : (l & 1)) * N + tl.rt * BM;
                 }
                 const int brow = gt.line0[tl.g] + tl.ct * BN_MAX;
@@ -353,10 +378,10 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                     unsigned char* sb = stage_base + stage * STAGE_BYTES;
                     mbar_expect_tx(&full[stage], bytes);
                     led.arm(stage, phase);
-                    const CUtensorMap* ah = src == 1 ? &tmA1_hi : &tmA2_hi;
-                    const CUtensorMap* al = src == 1 ? &tmA1_lo : &tmA2_lo;
-                    const CUtensorMap* bh = src == 1 ? &tmB1_hi : &tmB2_hi;
-                    const CUtensorMap* bl = src == 1 ? &tmB1_lo : &tmB2_lo;
+                    const CUtensorMap* ah = src == 1 ? &tmA1_hi : (src == 2 ? &tmA2_hi : &tmA3_hi);
+                    const CUtensorMap* al = src == 1 ? &tmA1_lo : (src == 2 ? &tmA2_lo : &tmA3_lo);
+                    const CUtensorMap* bh = src == 2 ? &tmB2_hi : &tmB1_hi;
+                    const CUtensorMap* bl = src == 2 ? &tmB2_lo : &tmB1_lo;
                     if (aug) {   // slot a -> A rows 0..63, slot b -> rows 64..127
                         tma_load_2d(sb, ah, &full[stage], kb * BK, arow1);
                         tma_load_2d(sb + A_BYTES, al, &full[stage], kb * BK, arow1);
@@ -365,9 +390,18 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                             tma_load_2d(sb + A_BYTES + KP * 128, al, &full[stage], kb * BK, arow2);
                         }
                     } else {
-                        const int arow = src == 1 ? arow1 : arow2;
-                        tma_load_2d(sb, ah, &full[stage], kb * BK, arow);
-                        tma_load_2d(sb + A_BYTES, al, &full[stage], kb * BK, arow);
+                        // near: column kb of the leaf's diagonal block; far: augmented
+                        // column kb; completion: T_l rows 0..63 of the leaf's columns
+                        int ax = kb * BK, arow = arow2;
+                        if (src == 1) {
+                            ax = (kb - tl.rt * (FL / BK)) * BK;
+                            arow = arow1;
+                        } else if (src == 3) {
+                            ax = 0;
+                            arow = l * N + tl.rt * BM;
+                        }
+                        tma_load_2d(sb, ah, &full[stage], ax, arow);
+                        tma_load_2d(sb + A_BYTES, al, &full[stage], ax, arow);
                     }
                     for (int b = 0; b < nbox; ++b) {
                         tma_load_2d_hint(sb + 2 * A_BYTES + b * BBOX * 128, bh, &full[stage], kb * BK,
@@ -398,7 +432,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 const Tile tl = decode(fs, gt, t);
                 const int l = gt.l[tl.g];
                 const int nkb = seg_count(fs, l, tl.rt);
-                const uint32_t idesc = idesc_tf32(BM, tl.nmma);
+                const uint32_t idesc = idesc_f16(BM, tl.nmma);
                 for (int c0 = 0; c0 < nkb && ok; c0 += fs.kc) {
                     const int c1 = min(nkb, c0 + fs.kc);
                     const int buf = gch & 1;
@@ -416,13 +450,13 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                         const uint32_t sb_hi = sa + 2 * A_BYTES;
                         const uint32_t sb_lo = sb_hi + B_BYTES;
 #pragma unroll
-                        for (int ks = 0; ks < BK / 8; ++ks) {
-                            const uint32_t off = ks * 32;
+                        for (int ks = 0; ks < BK / 16; ++ks) {
+                            const uint32_t off = ks * 32;   // 16 FP16 values = 32 bytes along K
                             const uint64_t dah = sdesc_sw128(sa + off), dal = sdesc_sw128(sa_lo + off);
                             const uint64_t dbh = sdesc_sw128(sb_hi + off), dbl = sdesc_sw128(sb_lo + off);
-                            mma_tf32(d, dah, dbh, idesc, accf);
-                            mma_tf32(d, dah, dbl, idesc, 1);
-                            mma_tf32(d, dal, dbh, idesc, 1);
+                            mma_f16(d, dah, dbh, idesc, accf);
+                            mma_f16(d, dah, dbl, idesc, 1);
+                            mma_f16(d, dal, dbh, idesc, 1);
                             accf = 1;
                         }
                         mma_commit(&empty[stage]);
@@ -492,50 +526,56 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             if (!ok) break;
             if (ncols <= 0 || !store_row) continue;
             const int S = ep.stride;
-            if (ep.mode == kOutAugSplit) {
+            if (ep.mode == kOutAugSplit) {   // moments / weights stay in the scaled domain
+                __half* o0 = reinterpret_cast<__half*>(ep.out0);
+                __half* o1 = reinterpret_cast<__half*>(ep.out1);
                 const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
 #pragma unroll
                 for (int j = 0; j < 128; ++j) {
                     if (j < ncols) {
-                        const float h = round_tf32(acc[j]);
+                        __half h, lo;
+                        split_f16(acc[j] * kFacUnscale, h, lo);
                         const size_t o = (line_base + j) * S + row;
-                        ep.out0[o] = h;
-                        ep.out1[o] = round_tf32(acc[j] - h);
+                        o0[o] = h;
+                        o1[o] = lo;
                     }
                 }
                 continue;
             }
             float2 ph = make_float2(1.f, 0.f);
             if (ep.phase) ph = ep.per_l ? ep.phase[(size_t)l * N + row] : ep.phase[(size_t)(l & 1) * N + phase_entry(l, row, N)];
+            const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
             if (ep.mode == kOutUserC64) {
                 float2* o = reinterpret_cast<float2*>(ep.out0);
                 const size_t chan_base = (size_t)gt.chan0[tl.g] + (cbase >> 1);
 #pragma unroll
                 for (int j = 0; j < 128; j += 2)
-                    if (j < ncols) o[(chan_base + (j >> 1)) * N + row] = make_float2(acc[j], acc[j + 1]);
-            } else if (ep.mode == kOutUserF32) {
-                const size_t chan_base = (size_t)gt.chan0[tl.g] + cbase;
+                    if (j < ncols) {
+                        const float u = ep.scale[line_base + j] * kFacUnscale;
+                        o[(chan_base + (j >> 1)) * N + row] = make_float2(acc[j] * u, acc[j + 1] * u);
+                    }
+            } else if (ep.mode == kOutUserF32 || ep.mode == kOutPlanarF32) {
+                float* o = reinterpret_cast<float*>(ep.out0);
+                const size_t base = ep.mode == kOutUserF32 ? (size_t)gt.chan0[tl.g] + cbase : line_base;
 #pragma unroll
                 for (int j = 0; j < 128; ++j)
-                    if (j < ncols) ep.out0[(chan_base + j) * N + row] = acc[j];
-            } else if (ep.mode == kOutPlanarF32) {
-                const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
-#pragma unroll
-                for (int j = 0; j < 128; ++j)
-                    if (j < ncols) ep.out0[(line_base + j) * N + row] = acc[j];
-            } else {   // kOutPlanarSplit: complex pairs with optional phase, TF32 split
-                const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+                    if (j < ncols) o[(base + j) * N + row] = acc[j] * (ep.scale[line_base + j] * kFacUnscale);
+            } else {   // kOutPlanarSplit: complex pairs with optional phase, FP16 pair, still scaled
+                __half* o0 = reinterpret_cast<__half*>(ep.out0);
+                __half* o1 = reinterpret_cast<__half*>(ep.out1);
 #pragma unroll
                 for (int j = 0; j < 128; j += 2) {
                     if (j < ncols) {
-                        const float re = acc[j] * ph.x - acc[j + 1] * ph.y;
-                        const float im = acc[j] * ph.y + acc[j + 1] * ph.x;
-                        const float hr = round_tf32(re), hi = round_tf32(im);
+                        const float re = (acc[j] * ph.x - acc[j + 1] * ph.y) * kFacUnscale;
+                        const float im = (acc[j] * ph.y + acc[j + 1] * ph.x) * kFacUnscale;
                         const size_t o = (line_base + j) * N + row;
-                        ep.out0[o] = hr;
-                        ep.out1[o] = round_tf32(re - hr);
-                        ep.out0[o + N] = hi;
-                        ep.out1[o + N] = round_tf32(im - hi);
+                        __half h, lo;
+                        split_f16(re, h, lo);
+                        o0[o] = h;
+                        o1[o] = lo;
+                        split_f16(im, h, lo);
+                        o0[o + N] = h;
+                        o1[o + N] = lo;
                     }
                 }
             }
@@ -552,20 +592,28 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
 
 // ------------------------------------------------------------ plan data
 
+// FP16 pair of a plan entry v stored times 2^14: hi = fp16(2^14 v),
+// lo = fp16(2^14 v - hi), both rounded to nearest.
+__device__ __forceinline__ void fac_pair(double v, __half& hi, __half& lo) {
+    const double x = v * (double)kFacScale;
+    hi = __double2half(x);
+    lo = __double2half(x - (double)__half2float(hi));
+}
+
 // beta_{r,j}[k] of every row r of the used slot s = (j, i) it takes (the rows
 // of the sibling interval i + 1), from the FP64 T_l:
 //   beta = sum_t Q_j[t][k] T_l[r][i len + t] / sqrt(w_{i len + t}),
-// zero on completion rows and for k >= l; written as TF32 pairs to
+// zero on completion rows and for k >= l; written as FP16 pairs to
 // B[l][r][(s,k)] and BT[l][(s,k)][r].  Block (position, l), KP threads (k).
 __global__ void k_ftc_beta(const double* __restrict__ T64, const double* __restrict__ Q,
-                           const size_t* __restrict__ qoff, FtcSpace fs, int N, float* bA_hi, float* bA_lo,
-                           float* bT_hi, float* bT_lo) {
+                           const size_t* __restrict__ qoff, FtcSpace fs, int N, __half* bA_hi, __half* bA_lo,
+                           __half* bT_hi, __half* bT_lo) {
     const int half = N / 2;
     const int j = blockIdx.x / half, q = blockIdx.x % half, l = blockIdx.y, k = threadIdx.x;
     const int len = FL << j;
     const int s = fs.slot_off[j] + q / len, i = 2 * (q / len);
     const int r = (i + 1) * len + q % len;
-    const int NA = fs.nslots * KP, NAF = fs.nslots_f * KP;
+    const int NAF = fs.nslots_f * KP;
     double b = 0.0;
     if (r >= n_extra(l) && k < l) {
         const double* row = T64 + ((size_t)l * N + r) * N + (size_t)i * len;
@@ -575,10 +623,10 @@ __global__ void k_ftc_beta(const double* __restrict__ T64, const double* __restr
             b = fma(row[t] / w, Qj[(size_t)t * KP + k], b);
         }
     }
-    const float h = round_tf32((float)b), lo = round_tf32((float)(b - (double)h));
+    __half h, lo;
+    fac_pair(b, h, lo);
     const size_t oa = ((size_t)l * N + r) * NAF + (size_t)s * KP + k;
     const size_t ot = (((size_t)l * fs.nslots + s) * KP + k) * N + r;
-    (void)NA;
     bA_hi[oa] = h;
     bA_lo[oa] = lo;
     bT_hi[ot] = h;
@@ -589,7 +637,7 @@ __global__ void k_ftc_beta(const double* __restrict__ T64, const double* __restr
 // columns c of used slot s = (j, i); parity p = 1 (odd l) carries
 // sqrt(w_0) = 1/sqrt(2).  Block (position, p), KP threads (k).
 __global__ void k_ftc_q(const double* __restrict__ Q, const size_t* __restrict__ qoff, FtcSpace fs, int N,
-                        float* qT_hi, float* qT_lo, float* qA_hi, float* qA_lo) {
+                        __half* qT_hi, __half* qT_lo, __half* qA_hi, __half* qA_lo) {
     const int half = N / 2;
     const int j = blockIdx.x / half, q = blockIdx.x % half, p = blockIdx.y, k = threadIdx.x;
     const int len = FL << j;
@@ -597,7 +645,8 @@ __global__ void k_ftc_q(const double* __restrict__ Q, const size_t* __restrict__
     const int c = i * len + t;
     const int NA = fs.nslots * KP;
     const double v = Q[qoff[j] + (size_t)t * KP + k] * ((p == 1 && c == 0) ? 0.70710678118654752440 : 1.0);
-    const float h = round_tf32((float)v), lo = round_tf32((float)(v - (double)h));
+    __half h, lo;
+    fac_pair(v, h, lo);
     const size_t ot = (((size_t)p * fs.nslots_f + s) * KP + k) * N + c;
     const size_t oa = ((size_t)p * N + c) * NA + (size_t)s * KP + k;
     qT_hi[ot] = h;
@@ -610,7 +659,8 @@ __global__ void k_ftc_q(const double* __restrict__ Q, const size_t* __restrict__
 // columns [len_j, 2 len_j) into B[l][r][(nslots + j, k)].  Block (j, l), KP
 // threads (k).
 __global__ void k_ftc_beta_right(const double* __restrict__ T64, const double* __restrict__ Q,
-                                 const size_t* __restrict__ qoff, FtcSpace fs, int N, float* bA_hi, float* bA_lo) {
+                                 const size_t* __restrict__ qoff, FtcSpace fs, int N, __half* bA_hi,
+                                 __half* bA_lo) {
     const int j = blockIdx.x, l = blockIdx.y, k = threadIdx.x;
     const int len = FL << j, NAF = fs.nslots_f * KP;
     const double* Qj = Q + qoff[j];
@@ -620,7 +670,8 @@ __global__ void k_ftc_beta_right(const double* __restrict__ T64, const double* _
             const double* row = T64 + ((size_t)l * N + r) * N + len;
             for (int t = 0; t < len; ++t) b = fma(row[t], Qj[(size_t)t * KP + k], b);
         }
-        const float h = round_tf32((float)b), lo = round_tf32((float)(b - (double)h));
+        __half h, lo;
+        fac_pair(b, h, lo);
         const size_t oa = ((size_t)l * N + r) * NAF + (size_t)(fs.nslots + j) * KP + k;
         bA_hi[oa] = h;
         bA_lo[oa] = lo;
@@ -630,7 +681,7 @@ __global__ void k_ftc_beta_right(const double* __restrict__ T64, const double* _
 // QT rows of the right slots: QT[p][(nslots + j, k)][len_j + t] = Q_j[t][k]
 // (columns >= 128 carry weight 1).  Block (position over all j, p), KP threads.
 __global__ void k_ftc_q_right(const double* __restrict__ Q, const size_t* __restrict__ qoff, FtcSpace fs, int N,
-                              float* qT_hi, float* qT_lo) {
+                              __half* qT_hi, __half* qT_lo) {
     int t = blockIdx.x, j = 0;
     while (t >= (FL << j)) {
         t -= FL << j;
@@ -638,10 +689,43 @@ __global__ void k_ftc_q_right(const double* __restrict__ Q, const size_t* __rest
     }
     const int p = blockIdx.y, k = threadIdx.x, c = (FL << j) + t;
     const double v = Q[qoff[j] + (size_t)t * KP + k];
-    const float h = round_tf32((float)v), lo = round_tf32((float)(v - (double)h));
+    __half h, lo;
+    fac_pair(v, h, lo);
     const size_t ot = (((size_t)p * fs.nslots_f + fs.nslots + j) * KP + k) * N + c;
     qT_hi[ot] = h;
     qT_lo[ot] = lo;
+}
+
+// Near band: the diagonal 128 x 128 block of leaf J of T_l,
+// D[l][J][r][c] = T_l[128 J + r][128 J + c], and its transpose Dt[l][J][c][r]
+// (A operands of the forward rows and the adjoint columns).  Block (J, l).
+__global__ void k_ftc_near(const double* __restrict__ T64, int N, __half* D_hi, __half* D_lo, __half* Dt_hi,
+                           __half* Dt_lo) {
+    const int J = blockIdx.x, l = blockIdx.y, nleaf = N / FL;
+    const size_t blk = ((size_t)l * nleaf + J) * FL * FL;
+    for (int e = threadIdx.x; e < FL * FL; e += blockDim.x) {
+        const int r = e / FL, c = e % FL;
+        __half h, lo;
+        fac_pair(T64[((size_t)l * N + FL * J + r) * N + FL * J + c], h, lo);
+        D_hi[blk + e] = h;
+        D_lo[blk + e] = lo;
+        Dt_hi[blk + (size_t)c * FL + r] = h;
+        Dt_lo[blk + (size_t)c * FL + r] = lo;
+    }
+}
+
+// Completion block of the adjoint columns: C[l][c][r] = T_l[r][c] for r < 64
+// (the completion rows n < n0_l <= 33 and regular rows, which vanish right of
+// their diagonal).  Block (column chunk, l).
+__global__ void k_ftc_comp(const double* __restrict__ T64, int N, __half* C_hi, __half* C_lo) {
+    const int l = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    for (int r = 0; r < BK; ++r) {
+        __half h, lo;
+        fac_pair(T64[((size_t)l * N + r) * N + c], h, lo);
+        C_hi[((size_t)l * N + c) * BK + r] = h;
+        C_lo[((size_t)l * N + c) * BK + r] = lo;
+    }
 }
 
 }  // namespace
@@ -651,15 +735,24 @@ struct FtcData {
     int np_m = 0, np_w = 0;                        // slot pairs of the MOMENTS / WEIGHTS tiles
     int pa_m[MAX_SLOTS], pb_m[MAX_SLOTS], pa_w[MAX_SLOTS], pb_w[MAX_SLOTS];
     int NA = 0, NAF = 0;   // augmented widths: adjoint (used slots), forward (+ right slots)
-    float* bA_hi = nullptr;
-    float* bA_lo = nullptr;
-    float* bT_hi = nullptr;
-    float* bT_lo = nullptr;
-    float* qT_hi = nullptr;
-    float* qT_lo = nullptr;
-    float* qA_hi = nullptr;
-    float* qA_lo = nullptr;
+    // FP16 pairs (times 2^14): B, BT, QT, QA, the diagonal blocks D and Dt and
+    // the completion block C
+    __half* bA_hi = nullptr;
+    __half* bA_lo = nullptr;
+    __half* bT_hi = nullptr;
+    __half* bT_lo = nullptr;
+    __half* qT_hi = nullptr;
+    __half* qT_lo = nullptr;
+    __half* qA_hi = nullptr;
+    __half* qA_lo = nullptr;
+    __half* D_hi = nullptr;
+    __half* D_lo = nullptr;
+    __half* Dt_hi = nullptr;
+    __half* Dt_lo = nullptr;
+    __half* C_hi = nullptr;
+    __half* C_lo = nullptr;
     CUtensorMap tm_bA_hi, tm_bA_lo, tm_bT_hi, tm_bT_lo, tm_qT_hi, tm_qT_lo, tm_qA_hi, tm_qA_lo;
+    CUtensorMap tm_D_hi, tm_D_lo, tm_Dt_hi, tm_Dt_lo, tm_C_hi, tm_C_lo;
 };
 
 // MOMENTS / WEIGHTS tiles hold two slots.  Each slot (j, i) of an odd level j
@@ -712,8 +805,8 @@ bool ftc_supported(int N) {
 
 int ftc_build(dsbt_plan* p, cudaStream_t st) {
     const int N = p->N;
-    DSBT_CHECK_ARG(ftc_supported(N), "DSBT_PLAN_FAST_TF32 needs N / 128 a power of two (N = %d)", N);
-    DSBT_CHECK_ARG(p->T64 != nullptr, "DSBT_PLAN_FAST_TF32: FP64 factors missing at build");
+    DSBT_CHECK_ARG(ftc_supported(N), "DSBT_PLAN_FAST_SPLIT needs N / 128 a power of two (N = %d)", N);
+    DSBT_CHECK_ARG(p->T64 != nullptr, "DSBT_PLAN_FAST_SPLIT: FP64 factors missing at build");
     FtcData* f = new (std::nothrow) FtcData();
     if (!f) return DSBT_ERR_NOMEM;
     p->ftc = f;
@@ -746,16 +839,24 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
     for (int j = 0; j < levels; ++j) std::copy(Qh[j].begin(), Qh[j].end(), Qall.begin() + qoff[j]);
     const size_t L = (size_t)p->l_max + 1;
     const size_t nbA = L * N * NAF, nbT = L * N * NA, nqT = 2 * (size_t)N * NAF, nq = 2 * (size_t)N * NA;
+    const size_t nD = L * N * FL, nC = L * N * BK;
+    const size_t hb = sizeof(__half);
     double* Qd = nullptr;
     size_t* qoffd = nullptr;
-    bool ok = cudaMalloc((void**)&f->bA_hi, nbA * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->bA_lo, nbA * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->bT_hi, nbT * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->bT_lo, nbT * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->qT_hi, nqT * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->qT_lo, nqT * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->qA_hi, nq * 4) == cudaSuccess &&
-              cudaMalloc((void**)&f->qA_lo, nq * 4) == cudaSuccess &&
+    bool ok = cudaMalloc((void**)&f->bA_hi, nbA * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->bA_lo, nbA * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->bT_hi, nbT * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->bT_lo, nbT * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->qT_hi, nqT * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->qT_lo, nqT * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->qA_hi, nq * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->qA_lo, nq * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->D_hi, nD * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->D_lo, nD * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->Dt_hi, nD * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->Dt_lo, nD * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->C_hi, nC * hb) == cudaSuccess &&
+              cudaMalloc((void**)&f->C_lo, nC * hb) == cudaSuccess &&
               cudaMalloc((void**)&Qd, qtot * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void**)&qoffd, levels * sizeof(size_t)) == cudaSuccess;
     ok = ok && cudaMemcpy(Qd, Qall.data(), qtot * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -764,17 +865,13 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
         cudaGetLastError();
         cudaFree(Qd);
         cudaFree(qoffd);
-        set_error("DSBT_PLAN_FAST_TF32: device allocation or copy failed");
+        set_error("DSBT_PLAN_FAST_SPLIT: device allocation or copy failed");
         return DSBT_ERR_NOMEM;
     }
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->bA_hi, 0, nbA * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->bA_lo, 0, nbA * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->bT_hi, 0, nbT * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->bT_lo, 0, nbT * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->qT_hi, 0, nqT * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->qT_lo, 0, nqT * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->qA_hi, 0, nq * 4, st));
-    DSBT_CUDA_TRY(cudaMemsetAsync(f->qA_lo, 0, nq * 4, st));
+    for (__half* a : {f->bA_hi, f->bA_lo}) DSBT_CUDA_TRY(cudaMemsetAsync(a, 0, nbA * hb, st));
+    for (__half* a : {f->bT_hi, f->bT_lo}) DSBT_CUDA_TRY(cudaMemsetAsync(a, 0, nbT * hb, st));
+    for (__half* a : {f->qT_hi, f->qT_lo}) DSBT_CUDA_TRY(cudaMemsetAsync(a, 0, nqT * hb, st));
+    for (__half* a : {f->qA_hi, f->qA_lo}) DSBT_CUDA_TRY(cudaMemsetAsync(a, 0, nq * hb, st));
     {
         ProfScope ps(kKPlan, st);
         k_ftc_beta<<<dim3(levels * (N / 2), (unsigned)L), KP, 0, st>>>(p->T64, Qd, qoffd, b, N, f->bA_hi, f->bA_lo,
@@ -782,39 +879,42 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
         k_ftc_q<<<dim3(levels * (N / 2), 2), KP, 0, st>>>(Qd, qoffd, b, N, f->qT_hi, f->qT_lo, f->qA_hi, f->qA_lo);
         k_ftc_beta_right<<<dim3(levels, (unsigned)L), KP, 0, st>>>(p->T64, Qd, qoffd, b, N, f->bA_hi, f->bA_lo);
         k_ftc_q_right<<<dim3(N - FL, 2), KP, 0, st>>>(Qd, qoffd, b, N, f->qT_hi, f->qT_lo);
+        k_ftc_near<<<dim3(b.nleaf, (unsigned)L), 256, 0, st>>>(p->T64, N, f->D_hi, f->D_lo, f->Dt_hi, f->Dt_lo);
+        k_ftc_comp<<<dim3((N + 255) / 256, (unsigned)L), 256, 0, st>>>(p->T64, N, f->C_hi, f->C_lo);
     }
     DSBT_CUDA_TRY(cudaGetLastError());
     DSBT_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(Qd);
     cudaFree(qoffd);
-    int rc = encode_tmap_f32_sw128(&f->tm_bA_hi, f->bA_hi, L * N, NAF, 128, 32);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_bA_lo, f->bA_lo, L * N, NAF, 128, 32);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_bT_hi, f->bT_hi, L * NA, N, 64, 32);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_bT_lo, f->bT_lo, L * NA, N, 64, 32);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qT_hi, f->qT_hi, 2 * (uint64_t)NAF, N, 64, 32);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qT_lo, f->qT_lo, 2 * (uint64_t)NAF, N, 64, 32);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qA_hi, f->qA_hi, 2 * (uint64_t)N, NA, 128, 32);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&f->tm_qA_lo, f->qA_lo, 2 * (uint64_t)N, NA, 128, 32);
+    int rc = encode_tmap_f16_sw128(&f->tm_bA_hi, f->bA_hi, L * N, NAF, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_bA_lo, f->bA_lo, L * N, NAF, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_bT_hi, f->bT_hi, L * NA, N, 64, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_bT_lo, f->bT_lo, L * NA, N, 64, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_qT_hi, f->qT_hi, 2 * (uint64_t)NAF, N, 64, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_qT_lo, f->qT_lo, 2 * (uint64_t)NAF, N, 64, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_qA_hi, f->qA_hi, 2 * (uint64_t)N, NA, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_qA_lo, f->qA_lo, 2 * (uint64_t)N, NA, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_D_hi, f->D_hi, L * N, FL, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_D_lo, f->D_lo, L * N, FL, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_Dt_hi, f->Dt_hi, L * N, FL, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_Dt_lo, f->Dt_lo, L * N, FL, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_C_hi, f->C_hi, L * N, BK, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_C_lo, f->C_lo, L * N, BK, 128, BK);
     return rc;
 }
 
 void ftc_free(dsbt_plan* p) {
     if (!p || !p->ftc) return;
     FtcData* f = p->ftc;
-    cudaFree(f->bA_hi);
-    cudaFree(f->bA_lo);
-    cudaFree(f->bT_hi);
-    cudaFree(f->bT_lo);
-    cudaFree(f->qT_hi);
-    cudaFree(f->qT_lo);
-    cudaFree(f->qA_hi);
-    cudaFree(f->qA_lo);
+    for (__half* a : {f->bA_hi, f->bA_lo, f->bT_hi, f->bT_lo, f->qT_hi, f->qT_lo, f->qA_hi, f->qA_lo, f->D_hi,
+                      f->D_lo, f->Dt_hi, f->Dt_lo, f->C_hi, f->C_lo})
+        cudaFree(a);
     delete f;
     p->ftc = nullptr;
 }
 
 size_t ftc_scratch_bytes(const dsbt_plan* p, size_t lines) {
-    return p->ftc ? 2 * lines * (size_t)p->ftc->NAF * sizeof(float) : 0;
+    return p->ftc ? 2 * lines * (size_t)p->ftc->NAF * sizeof(__half) : 0;
 }
 
 namespace {
@@ -822,7 +922,8 @@ namespace {
 // One launch of the segmented kernel over the groups (largest l first).
 int launch_ftc(const dsbt_plan* p, const GroupTable& g, int mode, const CUtensorMap& a1h, const CUtensorMap& a1l,
                const CUtensorMap& b1h, const CUtensorMap& b1l, const CUtensorMap& a2h, const CUtensorMap& a2l,
-               const CUtensorMap& b2h, const CUtensorMap& b2l, const EpiArgs& ep, int* sched, cudaStream_t st) {
+               const CUtensorMap& b2h, const CUtensorMap& b2l, const CUtensorMap& a3h, const CUtensorMap& a3l,
+               const EpiArgs& ep, int* sched, cudaStream_t st) {
     FtcSpace fs = p->ftc->base;
     fs.mode = mode;
     fs.kc = KC;
@@ -848,50 +949,63 @@ int launch_ftc(const dsbt_plan* p, const GroupTable& g, int mode, const CUtensor
     fs.total = fs.t0[g.ngroups];
     if (fs.total == 0) return DSBT_OK;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    // set before every launch: the limit belongs to the current device
-    DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_ftc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int rc = ensure_smem((const void*)k_contract_ftc, smem);
+    if (rc) return rc;
     int dev = 0, nsm = 0;
     DSBT_CUDA_TRY(cudaGetDevice(&dev));
     DSBT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int grid = fs.total < nsm ? fs.total : nsm;
     DSBT_CUDA_TRY(cudaMemsetAsync(sched, 0, sizeof(int), st));
     ProfScope ps(kKContractTF32, st);
-    k_contract_ftc<<<grid, NTHREADS, smem, st>>>(a1h, a1l, b1h, b1l, a2h, a2l, b2h, b2l, g, fs, p->N, ep, p->status,
-                                                 p->spin_limit, sched);
+    k_contract_ftc<<<grid, NTHREADS, smem, st>>>(a1h, a1l, b1h, b1l, a2h, a2l, b2h, b2l, a3h, a3l, g, fs, p->N, ep,
+                                                 p->status, p->spin_limit, sched);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
 
 }  // namespace
 
-int contract_tf32_fast(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi, const float* in_lo,
-                       int out_mode, float* out0, float* out1, const float2* phase, int* sched, float* scratch,
-                       cudaStream_t st) {
+int contract_split_fast(const dsbt_plan* p, const GroupTable& g, int dir, const __half* in_hi, const __half* in_lo,
+                        const float* scale, int out_mode, void* out0, void* out1, const float2* phase, int* sched,
+                        void* scratch, cudaStream_t st) {
     const FtcData* f = p->ftc;
+    if (!f) {
+        set_error("interval-scheme contraction needs a plan built with DSBT_PLAN_FAST_SPLIT");
+        return DSBT_ERR_UNSUPPORTED;
+    }
+    if (g.total_lines == 0) return DSBT_OK;
+    if (out_mode == kOutPlanarSplit || out_mode == kOutUserC64) {
+        for (int i = 0; i < g.ngroups; ++i) {
+            if ((g.line0[i] & 1) || ((g.line0[i + 1] - g.line0[i]) & 1)) {
+                set_error("complex output needs whole channels per group");
+                return DSBT_ERR_INVALID;
+            }
+        }
+    }
     const int N = p->N, NA = dir > 0 ? f->NAF : f->NA;   // augmented width of this direction
     const size_t R = (size_t)g.total_lines;
-    float* aug_hi = scratch;
-    float* aug_lo = scratch + R * NA;
+    __half* aug_hi = reinterpret_cast<__half*>(scratch);
+    __half* aug_lo = aug_hi + R * NA;
     CUtensorMap in_h, in_l, aug_h, aug_l;
-    int rc = encode_tmap_f32_sw128(&in_h, in_hi, R, N, BBOX, BK);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&in_l, in_lo, R, N, BBOX, BK);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&aug_h, aug_hi, R, NA, BBOX, BK);
-    if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&aug_l, aug_lo, R, NA, BBOX, BK);
+    int rc = encode_tmap_f16_sw128(&in_h, in_hi, R, N, BBOX, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&in_l, in_lo, R, N, BBOX, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&aug_h, aug_hi, R, NA, BBOX, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&aug_l, aug_lo, R, NA, BBOX, BK);
     if (rc != DSBT_OK) return rc;
-    const EpiArgs ep_aug{kOutAugSplit, aug_hi, aug_lo, nullptr, 0, NA};
-    const EpiArgs ep_out{out_mode, out0, out1, phase, p->knl != nullptr, N};
+    const EpiArgs ep_aug{kOutAugSplit, aug_hi, aug_lo, nullptr, 0, NA, nullptr};
+    const EpiArgs ep_out{out_mode, out0, out1, phase, p->knl != nullptr, N, scale};
     if (dir > 0) {
         rc = launch_ftc(p, g, kMoments, f->tm_qT_hi, f->tm_qT_lo, in_h, in_l, f->tm_qT_hi, f->tm_qT_lo, in_h, in_l,
-                        ep_aug, sched, st);
+                        f->tm_qT_hi, f->tm_qT_lo, ep_aug, sched, st);
         if (rc == DSBT_OK)
-            rc = launch_ftc(p, g, kEval, p->tm_T_hi, p->tm_T_lo, in_h, in_l, f->tm_bA_hi, f->tm_bA_lo, aug_h, aug_l,
-                            ep_out, sched, st);
+            rc = launch_ftc(p, g, kEval, f->tm_D_hi, f->tm_D_lo, in_h, in_l, f->tm_bA_hi, f->tm_bA_lo, aug_h, aug_l,
+                            f->tm_D_hi, f->tm_D_lo, ep_out, sched, st);
     } else {
         rc = launch_ftc(p, g, kWeights, f->tm_bT_hi, f->tm_bT_lo, in_h, in_l, f->tm_bT_hi, f->tm_bT_lo, in_h, in_l,
-                        ep_aug, sched, st);
+                        f->tm_bT_hi, f->tm_bT_lo, ep_aug, sched, st);
         if (rc == DSBT_OK)
-            rc = launch_ftc(p, g, kLeafOut, p->tm_Tt_hi, p->tm_Tt_lo, in_h, in_l, f->tm_qA_hi, f->tm_qA_lo, aug_h,
-                            aug_l, ep_out, sched, st);
+            rc = launch_ftc(p, g, kLeafOut, f->tm_Dt_hi, f->tm_Dt_lo, in_h, in_l, f->tm_qA_hi, f->tm_qA_lo, aug_h,
+                            aug_l, f->tm_C_hi, f->tm_C_lo, ep_out, sched, st);
     }
     return rc;
 }

@@ -421,21 +421,10 @@ unsigned tc_default_spin_limit() { return tc::kSpinLimit; }
 
 int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi,
                     const float* in_lo, int out_mode, float* out0, float* out1, const float2* phase,
-                    int* sched, cudaStream_t st, float* fast_scratch) {
+                    int* sched, cudaStream_t st) {
     if (!p->has_tmaps) {
         set_error("split-TF32 path needs a plan built with DSBT_PLAN_TF32X3");
         return DSBT_ERR_UNSUPPORTED;
-    }
-    if (p->ftc && fast_scratch && g.total_lines > 0) {
-        if (out_mode == kOutPlanarSplit || out_mode == kOutUserC64) {
-            for (int i = 0; i < g.ngroups; ++i) {
-                if ((g.line0[i] & 1) || ((g.line0[i + 1] - g.line0[i]) & 1)) {
-                    set_error("complex output needs whole channels per group");
-                    return DSBT_ERR_INVALID;
-                }
-            }
-        }
-        return contract_tf32_fast(p, g, dir, in_hi, in_lo, out_mode, out0, out1, phase, sched, fast_scratch, st);
     }
     const int N = p->N;
     TileSpace ts;
@@ -464,8 +453,8 @@ int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const floa
     if (rc == DSBT_OK) rc = encode_tmap_f32_sw128(&tb_lo, in_lo, (uint64_t)g.total_lines, N, BBOX, BK);
     if (rc != DSBT_OK) return rc;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    // set before every launch: the limit belongs to the current device
-    DSBT_CUDA_TRY(cudaFuncSetAttribute(k_contract_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    rc = ensure_smem((const void*)k_contract_tf32x3, smem);
+    if (rc) return rc;
     int dev = 0, nsm = 0;
     DSBT_CUDA_TRY(cudaGetDevice(&dev));
     DSBT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

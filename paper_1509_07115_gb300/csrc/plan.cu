@@ -347,14 +347,14 @@ extern "C" int dsbt_plan_create(int N, double r_max, int l_max, int flags, void*
     DSBT_CHECK_ARG(l_max >= 0 && l_max <= 64, "dsbt_plan_create: l_max=%d not in [0, 64]", l_max);
     DSBT_CHECK_ARG(n0_of(l_max) <= N, "dsbt_plan_create: l_max too large for N");
     DSBT_CHECK_ARG(r_max > 0.0 && isfinite(r_max), "dsbt_plan_create: r_max must be positive");
-    DSBT_CHECK_ARG((flags & (DSBT_PLAN_FP64 | DSBT_PLAN_TF32X3)) != 0 &&
+    DSBT_CHECK_ARG((flags & (DSBT_PLAN_FP64 | DSBT_PLAN_TF32X3 | DSBT_PLAN_FAST_SPLIT)) != 0 &&
                        (flags & ~(DSBT_PLAN_FP64 | DSBT_PLAN_TF32X3 | DSBT_PLAN_KCORR | DSBT_PLAN_FAST64 |
-                                  DSBT_PLAN_FAST_TF32)) == 0,
+                                  DSBT_PLAN_FAST_SPLIT)) == 0,
                    "dsbt_plan_create: flags=%d invalid", flags);
     DSBT_CHECK_ARG(!(flags & DSBT_PLAN_FAST64) || ((flags & DSBT_PLAN_FP64) && fast_supported(N)),
                    "dsbt_plan_create: DSBT_PLAN_FAST64 needs DSBT_PLAN_FP64 and N / 64 a power of two");
-    DSBT_CHECK_ARG(!(flags & DSBT_PLAN_FAST_TF32) || ((flags & DSBT_PLAN_TF32X3) && ftc_supported(N)),
-                   "dsbt_plan_create: DSBT_PLAN_FAST_TF32 needs DSBT_PLAN_TF32X3 and N / 128 a power of two");
+    DSBT_CHECK_ARG(!(flags & DSBT_PLAN_FAST_SPLIT) || ftc_supported(N),
+                   "dsbt_plan_create: DSBT_PLAN_FAST_SPLIT needs N / 128 a power of two");
     cudaStream_t st = (cudaStream_t)stream;
     dsbt_plan* p = new (std::nothrow) dsbt_plan();
     if (!p) {
@@ -409,7 +409,7 @@ extern "C" int dsbt_plan_create(int N, double r_max, int l_max, int flags, void*
     }
     int rc = plan_build_factors(p, st);
     if (rc == DSBT_OK && (flags & DSBT_PLAN_FAST64)) rc = fast_build(p, st);
-    if (rc == DSBT_OK && (flags & DSBT_PLAN_FAST_TF32)) rc = ftc_build(p, st);
+    if (rc == DSBT_OK && (flags & DSBT_PLAN_FAST_SPLIT)) rc = ftc_build(p, st);
     if (rc == DSBT_OK && (flags & DSBT_PLAN_TF32X3)) {
         const uint64_t rows = (uint64_t)L * N;
         rc = encode_tmap_f32_sw128(&p->tm_T_hi, p->Thi, rows, N, 128, 32);

@@ -4,6 +4,7 @@
 #include <vector>
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 
@@ -40,7 +41,7 @@ struct dsbt_plan {
     double* knl;
     // hierarchical FP64 data of DSBT_PLAN_FAST64 (fast64.cu), else nullptr
     dsbt::FastData* fast;
-    // interval bases and projections of DSBT_PLAN_FAST_TF32 (fast_tf32.cu), else nullptr
+    // interval bases and projections of DSBT_PLAN_FAST_SPLIT (fast_split.cu), else nullptr
     dsbt::FtcData* ftc;
     unsigned* status;          // device status word (kStatusOk / kStatusTimeout)
     unsigned spin_limit;       // polls of a bounded mbarrier wait in the tensor-core kernels
@@ -90,6 +91,9 @@ void kcorr_table(int N, double r_max, int l_max, std::vector<double>& out);
 
 int encode_tmap_f32_sw128(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
                           uint32_t box_rows, uint32_t box_cols);
+// The same over FP16 elements (box_cols = 64).
+int encode_tmap_f16_sw128(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
+                          uint32_t box_rows, uint32_t box_cols);
 
 // ---- sine/cosine transforms (dct.cu)
 // Forward F_l for every channel of the group table; writes planar lines.
@@ -99,6 +103,10 @@ int dct_forward_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const do
                     double* out, cudaStream_t st);
 int dct_forward_f32(const dsbt_plan* p, const GroupTable& g, bool cplx, const float* in,
                     float* out_hi, float* out_lo, cudaStream_t st);
+//   FP16 split: out_hi/out_lo = FP16 pair of 2^e f per channel (||2^e psi|| in
+//   [2^12, 2^13)), scale[line] = 2^-e
+int dct_forward_f16(const dsbt_plan* p, const GroupTable& g, bool cplx, const float* in, __half* out_hi,
+                    __half* out_lo, float* scale, cudaStream_t st);
 // Inverse F_l^T from planar lines to the caller's layout.
 int dct_inverse_f64(const dsbt_plan* p, const GroupTable& g, bool cplx, const double* in,
                     double* out, cudaStream_t st);
@@ -124,14 +132,19 @@ int contract_f64_fast(const dsbt_plan* p, const GroupTable& g, int dir, const do
 // Orthonormal basis [len][64] of the polynomials of degree < min(64, len) on
 // the points x_t = (2t+1)/len - 1 (Arnoldi with two Gram-Schmidt passes).
 void poly_basis(int len, std::vector<double>& Q);
-// DSBT_PLAN_FAST_TF32 (fast_tf32.cu)
+// DSBT_PLAN_FAST_SPLIT (fast_split.cu)
 bool ftc_supported(int N);
 int ftc_build(dsbt_plan* p, cudaStream_t st);
 void ftc_free(dsbt_plan* p);
 size_t ftc_scratch_bytes(const dsbt_plan* p, size_t lines);
-int contract_tf32_fast(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi, const float* in_lo,
-                       int out_mode, float* out0, float* out1, const float2* phase, int* sched, float* scratch,
-                       cudaStream_t st);
+// The interval-scheme contraction on FP16 pairs of planar lines scaled per
+// line by 1 / scale[line] (see dct_forward_f16).  Output modes: kOutAugSplit is
+// internal; kOutPlanarSplit writes the scaled FP16 pair (out0 hi, out1 lo);
+// kOutUserC64 / kOutUserF32 / kOutPlanarF32 write unscaled FP32.  `scratch`
+// holds ftc_scratch_bytes of the call's lines.
+int contract_split_fast(const dsbt_plan* p, const GroupTable& g, int dir, const __half* in_hi, const __half* in_lo,
+                        const float* scale, int out_mode, void* out0, void* out1, const float2* phase, int* sched,
+                        void* scratch, cudaStream_t st);
 
 // ---- angular rule of the TDSE (tdse.cu), shared with tdse3d.cu
 // L-point Gauss-Legendre nodes x (cos theta) and weights w.
@@ -145,10 +158,8 @@ void tdse_angular_rows(int L, int m, const std::vector<double>& x, const std::ve
 // B operand: TF32 split lines [lines][N] (hi, lo).  `sched` is a device int
 // (zeroed here before the launch) for the dynamic tile scheduler.  Output modes:
 enum OutMode { kOutUserC64 = 0, kOutUserF32 = 1, kOutPlanarF32 = 2, kOutPlanarSplit = 3 };
-// With a DSBT_PLAN_FAST_TF32 plan and `fast_scratch` (ftc_scratch_bytes of
-// the call's lines) the contraction runs the interval scheme of fast_tf32.cu.
 int contract_tf32x3(const dsbt_plan* p, const GroupTable& g, int dir, const float* in_hi,
                     const float* in_lo, int out_mode, float* out0, float* out1,
-                    const float2* phase, int* sched, cudaStream_t st, float* fast_scratch = nullptr);
+                    const float2* phase, int* sched, cudaStream_t st);
 
 }  // namespace dsbt

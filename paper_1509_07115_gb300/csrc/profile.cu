@@ -5,7 +5,9 @@
 // of CUDA events on the launch stream around the launch.  dsbt_profile_read
 // synchronises on the recorded events and sums their elapsed times per kernel.
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "plan.cuh"
@@ -29,6 +31,19 @@ struct Rec {
 std::vector<Rec> g_recs;
 
 }  // namespace
+
+int ensure_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;   // (kernel, device) -> bytes set
+    int dev = 0;
+    DSBT_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& have = done[{fn, dev}];
+    if (have >= bytes) return DSBT_OK;
+    DSBT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    have = bytes;
+    return DSBT_OK;
+}
 
 ProfScope::ProfScope(int kid, cudaStream_t st) : kid_(kid), st_(st), a_(nullptr), b_(nullptr) {
     g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -350,7 +350,7 @@ inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 int potential(const dsbt_tdse* t, const double2* x, double2* y, const double* E, int eidx, double ht,
               const double2* aux, double gscale, double* gacc, cudaStream_t st) {
     const size_t smem = (size_t)kLMax * kLMax * sizeof(double) + 3 * (size_t)kLMax * TI * sizeof(double2);
-    DSBT_CUDA_TRY(cudaFuncSetAttribute(k_tdse_potential, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (int rc0 = ensure_smem((const void*)k_tdse_potential, smem)) return rc0;
     ProfScope ps(kKTdsePot, st);
     k_tdse_potential<<<(t->N + TI - 1) / TI, 256, smem, st>>>(x, y, t->P, t->V, t->rr, t->eta, t->L, t->N, E,
                                                               eidx, ht, aux, gscale, gacc);
@@ -386,7 +386,7 @@ int step_velocity(const dsbt_tdse* t, const double2* in, double2* out, double2* 
     if (rc) return rc;
     {
         const size_t smem = (size_t)kLMax * kLMax * sizeof(double) + 2 * (size_t)kLMax * TI * sizeof(double2);
-        DSBT_CUDA_TRY(cudaFuncSetAttribute(k_tdse_velocity, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (int rc0 = ensure_smem((const void*)k_tdse_velocity, smem)) return rc0;
         ProfScope ps(kKTdseAng, st);
         k_tdse_velocity<<<(t->N + TI - 1) / TI, 256, smem, st>>>(c, t->P, t->eta, t->plan->knl, t->plan->dk,
                                                                  t->L, t->N, A, idx, tau, t->m0);

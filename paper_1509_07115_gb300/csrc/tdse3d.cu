@@ -257,7 +257,7 @@ int potential3d(const dsbt_tdse3d* t, const double2* x, double2* y, const double
                 cudaStream_t st) {
     const size_t smem = smem3d(t);
     if (smem > 48 * 1024)
-        DSBT_CUDA_TRY(cudaFuncSetAttribute(k_tdse3d_potential, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (int rc0 = ensure_smem((const void*)k_tdse3d_potential, smem)) return rc0;
     ProfScope ps(kKTdsePot, st);
     k_tdse3d_potential<<<(t->N + TI3 - 1) / TI3, 256, smem, st>>>(x, y, t->P, t->map, t->V, t->rr, t->eta, t->L,
                                                                   t->M, t->N, t->nchan, F, fidx, ht);
@@ -268,7 +268,7 @@ int potential3d(const dsbt_tdse3d* t, const double2* x, double2* y, const double
 int velocity3d(const dsbt_tdse3d* t, double2* c, const double* A, int aidx, cudaStream_t st) {
     const size_t smem = smem3d(t);
     if (smem > 48 * 1024)
-        DSBT_CUDA_TRY(cudaFuncSetAttribute(k_tdse3d_velocity, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (int rc0 = ensure_smem((const void*)k_tdse3d_velocity, smem)) return rc0;
     ProfScope ps(kKTdseAng, st);
     k_tdse3d_velocity<<<(t->N + TI3 - 1) / TI3, 256, smem, st>>>(c, t->P, t->map, t->lch, t->eta, t->plan->knl,
                                                                  t->plan->dk, t->L, t->M, t->N, t->nchan, A, aidx,

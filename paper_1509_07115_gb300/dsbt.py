@@ -21,7 +21,8 @@ DSBT_PLAN_FP64 = 1
 DSBT_PLAN_TF32X3 = 2
 DSBT_PLAN_KCORR = 4
 DSBT_PLAN_FAST64 = 8
-DSBT_PLAN_FAST_TF32 = 16
+DSBT_PLAN_FAST_SPLIT = 16
+DSBT_PLAN_FAST_TF32 = DSBT_PLAN_FAST_SPLIT   # earlier name of the same flag
 DTYPES = {torch.float64: 1, torch.complex128: 2, torch.float32: 3, torch.complex64: 4}
 
 _lib = None
@@ -130,11 +131,11 @@ class Plan:
     """A DSBT plan: T_l factors for l = 0..l_max on an N-point grid."""
 
     def __init__(self, N: int, r_max: float, l_max: int, fp64: bool = True, tf32x3: bool = True,
-                 kcorr: bool = False, fast64: bool = False, fast_tf32: bool = False):
+                 kcorr: bool = False, fast64: bool = False, fast_split: bool = False, fast_tf32: bool = False):
         lib = load()
         flags = (DSBT_PLAN_FP64 if fp64 else 0) | (DSBT_PLAN_TF32X3 if tf32x3 else 0) | \
             (DSBT_PLAN_KCORR if kcorr else 0) | (DSBT_PLAN_FAST64 if fast64 else 0) | \
-            (DSBT_PLAN_FAST_TF32 if fast_tf32 else 0)
+            (DSBT_PLAN_FAST_SPLIT if (fast_split or fast_tf32) else 0)
         h = ctypes.c_void_p()
         _check(lib.dsbt_plan_create(int(N), float(r_max), int(l_max), flags, _stream(), ctypes.byref(h)),
                "dsbt_plan_create")

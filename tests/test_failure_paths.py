@@ -46,7 +46,7 @@ def test_device_wait_timeout_is_reported_and_recovered(lib, fast):
     N, lmax = 1024, 9
     counts = [2 * l + 1 for l in range(lmax + 1)]
     x = inputs.gaussian_sum(31, N, 0.1, counts, dtype=torch.complex64, device="cuda")
-    p = lib.Plan(N, 0.1 * N, lmax, fp64=False, tf32x3=True, fast_tf32=fast)
+    p = lib.Plan(N, 0.1 * N, lmax, fp64=False, tf32x3=True, fast_split=fast)
     ref = p.forward_grouped(counts, x)
     torch.cuda.synchronize()
     assert p.device_status() == 0
@@ -60,7 +60,7 @@ def test_device_wait_timeout_is_reported_and_recovered(lib, fast):
     assert p.device_status() == 0
     assert torch.equal(again, ref)
     p.close()
-    fresh = lib.Plan(N, 0.1 * N, lmax, fp64=False, tf32x3=True, fast_tf32=fast)
+    fresh = lib.Plan(N, 0.1 * N, lmax, fp64=False, tf32x3=True, fast_split=fast)
     assert torch.equal(fresh.forward_grouped(counts, x), ref)
     assert fresh.device_status() == 0
     fresh.close()

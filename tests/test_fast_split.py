@@ -1,9 +1,9 @@
-"""Split-TF32 tensor-core contractions through the interval scheme
-(DSBT_PLAN_FAST_TF32, csrc/fast_tf32.cu): the near band of T_l per 128-row
-leaf plus the far field through 64 basis functions per used dyadic interval.
-Same results as the FP64 contraction with the dense T_l within the split-TF32
-bar (1e-6 of the channel norm), for every l (odd l carries the m = 0 weight)
-and grids of 2 to 32 leaves."""
+"""Split-precision tensor-core contractions through the interval scheme
+(DSBT_PLAN_FAST_SPLIT, csrc/fast_split.cu): the near band of T_l per 128-row
+leaf plus the far field through 64 basis functions per used dyadic interval,
+operands as scaled FP16 pairs.  Same results as the FP64 contraction with the
+dense T_l within the split-precision bar (1e-6 of the channel norm), for every
+l (odd l carries the m = 0 weight) and grids of 2 to 64 leaves."""
 import ctypes
 
 import numpy as np
@@ -13,13 +13,32 @@ import torch
 from paper_1509_07115_gb300 import dsbt, inputs
 
 
-def test_fast_tf32_flag_rules():
+def test_fast_split_flag_rules():
     lib = dsbt.load()
     h = ctypes.c_void_p()
-    assert lib.dsbt_plan_create(1024, 102.4, 4, dsbt.DSBT_PLAN_FAST_TF32 | dsbt.DSBT_PLAN_FP64, None,
-                                ctypes.byref(h)) == -1          # needs the split-TF32 factors
-    assert lib.dsbt_plan_create(768, 76.8, 4, dsbt.DSBT_PLAN_FAST_TF32 | dsbt.DSBT_PLAN_TF32X3, None,
+    assert lib.dsbt_plan_create(768, 76.8, 4, dsbt.DSBT_PLAN_FAST_SPLIT | dsbt.DSBT_PLAN_TF32X3, None,
                                 ctypes.byref(h)) == -1          # N / 128 = 6, not a power of two
+    assert lib.dsbt_plan_create(768, 76.8, 4, dsbt.DSBT_PLAN_FAST_SPLIT, None,
+                                ctypes.byref(h)) == -1
+
+
+@pytest.mark.gpu
+def test_fast_plan_without_dense_split_factors(lib):
+    """DSBT_PLAN_FAST_TF32 alone (no dense split copies of T_l, no FP64
+    factors kept) serves FP32 calls; FP64 calls are refused."""
+    N, lmax = 1024, 12
+    counts = [2] * (lmax + 1)
+    x = inputs.gaussian_sum(3, N, 0.1, counts)
+    nrm = np.linalg.norm(x, axis=1)
+    full = lib.Plan(N, 0.1 * N, lmax, fp64=True, tf32x3=False)
+    ref = full.forward_grouped(counts, torch.from_numpy(x).cuda()).cpu().numpy()
+    full.close()
+    p = lib.Plan(N, 0.1 * N, lmax, fp64=False, tf32x3=False, fast_split=True)
+    b = p.forward_grouped(counts, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    assert rel(b, ref, nrm) < 1e-6
+    with pytest.raises(lib.DSBTError):
+        p.forward_grouped(counts, torch.from_numpy(x).cuda())
+    p.close()
 
 
 def rel(a, b, nrm):
@@ -35,12 +54,12 @@ def counts_for(lmax):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("N", [256, 1024, 4096])
-def test_fast_tf32_matches_fp64(lib, N):
+def test_fast_split_matches_fp64(lib, N):
     r_max, lmax, tau = N * 0.1, 63, 0.05
     counts = counts_for(lmax)
     x = inputs.gaussian_sum(70 + N, N, r_max / N, counts)
     nrm = np.linalg.norm(x, axis=1)
-    plan = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, fast_tf32=True)
+    plan = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, fast_split=True)
     x128 = torch.from_numpy(x).cuda()
     x64 = x128.to(torch.complex64)
     ref_b = plan.forward_grouped(counts, x128).cpu().numpy()
@@ -57,7 +76,7 @@ def test_fast_tf32_matches_fp64(lib, N):
 
 
 @pytest.mark.gpu
-def test_fast_tf32_error_close_to_dense_tf32(lib):
+def test_fast_split_error_close_to_dense_tf32(lib):
     """The interval scheme adds no error of its own beyond the split-TF32
     rounding: its deviation from FP64 stays within 2x of the dense split-TF32
     contraction's on the same input."""
@@ -66,7 +85,7 @@ def test_fast_tf32_error_close_to_dense_tf32(lib):
     x = inputs.gaussian_sum(91, N, r_max / N, counts)
     nrm = np.linalg.norm(x, axis=1)
     x128 = torch.from_numpy(x).cuda()
-    fast = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, fast_tf32=True)
+    fast = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, fast_split=True)
     dense = lib.Plan(N, r_max, lmax, fp64=False, tf32x3=True)
     ref = fast.forward_grouped(counts, x128).cpu().numpy()
     e_fast = rel(fast.forward_grouped(counts, x128.to(torch.complex64)).cpu().numpy(), ref, nrm)
@@ -77,14 +96,14 @@ def test_fast_tf32_error_close_to_dense_tf32(lib):
 
 
 @pytest.mark.gpu
-def test_fast_tf32_real_lines_and_edges(lib):
+def test_fast_split_real_lines_and_edges(lib):
     """Real (DSBT_F32) channels, l_max = 64 (the largest: right slots of the
     completion rows at degree 63) and the largest grid N = 8192 (64 leaves,
     six levels) against the FP64 path of the same plan."""
     for N, lmax, counts in ((8192, 8, [2, 1, 1, 1, 1, 1, 1, 1, 2]),
                             (512, 64, [1] * 60 + [2, 1, 1, 2, 3])):
         r_max = N * 0.1
-        plan = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, fast_tf32=True)
+        plan = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, fast_split=True)
         x = inputs.gaussian_sum(5 + N, N, r_max / N, counts).real.copy()
         nrm = np.linalg.norm(x, axis=1)
         ref = plan.forward_grouped(counts, torch.from_numpy(x).cuda()).cpu().numpy()
@@ -96,13 +115,13 @@ def test_fast_tf32_real_lines_and_edges(lib):
 
 
 @pytest.mark.gpu
-def test_fast_tf32_host_streamed_matches_device(lib):
+def test_fast_split_host_streamed_matches_device(lib):
     """The host-streamed kinetic step (chunks that cut l groups) runs the
     interval scheme on every chunk: identical to the device call."""
     N, r_max, lmax = 1024, 102.4, 20
     counts = [3] * (lmax + 1)
     x = inputs.gaussian_sum(17, N, r_max / N, counts).astype(np.complex64)
-    plan = lib.Plan(N, r_max, lmax, fp64=False, tf32x3=True, fast_tf32=True)
+    plan = lib.Plan(N, r_max, lmax, fp64=False, tf32x3=True, fast_split=True)
     dev = plan.kinetic_grouped(counts, torch.from_numpy(x).cuda(), 0.05).cpu().numpy()
     xh = torch.from_numpy(x).pin_memory()
     out = plan.kinetic_grouped_host(counts, xh, 0.05, chunks=5)
@@ -112,7 +131,7 @@ def test_fast_tf32_host_streamed_matches_device(lib):
 
 
 @pytest.mark.gpu
-def test_fast_tf32_kinetic_with_corrected_momenta(lib):
+def test_fast_split_kinetic_with_corrected_momenta(lib):
     """DSBT_PLAN_KCORR with the interval scheme: the kinetic phase per (l, n)
     (the corrected momenta of Sec. 3) in the forward-rows epilogue, against the
     FP64 path of the same plan."""
@@ -120,7 +139,7 @@ def test_fast_tf32_kinetic_with_corrected_momenta(lib):
     counts = [2] * (lmax + 1)
     x = inputs.gaussian_sum(23, N, r_max / N, counts)
     nrm = np.linalg.norm(x, axis=1)
-    plan = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, kcorr=True, fast_tf32=True)
+    plan = lib.Plan(N, r_max, lmax, fp64=True, tf32x3=True, kcorr=True, fast_split=True)
     ref = plan.kinetic_grouped(counts, torch.from_numpy(x).cuda(), tau).cpu().numpy()
     k = plan.kinetic_grouped(counts, torch.from_numpy(x.astype(np.complex64)).cuda(), tau).cpu().numpy()
     plan.close()

@@ -120,8 +120,8 @@ def check_groups(counts, ls, x_np_of, got_of, ref_of, tol, what):
 @pytest.fixture(scope="module")
 def precision_plan(lib):
     """The bench's plan: N = 4096, r_max = 409.6, l <= 63, interval-scheme
-    split contraction (DSBT_PLAN_FAST_TF32), no FP64 factors."""
-    p = lib.Plan(4096, 409.6, 63, fp64=False, tf32x3=True, fast_tf32=True)
+    split contraction (DSBT_PLAN_FAST_SPLIT), no FP64 factors."""
+    p = lib.Plan(4096, 409.6, 63, fp64=False, tf32x3=True, fast_split=True)
     yield p
     p.close()
 
@@ -190,7 +190,7 @@ def test_largest_grid_l64_forward_inverse(lib):
     counts = [1] * (lmax + 1)
     for l in (0, 1, 2, 31, 32, 63, 64):
         counts[l] = 3
-    p = lib.Plan(N, 819.2, lmax, fp64=False, tf32x3=True, fast_tf32=True)
+    p = lib.Plan(N, 819.2, lmax, fp64=False, tf32x3=True, fast_split=True)
     x = inputs.gaussian_sum(4, N, 0.1, counts, dtype=torch.complex64, device="cuda")
     b = p.forward_grouped(counts, x)
     sets = [leaf_rows(N, l, 500 + l, per_leaf=2) for l in range(lmax + 1)]

@@ -17,7 +17,7 @@ def test_kcorr_flag_needs_a_factor_set():
     lib = dsbt.load()
     h = ctypes.c_void_p()
     assert lib.dsbt_plan_create(256, 25.6, 4, dsbt.DSBT_PLAN_KCORR, None, ctypes.byref(h)) == -1
-    assert lib.dsbt_plan_create(256, 25.6, 4, 16 | dsbt.DSBT_PLAN_FP64, None, ctypes.byref(h)) == -1   # unknown bit
+    assert lib.dsbt_plan_create(256, 25.6, 4, 1024 | dsbt.DSBT_PLAN_FP64, None, ctypes.byref(h)) == -1   # unknown bit
 
 
 @pytest.mark.gpu

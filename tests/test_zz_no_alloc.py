@@ -4,7 +4,7 @@ cudaMalloc's implicit synchronisation, fixed memory budgets).  It must give the
 results of dsbt_forward_grouped, which takes a caller workspace, on repeated
 calls (the static scratch keeps the previous call's contents), for every kind
 of plan (the dense factors, and the interval schemes of DSBT_PLAN_FAST64 and
-DSBT_PLAN_FAST_TF32, whose extra scratch also lives in the static array), and
+DSBT_PLAN_FAST_SPLIT, whose extra scratch also lives in the static array), and
 reject requests larger than its 64 MiB scratch before launching anything.
 
 Collected last (file name) so that a stop-at-first-failure run has already run
@@ -20,7 +20,7 @@ from paper_1509_07115_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = {torch.complex128: 1e-12, torch.complex64: 1e-6}
-PLANS = {"dense": {}, "fast64": {"fast64": True}, "fast_tf32": {"fast_tf32": True}}
+PLANS = {"dense": {}, "fast64": {"fast64": True}, "fast_split": {"fast_split": True}}
 
 
 @pytest.mark.parametrize("kind", sorted(PLANS))
