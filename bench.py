@@ -642,7 +642,10 @@ def main():
             dist.barrier()
 
     fast = not args.dense
-    plan = dsbt.Plan(N, R_MAX, L_MAX, fp64=not args.no_fp64, tf32x3=not fast, fast_split=fast)
+    # FP64 factors with the O(N l log N) FP64 scheme for the FP64 comparison leg
+    # (needs N / 64 a power of two)
+    fast64 = (not args.no_fp64) and (N // 64) & (N // 64 - 1) == 0 and N % 64 == 0
+    plan = dsbt.Plan(N, R_MAX, L_MAX, fp64=not args.no_fp64, tf32x3=not fast, fast_split=fast, fast64=fast64)
     x = inputs.gaussian_sum(rank_seed(rank), N, DR, counts, dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
     ws = plan.workspace(nchan, torch.complex64)
@@ -789,16 +792,20 @@ def main():
         n1 = sum(counts1)
         x64 = inputs.gaussian_sum(200 + rank, N, DR, counts1, dtype=torch.complex128, device=dev)
         y64 = torch.empty_like(x64)
-        ws64 = torch.empty(plan.workspace_bytes(n1, torch.complex128), dtype=torch.uint8, device=dev)
-        plan.kinetic_grouped(counts1, x64, TAU, out=y64, workspace=ws64)
-        torch.cuda.synchronize()
-        f_steps = 2
-        e0.record(stream)
-        for _ in range(f_steps):
-            plan.kinetic_grouped(counts1, x64, TAU, out=y64, workspace=ws64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        f_ms = e0.elapsed_time(e1) / f_steps
+
+        def time_fp64(p):
+            ws64 = torch.empty(p.workspace_bytes(n1, torch.complex128), dtype=torch.uint8, device=dev)
+            p.kinetic_grouped(counts1, x64, TAU, out=y64, workspace=ws64)
+            torch.cuda.synchronize()
+            f_steps = 2
+            e0.record(stream)
+            for _ in range(f_steps):
+                p.kinetic_grouped(counts1, x64, TAU, out=y64, workspace=ws64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / f_steps, ws64
+
+        f_ms, ws64 = time_fp64(plan)   # FAST64 when the grid allows it
         x32 = x64.to(torch.complex64)
         y32 = torch.empty_like(x32)
         ws32 = torch.empty(plan.workspace_bytes(n1, torch.complex64), dtype=torch.uint8, device=dev)
@@ -809,13 +816,26 @@ def main():
         err_rt = ((y32.to(torch.complex128) - y64).abs().amax(dim=1) / nrm).max().item()
         err_fw = ((b32.to(torch.complex128) - b64).abs().amax(dim=1) / nrm).max().item()
         drift = ((torch.linalg.vector_norm(b32.to(torch.complex128), dim=1) - nrm) / nrm).abs().max().item()
+        del ws64, ws32, b64, b32
         fp64_value = 2 * n1 / (f_ms * 1e-3)
+        dense_ms = None
+        if rank == 0 and fast64 and args.workload == "precision":
+            dplan = dsbt.Plan(N, R_MAX, L_MAX, fp64=True, tf32x3=False)   # dense FP64 T_l
+            dense_ms, wsd = time_fp64(dplan)
+            dplan.close()
+            del wsd
+            torch.cuda.empty_cache()
         if rank == 0:
             line["fp64_gpu"] = {"value": fp64_value, "unit": UNIT,
+                                "scheme": "O(N l log N) FP64 (DSBT_PLAN_FAST64)" if fast64 else "dense FP64",
                                 "sample": "batch 1 of the same workload (4096 complex128 channels)",
-                                "ms_per_step": f_ms, "speedup_of_split_tf32": value / world / fp64_value,
-                                "split_tf32_max_rel_err": {"kinetic_round_trip": err_rt, "forward": err_fw,
-                                                           "norm_drift": drift}}
+                                "ms_per_step": f_ms, "speedup_of_split_path": value / world / fp64_value,
+                                "split_max_rel_err": {"kinetic_round_trip": err_rt, "forward": err_fw,
+                                                      "norm_drift": drift}}
+            if dense_ms is not None:
+                line["fp64_gpu"]["dense_fp64"] = {"value": 2 * n1 / (dense_ms * 1e-3), "unit": UNIT,
+                                                  "ms_per_step": dense_ms,
+                                                  "speedup_of_split_path": value / world / (2 * n1 / (dense_ms * 1e-3))}
 
     # ---------------------------------------------------------- dense split-TF32 contraction (context)
     if rank == 0 and fast and args.workload == "precision":

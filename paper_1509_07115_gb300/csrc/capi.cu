@@ -76,6 +76,24 @@ __global__ void k_split_f16(const float* __restrict__ in, int cplx, int N, __hal
     }
 }
 
+// Interleaved complex128 channels <-> planar real lines (channel c -> lines
+// 2c, 2c+1), for the O(N l log N) FP64 contraction, which works on planar lines.
+__global__ void k_deinterleave64(const double2* __restrict__ in, double* __restrict__ lines, int N, long long total) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const long long c = i / N, n = i % N;
+    const double2 v = in[i];
+    lines[(2 * c) * N + n] = v.x;
+    lines[(2 * c + 1) * N + n] = v.y;
+}
+
+__global__ void k_interleave64(const double* __restrict__ lines, double2* __restrict__ out, int N, long long total) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const long long c = i / N, n = i % N;
+    out[i] = make_double2(lines[(2 * c) * N + n], lines[(2 * c + 1) * N + n]);
+}
+
 // exp(-i k~_n^2 tau / 2) on the unified momentum grid (Eq. (65)): storage index
 // k of parity class par (0: even l, n = k + 1; 1: odd l, n = k) maps to
 // k~ = n dk, except the odd-l coefficient n = 0, which takes k~_N = N dk.
@@ -240,7 +258,16 @@ int run_forward(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
     if (is_fp64(dtype)) {
         rc = dct_forward_f64(p, g, cplx, (const double*)in, w.f64a, st);
         if (rc) return rc;
-        return contract_f64(p, g, +1, w.f64a, 0, (double*)out, cplx ? 1 : 0, nullptr, st);
+        if (p->fast && cplx) {   // O(N l log N) contraction on planar lines, then interleave
+            rc = contract_f64(p, g, +1, w.f64a, 0, w.f64b, 0, nullptr, st, w.fast);
+            if (rc) return rc;
+            const long long total = (long long)g.chan0[g.ngroups] * p->N;
+            ProfScope ps(kKSplit, st);
+            k_interleave64<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(w.f64b, (double2*)out, p->N, total);
+            DSBT_CUDA_TRY(cudaGetLastError());
+            return DSBT_OK;
+        }
+        return contract_f64(p, g, +1, w.f64a, 0, (double*)out, cplx ? 1 : 0, nullptr, st, w.fast);
     }
     if (p->ftc) {   // interval scheme on FP16 pairs
         rc = dct_forward_f16(p, g, cplx, (const float*)in, w.h_hi_a, w.h_lo_a, w.scale, st);
@@ -261,7 +288,18 @@ int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
     Workspace w = carve(p, ws, g.chan0[g.ngroups], dtype);
     int rc;
     if (is_fp64(dtype)) {
-        rc = contract_f64(p, g, -1, (const double*)in, cplx ? 1 : 0, w.f64a, 0, nullptr, st);
+        const double* src = (const double*)in;
+        if (p->fast && cplx) {   // planar lines for the O(N l log N) contraction
+            const long long total = (long long)g.chan0[g.ngroups] * p->N;
+            {
+                ProfScope ps(kKSplit, st);
+                k_deinterleave64<<<(unsigned)((total + 255) / 256), 256, 0, st>>>((const double2*)in, w.f64b, p->N,
+                                                                                   total);
+            }
+            DSBT_CUDA_TRY(cudaGetLastError());
+            src = w.f64b;
+        }
+        rc = contract_f64(p, g, -1, src, (cplx && src == in) ? 1 : 0, w.f64a, 0, nullptr, st, w.fast);
         if (rc) return rc;
         return dct_inverse_f64(p, g, cplx, w.f64a, (double*)out, st);
     }

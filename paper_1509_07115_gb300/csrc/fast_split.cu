@@ -78,6 +78,7 @@ constexpr int STAGES = 2;
 // dense kernel, leaves no TMEM columns for a second buffer).
 constexpr int KC = 1;
 constexpr int EPI_WARPS = 8;
+constexpr int WC = BN_MAX / 2;                     // accumulator columns per epilogue warp
 constexpr int QS = 4;                              // tile-queue slots
 constexpr int A_BYTES = BM * BK * 2;               // 16 KiB
 constexpr int B_BYTES = BN_MAX * BK * 2;           // 32 KiB
@@ -497,20 +498,20 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 store_row = slot >= 0;
                 row = slot * KP + (trow & (KP - 1));
             }
-            const int cbase = tl.ct * BN_MAX + half * 128;
-            const int ncols = min(128, nl - cbase);
-            const int nch = (tl.nmma > half * 128) ? ((min(tl.nmma - half * 128, 128) + 31) >> 5) : 0;
-            const uint32_t tl_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
-            float acc[128];
+            const int cbase = tl.ct * BN_MAX + half * WC;
+            const int ncols = min(WC, nl - cbase);
+            const int nch = (tl.nmma > half * WC) ? ((min(tl.nmma - half * WC, WC) + 31) >> 5) : 0;
+            const uint32_t tl_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * WC);
+            float acc[WC];
 #pragma unroll
-            for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+            for (int j = 0; j < WC; ++j) acc[j] = 0.f;
             bool ok = true;
             for (int c0 = 0; c0 < nkb; c0 += fs.kc) {
                 const int buf = gch & 1;
                 if (!warp_all(mbar_wait(&acc_full[buf], (gch >> 1) & 1, abort_flag, status, spin))) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
+                for (int ch = 0; ch < WC / 32; ++ch) {
                     if (ch < nch) {
                         float v[32];
                         tmem_ld32(tl_addr + (uint32_t)buf * 256 + ch * 32, v);
@@ -531,7 +532,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 __half* o1 = reinterpret_cast<__half*>(ep.out1);
                 const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
 #pragma unroll
-                for (int j = 0; j < 128; ++j) {
+                for (int j = 0; j < WC; ++j) {
                     if (j < ncols) {
                         __half h, lo;
                         split_f16(acc[j] * kFacUnscale, h, lo);
@@ -549,7 +550,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 float2* o = reinterpret_cast<float2*>(ep.out0);
                 const size_t chan_base = (size_t)gt.chan0[tl.g] + (cbase >> 1);
 #pragma unroll
-                for (int j = 0; j < 128; j += 2)
+                for (int j = 0; j < WC; j += 2)
                     if (j < ncols) {
                         const float u = ep.scale[line_base + j] * kFacUnscale;
                         o[(chan_base + (j >> 1)) * N + row] = make_float2(acc[j] * u, acc[j + 1] * u);
@@ -558,13 +559,13 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 float* o = reinterpret_cast<float*>(ep.out0);
                 const size_t base = ep.mode == kOutUserF32 ? (size_t)gt.chan0[tl.g] + cbase : line_base;
 #pragma unroll
-                for (int j = 0; j < 128; ++j)
+                for (int j = 0; j < WC; ++j)
                     if (j < ncols) o[(base + j) * N + row] = acc[j] * (ep.scale[line_base + j] * kFacUnscale);
             } else {   // kOutPlanarSplit: complex pairs with optional phase, FP16 pair, still scaled
                 __half* o0 = reinterpret_cast<__half*>(ep.out0);
                 __half* o1 = reinterpret_cast<__half*>(ep.out1);
 #pragma unroll
-                for (int j = 0; j < 128; j += 2) {
+                for (int j = 0; j < WC; j += 2) {
                     if (j < ncols) {
                         const float re = (acc[j] * ph.x - acc[j + 1] * ph.y) * kFacUnscale;
                         const float im = (acc[j] * ph.y + acc[j + 1] * ph.x) * kFacUnscale;

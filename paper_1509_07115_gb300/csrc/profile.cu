@@ -17,7 +17,7 @@ namespace dsbt {
 namespace {
 
 const char* kNames[kNumKernels] = {"plan_build", "dct_forward", "dct_inverse", "contract_f64",
-                                   "contract_tf32x3", "kinetic_phase", "split_tf32", "tdse_potential",
+                                   "contract_tf32x3", "kinetic_phase", "split_lines", "tdse_potential",
                                    "tdse_angular", "tdse_reduce"};
 
 std::atomic<long long> g_launches{0};

@@ -247,3 +247,39 @@ def test_plan_rows_large_grids(lib, N):
         ref = T_rows(N, l, rows)
         assert np.abs(T - ref).max() < 1e-14, (N, l, np.abs(T - ref).max())
     p.close()
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_c2_fast64_forward_inverse_against_oracle(lib, cplx):
+    """The FP64 configuration (N = 2048, r_max = 204.8, l <= 31, all m: 1024
+    complex128 channels; or their real parts as FP64 lines) on a
+    DSBT_PLAN_FAST64 plan, whose O(N l log N) contraction also serves the
+    caller's interleaved and real layouts: sampled forward rows and sparse
+    inverse inputs against the oracle at 1e-12, round trip on every channel."""
+    N, lmax = 2048, 31
+    counts = inputs.all_m_counts(lmax)
+    x = inputs.gaussian_sum(1, N, 0.1, counts)
+    if not cplx:
+        x = x.real.copy()
+        x /= np.linalg.norm(x, axis=1, keepdims=True)
+    p = lib.Plan(N, 204.8, lmax, tf32x3=False, fast64=True)
+    b = p.forward_grouped(counts, torch.from_numpy(x).cuda())
+    y = p.inverse_grouped(counts, b).cpu().numpy()
+    bn = b.cpu().numpy()
+    sets = [leaf_rows(N, l, 800 + l, per_leaf=2) for l in range(lmax + 1)]
+    bs = sparse_batch(21, counts, N, sets, torch.complex128, "cuda")
+    if not cplx:
+        bs = bs.real.contiguous()
+    psi = p.inverse_grouped(counts, bs).cpu().numpy()
+    bs = bs.cpu().numpy()
+    p.close()
+    assert worst(y, x, np.linalg.norm(x, axis=1)) < TOL64
+    for l, c0, c in group_slices(counts):
+        if l not in (0, 1, 2, 15, 30, 31):
+            continue
+        sel = [c0, c0 + c - 1]
+        rows = sample_rows(N, l, 900 + l)
+        assert worst(bn[sel][:, rows], fwd_rows(l, x[sel], rows), np.linalg.norm(x[sel], axis=1)) < TOL64, l
+        S = sets[l]
+        ref = oracle.apply(_F(N, l % 2), bs[sel][:, S] @ T_rows(N, l, S), transpose=True)
+        assert worst(psi[sel], ref, np.linalg.norm(bs[sel], axis=1)) < TOL64, l
