@@ -495,16 +495,18 @@ def tdse_leg(dsbt, inputs, torch, dev, fp64_peak):
 
 # ---------------------------------------------------------------- uneven batch leg
 
-def batch_leg(dsbt, inputs, torch, dev, steps, warmup, peak):
+def batch_leg(dsbt, inputs, torch, dev, steps, warmup, peak, scheme="interval"):
     """64 transforms, N ~ U{512..8192 step 256}, l_max ~ U{8..64} (seed 0), 2l+1
     complex64 Gaussian-sum channels per l; one kinetic step of the whole batch
-    per graph replay (factors shared across grids, one persistent contraction
-    launch per direction, tile order and width autotuned)."""
+    per graph replay.  scheme "dense": factors shared across grids, one
+    persistent contraction launch per direction, tile order and width
+    autotuned; "interval": one interval-scheme plan per distinct grid, the
+    transforms' grouped calls forked over internal streams inside the graph."""
     work = inputs.grouped_workload(0)
     trs = [(N, lm, [2 * l + 1 for l in range(lm + 1)]) for N, lm in work]
     dr = 0.1
     t0 = time.perf_counter()
-    b = dsbt.Batch(trs, dr, autotune=True)
+    b = dsbt.Batch(trs, dr, autotune=True, scheme=scheme)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     xs = [inputs.gaussian_sum(300 + k, N, dr, c, dtype=torch.complex64, device=dev).reshape(-1)
@@ -531,9 +533,8 @@ def batch_leg(dsbt, inputs, torch, dev, steps, warmup, peak):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     nchan = sum(sum(c) for _, _, c in trs)
-    flop = sum(6.0 * N * N * sum(c) for N, _, c in trs)   # per contraction launch (one direction)
+    flop = sum(6.0 * N * N * sum(c) for N, _, c in trs)   # dense count, per contraction launch (one direction)
     n_c, ms_c = prof.get("contract_tf32x3", (1, 0.0))
-    ach = flop / (ms_c / n_c * 1e-3) / 1e12
     info = b.info()
     # sampled parity: one mid-size transform against the single-plan path
     k = max(range(len(trs)), key=lambda i: (trs[i][0] <= 2048, trs[i][0]))
@@ -546,20 +547,28 @@ def batch_leg(dsbt, inputs, torch, dev, steps, warmup, peak):
     err = ((yk - ref).abs().amax(dim=1) / torch.linalg.vector_norm(xk, dim=1)).max().item()
     p.close()
     b.close()
-    return {"config": "64 transforms, N ~ U{512..8192 step 256}, l_max ~ U{8..64} (seed 0), 2l+1 complex64 "
-                      "Gaussian-sum channels per l, dr = 0.1; one graph replay = kinetic step of the batch",
-            "channels": nchan, "value": 2 * nchan / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-            "steps": steps, "build_s": build_s, "autotune": info,
-            "kernels_ms_direct_call": {kk: v[1] for kk, v in prof.items()},
-            "roofline_contract": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": ach / peak, "flop_per_launch": flop,
-                                  "note": "dense N^2 flops of the contraction this batch runs (the interval "
-                                          "scheme's count would be several times lower)",
-                                  "peak_source": "measured tf32 matmul (burst, this run)"},
-            "hbm": {"algorithmic_bytes_per_step": 2 * 16.0 * sum(N * sum(c) for N, _, c in trs),
-                    "frac_whole_step": 2 * 16.0 * sum(N * sum(c) for N, _, c in trs) / (ms * 1e-3) / 1e9
-                    / load_peaks()[0]["hbm_gbs"]},
-            "max_rel_err_vs_single_plan": err}
+    del x, y
+    torch.cuda.empty_cache()
+    bytes_step = 2 * 16.0 * sum(N * sum(c) for N, _, c in trs)
+    out = {"scheme": scheme,
+           "config": "64 transforms, N ~ U{512..8192 step 256}, l_max ~ U{8..64} (seed 0), 2l+1 complex64 "
+                     "Gaussian-sum channels per l, dr = 0.1; one graph replay = kinetic step of the batch",
+           "channels": nchan, "value": 2 * nchan / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+           "steps": steps, "build_s": build_s,
+           "kernels_ms_direct_call": {kk: v[1] for kk, v in prof.items()},
+           "hbm": {"algorithmic_bytes_per_step": bytes_step,
+                   "frac_whole_step": bytes_step / (ms * 1e-3) / 1e9 / load_peaks()[0]["hbm_gbs"]},
+           "max_rel_err_vs_single_plan": err}
+    if scheme == "dense":
+        ach = flop / (ms_c / n_c * 1e-3) / 1e12
+        out["autotune"] = info
+        out["roofline_contract"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                    "frac": ach / peak, "flop_per_launch": flop,
+                                    "note": "dense N^2 flops of the contraction this batch runs",
+                                    "peak_source": "measured tf32 matmul (burst, this run)"}
+    else:
+        out["note"] = ("kernel times of the direct call are summed over the internal streams, which overlap")
+    return out
 
 
 # ---------------------------------------------------------------- GPU leg
@@ -849,7 +858,10 @@ def main():
     if rank == 0 and not args.no_batch and args.workload == "precision":
         plan.close()
         torch.cuda.empty_cache()
-        line["uneven_batch"] = batch_leg(dsbt, inputs, torch, dev, max(3, args.steps // 3), 2, probes["tf32_tflops"])
+        dense_b = batch_leg(dsbt, inputs, torch, dev, max(3, args.steps // 3), 2, probes["tf32_tflops"], "dense")
+        line["uneven_batch"] = batch_leg(dsbt, inputs, torch, dev, max(3, args.steps // 3), 2,
+                                         probes["tf32_tflops"], "interval")
+        line["uneven_batch"]["dense_persistent"] = dense_b
 
     # ---------------------------------------------------------- CPU oracle baseline
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -81,19 +81,21 @@ extern "C" {
                               Extra memory: 8 B x 64 x (l_max+1) x N x log2(N/64)
                               of plan data; FP64 workspaces grow by about
                               8 B x 128 x (N/64) per line. */
-#define DSBT_PLAN_FAST_SPLIT 16 /* N / 128 a power of two: split-precision
-                              contractions (all DSBT_F32 / DSBT_C64 calls) in
-                              O(N l log N) work on the tensor cores: near band of
-                              T_l per 128-row leaf (diagonal blocks), far field
-                              through 64 basis functions per used dyadic interval
-                              (the rows of T_l are polynomials of degree l - 1 in m
-                              left of the diagonal, Eqs. (38)-(42)), operands as
-                              FP16 pairs.  Needs l_max <= 64 (always true); with
-                              or without DSBT_PLAN_TF32X3 (whose dense copies it
-                              does not use).  Extra memory: about
-                              8 B x 64 x (l_max+1) x N x (N/128 - 1) of plan data
-                              (4.2 GB at N = 4096, l_max = 63) and
-                              4 B x 64 x (N/128 - 1 + log2(N/128)) per line of
+#define DSBT_PLAN_FAST_SPLIT 16 /* any plan grid (N / 128 leaves of 128 rows):
+                              split-precision contractions (all DSBT_F32 /
+                              DSBT_C64 calls) in O(N l log N) work on the tensor
+                              cores: near band of T_l per leaf (diagonal blocks),
+                              far field through 64 basis functions per dyadic
+                              interval of the column tree (the rows of T_l are
+                              polynomials of degree l - 1 in m left of the
+                              diagonal, Eqs. (38)-(42)), operands as FP16 pairs.
+                              Needs l_max <= 64 (always true); with or without
+                              DSBT_PLAN_TF32X3 (whose dense copies it does not
+                              use).  Extra memory: about
+                              8 B x 64 x (l_max+1) x N x (log2(N/128) + 4) of plan
+                              data (1.2 GB at N = 4096, l_max = 63) plus
+                              16 B x 64 x N x N/128 for the interval bases, and
+                              4 B x 64 x (N/128 + log2(N/128)) per line of
                               workspace. */
 #define DSBT_PLAN_FAST_TF32 DSBT_PLAN_FAST_SPLIT /* earlier name of the same flag */
 
@@ -444,6 +446,22 @@ typedef struct dsbt_batch dsbt_batch;
  * Synchronises the stream. */
 DSBT_API int dsbt_batch_create(int ntrans, const int* N, const int* l_max, const int* counts, double dr,
                                int autotune_tiles, void* stream, dsbt_batch** out);
+
+/* dsbt_batch_create with flags: DSBT_BATCH_AUTOTUNE (as autotune_tiles above)
+ * and DSBT_BATCH_INTERVAL: instead of the shared dense factors and the
+ * persistent launch, one DSBT_PLAN_FAST_SPLIT plan per distinct grid (l_max
+ * the largest of the transforms on that grid), and each transform one
+ * grouped call on its grid's plan (the O(N l log N) interval scheme), spread
+ * over four internal streams that fork from and join back into the caller's
+ * stream; dsbt_batch_capture_kinetic captures the whole fork-join graph.  Plan
+ * data about 8 B x 64 x (l_max+1) x N x (log2(N/128) + 4) per distinct grid
+ * plus a workspace per internal stream.  On such a batch dsbt_batch_info
+ * reports order -1 and width 0, and dsbt_batch_set_tiles is unsupported.
+ * Same results as the dense batch within the split-precision bar. */
+#define DSBT_BATCH_AUTOTUNE 1
+#define DSBT_BATCH_INTERVAL 2
+DSBT_API int dsbt_batch_create_ex(int ntrans, const int* N, const int* l_max, const int* counts, double dr,
+                                  int flags, void* stream, dsbt_batch** out);
 DSBT_API int dsbt_batch_destroy(dsbt_batch* batch);
 
 /* Complex elements of one batch array, the chosen tile order and width, and

@@ -546,6 +546,16 @@ struct dsbt_batch {
     int order = 3, ci = 2;                 // selected order and width index (autotuned)
     float tune_ms[dsbt::kOrders][3] = {{0}};
     std::vector<dsbt::GroupTable> gtab;   // per transform, for the sine/cosine kernels
+    // interval scheme (DSBT_BATCH_INTERVAL): one DSBT_PLAN_FAST_SPLIT plan per
+    // distinct grid, transforms spread over internal streams
+    bool interval = false;
+    std::vector<dsbt_plan*> fplans;        // per distinct grid (index cidx)
+    std::vector<std::vector<int>> pcounts; // per transform, padded to its plan's l_max + 1
+    std::vector<int> stream_of;            // per transform
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;        // per stream, plus the fork event at the end
+    std::vector<unsigned char*> sws;       // per stream workspace
+    std::vector<size_t> sws_bytes;
 };
 
 namespace dsbt {
@@ -553,6 +563,10 @@ namespace {
 
 void batch_free(dsbt_batch* b) {
     if (!b) return;
+    for (auto* p : b->fplans) plan_release(p);
+    for (auto* w : b->sws) cudaFree(w);
+    for (auto e : b->joins) cudaEventDestroy(e);
+    for (auto s_ : b->streams) cudaStreamDestroy(s_);
     if (b->shared) plan_release(b->shared);
     for (auto* p : b->tw) plan_release(p);
     cudaFree(b->comp);
@@ -797,7 +811,31 @@ int launch_contract(const dsbt_batch* b, int order, int ci, int dir, int mode, f
     return DSBT_OK;
 }
 
+// Interval scheme: each transform is one grouped call on its grid's plan, in
+// the batch's internal streams (forked from and joined back into st, so a
+// capture of st takes the whole fork-join graph).
+int run_batch_interval(const dsbt_batch* b, int kinetic, double tau, const float* in, float* out, cudaStream_t st) {
+    const int S = (int)b->streams.size();
+    cudaEvent_t fork = b->joins[S];
+    DSBT_CUDA_TRY(cudaEventRecord(fork, st));
+    for (int k = 0; k < S; ++k) DSBT_CUDA_TRY(cudaStreamWaitEvent(b->streams[k], fork, 0));
+    for (int t = 0; t < b->T; ++t) {
+        if (b->nchan[t] == 0) continue;
+        const int k = b->stream_of[t];
+        const int rc = grouped_device_call(kinetic ? 2 : 0, b->fplans[b->cidx[t]], b->pcounts[t].data(), DSBT_C64,
+                                               tau, in + 2 * b->uoff[t], out + 2 * b->uoff[t], b->sws[k],
+                                               b->sws_bytes[k], b->streams[k]);
+        if (rc) return rc;
+    }
+    for (int k = 0; k < S; ++k) {
+        DSBT_CUDA_TRY(cudaEventRecord(b->joins[k], b->streams[k]));
+        DSBT_CUDA_TRY(cudaStreamWaitEvent(st, b->joins[k], 0));
+    }
+    return DSBT_OK;
+}
+
 int run_batch(const dsbt_batch* b, int kinetic, double tau, const float* in, float* out, cudaStream_t st) {
+    if (b->interval) return run_batch_interval(b, kinetic, tau, in, out, st);
     int rc;
     if (kinetic) {
         ProfScope ps(kKPhase, st);
@@ -936,16 +974,90 @@ extern "C" int dsbt_batch_tiles(int ntrans, const int* N, const int* l_max, cons
     return DSBT_OK;
 }
 
+namespace dsbt {
+namespace {
+
+// The interval-scheme batch: plans per distinct grid, streams, workspaces.
+int create_interval(dsbt_batch* b, cudaStream_t st) {
+    b->interval = true;
+    const int ND = (int)b->dN.size();
+    std::vector<int> lmax_d(ND, 0);
+    for (int t = 0; t < b->T; ++t) lmax_d[b->cidx[t]] = std::max(lmax_d[b->cidx[t]], b->lmax[t]);
+    for (int d = 0; d < ND; ++d) {
+        dsbt_plan* p = nullptr;
+        const int rc = dsbt_plan_create(b->dN[d], b->dN[d] * b->dr, lmax_d[d], DSBT_PLAN_FAST_SPLIT, st, &p);
+        if (rc) return rc;
+        b->fplans.push_back(p);
+    }
+    // transforms by decreasing work, each to the least loaded stream
+    const int S = std::min(4, b->T);
+    std::vector<int> ord(b->T);
+    for (int t = 0; t < b->T; ++t) ord[t] = t;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+        return (double)b->N[x] * b->nchan[x] > (double)b->N[y] * b->nchan[y];
+    });
+    std::vector<double> load(S, 0.0);
+    std::vector<size_t> need(S, 0);
+    b->stream_of.assign(b->T, 0);
+    b->pcounts.resize(b->T);
+    for (int t : ord) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        b->stream_of[t] = k;
+        load[k] += (double)b->N[t] * b->nchan[t];
+        const dsbt_plan* p = b->fplans[b->cidx[t]];
+        b->pcounts[t].assign(p->l_max + 1, 0);
+        for (int l = 0; l <= b->lmax[t]; ++l) b->pcounts[t][l] = b->counts[b->counts_off[t] + l];
+        need[k] = std::max(need[k], dsbt_workspace_size(p, b->nchan[t], DSBT_C64));
+    }
+    for (int k = 0; k < S; ++k) {
+        cudaStream_t sk = nullptr;
+        DSBT_CUDA_TRY(cudaStreamCreateWithFlags(&sk, cudaStreamNonBlocking));
+        b->streams.push_back(sk);
+        unsigned char* w = nullptr;
+        if (cudaMalloc((void**)&w, need[k] + 256) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("dsbt_batch_create: workspace allocation of %zu bytes failed", need[k]);
+            return DSBT_ERR_NOMEM;
+        }
+        b->sws.push_back(w);
+        b->sws_bytes.push_back(need[k] + 256);
+    }
+    for (int k = 0; k <= S; ++k) {
+        cudaEvent_t e = nullptr;
+        DSBT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->joins.push_back(e);
+    }
+    DSBT_CUDA_TRY(cudaStreamSynchronize(st));
+    return DSBT_OK;
+}
+
+}  // namespace
+}  // namespace dsbt
+
 extern "C" int dsbt_batch_create(int ntrans, const int* N, const int* l_max, const int* counts, double dr,
                                  int autotune_tiles, void* stream, dsbt_batch** out) {
+    return dsbt_batch_create_ex(ntrans, N, l_max, counts, dr, autotune_tiles ? DSBT_BATCH_AUTOTUNE : 0, stream, out);
+}
+
+extern "C" int dsbt_batch_create_ex(int ntrans, const int* N, const int* l_max, const int* counts, double dr,
+                                    int flags, void* stream, dsbt_batch** out) {
     DSBT_CHECK_ARG(out != nullptr, "dsbt_batch_create: NULL argument");
+    DSBT_CHECK_ARG((flags & ~(DSBT_BATCH_AUTOTUNE | DSBT_BATCH_INTERVAL)) == 0, "dsbt_batch_create: flags=%d invalid",
+                   flags);
     *out = nullptr;
+    const int autotune_tiles = (flags & DSBT_BATCH_AUTOTUNE) != 0;
     cudaStream_t st = (cudaStream_t)stream;
     dsbt_batch* b = new (std::nothrow) dsbt_batch();
     if (!b) return DSBT_ERR_NOMEM;
     {
         const int rc0 = batch_describe(b, ntrans, N, l_max, counts, dr);
         if (rc0) { delete b; return rc0; }
+    }
+    if (flags & DSBT_BATCH_INTERVAL) {
+        const int rc1 = create_interval(b, st);
+        if (rc1) { batch_free(b); return rc1; }
+        *out = b;
+        return DSBT_OK;
     }
     // shared factors at (N_max, l_max)
     int rc = dsbt_plan_create(b->Nmax, b->Nmax * dr, b->L - 1, DSBT_PLAN_TF32X3, stream, &b->shared);
@@ -1089,8 +1201,8 @@ extern "C" int dsbt_batch_info(const dsbt_batch* b, long long* total_elems, int*
                                float* tune_ms) {
     DSBT_CHECK_ARG(b != nullptr, "dsbt_batch_info: NULL batch");
     if (total_elems) *total_elems = b->total_elems;
-    if (order) *order = b->order;
-    if (bn_cap) *bn_cap = kBnCaps[b->ci];
+    if (order) *order = b->interval ? -1 : b->order;
+    if (bn_cap) *bn_cap = b->interval ? 0 : kBnCaps[b->ci];
     if (tune_ms)
         for (int o = 0; o < kOrders; ++o)
             for (int c = 0; c < 3; ++c) tune_ms[o * 3 + c] = b->tune_ms[o][c];
@@ -1099,6 +1211,10 @@ extern "C" int dsbt_batch_info(const dsbt_batch* b, long long* total_elems, int*
 
 extern "C" int dsbt_batch_set_tiles(dsbt_batch* b, int order, int bn_cap, void* stream) {
     DSBT_CHECK_ARG(b != nullptr, "dsbt_batch_set_tiles: NULL batch");
+    if (b->interval) {
+        set_error("dsbt_batch_set_tiles: a batch on the interval scheme has no tile list");
+        return DSBT_ERR_UNSUPPORTED;
+    }
     DSBT_CHECK_ARG(order >= 0 && order < kOrders, "dsbt_batch_set_tiles: order %d not in 0..%d", order, kOrders - 1);
     int ci = -1;
     for (int c = 0; c < 3; ++c)

@@ -90,7 +90,9 @@ constexpr int FL = 128;                            // leaf = output row tile
 constexpr int KP = 64;                             // basis functions per interval (>= l_max)
 constexpr int MAX_LEVELS = 6;                      // N / 128 <= 64 (plans have N <= 8192)
 constexpr int MAX_SLOTS = (1 << MAX_LEVELS) - 1;
-constexpr int MAX_SEGS = MAX_LEVELS + 3;
+constexpr int MAX_RIGHT = 2 * MAX_LEVELS;          // intervals covering the columns right of leaf 0
+constexpr int MAX_FSLOTS = MAX_SLOTS + MAX_RIGHT;
+constexpr int MAX_SEGS = MAX_RIGHT + 2;
 
 enum Mode { kMoments = 0, kEval = 1, kWeights = 2, kLeafOut = 3 };
 
@@ -99,11 +101,15 @@ struct FtcSpace {
     int kc;                        // K blocks per main-accumulator chunk
     int RT;                        // row tiles of this launch
     int KB;                        // K blocks of N
-    int nleaf, levels, nslots;
-    int nslots_f;                  // forward slots: the used ones, then the right intervals (j, 1)
+    int nleaf, levels, nslots;     // leaves of 128 (any count 2..64), tree levels, used slots
+    int nslots_f;                  // forward slots: the used ones, then the right intervals
+    int nright;                    // right intervals (rj, ri): the columns right of leaf 0
+    int rj[MAX_RIGHT], ri[MAX_RIGHT];
+    int FW;                        // slots per row of the compact B table: max(levels, nright)
+    int a_oob;                     // a row past the end of the MOMENTS / WEIGHTS A operand
     int slot_off[MAX_LEVELS + 1];  // first slot of level j
     int npairs;                    // MOMENTS / WEIGHTS tiles: slot pairs (b = -1: single slot)
-    int pair_a[MAX_SLOTS], pair_b[MAX_SLOTS];
+    int pair_a[MAX_FSLOTS], pair_b[MAX_FSLOTS];
     int total;                     // tiles
     int order[kMaxGroups];         // group visited at position i
     int t0[kMaxGroups + 1];        // first tile of position i
@@ -133,13 +139,20 @@ __device__ __forceinline__ Tile decode(const FtcSpace& fs, const GroupTable& gt,
     return tl;
 }
 
+// Intervals of level j that start inside the grid (the last may end past it).
+__host__ __device__ inline int n_at(const FtcSpace& fs, int j) { return (fs.nleaf + (1 << j) - 1) >> j; }
+
+// Interval (j, i) is "used" (has a slot) when i is even and its right sibling
+// starts inside the grid: the rows of that sibling take it as a far interval.
+__host__ __device__ inline bool used(const FtcSpace& fs, int j, int i) { return (i & 1) == 0 && i + 1 < n_at(fs, j); }
+
 // slot s -> (level j, interval i); slots s >= nslots (forward only) are the
-// right intervals (j, 1), j = s - nslots, that cover the columns right of
-// leaf 0 for the completion rows.
+// right intervals (rj, ri) that cover the columns right of leaf 0 for the
+// completion rows.
 __host__ __device__ inline void slot_ji(const FtcSpace& fs, int s, int& j, int& i) {
     if (s >= fs.nslots) {
-        j = s - fs.nslots;
-        i = 1;
+        j = fs.rj[s - fs.nslots];
+        i = fs.ri[s - fs.nslots];
         return;
     }
     j = 0;
@@ -154,21 +167,24 @@ __device__ __forceinline__ void aug_range(const FtcSpace& fs, int s, int& k0, in
     slot_ji(fs, s, j, i);
     const int lb = (FL << j) / BK;
     k0 = (fs.mode == kMoments) ? i * lb : (i + 1) * lb;
-    k1 = k0 + lb;
+    k1 = min(k0 + lb, fs.KB);   // a sibling at the right edge may end past the grid
 }
 
 // K blocks of one tile: segments [k0, k1) of operand source src (1 near: the
 // lines against a diagonal 128 x 128 block of T_l / T_l^T or, for MOMENTS and
 // WEIGHTS, the basis rows; 2 far: the augmented lines against B / QA; 3: the
 // completion block, T_l rows < 64 transposed, against the lines' K block 0).
+// The B operand's K block is kb; the A operand's is ak + (kb - k0) (A tables
+// that are stored compactly index K differently from the lines).
 struct Segs {
     int n;
-    int src[MAX_SEGS], k0[MAX_SEGS], k1[MAX_SEGS];
-    __device__ __forceinline__ void add(int s, int a, int b) {
+    int src[MAX_SEGS], k0[MAX_SEGS], k1[MAX_SEGS], ak[MAX_SEGS];
+    __device__ __forceinline__ void add(int s, int a, int b, int a_k) {
         if (b > a) {
             src[n] = s;
             k0[n] = a;
             k1[n] = b;
+            ak[n] = a_k;
             ++n;
         }
     }
@@ -177,18 +193,20 @@ struct Segs {
         for (int q = 0; q < n; ++q) c += k1[q] - k0[q];
         return c;
     }
-    __device__ __forceinline__ void at(int i, int& s, int& kb) const {
+    __device__ __forceinline__ void at(int i, int& s, int& kb, int& akb) const {
         for (int q = 0; q < n; ++q) {
             const int len = k1[q] - k0[q];
             if (i < len) {
                 s = src[q];
                 kb = k0[q] + i;
+                akb = ak[q] + i;
                 return;
             }
             i -= len;
         }
         s = 1;
         kb = 0;
+        akb = 0;
     }
 };
 
@@ -197,6 +215,7 @@ __device__ __forceinline__ Segs segments(const FtcSpace& fs, int l, int rt) {
     sg.n = 0;
     const int nx = n_extra(l);
     const int nf = (l + BK - 1) / BK;   // far K blocks per slot (basis functions k < l)
+    constexpr int SB = KP / BK;         // K blocks per slot
     if (fs.mode == kMoments || fs.mode == kWeights) {
         // the K ranges of the tile's two slots are dyadic intervals: nested
         // (one segment, the larger) or disjoint (two segments)
@@ -204,39 +223,42 @@ __device__ __forceinline__ Segs segments(const FtcSpace& fs, int l, int rt) {
         aug_range(fs, fs.pair_a[rt], a0, a1);
         if (fs.pair_b[rt] >= 0) aug_range(fs, fs.pair_b[rt], b0, b1);
         if (b1 <= b0 || (b0 >= a0 && b1 <= a1)) {
-            sg.add(1, a0, a1);
+            sg.add(1, a0, a1, a0);
         } else if (a0 >= b0 && a1 <= b1) {
-            sg.add(1, b0, b1);
+            sg.add(1, b0, b1, b0);
         } else {
-            sg.add(1, a0, a1);
-            sg.add(1, b0, b1);
+            sg.add(1, a0, a1, a0);
+            sg.add(1, b0, b1, b0);
         }
     } else if (fs.mode == kEval) {
+        // A: the leaf's diagonal block (K blocks 0, 1) and the compact B table,
+        // whose slot q of a row is the far interval at level q (regular rows)
+        // or right interval q (completion rows)
         if (rt == 0) {
             // leaf 0: near band; the completion rows (polynomials of degree < l
             // in m as well) take the columns right of it through the right slots
-            sg.add(1, 0, FL / BK);
+            sg.add(1, 0, FL / BK, 0);
             if (nx > 0)
-                for (int j = 0; j < fs.levels; ++j) {
-                    const int s = fs.nslots + j;
-                    sg.add(2, s * (KP / BK), s * (KP / BK) + nf);
+                for (int q = 0; q < fs.nright; ++q) {
+                    const int s = fs.nslots + q;
+                    sg.add(2, s * SB, s * SB + nf, q * SB);
                 }
         } else {
             for (int j = 0; j < fs.levels; ++j)
                 if ((rt >> j) & 1) {
                     const int s = fs.slot_off[j] + (((rt >> j) - 1) >> 1);
-                    sg.add(2, s * (KP / BK), s * (KP / BK) + nf);
+                    sg.add(2, s * SB, s * SB + nf, j * SB);
                 }
-            sg.add(1, rt * (FL / BK), (rt + 1) * (FL / BK));
+            sg.add(1, rt * (FL / BK), (rt + 1) * (FL / BK), 0);
         }
-    } else {   // kLeafOut
-        if (rt > 0 && nx > 0) sg.add(3, 0, 1);   // completion rows n < n0_l (storage rows < 64)
-        sg.add(1, rt * (FL / BK), (rt + 1) * (FL / BK));
+    } else {   // kLeafOut: A = the transposed diagonal block, the completion block, QA (dense)
+        if (rt > 0 && nx > 0) sg.add(3, 0, 1, 0);   // completion rows n < n0_l (storage rows < 64)
+        sg.add(1, rt * (FL / BK), (rt + 1) * (FL / BK), 0);
         for (int j = 0; j < fs.levels; ++j) {
             const int i = rt >> j;
-            if ((i & 1) == 0 && i + 1 < (fs.nleaf >> j)) {
+            if (used(fs, j, i)) {
                 const int s = fs.slot_off[j] + (i >> 1);
-                sg.add(2, s * (KP / BK), s * (KP / BK) + nf);
+                sg.add(2, s * SB, s * SB + nf, s * SB);
             }
         }
     }
@@ -256,12 +278,10 @@ __device__ __forceinline__ int seg_count(const FtcSpace& fs, int l, int rt) {
         if (a0 >= b0 && a1 <= b1) return b1 - b0;
         return (a1 - a0) + (b1 - b0);
     }
-    if (fs.mode == kEval) return rt == 0 ? FL / BK + (nx > 0 ? fs.levels * nf : 0) : __popc(rt) * nf + FL / BK;
+    if (fs.mode == kEval) return rt == 0 ? FL / BK + (nx > 0 ? fs.nright * nf : 0) : __popc(rt) * nf + FL / BK;
     int c = ((rt > 0 && nx > 0) ? 1 : 0) + FL / BK;
-    for (int j = 0; j < fs.levels; ++j) {
-        const int i = rt >> j;
-        if ((i & 1) == 0 && i + 1 < (fs.nleaf >> j)) c += nf;
-    }
+    for (int j = 0; j < fs.levels; ++j)
+        if (used(fs, j, rt >> j)) c += nf;
     return c;
 }
 
@@ -360,12 +380,22 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 const bool pair = aug && fs.pair_b[tl.rt] >= 0;
                 const uint32_t bytes = 2 * a_bytes * (pair ? 2 : 1) + 2 * nbox * BBOX * BK * 2;
                 int arow1, arow2 = 0;
+                int ra0 = 0, ra1 = 0, rb0 = 0, rb1 = 0;   // own K ranges of the two slots
+                if (aug) {
+                    aug_range(fs, fs.pair_a[tl.rt], ra0, ra1);
+                    if (pair) aug_range(fs, fs.pair_b[tl.rt], rb0, rb1);
+                }
                 if (fs.mode == kMoments) {
                     arow1 = ((l & 1) * fs.nslots_f + fs.pair_a[tl.rt]) * KP;
                     if (pair) arow2 = ((l & 1) * fs.nslots_f + fs.pair_b[tl.rt]) * KP;
-                } else if (fs.mode == kWeights) {
-                    arow1 = (l * fs.nslots + fs.pair_a[tl.rt]) * KP;
-                    if (pair) arow2 = (l * fs.nslots + fs.pair_b[tl.rt]) * KP;
+                } else if (fs.mode == kWeights) {   // compact BT: rows (l, level, k)
+                    int j, i;
+                    slot_ji(fs, fs.pair_a[tl.rt], j, i);
+                    arow1 = (l * fs.levels + j) * KP;
+                    if (pair) {
+                        slot_ji(fs, fs.pair_b[tl.rt], j, i);
+                        arow2 = (l * fs.levels + j) * KP;
+                    }
                 } else {
                     arow1 = (l * fs.nleaf + tl.rt) * BM;   // diagonal block of leaf rt
                     arow2 = (fs.mode == kEval ? l : (l & 1)) * N + tl.rt * BM;
@@ -373,8 +403,8 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 const int brow = gt.line0[tl.g] + tl.ct * BN_MAX;
                 const int nkb = sg.count();
                 for (int i = 0; i < nkb; ++i) {
-                    int src, kb;
-                    sg.at(i, src, kb);
+                    int src, kb, akb;
+                    sg.at(i, src, kb, akb);
                     if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                     unsigned char* sb = stage_base + stage * STAGE_BYTES;
                     mbar_expect_tx(&full[stage], bytes);
@@ -384,25 +414,25 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                     const CUtensorMap* bh = src == 2 ? &tmB2_hi : &tmB1_hi;
                     const CUtensorMap* bl = src == 2 ? &tmB2_lo : &tmB1_lo;
                     if (aug) {   // slot a -> A rows 0..63, slot b -> rows 64..127
-                        tma_load_2d(sb, ah, &full[stage], kb * BK, arow1);
-                        tma_load_2d(sb + A_BYTES, al, &full[stage], kb * BK, arow1);
+                        // a slot's rows are loaded only on its own K range: elsewhere
+                        // (the other slot of a disjoint pair) the load starts past the
+                        // table's last row and the copy fills zeros
+                        const int ya = (kb >= ra0 && kb < ra1) ? arow1 : fs.a_oob;
+                        tma_load_2d(sb, ah, &full[stage], kb * BK, ya);
+                        tma_load_2d(sb + A_BYTES, al, &full[stage], kb * BK, ya);
                         if (pair) {
-                            tma_load_2d(sb + KP * 128, ah, &full[stage], kb * BK, arow2);
-                            tma_load_2d(sb + A_BYTES + KP * 128, al, &full[stage], kb * BK, arow2);
+                            const int yb = (kb >= rb0 && kb < rb1) ? arow2 : fs.a_oob;
+                            tma_load_2d(sb + KP * 128, ah, &full[stage], kb * BK, yb);
+                            tma_load_2d(sb + A_BYTES + KP * 128, al, &full[stage], kb * BK, yb);
                         }
                     } else {
-                        // near: column kb of the leaf's diagonal block; far: augmented
-                        // column kb; completion: T_l rows 0..63 of the leaf's columns
-                        int ax = kb * BK, arow = arow2;
-                        if (src == 1) {
-                            ax = (kb - tl.rt * (FL / BK)) * BK;
-                            arow = arow1;
-                        } else if (src == 3) {
-                            ax = 0;
-                            arow = l * N + tl.rt * BM;
-                        }
-                        tma_load_2d(sb, ah, &full[stage], ax, arow);
-                        tma_load_2d(sb + A_BYTES, al, &full[stage], ax, arow);
+                        // near: K block akb of the leaf's diagonal block; far: slot
+                        // akb of the compact B table (forward) or augmented column
+                        // kb of QA (adjoint); completion: T_l rows 0..63 of the leaf's
+                        // columns
+                        const int arow = src == 1 ? arow1 : (src == 2 ? arow2 : l * N + tl.rt * BM);
+                        tma_load_2d(sb, ah, &full[stage], akb * BK, arow);
+                        tma_load_2d(sb + A_BYTES, al, &full[stage], akb * BK, arow);
                     }
                     for (int b = 0; b < nbox; ++b) {
                         tma_load_2d_hint(sb + 2 * A_BYTES + b * BBOX * 128, bh, &full[stage], kb * BK,
@@ -602,19 +632,21 @@ __device__ __forceinline__ void fac_pair(double v, __half& hi, __half& lo) {
 }
 
 // beta_{r,j}[k] of every row r of the used slot s = (j, i) it takes (the rows
-// of the sibling interval i + 1), from the FP64 T_l:
+// of the sibling interval i + 1 inside the grid), from the FP64 T_l:
 //   beta = sum_t Q_j[t][k] T_l[r][i len + t] / sqrt(w_{i len + t}),
-// zero on completion rows and for k >= l; written as FP16 pairs to
-// B[l][r][(s,k)] and BT[l][(s,k)][r].  Block (position, l), KP threads (k).
+// zero on completion rows and for k >= l; written as FP16 pairs to the compact
+// tables B[l][r][j][k] (a row takes at most one far interval per level) and
+// BT[l][j][k][r].  Block (position, l), KP threads (k).
 __global__ void k_ftc_beta(const double* __restrict__ T64, const double* __restrict__ Q,
                            const size_t* __restrict__ qoff, FtcSpace fs, int N, __half* bA_hi, __half* bA_lo,
                            __half* bT_hi, __half* bT_lo) {
-    const int half = N / 2;
-    const int j = blockIdx.x / half, q = blockIdx.x % half, l = blockIdx.y, k = threadIdx.x;
+    // positions q < N per level: the used slots of a level span fewer than N
+    // columns (N / 2 when N / 128 is a power of two)
+    const int j = blockIdx.x / N, q = blockIdx.x % N, l = blockIdx.y, k = threadIdx.x;
     const int len = FL << j;
-    const int s = fs.slot_off[j] + q / len, i = 2 * (q / len);
+    const int i = 2 * (q / len);
     const int r = (i + 1) * len + q % len;
-    const int NAF = fs.nslots_f * KP;
+    if (!used(fs, j, i) || r >= N) return;
     double b = 0.0;
     if (r >= n_extra(l) && k < l) {
         const double* row = T64 + ((size_t)l * N + r) * N + (size_t)i * len;
@@ -626,8 +658,8 @@ __global__ void k_ftc_beta(const double* __restrict__ T64, const double* __restr
     }
     __half h, lo;
     fac_pair(b, h, lo);
-    const size_t oa = ((size_t)l * N + r) * NAF + (size_t)s * KP + k;
-    const size_t ot = (((size_t)l * fs.nslots + s) * KP + k) * N + r;
+    const size_t oa = (((size_t)l * N + r) * fs.FW + j) * KP + k;
+    const size_t ot = (((size_t)l * fs.levels + j) * KP + k) * N + r;
     bA_hi[oa] = h;
     bA_lo[oa] = lo;
     bT_hi[ot] = h;
@@ -639,10 +671,11 @@ __global__ void k_ftc_beta(const double* __restrict__ T64, const double* __restr
 // sqrt(w_0) = 1/sqrt(2).  Block (position, p), KP threads (k).
 __global__ void k_ftc_q(const double* __restrict__ Q, const size_t* __restrict__ qoff, FtcSpace fs, int N,
                         __half* qT_hi, __half* qT_lo, __half* qA_hi, __half* qA_lo) {
-    const int half = N / 2;
-    const int j = blockIdx.x / half, q = blockIdx.x % half, p = blockIdx.y, k = threadIdx.x;
+    const int j = blockIdx.x / N, q = blockIdx.x % N, p = blockIdx.y, k = threadIdx.x;
     const int len = FL << j;
-    const int s = fs.slot_off[j] + q / len, i = 2 * (q / len), t = q % len;
+    const int i = 2 * (q / len), t = q % len;
+    if (!used(fs, j, i)) return;
+    const int s = fs.slot_off[j] + q / len;
     const int c = i * len + t;
     const int NA = fs.nslots * KP;
     const double v = Q[qoff[j] + (size_t)t * KP + k] * ((p == 1 && c == 0) ? 0.70710678118654752440 : 1.0);
@@ -656,43 +689,43 @@ __global__ void k_ftc_q(const double* __restrict__ Q, const size_t* __restrict__
     qA_lo[oa] = lo;
 }
 
-// Right slots (j, 1): beta of the completion rows r < n0_l - p_l on the
-// columns [len_j, 2 len_j) into B[l][r][(nslots + j, k)].  Block (j, l), KP
-// threads (k).
+// Right intervals q = (rj, ri): beta of the completion rows r < n0_l - p_l on
+// the columns [ri len, (ri + 1) len) (all right of leaf 0, weight 1) into
+// B[l][r][q][k].  Block (q, l), KP threads (k).
 __global__ void k_ftc_beta_right(const double* __restrict__ T64, const double* __restrict__ Q,
                                  const size_t* __restrict__ qoff, FtcSpace fs, int N, __half* bA_hi,
                                  __half* bA_lo) {
-    const int j = blockIdx.x, l = blockIdx.y, k = threadIdx.x;
-    const int len = FL << j, NAF = fs.nslots_f * KP;
+    const int q = blockIdx.x, l = blockIdx.y, k = threadIdx.x;
+    const int j = fs.rj[q], len = FL << j, c0 = fs.ri[q] * len;
     const double* Qj = Q + qoff[j];
     for (int r = 0; r < n_extra(l); ++r) {
         double b = 0.0;
         if (k < l) {
-            const double* row = T64 + ((size_t)l * N + r) * N + len;
+            const double* row = T64 + ((size_t)l * N + r) * N + c0;
             for (int t = 0; t < len; ++t) b = fma(row[t], Qj[(size_t)t * KP + k], b);
         }
         __half h, lo;
         fac_pair(b, h, lo);
-        const size_t oa = ((size_t)l * N + r) * NAF + (size_t)(fs.nslots + j) * KP + k;
+        const size_t oa = (((size_t)l * N + r) * fs.FW + q) * KP + k;
         bA_hi[oa] = h;
         bA_lo[oa] = lo;
     }
 }
 
-// QT rows of the right slots: QT[p][(nslots + j, k)][len_j + t] = Q_j[t][k]
-// (columns >= 128 carry weight 1).  Block (position over all j, p), KP threads.
+// QT rows of the right intervals: QT[p][(nslots + q, k)][ri len + t] = Q_j[t][k]
+// (columns >= 128 carry weight 1).  Block (position over all q, p), KP threads.
 __global__ void k_ftc_q_right(const double* __restrict__ Q, const size_t* __restrict__ qoff, FtcSpace fs, int N,
                               __half* qT_hi, __half* qT_lo) {
-    int t = blockIdx.x, j = 0;
-    while (t >= (FL << j)) {
-        t -= FL << j;
-        ++j;
+    int t = blockIdx.x, q = 0;
+    while (q + 1 < fs.nright && t >= (FL << fs.rj[q])) {
+        t -= FL << fs.rj[q];
+        ++q;
     }
-    const int p = blockIdx.y, k = threadIdx.x, c = (FL << j) + t;
+    const int j = fs.rj[q], p = blockIdx.y, k = threadIdx.x, c = fs.ri[q] * (FL << j) + t;
     const double v = Q[qoff[j] + (size_t)t * KP + k];
     __half h, lo;
     fac_pair(v, h, lo);
-    const size_t ot = (((size_t)p * fs.nslots_f + fs.nslots + j) * KP + k) * N + c;
+    const size_t ot = (((size_t)p * fs.nslots_f + fs.nslots + q) * KP + k) * N + c;
     qT_hi[ot] = h;
     qT_lo[ot] = lo;
 }
@@ -734,7 +767,7 @@ __global__ void k_ftc_comp(const double* __restrict__ T64, int N, __half* C_hi, 
 struct FtcData {
     FtcSpace base{};   // nleaf, levels, nslots, slot_off
     int np_m = 0, np_w = 0;                        // slot pairs of the MOMENTS / WEIGHTS tiles
-    int pa_m[MAX_SLOTS], pb_m[MAX_SLOTS], pa_w[MAX_SLOTS], pb_w[MAX_SLOTS];
+    int pa_m[MAX_FSLOTS], pb_m[MAX_FSLOTS], pa_w[MAX_FSLOTS], pb_w[MAX_FSLOTS];
     int NA = 0, NAF = 0;   // augmented widths: adjoint (used slots), forward (+ right slots)
     // FP16 pairs (times 2^14): B, BT, QT, QA, the diagonal blocks D and Dt and
     // the completion block C
@@ -759,25 +792,31 @@ struct FtcData {
 // MOMENTS / WEIGHTS tiles hold two slots.  Each slot (j, i) of an odd level j
 // takes the child slot whose range lies inside its own: (j - 1, 2i) for the
 // moments (the interval's columns), (j - 1, 2i + 2) for the adjoint weights
-// (the sibling's rows), so the child adds no K blocks; the other slots go two
-// by two in order of decreasing length.  Tiles are sorted longest first.
+// (the sibling's rows; when that child is a used slot), so the child adds no K
+// blocks; a right interval takes its left half, a used slot, the same way; the
+// other slots go two by two in order of decreasing length.  Tiles are sorted
+// longest first.
 static void build_pairs(const FtcSpace& b, int child, bool right, int& npairs, int* pa, int* pb) {
     const int ns = right ? b.nslots_f : b.nslots;
-    std::vector<int> used(ns, 0);
+    std::vector<int> taken(ns, 0);
     std::vector<std::pair<int, int>> pairs;
     auto slot = [&](int j, int i) { return b.slot_off[j] + i / 2; };
     for (int j = 1; j < b.levels; j += 2)
-        for (int i = 0; i + 1 < (b.nleaf >> j); i += 2) {
+        for (int i = 0; i < n_at(b, j); i += 2) {
+            if (!used(b, j, i)) continue;
             const int c = 2 * i + child;
+            if (!used(b, j - 1, c)) continue;
             pairs.push_back({slot(j, i), slot(j - 1, c)});
-            used[slot(j, i)] = used[slot(j - 1, c)] = 1;
+            taken[slot(j, i)] = taken[slot(j - 1, c)] = 1;
         }
-    if (right)   // right slot (j, 1) contains the used slot (j - 1, 2)
-        for (int j = 1; j < b.levels; ++j)
-            if (3 < (b.nleaf >> (j - 1)) && !used[slot(j - 1, 2)]) {
-                pairs.push_back({b.nslots + j, slot(j - 1, 2)});
-                used[b.nslots + j] = used[slot(j - 1, 2)] = 1;
+    if (right)
+        for (int q = 0; q < b.nright; ++q) {
+            const int j = b.rj[q], i = b.ri[q];
+            if (j >= 1 && used(b, j - 1, 2 * i) && !taken[slot(j - 1, 2 * i)]) {
+                pairs.push_back({b.nslots + q, slot(j - 1, 2 * i)});
+                taken[b.nslots + q] = taken[slot(j - 1, 2 * i)] = 1;
             }
+        }
     auto level_of = [&](int s) {
         int j, i;
         slot_ji(b, s, j, i);
@@ -785,7 +824,7 @@ static void build_pairs(const FtcSpace& b, int child, bool right, int& npairs, i
     };
     std::vector<int> rest;
     for (int s = 0; s < ns; ++s)
-        if (!used[s]) rest.push_back(s);
+        if (!taken[s]) rest.push_back(s);
     std::stable_sort(rest.begin(), rest.end(), [&](int x, int y) { return level_of(x) > level_of(y); });
     for (size_t q = 0; q < rest.size(); q += 2)
         pairs.push_back({rest[q], q + 1 < rest.size() ? rest[q + 1] : -1});
@@ -799,14 +838,29 @@ static void build_pairs(const FtcSpace& b, int child, bool right, int& npairs, i
     }
 }
 
+// The columns [128, N) right of leaf 0 as dyadic intervals (j, i), greedy from
+// leaf 1: each the longest interval that starts there on its own alignment and
+// ends inside the grid.  For N / 128 = 2^L these are (j, 1), j < L.
+static void right_intervals(FtcSpace& b) {
+    b.nright = 0;
+    for (int p = 1; p < b.nleaf;) {
+        int j = 0;
+        while ((p % (2 << j)) == 0 && p + (2 << j) <= b.nleaf) ++j;
+        b.rj[b.nright] = j;
+        b.ri[b.nright] = p >> j;
+        ++b.nright;
+        p += 1 << j;
+    }
+}
+
 bool ftc_supported(int N) {
     const int nleaf = N / FL;
-    return N % FL == 0 && nleaf >= 2 && nleaf <= (1 << MAX_LEVELS) && (nleaf & (nleaf - 1)) == 0;
+    return N % FL == 0 && nleaf >= 2 && nleaf <= (1 << MAX_LEVELS);
 }
 
 int ftc_build(dsbt_plan* p, cudaStream_t st) {
     const int N = p->N;
-    DSBT_CHECK_ARG(ftc_supported(N), "DSBT_PLAN_FAST_SPLIT needs N / 128 a power of two (N = %d)", N);
+    DSBT_CHECK_ARG(ftc_supported(N), "DSBT_PLAN_FAST_SPLIT needs N a multiple of 128, 256 <= N <= 8192 (N = %d)", N);
     DSBT_CHECK_ARG(p->T64 != nullptr, "DSBT_PLAN_FAST_SPLIT: FP64 factors missing at build");
     FtcData* f = new (std::nothrow) FtcData();
     if (!f) return DSBT_ERR_NOMEM;
@@ -816,9 +870,11 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
     b.levels = 0;
     while ((1 << b.levels) < b.nleaf) ++b.levels;
     b.slot_off[0] = 0;
-    for (int j = 0; j < b.levels; ++j) b.slot_off[j + 1] = b.slot_off[j] + (b.nleaf >> (j + 1));
+    for (int j = 0; j < b.levels; ++j) b.slot_off[j + 1] = b.slot_off[j] + n_at(b, j) / 2;   // used slots
     b.nslots = b.slot_off[b.levels];
-    b.nslots_f = b.nslots + b.levels;
+    right_intervals(b);
+    b.nslots_f = b.nslots + b.nright;
+    b.FW = std::max(b.levels, b.nright);
     b.KB = N / BK;
     f->NA = b.nslots * KP;
     f->NAF = b.nslots_f * KP;
@@ -839,7 +895,9 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
     std::vector<double> Qall(qtot);
     for (int j = 0; j < levels; ++j) std::copy(Qh[j].begin(), Qh[j].end(), Qall.begin() + qoff[j]);
     const size_t L = (size_t)p->l_max + 1;
-    const size_t nbA = L * N * NAF, nbT = L * N * NA, nqT = 2 * (size_t)N * NAF, nq = 2 * (size_t)N * NA;
+    // compact B [l][r][FW][64] and BT [l][levels][64][N]; dense QT [2][NAF][N] and QA [2][N][NA]
+    const size_t nbA = L * N * b.FW * KP, nbT = L * b.levels * KP * N, nqT = 2 * (size_t)N * NAF,
+                 nq = 2 * (size_t)N * NA;
     const size_t nD = L * N * FL, nC = L * N * BK;
     const size_t hb = sizeof(__half);
     double* Qd = nullptr;
@@ -875,10 +933,10 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
     for (__half* a : {f->qA_hi, f->qA_lo}) DSBT_CUDA_TRY(cudaMemsetAsync(a, 0, nq * hb, st));
     {
         ProfScope ps(kKPlan, st);
-        k_ftc_beta<<<dim3(levels * (N / 2), (unsigned)L), KP, 0, st>>>(p->T64, Qd, qoffd, b, N, f->bA_hi, f->bA_lo,
+        k_ftc_beta<<<dim3(levels * N, (unsigned)L), KP, 0, st>>>(p->T64, Qd, qoffd, b, N, f->bA_hi, f->bA_lo,
                                                                        f->bT_hi, f->bT_lo);
-        k_ftc_q<<<dim3(levels * (N / 2), 2), KP, 0, st>>>(Qd, qoffd, b, N, f->qT_hi, f->qT_lo, f->qA_hi, f->qA_lo);
-        k_ftc_beta_right<<<dim3(levels, (unsigned)L), KP, 0, st>>>(p->T64, Qd, qoffd, b, N, f->bA_hi, f->bA_lo);
+        k_ftc_q<<<dim3(levels * N, 2), KP, 0, st>>>(Qd, qoffd, b, N, f->qT_hi, f->qT_lo, f->qA_hi, f->qA_lo);
+        k_ftc_beta_right<<<dim3(b.nright, (unsigned)L), KP, 0, st>>>(p->T64, Qd, qoffd, b, N, f->bA_hi, f->bA_lo);
         k_ftc_q_right<<<dim3(N - FL, 2), KP, 0, st>>>(Qd, qoffd, b, N, f->qT_hi, f->qT_lo);
         k_ftc_near<<<dim3(b.nleaf, (unsigned)L), 256, 0, st>>>(p->T64, N, f->D_hi, f->D_lo, f->Dt_hi, f->Dt_lo);
         k_ftc_comp<<<dim3((N + 255) / 256, (unsigned)L), 256, 0, st>>>(p->T64, N, f->C_hi, f->C_lo);
@@ -887,10 +945,10 @@ int ftc_build(dsbt_plan* p, cudaStream_t st) {
     DSBT_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(Qd);
     cudaFree(qoffd);
-    int rc = encode_tmap_f16_sw128(&f->tm_bA_hi, f->bA_hi, L * N, NAF, 128, BK);
-    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_bA_lo, f->bA_lo, L * N, NAF, 128, BK);
-    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_bT_hi, f->bT_hi, L * NA, N, 64, BK);
-    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_bT_lo, f->bT_lo, L * NA, N, 64, BK);
+    int rc = encode_tmap_f16_sw128(&f->tm_bA_hi, f->bA_hi, L * N, (uint64_t)b.FW * KP, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_bA_lo, f->bA_lo, L * N, (uint64_t)b.FW * KP, 128, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_bT_hi, f->bT_hi, L * levels * KP, N, 64, BK);
+    if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_bT_lo, f->bT_lo, L * levels * KP, N, 64, BK);
     if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_qT_hi, f->qT_hi, 2 * (uint64_t)NAF, N, 64, BK);
     if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_qT_lo, f->qT_lo, 2 * (uint64_t)NAF, N, 64, BK);
     if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&f->tm_qA_hi, f->qA_hi, 2 * (uint64_t)N, NA, 128, BK);
@@ -932,6 +990,8 @@ int launch_ftc(const dsbt_plan* p, const GroupTable& g, int mode, const CUtensor
     if (aug) {
         const FtcData* f = p->ftc;
         const bool m = mode == kMoments;
+        // first row past the A table of the tile's slots (QT or the compact BT)
+        fs.a_oob = m ? 2 * fs.nslots_f * KP : (p->l_max + 1) * fs.levels * KP;
         fs.npairs = m ? f->np_m : f->np_w;
         for (int q = 0; q < fs.npairs; ++q) {
             fs.pair_a[q] = m ? f->pa_m[q] : f->pa_w[q];

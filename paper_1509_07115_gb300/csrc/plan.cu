@@ -354,7 +354,7 @@ extern "C" int dsbt_plan_create(int N, double r_max, int l_max, int flags, void*
     DSBT_CHECK_ARG(!(flags & DSBT_PLAN_FAST64) || ((flags & DSBT_PLAN_FP64) && fast_supported(N)),
                    "dsbt_plan_create: DSBT_PLAN_FAST64 needs DSBT_PLAN_FP64 and N / 64 a power of two");
     DSBT_CHECK_ARG(!(flags & DSBT_PLAN_FAST_SPLIT) || ftc_supported(N),
-                   "dsbt_plan_create: DSBT_PLAN_FAST_SPLIT needs N / 128 a power of two");
+                   "dsbt_plan_create: DSBT_PLAN_FAST_SPLIT needs N a multiple of 128 with 2 to 64 leaves");
     cudaStream_t st = (cudaStream_t)stream;
     dsbt_plan* p = new (std::nothrow) dsbt_plan();
     if (!p) {

@@ -75,6 +75,11 @@ class ProfScope {
 // Turns event recording on/off without clearing records; returns the old state.
 int profile_set_enabled(int on);
 
+// ---- grouped calls on device buffers with a caller workspace (capi.cu):
+// which = 0 forward, 1 inverse, 2 kinetic step (dsbt_*_grouped semantics)
+int grouped_device_call(int which, const dsbt_plan* p, const int* counts, int dtype, double tau,
+                        const void* in, void* out, void* ws, size_t ws_b, cudaStream_t st);
+
 // ---- plan build (plan.cu)
 int plan_build_factors(dsbt_plan* p, cudaStream_t st);
 int plan_probe(dsbt_plan* p, cudaStream_t st);

@@ -75,6 +75,7 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_kernel_name.argtypes = [i]
         lib.dsbt_kernel_name.restype = ctypes.c_char_p
         lib.dsbt_batch_create.argtypes = [i, _c_int_p, _c_int_p, _c_int_p, d, i, vp, ctypes.POINTER(vp)]
+        lib.dsbt_batch_create_ex.argtypes = [i, _c_int_p, _c_int_p, _c_int_p, d, i, vp, ctypes.POINTER(vp)]
         lib.dsbt_batch_destroy.argtypes = [vp]
         lib.dsbt_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), _c_int_p, _c_int_p,
                                         ctypes.POINTER(ctypes.c_float)]
@@ -380,7 +381,12 @@ class Batch:
     Batch arrays: complex64 CUDA tensors of total_elems elements, transforms back
     to back, each [sum(counts_t)][N_t] l-major."""
 
-    def __init__(self, transforms, dr: float, autotune: bool = True):
+    def __init__(self, transforms, dr: float, autotune: bool = True, scheme: str = "dense"):
+        """scheme: "dense" (shared split-TF32 factors, one persistent launch per
+        direction, tile order and width autotuned when autotune) or "interval"
+        (one interval-scheme plan per distinct grid, DSBT_BATCH_INTERVAL)."""
+        if scheme not in ("dense", "interval"):
+            raise ValueError("scheme is 'dense' or 'interval'")
         Ns = [int(t[0]) for t in transforms]
         lms = [int(t[1]) for t in transforms]
         cnt = []
@@ -390,8 +396,10 @@ class Batch:
             cnt += [int(v) for v in c]
         arr = lambda v: (ctypes.c_int * len(v))(*v)
         h = ctypes.c_void_p()
-        _check(load().dsbt_batch_create(len(Ns), arr(Ns), arr(lms), arr(cnt), float(dr), int(bool(autotune)),
-                                        _stream(), ctypes.byref(h)), "dsbt_batch_create")
+        flags = (1 if (autotune and scheme == "dense") else 0) | (2 if scheme == "interval" else 0)
+        _check(load().dsbt_batch_create_ex(len(Ns), arr(Ns), arr(lms), arr(cnt), float(dr), flags,
+                                           _stream(), ctypes.byref(h)), "dsbt_batch_create")
+        self.scheme = scheme
         self._h = h
         self.transforms = [(Ns[k], lms[k], list(transforms[k][2])) for k in range(len(Ns))]
         self.dr = float(dr)
@@ -417,6 +425,8 @@ class Batch:
         _check(load().dsbt_batch_info(self._h, ctypes.byref(n), ctypes.byref(o), ctypes.byref(b), ms),
                "dsbt_batch_info")
         names = self.TILE_ORDERS
+        if o.value < 0:   # interval scheme: no tile list
+            return {"total_elems": n.value, "order": None, "bn_cap": 0, "tune_ms": {}}
         return {"total_elems": n.value, "order": names[o.value], "bn_cap": b.value,
                 "tune_ms": {f"{names[k // 3]}/{[128, 192, 256][k % 3]}": ms[k] for k in range(12)}}
 

@@ -133,3 +133,78 @@ def test_full_uneven_workload_sampled(lib):
         start += n
     assert worst < 2e-6, worst
     b.close()
+
+
+def test_interval_scheme_batch(lib):
+    """DSBT_BATCH_INTERVAL: one interval-scheme plan per distinct grid (grids of
+    2, 6, 4, 10 and 8 leaves), transforms on internal streams.  Forward against
+    the oracle at each transform's own N, kinetic step against the dense batch,
+    and a CUDA-graph replay (the fork-join over the internal streams) equal to
+    the direct call."""
+    trs = [(N, lm, [2 * l + 1 for l in range(lm + 1)]) for N, lm in TRANSFORMS]
+    trs[1][2][4] = 0
+    xs = [inputs.gaussian_sum(20 + k, N, DR, c).astype(np.complex64) for k, (N, lm, c) in enumerate(trs)]
+    x = torch.from_numpy(np.concatenate([v.reshape(-1) for v in xs])).cuda()
+    b = lib.Batch(trs, DR, scheme="interval")
+    assert b.info()["order"] is None
+    check_forward(b, trs, xs, x)
+    tau = 0.05
+    y = b.kinetic(x, tau)
+    dense = lib.Batch(trs, DR, autotune=False)
+    yd = dense.kinetic(x, tau)
+    dense.close()
+    assert (y - yd).abs().max().item() < 2e-6          # unit-norm channels
+    out = torch.empty_like(x)
+    g = b.capture_kinetic(x, tau, out)
+    out.zero_()
+    b.launch_graph(g)
+    b.launch_graph(g)
+    torch.cuda.synchronize()
+    assert torch.equal(out, y)
+    with pytest.raises(lib.DSBTError):
+        b.set_tiles("l-major", 256)
+    b.close()
+
+
+def test_interval_scheme_full_uneven_workload(lib):
+    """The 64-transform workload on the interval scheme: sampled forward rows of
+    the largest and a small transform against the oracle, kinetic norm drift on
+    every channel."""
+    work = inputs.grouped_workload(0)
+    trs = [(N, lm, [2 * l + 1 for l in range(lm + 1)]) for N, lm in work]
+    b = lib.Batch(trs, 0.1, scheme="interval")
+    xs = [inputs.gaussian_sum(300 + k, N, 0.1, c, dtype=torch.complex64, device="cuda").reshape(-1)
+          for k, (N, lm, c) in enumerate(trs)]
+    x = torch.cat(xs)
+    del xs
+    y = b.forward(x)
+    offs = b.offsets()
+    big = max(range(len(trs)), key=lambda i: trs[i][0] * 100 + trs[i][1])
+    small = min(range(len(trs)), key=lambda i: trs[i][0])
+    for k in (big, small):
+        N, lm, c = trs[k]
+        yk = y[offs[k]:offs[k] + sum(c) * N].reshape(-1, N).cpu().numpy()
+        xk = x[offs[k]:offs[k] + sum(c) * N].reshape(-1, N).cpu().numpy().astype(np.complex128)
+        c0 = 0
+        for l in range(lm + 1):
+            if l in (0, 1, lm // 2, lm):
+                sel = [c0, c0 + c[l] - 1]
+                rows = [0, 1, 31, 32, 200, N - 1]
+                ref = oracle.forward_rows(l, xk[sel], rows)
+                e = (np.abs(yk[sel][:, rows] - ref).max(axis=1) / np.linalg.norm(xk[sel], axis=1)).max()
+                assert e < 1e-6, (N, l, e)
+            c0 += c[l]
+    del y
+    z = b.kinetic(x, 0.05)
+    torch.cuda.synchronize()
+    start = 0
+    worst = 0.0
+    for k, (N, lm, c) in enumerate(trs):
+        n = sum(c) * N
+        a = x[start:start + n].reshape(-1, N).to(torch.complex128)
+        bz = z[start:start + n].reshape(-1, N).to(torch.complex128)
+        na, nb = torch.linalg.vector_norm(a, dim=1), torch.linalg.vector_norm(bz, dim=1)
+        worst = max(worst, ((nb - na) / na).abs().max().item())
+        start += n
+    assert worst < 2e-6, worst
+    b.close()

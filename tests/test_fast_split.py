@@ -16,10 +16,10 @@ from paper_1509_07115_gb300 import dsbt, inputs
 def test_fast_split_flag_rules():
     lib = dsbt.load()
     h = ctypes.c_void_p()
-    assert lib.dsbt_plan_create(768, 76.8, 4, dsbt.DSBT_PLAN_FAST_SPLIT | dsbt.DSBT_PLAN_TF32X3, None,
-                                ctypes.byref(h)) == -1          # N / 128 = 6, not a power of two
-    assert lib.dsbt_plan_create(768, 76.8, 4, dsbt.DSBT_PLAN_FAST_SPLIT, None,
-                                ctypes.byref(h)) == -1
+    assert lib.dsbt_plan_create(300, 30.0, 4, dsbt.DSBT_PLAN_FAST_SPLIT | dsbt.DSBT_PLAN_TF32X3, None,
+                                ctypes.byref(h)) == -1          # N not a multiple of 256
+    assert lib.dsbt_plan_create(8448, 844.8, 4, dsbt.DSBT_PLAN_FAST_SPLIT, None,
+                                ctypes.byref(h)) == -1          # 66 leaves, past the largest grid
 
 
 @pytest.mark.gpu
@@ -144,3 +144,38 @@ def test_fast_split_kinetic_with_corrected_momenta(lib):
     k = plan.kinetic_grouped(counts, torch.from_numpy(x.astype(np.complex64)).cuda(), tau).cpu().numpy()
     plan.close()
     assert rel(k, ref, nrm) < 1e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("N", [768, 1280, 2304, 6400, 7936])
+def test_fast_split_any_leaf_count(lib, N):
+    """Grids whose leaf count N / 128 is not a power of two (6, 10, 18, 50, 62
+    leaves): the used intervals, the right intervals of the completion rows and
+    the partial siblings at the right edge, against the FP64 path of the same
+    plan (forward, inverse, kinetic step) and the oracle on sampled rows."""
+    import oracle
+    lmax = 40 if N <= 2304 else 64
+    counts = [1] * (lmax + 1)
+    for l in (0, 1, 2, 3, 17, lmax - 1, lmax):
+        counts[l] = 3
+    x = inputs.gaussian_sum(90 + N // 256, N, 0.1, counts)
+    nrm = np.linalg.norm(x, axis=1)
+    plan = lib.Plan(N, 0.1 * N, lmax, fp64=True, tf32x3=False, fast_split=True)
+    x128 = torch.from_numpy(x).cuda()
+    x64 = x128.to(torch.complex64)
+    ref_b = plan.forward_grouped(counts, x128).cpu().numpy()
+    b = plan.forward_grouped(counts, x64).cpu().numpy()
+    assert rel(b, ref_b, nrm) < 1e-6
+    f = plan.inverse_grouped(counts, torch.from_numpy(ref_b).cuda().to(torch.complex64)).cpu().numpy()
+    assert rel(f, x, nrm) < 1e-6
+    ref_k = plan.kinetic_grouped(counts, x128, 0.05).cpu().numpy()
+    k = plan.kinetic_grouped(counts, x64, 0.05).cpu().numpy()
+    assert rel(k, ref_k, nrm) < 1e-6
+    plan.close()
+    rows = sorted({0, 1, 30, 127, 128, 129, N // 2, N - 129, N - 128, N - 1})
+    c0 = 0
+    for l, c in enumerate(counts):
+        if l in (0, 1, lmax):
+            ref = oracle.forward_rows(l, x[c0:c0 + c], rows)
+            assert rel(b[c0:c0 + c][:, rows], ref, nrm[c0:c0 + c]) < 1e-6, (N, l)
+        c0 += c
