@@ -165,10 +165,23 @@ def probe_peaks(torch, dev):
     d = torch.empty(nb, dtype=torch.uint8, device=dev)
     out["h2d_gbs"] = nb / (best_ms(lambda: d.copy_(h, non_blocking=True), 5) * 1e-3) / 1e9
     out["d2h_gbs"] = nb / (best_ms(lambda: h.copy_(d, non_blocking=True), 5) * 1e-3) / 1e9
-    del h, d
+    # both directions at once (another pinned pair, a second stream): the bound of
+    # a step that copies its inputs in and its results out concurrently
+    h2 = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    d2 = torch.empty(nb, dtype=torch.uint8, device=dev)
+    s2 = torch.cuda.Stream()
+
+    def both():
+        s2.wait_stream(st)
+        d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+        st.wait_stream(s2)
+    out["bidir_gbs_each_way"] = nb / (best_ms(both, 5) * 1e-3) / 1e9
+    del h, d, h2, d2
     torch.cuda.empty_cache()
     out["how"] = ("torch.matmul 8192^3 (2 N^3 flop), best of 3 (fp64) / 10 (tf32 with allow_tf32, fp16), "
-                  "CUDA events; pinned 1 GiB copies best of 5")
+                  "CUDA events; pinned 1 GiB copies best of 5, one way and both ways at once")
     return out
 
 
@@ -294,6 +307,38 @@ def oracle_sample(per_thread=2, ls=(1, 2), seed=11):
         list(ex.map(one, jobs))
     t_xform = time.perf_counter() - t0
     return 2 * len(jobs), t_xform, t_build, nt
+
+
+def gpu_local_cpus(index: int):
+    """CPU cores local to GPU `index` (the "CPU Affinity" column of
+    `nvidia-smi topo -m`), or None.  Pinned host buffers are first touched by
+    the allocating thread, so running the host side there keeps the pinned
+    memory of the host-streamed leg on the GPU's own NUMA node."""
+    try:
+        txt = subprocess.run(["nvidia-smi", "topo", "-m"], capture_output=True, text=True, timeout=20).stdout
+    except Exception:
+        return None
+    lines = [ln for ln in txt.splitlines() if ln.strip()]
+    hdr = next((ln for ln in lines if "CPU Affinity" in ln), None)
+    if hdr is None:
+        return None
+    cols = [c.strip() for c in hdr.split("\t")]
+    row = next((ln for ln in lines if ln.split("\t")[0].strip() == f"GPU{index}"), None)
+    if row is None:
+        return None
+    cells = [c.strip() for c in row.split("\t")]
+    try:
+        spec = cells[cols.index("CPU Affinity")]
+    except (ValueError, IndexError):
+        return None
+    cpus = set()
+    try:
+        for part in spec.split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+    except ValueError:
+        return None
+    return sorted(cpus & set(os.sched_getaffinity(0))) or None
 
 
 def rank_seed(rank: int, base: int = 100) -> int:
@@ -639,6 +684,9 @@ def main():
 
     from paper_1509_07115_gb300 import dsbt, inputs
 
+    cpus = gpu_local_cpus(local)
+    if cpus:
+        os.sched_setaffinity(0, cpus)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -725,7 +773,8 @@ def main():
     if args.no_probe:   # nominal ratios to the measured BF16 rate; no copy figures
         bf = peaks["bf16_tflops"]
         probes = {"fp64_tflops": bf * 1.25 / 2250, "tf32_tflops": bf * 1.1 / 2.25, "fp16_tflops": bf,
-                  "h2d_gbs": None, "d2h_gbs": None, "how": "not probed: nominal ratios to bf16_tflops"}
+                  "h2d_gbs": None, "d2h_gbs": None, "bidir_gbs_each_way": None,
+                  "how": "not probed: nominal ratios to bf16_tflops"}
     else:
         probes = probe_peaks(torch, dev)
     hbm = peaks["hbm_gbs"]
@@ -782,7 +831,9 @@ def main():
                 "data": "synthetic (seeded Gaussian-sum radial functions r sum_j c_j r^l exp(-a_j r^2))",
                 "config": {"workload": WORKLOAD, "N": N, "r_max": R_MAX, "l_max": L_MAX, "batch": BATCH,
                            "channels_per_gpu": nchan, "tau": TAU,
-                           "l2": "inputs larger than L2 (1.07 GB in + 1.07 GB out per step per GPU)"},
+                           "l2": "inputs larger than L2 (1.07 GB in + 1.07 GB out per step per GPU)",
+                           "host_cpus": f"{cpus[0]}-{cpus[-1]} ({len(cpus)} cores local to the GPU)" if cpus
+                           else "not pinned"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                         "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
                         "api": f"dsbt_kinetic_grouped_host, pinned host buffers, {args.e2e_chunks} chunks"},
@@ -793,6 +844,7 @@ def main():
             line["e2e"]["copy_bound"] = {
                 "h2d_gbs_achieved": nbytes / (1e-3 * job_ms_e2e / e2e_steps) / 1e9,
                 "h2d_gbs_pinned_peak": probes["h2d_gbs"], "d2h_gbs_pinned_peak": probes["d2h_gbs"],
+                "bidir_gbs_each_way_peak": probes["bidir_gbs_each_way"],
                 "note": "each step copies the batch in and out; copies run both ways at once, overlapped with compute"}
 
     # ---------------------------------------------------------- FP64 GPU path (sample) + error

@@ -450,14 +450,17 @@ DSBT_API int dsbt_batch_create(int ntrans, const int* N, const int* l_max, const
 /* dsbt_batch_create with flags: DSBT_BATCH_AUTOTUNE (as autotune_tiles above)
  * and DSBT_BATCH_INTERVAL: instead of the shared dense factors and the
  * persistent launch, one DSBT_PLAN_FAST_SPLIT plan per distinct grid (l_max
- * the largest of the transforms on that grid), and each transform one
- * grouped call on its grid's plan (the O(N l log N) interval scheme), spread
- * over four internal streams that fork from and join back into the caller's
- * stream; dsbt_batch_capture_kinetic captures the whole fork-join graph.  Plan
- * data about 8 B x 64 x (l_max+1) x N x (log2(N/128) + 4) per distinct grid
- * plus a workspace per internal stream.  On such a batch dsbt_batch_info
- * reports order -1 and width 0, and dsbt_batch_set_tiles is unsupported.
- * Same results as the dense batch within the split-precision bar. */
+ * the largest of the transforms on that grid), and per grid one grouped call
+ * on its plan (the O(N l log N) interval scheme) over the channels of every
+ * transform on that grid, which the sine/cosine kernels gather from and
+ * scatter back to the batch arrays through a table of channel offsets; the
+ * grids' calls are spread over four internal streams that fork from and join
+ * back into the caller's stream, and dsbt_batch_capture_kinetic captures the
+ * whole fork-join graph.  Plan data about 8 B x 64 x (l_max+1) x N x
+ * (log2(N/128) + 4) per distinct grid plus a workspace per internal stream.
+ * On such a batch dsbt_batch_info reports order -1 and width 0, and
+ * dsbt_batch_set_tiles is unsupported.  Same results as the dense batch
+ * within the split-precision bar. */
 #define DSBT_BATCH_AUTOTUNE 1
 #define DSBT_BATCH_INTERVAL 2
 DSBT_API int dsbt_batch_create_ex(int ntrans, const int* N, const int* l_max, const int* counts, double dr,

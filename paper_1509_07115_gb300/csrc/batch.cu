@@ -550,8 +550,10 @@ struct dsbt_batch {
     // distinct grid, transforms spread over internal streams
     bool interval = false;
     std::vector<dsbt_plan*> fplans;        // per distinct grid (index cidx)
-    std::vector<std::vector<int>> pcounts; // per transform, padded to its plan's l_max + 1
-    std::vector<int> stream_of;            // per transform
+    std::vector<std::vector<int>> pcounts; // per distinct grid: channels of every l over its transforms
+    std::vector<long long*> uoffs;         // per distinct grid: element offset of each merged channel
+    std::vector<int> nchan_d;              // per distinct grid: merged channels
+    std::vector<int> stream_of;            // per distinct grid
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> joins;        // per stream, plus the fork event at the end
     std::vector<unsigned char*> sws;       // per stream workspace
@@ -564,6 +566,7 @@ namespace {
 void batch_free(dsbt_batch* b) {
     if (!b) return;
     for (auto* p : b->fplans) plan_release(p);
+    for (auto* u : b->uoffs) cudaFree(u);
     for (auto* w : b->sws) cudaFree(w);
     for (auto e : b->joins) cudaEventDestroy(e);
     for (auto s_ : b->streams) cudaStreamDestroy(s_);
@@ -811,20 +814,21 @@ int launch_contract(const dsbt_batch* b, int order, int ci, int dir, int mode, f
     return DSBT_OK;
 }
 
-// Interval scheme: each transform is one grouped call on its grid's plan, in
-// the batch's internal streams (forked from and joined back into st, so a
-// capture of st takes the whole fork-join graph).
+// Interval scheme: the transforms of each distinct grid form one grouped call
+// on that grid's plan (channels of every l gathered from the batch array
+// through the grid's offset table), in the batch's internal streams (forked
+// from and joined back into st, so a capture of st takes the whole fork-join
+// graph).
 int run_batch_interval(const dsbt_batch* b, int kinetic, double tau, const float* in, float* out, cudaStream_t st) {
     const int S = (int)b->streams.size();
     cudaEvent_t fork = b->joins[S];
     DSBT_CUDA_TRY(cudaEventRecord(fork, st));
     for (int k = 0; k < S; ++k) DSBT_CUDA_TRY(cudaStreamWaitEvent(b->streams[k], fork, 0));
-    for (int t = 0; t < b->T; ++t) {
-        if (b->nchan[t] == 0) continue;
-        const int k = b->stream_of[t];
-        const int rc = grouped_device_call(kinetic ? 2 : 0, b->fplans[b->cidx[t]], b->pcounts[t].data(), DSBT_C64,
-                                               tau, in + 2 * b->uoff[t], out + 2 * b->uoff[t], b->sws[k],
-                                               b->sws_bytes[k], b->streams[k]);
+    for (size_t d = 0; d < b->fplans.size(); ++d) {
+        if (b->nchan_d[d] == 0) continue;
+        const int k = b->stream_of[d];
+        const int rc = grouped_device_call(kinetic ? 2 : 0, b->fplans[d], b->pcounts[d].data(), DSBT_C64, tau, in, out,
+                                           b->sws[k], b->sws_bytes[k], b->streams[k], b->uoffs[d]);
         if (rc) return rc;
     }
     for (int k = 0; k < S; ++k) {
@@ -989,25 +993,51 @@ int create_interval(dsbt_batch* b, cudaStream_t st) {
         if (rc) return rc;
         b->fplans.push_back(p);
     }
-    // transforms by decreasing work, each to the least loaded stream
-    const int S = std::min(4, b->T);
-    std::vector<int> ord(b->T);
-    for (int t = 0; t < b->T; ++t) ord[t] = t;
+    // merged calls: per grid, the channels of every l over its transforms in
+    // batch order, with their element offsets in the batch array
+    b->pcounts.assign(ND, {});
+    b->nchan_d.assign(ND, 0);
+    std::vector<std::vector<long long>> offs(ND);
+    for (int d = 0; d < ND; ++d) {
+        b->pcounts[d].assign(lmax_d[d] + 1, 0);
+        for (int l = 0; l <= lmax_d[d]; ++l)
+            for (int t = 0; t < b->T; ++t) {
+                if (b->cidx[t] != d || l > b->lmax[t]) continue;
+                int c0 = 0;
+                for (int q = 0; q < l; ++q) c0 += b->counts[b->counts_off[t] + q];
+                const int c = b->counts[b->counts_off[t] + l];
+                for (int i = 0; i < c; ++i) offs[d].push_back(b->uoff[t] + (long long)(c0 + i) * b->dN[d]);
+                b->pcounts[d][l] += c;
+            }
+        b->nchan_d[d] = (int)offs[d].size();
+        long long* u = nullptr;
+        if (!offs[d].empty()) {
+            if (cudaMalloc((void**)&u, offs[d].size() * sizeof(long long)) != cudaSuccess ||
+                cudaMemcpy(u, offs[d].data(), offs[d].size() * sizeof(long long), cudaMemcpyHostToDevice) !=
+                    cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(u);
+                set_error("dsbt_batch_create: offset table upload failed");
+                return DSBT_ERR_NOMEM;
+            }
+        }
+        b->uoffs.push_back(u);
+    }
+    // grids by decreasing work, each to the least loaded stream
+    const int S = std::min(4, ND);
+    std::vector<int> ord(ND);
+    for (int d = 0; d < ND; ++d) ord[d] = d;
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
-        return (double)b->N[x] * b->nchan[x] > (double)b->N[y] * b->nchan[y];
+        return (double)b->dN[x] * b->nchan_d[x] > (double)b->dN[y] * b->nchan_d[y];
     });
     std::vector<double> load(S, 0.0);
     std::vector<size_t> need(S, 0);
-    b->stream_of.assign(b->T, 0);
-    b->pcounts.resize(b->T);
-    for (int t : ord) {
+    b->stream_of.assign(ND, 0);
+    for (int d : ord) {
         const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        b->stream_of[t] = k;
-        load[k] += (double)b->N[t] * b->nchan[t];
-        const dsbt_plan* p = b->fplans[b->cidx[t]];
-        b->pcounts[t].assign(p->l_max + 1, 0);
-        for (int l = 0; l <= b->lmax[t]; ++l) b->pcounts[t][l] = b->counts[b->counts_off[t] + l];
-        need[k] = std::max(need[k], dsbt_workspace_size(p, b->nchan[t], DSBT_C64));
+        b->stream_of[d] = k;
+        load[k] += (double)b->dN[d] * b->nchan_d[d];
+        need[k] = std::max(need[k], dsbt_workspace_size(b->fplans[d], b->nchan_d[d], DSBT_C64));
     }
     for (int k = 0; k < S; ++k) {
         cudaStream_t sk = nullptr;

@@ -376,7 +376,7 @@ int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, 
 }
 
 int grouped_call(int which, const dsbt_plan* p, const int* counts, int dtype, double tau, const void* in,
-                 void* out, void* ws, size_t ws_b, void* stream) {
+                 void* out, void* ws, size_t ws_b, void* stream, const long long* uoff = nullptr) {
     DSBT_CHECK_ARG(p != nullptr, "plan is NULL");
     DSBT_CHECK_ARG(counts != nullptr, "counts is NULL");
     int ls[kMaxGroups];
@@ -392,6 +392,11 @@ int grouped_call(int which, const dsbt_plan* p, const int* counts, int dtype, do
     GroupTable g;
     rc = build_groups(p, counts, p->l_max + 1, ls, dtype, g);
     if (rc) return rc;
+    if (uoff) {   // channels gathered from the caller's arrays by offset: interval-scheme C64 paths only
+        DSBT_CHECK_ARG(p->ftc != nullptr && dtype == DSBT_C64 && which != 1,
+                       "channel offsets need a DSBT_PLAN_FAST_SPLIT plan, complex64, forward or kinetic");
+        g.uoff = uoff;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     if (which == 0) return run_forward(p, g, dtype, in, out, ws, st);
     if (which == 1) return run_inverse(p, g, dtype, in, out, ws, st);
@@ -426,8 +431,8 @@ int forward_grouped_with_scratch(const dsbt_plan* p, const int* counts, int dtyp
 // Grouped forward (which = 0), inverse (1) or kinetic step (2) on device
 // buffers with a caller-supplied workspace (the host-streamed entry points).
 int grouped_device_call(int which, const dsbt_plan* p, const int* counts, int dtype, double tau,
-                        const void* in, void* out, void* ws, size_t ws_b, cudaStream_t st) {
-    return grouped_call(which, p, counts, dtype, tau, in, out, ws, ws_b, st);
+                        const void* in, void* out, void* ws, size_t ws_b, cudaStream_t st, const long long* uoff) {
+    return grouped_call(which, p, counts, dtype, tau, in, out, ws, ws_b, st, uoff);
 }
 
 // Grouped kinetic step with a scratch buffer supplied by the caller of this

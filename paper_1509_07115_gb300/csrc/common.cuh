@@ -74,6 +74,11 @@ struct GroupTable {
     int l[kMaxGroups];          // angular momentum of the group
     int chan0[kMaxGroups + 1];  // first channel of the group (prefix, +1 sentinel)
     int line0[kMaxGroups + 1];  // first real line (complex channel = 2 lines)
+    // Element offset of each channel in the caller's arrays (device array, one
+    // per channel), or nullptr: channel c at c * N.  Set only for the
+    // interval-scheme path of the uneven batch, which gathers the channels of
+    // several transforms on one grid into one call.
+    const long long* uoff = nullptr;
 };
 
 // Device-side status word written by kernels whose waits gave up.

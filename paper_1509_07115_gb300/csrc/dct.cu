@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
         local = chan - g.chan0[gi];
     }
     const bool even = (l & 1) == 0;
+    const size_t ubase = !live ? 0 : (g.uoff ? (size_t)g.uoff[chan] : (size_t)chan * N);   // caller's element offset
     // load pairs (x_{2j}, x_{2j+1}) -> v_j, v_{N-1-j}; all loads issued before the stores
     C a[8], b[8];
 #pragma unroll
@@ -349,10 +350,10 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
         if (!live) {
             a[u].x = a[u].y = b[u].x = b[u].y = (R)0;
         } else if (cplx) {
-            ld_pair(reinterpret_cast<const C*>(in) + (size_t)chan * N + 2 * j, a[u], b[u]);
+            ld_pair(reinterpret_cast<const C*>(in) + ubase + 2 * j, a[u], b[u]);
         } else {
-            a[u].x = in[(size_t)chan * N + 2 * j];
-            b[u].x = in[(size_t)chan * N + 2 * j + 1];
+            a[u].x = in[ubase + 2 * j];
+            b[u].x = in[ubase + 2 * j + 1];
             a[u].y = b[u].y = (R)0;
         }
     }
@@ -526,6 +527,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_inv(GroupTa
     __shared__ C sroot[32];
     fft_from_registers<Q>(s, vk, tw, sroot, N, lt, T);
     if (!live) return;
+    const size_t ubase = g.uoff ? (size_t)g.uoff[chan] : (size_t)chan * N;   // caller's element offset
     const R invN = (R)(1.0 / (double)N);
     for (int j = lt; j < (N >> 1); j += T) {
         C a = s[padi(j)], b = s[padi(N - 1 - j)];   // x_{2j}, x_{2j+1} (conjugated, unscaled)
@@ -533,10 +535,10 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_inv(GroupTa
         b.x *= invN; b.y = -b.y * invN;
         if (even) { b.x = -b.x; b.y = -b.y; }
         if (cplx) {
-            st_pair(reinterpret_cast<C*>(out) + (size_t)chan * N + 2 * j, a, b);
+            st_pair(reinterpret_cast<C*>(out) + ubase + 2 * j, a, b);
         } else {
-            out[(size_t)chan * N + 2 * j] = a.x;
-            out[(size_t)chan * N + 2 * j + 1] = b.x;
+            out[ubase + 2 * j] = a.x;
+            out[ubase + 2 * j + 1] = b.x;
         }
     }
 }

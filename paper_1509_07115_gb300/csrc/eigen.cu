@@ -18,8 +18,6 @@
 
 namespace dsbt {
 
-int grouped_device_call(int which, const dsbt_plan* p, const int* counts, int dtype, double tau,
-                        const void* in, void* out, void* ws, size_t ws_b, cudaStream_t st);
 
 namespace {
 

@@ -576,21 +576,38 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             float2 ph = make_float2(1.f, 0.f);
             if (ep.phase) ph = ep.per_l ? ep.phase[(size_t)l * N + row] : ep.phase[(size_t)(l & 1) * N + phase_entry(l, row, N)];
             const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
-            if (ep.mode == kOutUserC64) {
-                float2* o = reinterpret_cast<float2*>(ep.out0);
-                const size_t chan_base = (size_t)gt.chan0[tl.g] + (cbase >> 1);
-#pragma unroll
-                for (int j = 0; j < WC; j += 2)
-                    if (j < ncols) {
-                        const float u = ep.scale[line_base + j] * kFacUnscale;
-                        o[(chan_base + (j >> 1)) * N + row] = make_float2(acc[j] * u, acc[j + 1] * u);
-                    }
-            } else if (ep.mode == kOutUserF32 || ep.mode == kOutPlanarF32) {
+            if (ep.mode == kOutPlanarF32) {
                 float* o = reinterpret_cast<float*>(ep.out0);
-                const size_t base = ep.mode == kOutUserF32 ? (size_t)gt.chan0[tl.g] + cbase : line_base;
 #pragma unroll
                 for (int j = 0; j < WC; ++j)
-                    if (j < ncols) o[(base + j) * N + row] = acc[j] * (ep.scale[line_base + j] * kFacUnscale);
+                    if (j < ncols) o[(line_base + j) * N + row] = acc[j] * (ep.scale[line_base + j] * kFacUnscale);
+            } else if (ep.mode == kOutUserC64) {
+                float2* o = reinterpret_cast<float2*>(ep.out0);
+                const size_t chan_base = (size_t)gt.chan0[tl.g] + (cbase >> 1);
+                if (gt.uoff) {   // channels gathered by offset (uneven batch)
+#pragma unroll
+                    for (int j = 0; j < WC; j += 2)
+                        if (j < ncols) {
+                            const float u = ep.scale[line_base + j] * kFacUnscale;
+                            o[(size_t)gt.uoff[chan_base + (j >> 1)] + row] = make_float2(acc[j] * u, acc[j + 1] * u);
+                        }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < WC; j += 2)
+                        if (j < ncols) {
+                            const float u = ep.scale[line_base + j] * kFacUnscale;
+                            o[(chan_base + (j >> 1)) * N + row] = make_float2(acc[j] * u, acc[j + 1] * u);
+                        }
+                }
+            } else if (ep.mode == kOutUserF32) {
+                float* o = reinterpret_cast<float*>(ep.out0);
+                const size_t chan_base = (size_t)gt.chan0[tl.g] + cbase;
+#pragma unroll
+                for (int j = 0; j < WC; ++j)
+                    if (j < ncols) {
+                        const size_t at = gt.uoff ? (size_t)gt.uoff[chan_base + j] : (chan_base + j) * N;
+                        o[at + row] = acc[j] * (ep.scale[line_base + j] * kFacUnscale);
+                    }
             } else {   // kOutPlanarSplit: complex pairs with optional phase, FP16 pair, still scaled
                 __half* o0 = reinterpret_cast<__half*>(ep.out0);
                 __half* o1 = reinterpret_cast<__half*>(ep.out1);

@@ -76,9 +76,13 @@ class ProfScope {
 int profile_set_enabled(int on);
 
 // ---- grouped calls on device buffers with a caller workspace (capi.cu):
-// which = 0 forward, 1 inverse, 2 kinetic step (dsbt_*_grouped semantics)
+// which = 0 forward, 1 inverse, 2 kinetic step (dsbt_*_grouped semantics).
+// uoff (device, one per channel in call order, optional): the channel's element
+// offset in `in` / `out` instead of c * N (interval-scheme plans, complex64,
+// forward and kinetic only).
 int grouped_device_call(int which, const dsbt_plan* p, const int* counts, int dtype, double tau,
-                        const void* in, void* out, void* ws, size_t ws_b, cudaStream_t st);
+                        const void* in, void* out, void* ws, size_t ws_b, cudaStream_t st,
+                        const long long* uoff = nullptr);
 
 // ---- plan build (plan.cu)
 int plan_build_factors(dsbt_plan* p, cudaStream_t st);
