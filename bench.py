@@ -514,6 +514,13 @@ def tdse_leg(dsbt, inputs, torch, dev, fp64_peak):
     prof3 = dsbt.profile_read()
     dsbt.profile_enable(False)
     norm3 = torch.linalg.vector_norm(psi3).item()
+    # adjoint gradient of the norm beyond r = 50 over the 3 x 50 field components
+    psi30 = torch.from_numpy(c3).to(dev)
+    e0.record(st)
+    O3, g3 = t3.gradient(psi30, F3[:50], steps3, 2, 50.0, K=10)
+    e1.record(st)
+    torch.cuda.synchronize()
+    grad3_ms = e0.elapsed_time(e1)
     t3.close()
     p3.close()
     return {"config": "m=0, l=0..63, N=2048, dr=0.1, 400 steps of 0.05, soft-Coulomb -1/sqrt(r^2+0.5), "
@@ -524,7 +531,10 @@ def tdse_leg(dsbt, inputs, torch, dev, fp64_peak):
             "all_m": {"config": "N=2048, L=32 per m, M=8 (544 channels, l <= 39), field along x, "
                                 "100 steps of 0.05, DSBT_PLAN_FAST64 plan", "propagate_ms_per_step": ms3 / steps3,
                       "kernels_ms_per_step": {k: v[1] / steps3 for k, v in prof3.items()},
-                      "norm_after": norm3},
+                      "norm_after": norm3,
+                      "gradient_ms_total": grad3_ms, "gradient_observable": O3.item(),
+                      "gradient_config": "dO/dF over 50 samples x 3 components, O = norm beyond r = 50, "
+                                         "checkpoint every 10 steps"},
             "fast64": {"propagate_ms_per_step": fast_ms / steps,
                        "kernels_ms_per_step": {k: v[1] / steps for k, v in fprof.items()},
                        "max_abs_diff_vs_dense": fast_dev,

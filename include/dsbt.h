@@ -422,6 +422,23 @@ DSBT_API int dsbt_tdse3d_propagate_velocity(const dsbt_tdse3d* tdse, void* psi, 
                                             int nsteps, int hold, void* workspace, size_t workspace_bytes,
                                             void* stream);
 
+/*
+ * Gradient of O = sum over r_i > r_cut and all channels of |psi_S|^2 (psi_S the
+ * state after nsteps length-gauge steps of dsbt_tdse3d_propagate from psi0,
+ * which is not modified) with respect to the 3 x nsamples field components F
+ * (same layout as in dsbt_tdse3d_propagate), by the adjoint method: a forward
+ * sweep storing a checkpoint every checkpoint_every steps, then a backward
+ * sweep that recomputes each segment and runs the adjoint step (the same step
+ * with tau -> -tau, Y and T_l being unitary / orthogonal), accumulating
+ * tau Im <Y lambda, r n_c Y psi> in the angular kernel (n the direction of the
+ * angular node).  Writes O (device double) and dOdF (device [nsamples][3]).
+ * The paper has no gradient; this extends its propagator (Sec. 4.1).
+ */
+DSBT_API size_t dsbt_tdse3d_gradient_workspace_size(const dsbt_tdse3d* tdse, int nsteps, int checkpoint_every);
+DSBT_API int dsbt_tdse3d_gradient(const dsbt_tdse3d* tdse, const void* psi0, const double* F, int nsamples,
+                                  int nsteps, int hold, double r_cut, int checkpoint_every, double* O,
+                                  double* dOdF, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batch of uneven transforms (different grids and l_max) sharing one factor
  * set.  The regular rows of T_l (Sec. 2.4) do not depend on the grid size N;

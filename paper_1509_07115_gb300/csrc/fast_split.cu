@@ -77,8 +77,8 @@ constexpr int STAGES = 2;
 // kernel's (2 blocks: 8.3e-7; a separate correction accumulator, as in the
 // dense kernel, leaves no TMEM columns for a second buffer).
 constexpr int KC = 1;
-constexpr int EPI_WARPS = 8;
-constexpr int WC = BN_MAX / 2;                     // accumulator columns per epilogue warp
+constexpr int EPI_WARPS = 8;                       // two per TMEM lane quarter
+constexpr int WC = BN_MAX * 4 / EPI_WARPS;         // accumulator columns per epilogue warp
 constexpr int QS = 4;                              // tile-queue slots
 constexpr int A_BYTES = BM * BK * 2;               // 16 KiB
 constexpr int B_BYTES = BN_MAX * BK * 2;           // 32 KiB
@@ -505,7 +505,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
         // ------------------------------------------------ epilogue (EPI_WARPS warps)
         const int ew = warp - 2;
         const int quarter = warp & 3;
-        const int half = ew >> 2;
+        const int half = ew >> 2;   // column group of the warp: columns [half WC, (half + 1) WC)
         uint32_t gch = 0;   // chunks drained so far (same order as the MMA issuer)
         int qslot = 0;
         uint32_t qphase = 0;

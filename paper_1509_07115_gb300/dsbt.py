@@ -100,6 +100,9 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_tdse3d_workspace_size.restype = sz
         lib.dsbt_tdse3d_propagate.argtypes = [vp, vp, vp, i, i, vp, sz, vp]
         lib.dsbt_tdse3d_propagate_velocity.argtypes = [vp, vp, vp, vp, i, i, vp, sz, vp]
+        lib.dsbt_tdse3d_gradient_workspace_size.argtypes = [vp, i, i]
+        lib.dsbt_tdse3d_gradient_workspace_size.restype = sz
+        lib.dsbt_tdse3d_gradient.argtypes = [vp, vp, vp, i, i, i, d, i, vp, vp, vp, sz, vp]
         lib.dsbt_tdse_propagate_velocity.argtypes = [vp, vp, vp, vp, i, i, d, vp, sz, vp]
         lib.dsbt_tdse_workspace_size.argtypes = [vp, i, i]
         lib.dsbt_tdse_workspace_size.restype = sz
@@ -545,6 +548,24 @@ class Tdse3d:
                                                      int(nsteps), int(hold), _ptr(self._ws), self._ws.numel(),
                                                      _stream()), "dsbt_tdse3d_propagate_velocity")
         return psi
+
+    def gradient(self, psi0: torch.Tensor, F, nsteps: int, hold: int, r_cut: float, K: int = 20):
+        """(O, dO/dF): O = sum over r > r_cut of |psi_S|^2 after nsteps length-gauge
+        steps from psi0 (unchanged), dO/dF [nsamples][3] by the adjoint method with
+        a checkpoint every K steps."""
+        if psi0.dtype != torch.complex128 or not psi0.is_cuda or tuple(psi0.shape) != (self.nchan, self.N) \
+                or not psi0.is_contiguous():
+            raise ValueError(f"state must be a contiguous complex128 CUDA tensor of shape ({self.nchan}, {self.N})")
+        Fp = torch.as_tensor(F).to(device="cuda", dtype=torch.float64).contiguous()
+        ns = Fp.numel() // 3
+        nb = int(load().dsbt_tdse3d_gradient_workspace_size(self._h, int(nsteps), int(K)))
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        O = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = torch.empty((ns, 3), dtype=torch.float64, device="cuda")
+        _check(load().dsbt_tdse3d_gradient(self._h, _ptr(psi0), _ptr(Fp), int(ns), int(nsteps), int(hold),
+                                           float(r_cut), int(K), _ptr(O), _ptr(g), _ptr(ws), nb, _stream()),
+               "dsbt_tdse3d_gradient")
+        return O, g
 
 
 class Tdse:
