@@ -803,10 +803,11 @@ def main():
     bytes_launch = bytes_step / launches_per_step
     achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
     if fast:
-        # four launches per step (moments, forward rows, adjoint weights, adjoint
-        # columns); algorithmic flops of the interval scheme, 3 split products
+        # two launches per step (forward: moments and rows; adjoint: weights and
+        # columns, each pair interleaved in one launch); algorithmic flops of the
+        # interval scheme, 3 split products
         flop_per_step = 2 * 3 * 2.0 * sum(2 * c * fast_tf32_mac_per_line(N, l) for l, c in enumerate(counts))
-        kname, tname = "contract_ftc (interval scheme, DSBT_PLAN_FAST_TF32)", "contract_ftc_precision_form.json"
+        kname, tname = "contract_ftc (interval scheme, DSBT_PLAN_FAST_SPLIT)", "contract_ftc_precision_form.json"
     else:
         flop_per_step = 2 * FLOP_PER_CHANNEL * nchan
         kname, tname = "contract_tf32x3", "contract_tf32x3_precision_form.json"

@@ -273,7 +273,7 @@ int run_forward(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
         rc = dct_forward_f16(p, g, cplx, (const float*)in, w.h_hi_a, w.h_lo_a, w.scale, st);
         if (rc) return rc;
         return contract_split_fast(p, g, +1, w.h_hi_a, w.h_lo_a, w.scale, cplx ? kOutUserC64 : kOutUserF32, out,
-                                   nullptr, nullptr, w.sched, w.ftc, st);
+                                   nullptr, nullptr, w.ftc, st);
     }
     rc = dct_forward_f32(p, g, cplx, (const float*)in, w.hi_a, w.lo_a, st);
     if (rc) return rc;
@@ -311,7 +311,7 @@ int run_inverse(const dsbt_plan* p, const GroupTable& g, int dtype, const void* 
         }
         DSBT_CUDA_TRY(cudaGetLastError());
         rc = contract_split_fast(p, g, -1, w.h_hi_b, w.h_lo_b, w.scale, kOutPlanarF32, w.planar, nullptr, nullptr,
-                                 w.sched, w.ftc, st);
+                                 w.ftc, st);
         if (rc) return rc;
         return dct_inverse_f32(p, g, cplx, w.planar, (float*)out, st);
     }
@@ -361,10 +361,10 @@ int run_kinetic(const dsbt_plan* p, const GroupTable& g, int dtype, double tau, 
         rc = dct_forward_f16(p, g, true, (const float*)in, w.h_hi_a, w.h_lo_a, w.scale, st);
         if (!rc)
             rc = contract_split_fast(p, g, +1, w.h_hi_a, w.h_lo_a, w.scale, kOutPlanarSplit, w.h_hi_b, w.h_lo_b,
-                                     w.ph32, w.sched, w.ftc, st);
+                                     w.ph32, w.ftc, st);
         if (!rc)
             rc = contract_split_fast(p, g, -1, w.h_hi_b, w.h_lo_b, w.scale, kOutPlanarF32, w.planar, nullptr,
-                                     nullptr, w.sched, w.ftc, st);
+                                     nullptr, w.ftc, st);
         if (!rc) rc = dct_inverse_f32(p, g, true, w.planar, (float*)out, st);
         return rc;
     }

@@ -40,11 +40,14 @@
 // "right" slots: the intervals (j, 1), j = 0 .. levels - 1.
 // With B[r][(s,k)] = beta_{r,j}[k] (zero unless s is a far slot of r), BT its
 // transpose, QT[(s,k)][t] = Q_j[t - i len][k] sqrt(w_t) and QA its transpose,
-// all split into TF32 pairs.  MOMENTS and WEIGHTS tiles hold two slots (64
+// all split into FP16 pairs.  MOMENTS and WEIGHTS tiles hold two slots (64
 // rows of QT / BT each; a slot of odd level with the child slot whose range it
 // contains, else two slots of similar length).  K blocks of a tile come from up to two operand
 // sources (near: T / T^T against the lines; far: B / QA against M / W), listed
-// per tile by segments.
+// per tile by segments.  Each direction is one persistent launch over both
+// kinds of tiles: a row tile loads its near band first, then waits (bounded,
+// on a per-unit device counter that the moment tiles' epilogue warps raise
+// after their stores) before it loads the augmented lines.
 //
 // Work per line (N = 4096, l = 63): near 0.5 M, far 0.7 M, moments 1.3 M (half
 // of it on the ignored lanes), leaf 0 0.5 M multiply-adds, against 8.7 M for the
@@ -93,13 +96,22 @@ constexpr int MAX_SLOTS = (1 << MAX_LEVELS) - 1;
 constexpr int MAX_RIGHT = 2 * MAX_LEVELS;          // intervals covering the columns right of leaf 0
 constexpr int MAX_FSLOTS = MAX_SLOTS + MAX_RIGHT;
 constexpr int MAX_SEGS = MAX_RIGHT + 2;
+// Default: the plain order (every first-kind tile, then every second-kind
+// tile).  A short lag makes row tiles wait: the longest moment tiles stream
+// about 3 MB of lines each, tens of microseconds at one SM's share of the HBM
+// rate, while the whole GPU finishes a unit in about 4 us, so a row tile
+// trails its unit by 16 or more units to find it done, and that many units'
+// lines no longer fit in L2 (N = 4096, l <= 63 x 8: lag 16 is 12 % slower
+// than the plain order, lag 4 2x).
+constexpr int kDefaultLag = 1 << 30;
 
 enum Mode { kMoments = 0, kEval = 1, kWeights = 2, kLeafOut = 3 };
 
 struct FtcSpace {
-    int mode;
+    int amode;                     // first kind of this launch: kMoments (forward) or kWeights (adjoint)
+    int omode;                     // second kind: kEval (forward) or kLeafOut (adjoint)
     int kc;                        // K blocks per main-accumulator chunk
-    int RT;                        // row tiles of this launch
+    int RT;                        // row tiles of a second-kind unit (the leaves)
     int KB;                        // K blocks of N
     int nleaf, levels, nslots;     // leaves of 128 (any count 2..64), tree levels, used slots
     int nslots_f;                  // forward slots: the used ones, then the right intervals
@@ -108,30 +120,89 @@ struct FtcSpace {
     int FW;                        // slots per row of the compact B table: max(levels, nright)
     int a_oob;                     // a row past the end of the MOMENTS / WEIGHTS A operand
     int slot_off[MAX_LEVELS + 1];  // first slot of level j
-    int npairs;                    // MOMENTS / WEIGHTS tiles: slot pairs (b = -1: single slot)
+    int npairs;                    // MOMENTS / WEIGHTS tiles of a unit: slot pairs (b = -1: single slot)
     int pair_a[MAX_FSLOTS], pair_b[MAX_FSLOTS];
+    // A unit is one column tile (BN_MAX lines) of one group.  Units are numbered
+    // group by group (largest l first); unit u's first-kind tiles come before
+    // its second-kind tiles, which read what they wrote, and the launch runs
+    // block k = [first kind of unit k] [second kind of unit k - lag], so the
+    // second pass over a unit's lines finds them (and its fresh augmented
+    // lines) in L2.
+    int npos;                      // groups of the launch
+    int units;                     // U
+    int lag;                       // 1 <= lag <= U
     int total;                     // tiles
-    int order[kMaxGroups];         // group visited at position i
-    int t0[kMaxGroups + 1];        // first tile of position i
-    int ct[kMaxGroups];            // column tiles of the group at position i (0: group skipped)
+    int order[kMaxGroups];         // group at position i
+    int u0[kMaxGroups + 1];        // first unit of position i
+    int acum[kMaxGroups + 1];      // first-kind tiles before position i
+    int ta[kMaxGroups];            // first-kind tiles per unit at position i (npairs, or 0 for l = 0)
 };
 
 struct Tile {
-    int g, rt, ct, nmma;
+    int g, rt, ct, nmma, mode, unit, wait;   // mode < 0: no more tiles
 };
 
+// Position of unit u (u0 is increasing).
+__device__ __forceinline__ int unit_pos(const FtcSpace& fs, int u) {
+    int lo = 0, hi = fs.npos;   // u0[lo] <= u < u0[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (fs.u0[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// First tile of block k < U, a block of position i.
+__device__ __forceinline__ int block_start(const FtcSpace& fs, int i, int k) {
+    return fs.acum[i] + (k - fs.u0[i]) * fs.ta[i] + fs.RT * max(0, k - fs.lag);
+}
+
+// Tile t -> (kind, unit, row tile or pair, group, column tile): the last block
+// k whose first tile is <= t (blocks may be empty), found by a search over the
+// positions, then over the position's units; blocks k >= U hold second-kind
+// tiles only.
 __device__ __forceinline__ Tile decode(const FtcSpace& fs, const GroupTable& gt, int t) {
+    const int tail = fs.acum[fs.npos];   // first-kind tiles of the launch
+    int k, na = 0;
+    if (t >= tail + fs.RT * max(0, fs.units - fs.lag)) {
+        k = fs.lag + (t - tail) / fs.RT;
+    } else {
+        int lo = 0, hi = fs.npos;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (block_start(fs, mid, fs.u0[mid]) <= t) lo = mid;
+            else hi = mid;
+        }
+        const int i = lo;
+        int a = fs.u0[i], c = fs.u0[i + 1];   // block_start(a) <= t < block_start(c)
+        while (c - a > 1) {
+            const int mid = (a + c) >> 1;
+            if (block_start(fs, i, mid) <= t) a = mid;
+            else c = mid;
+        }
+        k = a;
+        na = fs.ta[i];
+    }
+    const int start = k < fs.units ? block_start(fs, unit_pos(fs, k), k) : tail + fs.RT * (k - fs.lag);
+    int local = t - start;
     Tile tl;
-    int i = 0;
-    while (fs.t0[i + 1] <= t) ++i;
+    if (local < na) {
+        tl.mode = fs.amode;
+        tl.unit = k;
+        tl.rt = local;   // pairs are sorted longest first
+    } else {
+        local -= na;
+        tl.mode = fs.omode;
+        tl.unit = k - fs.lag;
+        if (fs.omode == kEval) tl.rt = (local == 0) ? 0 : fs.RT - local;   // dense leaf 0 first
+        else tl.rt = local;
+    }
+    const int i = unit_pos(fs, tl.unit);
     const int g = fs.order[i];
-    const int local = t - fs.t0[i];
-    const int q = local / fs.ct[i];
     tl.g = g;
-    tl.ct = local - q * fs.ct[i];
-    if (fs.mode == kMoments || fs.mode == kWeights) tl.rt = q;   // pairs are sorted longest first
-    else if (fs.mode == kEval) tl.rt = (q == 0) ? 0 : fs.RT - q;            // dense leaf 0 first
-    else tl.rt = q;
+    tl.ct = tl.unit - fs.u0[i];
+    tl.wait = tl.mode == fs.omode && fs.ta[i] > 0;   // the unit has first-kind tiles
     const int nl = gt.line0[g + 1] - gt.line0[g];
     int left = nl - tl.ct * BN_MAX;
     if (left > BN_MAX) left = BN_MAX;
@@ -162,11 +233,11 @@ __host__ __device__ inline void slot_ji(const FtcSpace& fs, int s, int& j, int& 
 
 // K blocks [k0, k1) a MOMENTS (the interval's columns) or WEIGHTS (its
 // sibling's rows) slot contracts over.
-__device__ __forceinline__ void aug_range(const FtcSpace& fs, int s, int& k0, int& k1) {
+__device__ __forceinline__ void aug_range(const FtcSpace& fs, int mode, int s, int& k0, int& k1) {
     int j, i;
     slot_ji(fs, s, j, i);
     const int lb = (FL << j) / BK;
-    k0 = (fs.mode == kMoments) ? i * lb : (i + 1) * lb;
+    k0 = (mode == kMoments) ? i * lb : (i + 1) * lb;
     k1 = min(k0 + lb, fs.KB);   // a sibling at the right edge may end past the grid
 }
 
@@ -210,18 +281,18 @@ struct Segs {
     }
 };
 
-__device__ __forceinline__ Segs segments(const FtcSpace& fs, int l, int rt) {
+__device__ __forceinline__ Segs segments(const FtcSpace& fs, int mode, int l, int rt) {
     Segs sg;
     sg.n = 0;
     const int nx = n_extra(l);
     const int nf = (l + BK - 1) / BK;   // far K blocks per slot (basis functions k < l)
     constexpr int SB = KP / BK;         // K blocks per slot
-    if (fs.mode == kMoments || fs.mode == kWeights) {
+    if (mode == kMoments || mode == kWeights) {
         // the K ranges of the tile's two slots are dyadic intervals: nested
         // (one segment, the larger) or disjoint (two segments)
         int a0, a1, b0 = 0, b1 = 0;
-        aug_range(fs, fs.pair_a[rt], a0, a1);
-        if (fs.pair_b[rt] >= 0) aug_range(fs, fs.pair_b[rt], b0, b1);
+        aug_range(fs, mode, fs.pair_a[rt], a0, a1);
+        if (fs.pair_b[rt] >= 0) aug_range(fs, mode, fs.pair_b[rt], b0, b1);
         if (b1 <= b0 || (b0 >= a0 && b1 <= a1)) {
             sg.add(1, a0, a1, a0);
         } else if (a0 >= b0 && a1 <= b1) {
@@ -230,10 +301,11 @@ __device__ __forceinline__ Segs segments(const FtcSpace& fs, int l, int rt) {
             sg.add(1, a0, a1, a0);
             sg.add(1, b0, b1, b0);
         }
-    } else if (fs.mode == kEval) {
+    } else if (mode == kEval) {
         // A: the leaf's diagonal block (K blocks 0, 1) and the compact B table,
         // whose slot q of a row is the far interval at level q (regular rows)
-        // or right interval q (completion rows)
+        // or right interval q (completion rows).  The near band comes first:
+        // its loads need nothing from this launch's first kind.
         if (rt == 0) {
             // leaf 0: near band; the completion rows (polynomials of degree < l
             // in m as well) take the columns right of it through the right slots
@@ -244,12 +316,12 @@ __device__ __forceinline__ Segs segments(const FtcSpace& fs, int l, int rt) {
                     sg.add(2, s * SB, s * SB + nf, q * SB);
                 }
         } else {
+            sg.add(1, rt * (FL / BK), (rt + 1) * (FL / BK), 0);
             for (int j = 0; j < fs.levels; ++j)
                 if ((rt >> j) & 1) {
                     const int s = fs.slot_off[j] + (((rt >> j) - 1) >> 1);
                     sg.add(2, s * SB, s * SB + nf, j * SB);
                 }
-            sg.add(1, rt * (FL / BK), (rt + 1) * (FL / BK), 0);
         }
     } else {   // kLeafOut: A = the transposed diagonal block, the completion block, QA (dense)
         if (rt > 0 && nx > 0) sg.add(3, 0, 1, 0);   // completion rows n < n0_l (storage rows < 64)
@@ -267,18 +339,18 @@ __device__ __forceinline__ Segs segments(const FtcSpace& fs, int l, int rt) {
 
 // Number of K blocks of a tile (what segments(...).count() gives), without
 // building the list.
-__device__ __forceinline__ int seg_count(const FtcSpace& fs, int l, int rt) {
+__device__ __forceinline__ int seg_count(const FtcSpace& fs, int mode, int l, int rt) {
     const int nx = n_extra(l);
     const int nf = (l + BK - 1) / BK;
-    if (fs.mode == kMoments || fs.mode == kWeights) {
+    if (mode == kMoments || mode == kWeights) {
         int a0, a1, b0 = 0, b1 = 0;
-        aug_range(fs, fs.pair_a[rt], a0, a1);
-        if (fs.pair_b[rt] >= 0) aug_range(fs, fs.pair_b[rt], b0, b1);
+        aug_range(fs, mode, fs.pair_a[rt], a0, a1);
+        if (fs.pair_b[rt] >= 0) aug_range(fs, mode, fs.pair_b[rt], b0, b1);
         if (b1 <= b0 || (b0 >= a0 && b1 <= a1)) return a1 - a0;
         if (a0 >= b0 && a1 <= b1) return b1 - b0;
         return (a1 - a0) + (b1 - b0);
     }
-    if (fs.mode == kEval) return rt == 0 ? FL / BK + (nx > 0 ? fs.nright * nf : 0) : __popc(rt) * nf + FL / BK;
+    if (mode == kEval) return rt == 0 ? FL / BK + (nx > 0 ? fs.nright * nf : 0) : __popc(rt) * nf + FL / BK;
     int c = ((rt > 0 && nx > 0) ? 1 : 0) + FL / BK;
     for (int j = 0; j < fs.levels; ++j)
         if (used(fs, j, rt >> j)) c += nf;
@@ -286,13 +358,15 @@ __device__ __forceinline__ int seg_count(const FtcSpace& fs, int l, int rt) {
 }
 
 struct EpiArgs {
-    int mode;              // OutMode, or kOutAugSplit for MOMENTS / WEIGHTS
-    void* out0;            // FP16 pair (kOutAugSplit, kOutPlanarSplit) or FP32 values
+    int mode;              // OutMode of the second kind's output
+    void* out0;            // FP16 pair (kOutPlanarSplit) or FP32 values
     void* out1;
     const float2* phase;
     int per_l;
-    int stride;            // output row stride (N, or NA for the augmented lines)
     const float* scale;    // per line: 2^-e, the factor that leaves the scaled domain
+    __half* aug0;          // the first kind's output, the augmented lines [line][astride] (FP16 pair)
+    __half* aug1;
+    int astride;
 };
 
 // FP16 pair of v: hi = fp16(v), lo = fp16(v - hi).
@@ -300,17 +374,66 @@ __device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
     hi = __float2half_rn(v);
     lo = __float2half_rn(v - __half2float(hi));
 }
-constexpr int kOutAugSplit = 16;
+// Barriers, the tile queue and two words after the stages (the launch adds
+// 512 bytes past the 1024-byte alignment of the stages).
+static_assert((2 * STAGES + 4 + 2 * QS + 1) * 8 + QS * sizeof(Tile) + 8 <= 512, "control area");
+
+// Counter block of a launch (zeroed before it): the tile scheduler, the
+// launch-wide abort word and, per unit, the first-kind epilogue warps done.
+constexpr int kCtrSched = 0, kCtrAbort = 1, kCtrUnits = 2;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Orders this thread's generic-proxy global accesses with its async-proxy
+// (TMA) ones.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// A second-kind tile's producer waits, before its first load of augmented
+// lines, until every first-kind epilogue warp of its unit has stored its part:
+// at most `spin` polls, and it gives up at once when this CTA or another one
+// aborted.  The first-kind tiles of a unit come earlier in the tile order and
+// need nothing from later tiles, so the wait ends while the hardware runs.
+__device__ __forceinline__ bool wait_unit(const int* cnt, int target, const int* gabort, volatile int* abort_flag,
+                                          unsigned* status, uint32_t spin) {
+    for (uint32_t it = 0; it < spin; ++it) {
+        if (ld_acquire(cnt) >= target) {
+            fence_proxy_async_global();   // the TMA loads that follow see the stores
+            return true;
+        }
+        if (*abort_flag || *(volatile const int*)gabort) {
+            *abort_flag = 1;
+            return false;
+        }
+        __nanosleep(64);
+    }
+    *abort_flag = 1;
+    atomicExch(status, (unsigned)kStatusTimeout);
+    return false;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 
 // The kernel: roles and bounded waits as in gemm_tf32x3.cu; what differs is
-// where each K block comes from and the two alternating accumulator buffers.
+// where each K block comes from, the two kinds of tiles in one launch and the
+// two alternating accumulator buffers.
 __global__ void __launch_bounds__(NTHREADS, 1)
-k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constant__ CUtensorMap tmA1_lo,
+k_contract_ftc(const __grid_constant__ CUtensorMap tmA0_hi, const __grid_constant__ CUtensorMap tmA0_lo,
+               const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constant__ CUtensorMap tmA1_lo,
                const __grid_constant__ CUtensorMap tmB1_hi, const __grid_constant__ CUtensorMap tmB1_lo,
                const __grid_constant__ CUtensorMap tmA2_hi, const __grid_constant__ CUtensorMap tmA2_lo,
                const __grid_constant__ CUtensorMap tmB2_hi, const __grid_constant__ CUtensorMap tmB2_lo,
                const __grid_constant__ CUtensorMap tmA3_hi, const __grid_constant__ CUtensorMap tmA3_lo,
-               GroupTable gt, FtcSpace fs, int N, EpiArgs ep, unsigned* status, uint32_t spin, int* sched) {
+               GroupTable gt, FtcSpace fs, int N, EpiArgs ep, unsigned* status, uint32_t spin, int* ctr) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage_base = smem;
@@ -321,12 +444,12 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
     uint64_t* tq_full = acc_empty + 2;
     uint64_t* tq_empty = tq_full + QS;
     uint64_t* drain_bar = tq_empty + QS;    // the MMA issuer's exit drain
-    int* tile_q = (int*)(drain_bar + 1);
+    Tile* tile_q = (Tile*)(drain_bar + 1);   // decoded by the producer for the other roles
     uint32_t* tmem_slot = (uint32_t*)(tile_q + QS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool aug = fs.mode == kMoments || fs.mode == kWeights;   // two slots per tile, 64 A rows each
+    const int unit_target = fs.npairs * EPI_WARPS;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -361,34 +484,39 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             uint32_t phase = 0;
             bool ok = true;
             StageLedger led;
-            const uint64_t pol_b = policy_evict_last();
+            // the first kind's lines are read again by the second kind, and the
+            // augmented lines by several row tiles: keep them; a row tile's
+            // near band is the last use of its lines
+            const uint64_t pol_keep = policy_evict_last(), pol_last = policy_evict_first();
             int qslot = 0;
             uint32_t qphase = 0;
-            const uint32_t a_bytes = (aug ? 64u : 128u) * BK * 2u;
             while (ok) {
                 if (!mbar_wait(&tq_empty[qslot], qphase ^ 1, abort_flag, status, spin)) { ok = false; break; }
-                int t = atomicAdd(sched, 1);
-                if (t >= fs.total) t = -1;
-                tile_q[qslot] = t;
+                const int t = atomicAdd(ctr + kCtrSched, 1);
+                Tile tl;
+                if (t < fs.total) tl = decode(fs, gt, t);
+                else tl.mode = -1;
+                tile_q[qslot] = tl;
                 mbar_arrive(&tq_full[qslot]);
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
-                if (t < 0) break;
-                const Tile tl = decode(fs, gt, t);
+                if (tl.mode < 0) break;
+                const bool aug = tl.mode == fs.amode;   // two slots per tile, 64 A rows each
                 const int l = gt.l[tl.g];
-                const Segs sg = segments(fs, l, tl.rt);
+                const Segs sg = segments(fs, tl.mode, l, tl.rt);
                 const int nbox = (tl.nmma + BBOX - 1) / BBOX;
                 const bool pair = aug && fs.pair_b[tl.rt] >= 0;
+                const uint32_t a_bytes = (aug ? 64u : 128u) * BK * 2u;
                 const uint32_t bytes = 2 * a_bytes * (pair ? 2 : 1) + 2 * nbox * BBOX * BK * 2;
                 int arow1, arow2 = 0;
                 int ra0 = 0, ra1 = 0, rb0 = 0, rb1 = 0;   // own K ranges of the two slots
                 if (aug) {
-                    aug_range(fs, fs.pair_a[tl.rt], ra0, ra1);
-                    if (pair) aug_range(fs, fs.pair_b[tl.rt], rb0, rb1);
+                    aug_range(fs, tl.mode, fs.pair_a[tl.rt], ra0, ra1);
+                    if (pair) aug_range(fs, tl.mode, fs.pair_b[tl.rt], rb0, rb1);
                 }
-                if (fs.mode == kMoments) {
+                if (tl.mode == kMoments) {
                     arow1 = ((l & 1) * fs.nslots_f + fs.pair_a[tl.rt]) * KP;
                     if (pair) arow2 = ((l & 1) * fs.nslots_f + fs.pair_b[tl.rt]) * KP;
-                } else if (fs.mode == kWeights) {   // compact BT: rows (l, level, k)
+                } else if (tl.mode == kWeights) {   // compact BT: rows (l, level, k)
                     int j, i;
                     slot_ji(fs, fs.pair_a[tl.rt], j, i);
                     arow1 = (l * fs.levels + j) * KP;
@@ -398,19 +526,25 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                     }
                 } else {
                     arow1 = (l * fs.nleaf + tl.rt) * BM;   // diagonal block of leaf rt
-                    arow2 = (fs.mode == kEval ? l : (l & 1)) * N + tl.rt * BM;
+                    arow2 = (tl.mode == kEval ? l : (l & 1)) * N + tl.rt * BM;
                 }
                 const int brow = gt.line0[tl.g] + tl.ct * BN_MAX;
                 const int nkb = sg.count();
+                bool waited = !tl.wait;
                 for (int i = 0; i < nkb; ++i) {
                     int src, kb, akb;
                     sg.at(i, src, kb, akb);
+                    if (src == 2 && !waited) {
+                        if (!wait_unit(ctr + kCtrUnits + tl.unit, unit_target, ctr + kCtrAbort, abort_flag, status,
+                                       spin)) { ok = false; break; }
+                        waited = true;
+                    }
                     if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, status, spin)) { ok = false; break; }
                     unsigned char* sb = stage_base + stage * STAGE_BYTES;
                     mbar_expect_tx(&full[stage], bytes);
                     led.arm(stage, phase);
-                    const CUtensorMap* ah = src == 1 ? &tmA1_hi : (src == 2 ? &tmA2_hi : &tmA3_hi);
-                    const CUtensorMap* al = src == 1 ? &tmA1_lo : (src == 2 ? &tmA2_lo : &tmA3_lo);
+                    const CUtensorMap* ah = aug ? &tmA0_hi : (src == 1 ? &tmA1_hi : (src == 2 ? &tmA2_hi : &tmA3_hi));
+                    const CUtensorMap* al = aug ? &tmA0_lo : (src == 1 ? &tmA1_lo : (src == 2 ? &tmA2_lo : &tmA3_lo));
                     const CUtensorMap* bh = src == 2 ? &tmB2_hi : &tmB1_hi;
                     const CUtensorMap* bl = src == 2 ? &tmB2_lo : &tmB1_lo;
                     if (aug) {   // slot a -> A rows 0..63, slot b -> rows 64..127
@@ -434,11 +568,12 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                         tma_load_2d(sb, ah, &full[stage], akb * BK, arow);
                         tma_load_2d(sb + A_BYTES, al, &full[stage], akb * BK, arow);
                     }
+                    const uint64_t pol = (!aug && src == 1) ? pol_last : pol_keep;
                     for (int b = 0; b < nbox; ++b) {
                         tma_load_2d_hint(sb + 2 * A_BYTES + b * BBOX * 128, bh, &full[stage], kb * BK,
-                                         brow + b * BBOX, pol_b);
+                                         brow + b * BBOX, pol);
                         tma_load_2d_hint(sb + 2 * A_BYTES + B_BYTES + b * BBOX * 128, bl, &full[stage],
-                                         kb * BK, brow + b * BBOX, pol_b);
+                                         kb * BK, brow + b * BBOX, pol);
                     }
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
@@ -456,13 +591,12 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
             uint32_t qphase = 0;
             while (ok) {
                 if (!mbar_wait(&tq_full[qslot], qphase, abort_flag, status, spin)) break;
-                const int t = ((volatile int*)tile_q)[qslot];
+                const Tile tl = tile_q[qslot];
                 mbar_arrive(&tq_empty[qslot]);
                 if (++qslot == QS) { qslot = 0; qphase ^= 1; }
-                if (t < 0) break;
-                const Tile tl = decode(fs, gt, t);
+                if (tl.mode < 0) break;
                 const int l = gt.l[tl.g];
-                const int nkb = seg_count(fs, l, tl.rt);
+                const int nkb = seg_count(fs, tl.mode, l, tl.rt);
                 const uint32_t idesc = idesc_f16(BM, tl.nmma);
                 for (int c0 = 0; c0 < nkb && ok; c0 += fs.kc) {
                     const int c1 = min(nkb, c0 + fs.kc);
@@ -511,14 +645,14 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
         uint32_t qphase = 0;
         while (true) {
             if (!warp_all(mbar_wait(&tq_full[qslot], qphase, abort_flag, status, spin))) break;
-            const int t = ((volatile int*)tile_q)[qslot];
+            const Tile tl = tile_q[qslot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&tq_empty[qslot]);
             if (++qslot == QS) { qslot = 0; qphase ^= 1; }
-            if (t < 0) break;
-            const Tile tl = decode(fs, gt, t);
+            if (tl.mode < 0) break;
+            const bool aug = tl.mode == fs.amode;
             const int l = gt.l[tl.g];
-            const int nkb = seg_count(fs, l, tl.rt);
+            const int nkb = seg_count(fs, tl.mode, l, tl.rt);
             const int nl = gt.line0[tl.g + 1] - gt.line0[tl.g];
             const int trow = quarter * 32 + lane;                 // TMEM lane = A row of the tile
             int row = tl.rt * BM + trow;
@@ -555,24 +689,34 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
                 ++gch;
             }
             if (!ok) break;
-            if (ncols <= 0 || !store_row) continue;
-            const int S = ep.stride;
-            if (ep.mode == kOutAugSplit) {   // moments / weights stay in the scaled domain
-                __half* o0 = reinterpret_cast<__half*>(ep.out0);
-                __half* o1 = reinterpret_cast<__half*>(ep.out1);
-                const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
+            const bool do_store = ncols > 0 && store_row;   // warp-uniform
+            if (aug) {   // moments / weights stay in the scaled domain
+                if (do_store) {
+                    const int S = ep.astride;
+                    __half* o0 = ep.aug0;
+                    __half* o1 = ep.aug1;
+                    const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
 #pragma unroll
-                for (int j = 0; j < WC; ++j) {
-                    if (j < ncols) {
-                        __half h, lo;
-                        split_f16(acc[j] * kFacUnscale, h, lo);
-                        const size_t o = (line_base + j) * S + row;
-                        o0[o] = h;
-                        o1[o] = lo;
+                    for (int j = 0; j < WC; ++j) {
+                        if (j < ncols) {
+                            __half h, lo;
+                            split_f16(acc[j] * kFacUnscale, h, lo);
+                            const size_t o = (line_base + j) * S + row;
+                            o0[o] = h;
+                            o1[o] = lo;
+                        }
                     }
+                }
+                // release this warp's part of the unit to the second kind's TMA loads
+                fence_proxy_async_global();
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    atomicAdd(ctr + kCtrUnits + tl.unit, 1);
                 }
                 continue;
             }
+            if (!do_store) continue;
             float2 ph = make_float2(1.f, 0.f);
             if (ep.phase) ph = ep.per_l ? ep.phase[(size_t)l * N + row] : ep.phase[(size_t)(l & 1) * N + phase_entry(l, row, N)];
             const size_t line_base = (size_t)gt.line0[tl.g] + cbase;
@@ -632,6 +776,7 @@ k_contract_ftc(const __grid_constant__ CUtensorMap tmA1_hi, const __grid_constan
 
     tc_fence_before();
     __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(ctr + kCtrAbort, 1);   // waiters elsewhere give up
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, 512);
@@ -786,6 +931,7 @@ struct FtcData {
     int np_m = 0, np_w = 0;                        // slot pairs of the MOMENTS / WEIGHTS tiles
     int pa_m[MAX_FSLOTS], pb_m[MAX_FSLOTS], pa_w[MAX_FSLOTS], pb_w[MAX_FSLOTS];
     int NA = 0, NAF = 0;   // augmented widths: adjoint (used slots), forward (+ right slots)
+    int lag = kDefaultLag;  // units between a unit's first and second kind in the tile order
     // FP16 pairs (times 2^14): B, BT, QT, QA, the diagonal blocks D and Dt and
     // the completion block C
     __half* bA_hi = nullptr;
@@ -989,54 +1135,76 @@ void ftc_free(dsbt_plan* p) {
     p->ftc = nullptr;
 }
 
+// Augmented lines (an FP16 pair of NAF values per line), then the counter
+// block of a launch: scheduler, abort word and one counter per unit (a unit
+// is a column tile of BN_MAX lines of one group).
+static size_t ftc_aug_bytes(const dsbt_plan* p, size_t lines) {
+    return (2 * lines * (size_t)p->ftc->NAF * sizeof(__half) + 255) & ~(size_t)255;
+}
+
 size_t ftc_scratch_bytes(const dsbt_plan* p, size_t lines) {
-    return p->ftc ? 2 * lines * (size_t)p->ftc->NAF * sizeof(__half) : 0;
+    if (!p->ftc) return 0;
+    return ftc_aug_bytes(p, lines) + sizeof(int) * (kCtrUnits + lines / BN_MAX + kMaxGroups + 1);
+}
+
+void ftc_set_lag(dsbt_plan* p, int lag) {
+    if (p->ftc) p->ftc->lag = lag;
 }
 
 namespace {
 
-// One launch of the segmented kernel over the groups (largest l first).
-int launch_ftc(const dsbt_plan* p, const GroupTable& g, int mode, const CUtensorMap& a1h, const CUtensorMap& a1l,
-               const CUtensorMap& b1h, const CUtensorMap& b1l, const CUtensorMap& a2h, const CUtensorMap& a2l,
-               const CUtensorMap& b2h, const CUtensorMap& b2l, const CUtensorMap& a3h, const CUtensorMap& a3l,
-               const EpiArgs& ep, int* sched, cudaStream_t st) {
-    FtcSpace fs = p->ftc->base;
-    fs.mode = mode;
+// One launch over the groups (largest l first): the first kind (MOMENTS or
+// WEIGHTS) and the second (EVAL or LEAFOUT) of every unit, interleaved.
+int launch_fused(const dsbt_plan* p, const GroupTable& g, int dir, const CUtensorMap& a0h, const CUtensorMap& a0l,
+                 const CUtensorMap& a1h, const CUtensorMap& a1l, const CUtensorMap& b1h, const CUtensorMap& b1l,
+                 const CUtensorMap& a2h, const CUtensorMap& a2l, const CUtensorMap& b2h, const CUtensorMap& b2l,
+                 const CUtensorMap& a3h, const CUtensorMap& a3l, const EpiArgs& ep, int* ctr, size_t lines,
+                 cudaStream_t st) {
+    const FtcData* f = p->ftc;
+    FtcSpace fs = f->base;
+    const bool fwd = dir > 0;
+    fs.amode = fwd ? kMoments : kWeights;
+    fs.omode = fwd ? kEval : kLeafOut;
     fs.kc = KC;
-    const bool aug = mode == kMoments || mode == kWeights;
-    if (aug) {
-        const FtcData* f = p->ftc;
-        const bool m = mode == kMoments;
-        // first row past the A table of the tile's slots (QT or the compact BT)
-        fs.a_oob = m ? 2 * fs.nslots_f * KP : (p->l_max + 1) * fs.levels * KP;
-        fs.npairs = m ? f->np_m : f->np_w;
-        for (int q = 0; q < fs.npairs; ++q) {
-            fs.pair_a[q] = m ? f->pa_m[q] : f->pa_w[q];
-            fs.pair_b[q] = m ? f->pb_m[q] : f->pb_w[q];
-        }
+    // first row past the A table of the tile's slots (QT or the compact BT)
+    fs.a_oob = fwd ? 2 * fs.nslots_f * KP : (p->l_max + 1) * fs.levels * KP;
+    fs.npairs = fwd ? f->np_m : f->np_w;
+    for (int q = 0; q < fs.npairs; ++q) {
+        fs.pair_a[q] = fwd ? f->pa_m[q] : f->pa_w[q];
+        fs.pair_b[q] = fwd ? f->pb_m[q] : f->pb_w[q];
     }
-    fs.RT = aug ? fs.npairs : p->N / BM;
-    fs.t0[0] = 0;
+    fs.RT = p->N / BM;
+    fs.npos = g.ngroups;
+    fs.u0[0] = 0;
+    fs.acum[0] = 0;
     for (int i = 0; i < g.ngroups; ++i) {
         const int gi = g.ngroups - 1 - i;
         const int nl = g.line0[gi + 1] - g.line0[gi];
         fs.order[i] = gi;
-        fs.ct[i] = (aug && g.l[gi] == 0) ? 0 : (nl + BN_MAX - 1) / BN_MAX;
-        fs.t0[i + 1] = fs.t0[i] + fs.RT * fs.ct[i];
+        const int ct = (nl + BN_MAX - 1) / BN_MAX;
+        fs.ta[i] = g.l[gi] == 0 ? 0 : fs.npairs;   // T_0 has no entries left of its diagonal
+        fs.u0[i + 1] = fs.u0[i] + ct;
+        fs.acum[i + 1] = fs.acum[i] + ct * fs.ta[i];
     }
-    fs.total = fs.t0[g.ngroups];
-    if (fs.total == 0) return DSBT_OK;
-    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+    fs.units = fs.u0[g.ngroups];
+    if (fs.units == 0) return DSBT_OK;
+    if ((size_t)fs.units > lines / BN_MAX + kMaxGroups + 1) {
+        set_error("interval-scheme contraction: unit counters exceed the scratch");
+        return DSBT_ERR_INVALID;
+    }
+    fs.lag = std::max(1, std::min(f->lag, fs.units));
+    fs.total = fs.acum[g.ngroups] + fs.units * fs.RT;
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 512;
     int rc = ensure_smem((const void*)k_contract_ftc, smem);
     if (rc) return rc;
     int dev = 0, nsm = 0;
     DSBT_CUDA_TRY(cudaGetDevice(&dev));
     DSBT_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int grid = fs.total < nsm ? fs.total : nsm;
-    DSBT_CUDA_TRY(cudaMemsetAsync(sched, 0, sizeof(int), st));
+    DSBT_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(int) * (kCtrUnits + fs.units), st));
     ProfScope ps(kKContractTF32, st);
-    k_contract_ftc<<<grid, NTHREADS, smem, st>>>(a1h, a1l, b1h, b1l, a2h, a2l, b2h, b2l, a3h, a3l, g, fs, p->N, ep,
-                                                 p->status, p->spin_limit, sched);
+    k_contract_ftc<<<grid, NTHREADS, smem, st>>>(a0h, a0l, a1h, a1l, b1h, b1l, a2h, a2l, b2h, b2l, a3h, a3l, g, fs,
+                                                 p->N, ep, p->status, p->spin_limit, ctr);
     DSBT_CUDA_TRY(cudaGetLastError());
     return DSBT_OK;
 }
@@ -1044,8 +1212,8 @@ int launch_ftc(const dsbt_plan* p, const GroupTable& g, int mode, const CUtensor
 }  // namespace
 
 int contract_split_fast(const dsbt_plan* p, const GroupTable& g, int dir, const __half* in_hi, const __half* in_lo,
-                        const float* scale, int out_mode, void* out0, void* out1, const float2* phase, int* sched,
-                        void* scratch, cudaStream_t st) {
+                        const float* scale, int out_mode, void* out0, void* out1, const float2* phase, void* scratch,
+                        cudaStream_t st) {
     const FtcData* f = p->ftc;
     if (!f) {
         set_error("interval-scheme contraction needs a plan built with DSBT_PLAN_FAST_SPLIT");
@@ -1064,28 +1232,19 @@ int contract_split_fast(const dsbt_plan* p, const GroupTable& g, int dir, const 
     const size_t R = (size_t)g.total_lines;
     __half* aug_hi = reinterpret_cast<__half*>(scratch);
     __half* aug_lo = aug_hi + R * NA;
+    int* ctr = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(scratch) + ftc_aug_bytes(p, R));
     CUtensorMap in_h, in_l, aug_h, aug_l;
     int rc = encode_tmap_f16_sw128(&in_h, in_hi, R, N, BBOX, BK);
     if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&in_l, in_lo, R, N, BBOX, BK);
     if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&aug_h, aug_hi, R, NA, BBOX, BK);
     if (rc == DSBT_OK) rc = encode_tmap_f16_sw128(&aug_l, aug_lo, R, NA, BBOX, BK);
     if (rc != DSBT_OK) return rc;
-    const EpiArgs ep_aug{kOutAugSplit, aug_hi, aug_lo, nullptr, 0, NA, nullptr};
-    const EpiArgs ep_out{out_mode, out0, out1, phase, p->knl != nullptr, N, scale};
-    if (dir > 0) {
-        rc = launch_ftc(p, g, kMoments, f->tm_qT_hi, f->tm_qT_lo, in_h, in_l, f->tm_qT_hi, f->tm_qT_lo, in_h, in_l,
-                        f->tm_qT_hi, f->tm_qT_lo, ep_aug, sched, st);
-        if (rc == DSBT_OK)
-            rc = launch_ftc(p, g, kEval, f->tm_D_hi, f->tm_D_lo, in_h, in_l, f->tm_bA_hi, f->tm_bA_lo, aug_h, aug_l,
-                            f->tm_D_hi, f->tm_D_lo, ep_out, sched, st);
-    } else {
-        rc = launch_ftc(p, g, kWeights, f->tm_bT_hi, f->tm_bT_lo, in_h, in_l, f->tm_bT_hi, f->tm_bT_lo, in_h, in_l,
-                        f->tm_bT_hi, f->tm_bT_lo, ep_aug, sched, st);
-        if (rc == DSBT_OK)
-            rc = launch_ftc(p, g, kLeafOut, f->tm_Dt_hi, f->tm_Dt_lo, in_h, in_l, f->tm_qA_hi, f->tm_qA_lo, aug_h,
-                            aug_l, f->tm_C_hi, f->tm_C_lo, ep_out, sched, st);
-    }
-    return rc;
+    const EpiArgs ep{out_mode, out0, out1, phase, p->knl != nullptr, scale, aug_hi, aug_lo, NA};
+    if (dir > 0)
+        return launch_fused(p, g, dir, f->tm_qT_hi, f->tm_qT_lo, f->tm_D_hi, f->tm_D_lo, in_h, in_l, f->tm_bA_hi,
+                            f->tm_bA_lo, aug_h, aug_l, f->tm_D_hi, f->tm_D_lo, ep, ctr, R, st);
+    return launch_fused(p, g, dir, f->tm_bT_hi, f->tm_bT_lo, f->tm_Dt_hi, f->tm_Dt_lo, in_h, in_l, f->tm_qA_hi,
+                        f->tm_qA_lo, aug_h, aug_l, f->tm_C_hi, f->tm_C_lo, ep, ctr, R, st);
 }
 
 }  // namespace dsbt

@@ -481,6 +481,17 @@ extern "C" int dsbt_plan_set_spin_limit(dsbt_plan* plan, unsigned polls) {
     return DSBT_OK;
 }
 
+extern "C" int dsbt_plan_set_fast_lag(dsbt_plan* plan, int lag) {
+    DSBT_CHECK_ARG(plan != nullptr, "dsbt_plan_set_fast_lag: plan is NULL");
+    DSBT_CHECK_ARG(lag >= 1, "dsbt_plan_set_fast_lag: lag must be >= 1 (got %d)", lag);
+    if (!plan->ftc) {
+        set_error("dsbt_plan_set_fast_lag: plan was built without DSBT_PLAN_FAST_SPLIT");
+        return DSBT_ERR_UNSUPPORTED;
+    }
+    ftc_set_lag(plan, lag);
+    return DSBT_OK;
+}
+
 extern "C" int dsbt_plan_perturb_T(dsbt_plan* plan, int l, int row, int col, double delta, void* stream) {
     DSBT_CHECK_ARG(plan != nullptr, "dsbt_plan_perturb_T: plan is NULL");
     DSBT_CHECK_ARG(l >= 0 && l <= plan->l_max && row >= 0 && row < plan->N && col >= 0 && col < plan->N,

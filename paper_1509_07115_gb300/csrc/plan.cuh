@@ -146,14 +146,17 @@ bool ftc_supported(int N);
 int ftc_build(dsbt_plan* p, cudaStream_t st);
 void ftc_free(dsbt_plan* p);
 size_t ftc_scratch_bytes(const dsbt_plan* p, size_t lines);
+// Units between a unit's two kinds of tiles in the interval-scheme launch.
+void ftc_set_lag(dsbt_plan* p, int lag);
 // The interval-scheme contraction on FP16 pairs of planar lines scaled per
-// line by 1 / scale[line] (see dct_forward_f16).  Output modes: kOutAugSplit is
-// internal; kOutPlanarSplit writes the scaled FP16 pair (out0 hi, out1 lo);
-// kOutUserC64 / kOutUserF32 / kOutPlanarF32 write unscaled FP32.  `scratch`
-// holds ftc_scratch_bytes of the call's lines.
+// line by 1 / scale[line] (see dct_forward_f16), one launch per direction.
+// Output modes: kOutPlanarSplit writes the scaled FP16 pair (out0 hi, out1
+// lo); kOutUserC64 / kOutUserF32 / kOutPlanarF32 write unscaled FP32.
+// `scratch` holds ftc_scratch_bytes of the call's lines (the augmented lines
+// and the launch's counters, zeroed here).
 int contract_split_fast(const dsbt_plan* p, const GroupTable& g, int dir, const __half* in_hi, const __half* in_lo,
-                        const float* scale, int out_mode, void* out0, void* out1, const float2* phase, int* sched,
-                        void* scratch, cudaStream_t st);
+                        const float* scale, int out_mode, void* out0, void* out1, const float2* phase, void* scratch,
+                        cudaStream_t st);
 
 // ---- angular rule of the TDSE (tdse.cu), shared with tdse3d.cu
 // L-point Gauss-Legendre nodes x (cos theta) and weights w.

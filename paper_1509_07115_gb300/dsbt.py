@@ -67,6 +67,7 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
         lib.dsbt_device_status.argtypes = [vp, i, _c_int_p]
         lib.dsbt_plan_check.argtypes = [vp, ctypes.POINTER(d), vp]
         lib.dsbt_plan_set_spin_limit.argtypes = [vp, ctypes.c_uint]
+        lib.dsbt_plan_set_fast_lag.argtypes = [vp, i]
         lib.dsbt_plan_perturb_T.argtypes = [vp, i, i, i, d, vp]
         lib.dsbt_last_error.restype = ctypes.c_char_p
         lib.dsbt_launch_count.restype = ctypes.c_longlong
@@ -321,6 +322,12 @@ class Plan:
     def set_spin_limit(self, polls: int):
         """Testing hook: polls of each bounded device-side wait (0 = default)."""
         _check(load().dsbt_plan_set_spin_limit(self._h, int(polls)), "dsbt_plan_set_spin_limit")
+
+    def set_fast_lag(self, lag: int):
+        """Tile order of the interval-scheme contraction: units between a
+        unit's moment (weight) tiles and its row tiles (>= 1; results do not
+        depend on it)."""
+        _check(load().dsbt_plan_set_fast_lag(self._h, int(lag)), "dsbt_plan_set_fast_lag")
 
     def perturb_T(self, l: int, row: int, col: int, delta: float):
         """Testing hook: add delta to one entry of the FP64 T_l."""
