@@ -26,6 +26,10 @@
 // on the V_k it has just formed in registers.  (Loading each thread's first
 // butterfly inputs straight from global memory in the forward transform made
 // it slower: the stride-2 loads cost more than the shared-memory pass.)
+// The grids 2048, 4096 and 8192 have their own instantiations with N fixed at
+// compile time: every padded shared-memory index is then one base per thread
+// plus constant offsets (all index steps are multiples of 16), which removes
+// most of the integer work of the stages.
 #include <cuda_fp16.h>
 
 #include "plan.cuh"
@@ -103,21 +107,35 @@ template <typename C> __device__ __forceinline__ void dft16(C* x) {
 
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
 
+// Padded distance of two elements d apart, for d a multiple of 16: padi(i + d)
+// = padi(i) + pstride(d) for every i >= 0 (and padi(i - d) = padi(i) -
+// pstride(d) for i >= d).  Every distance the transforms step by is a multiple
+// of 16 (N = 256 q), so each thread forms one padded base index and adds
+// multiples of a stride that is a compile-time constant when N is.
+__device__ __forceinline__ int pstride(int d) { return d + (d >> 4); }
+
 // One Stockham stage of radix RX on one line's padded shared buffer s; the
 // line has T = N/16 threads (lt = thread index within the line), each owning
 // 16/RX butterflies.  Barriers are CTA-wide (all lines run the same stages).
-template <int RX, typename C>
+template <int RX, int NS, typename C>
 __device__ __forceinline__ void stockham_stage(C* s, const C* __restrict__ tw, int N, int Ls, int lt, int T) {
     constexpr int PER = 16 / RX;
     const int nb = N / RX;
+    const int sn = pstride(nb);
     C x[PER][RX];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int j = lt + u * T;
         const int k = j & (Ls - 1);
         const int b = k * (N / (Ls * RX));     // twiddle w = W_N^b, factor r uses w^r
+        if (NS > 0) {   // constant strides from one padded base
+            const C* src = s + padi(j);
 #pragma unroll
-        for (int r = 0; r < RX; ++r) x[u][r] = s[padi(j + r * nb)];
+            for (int r = 0; r < RX; ++r) x[u][r] = src[r * sn];
+        } else {        // fewer live registers for run-time N
+#pragma unroll
+            for (int r = 0; r < RX; ++r) x[u][r] = s[padi(j + r * nb)];
+        }
         if (k > 0) {
             if (RX == 16) {
                 const C w1 = tw[b], w4 = tw[4 * b];
@@ -144,13 +162,22 @@ __device__ __forceinline__ void stockham_stage(C* s, const C* __restrict__ tw, i
         else dft2(x[u][0], x[u][1]);
     }
     __syncthreads();
+    // outputs base + q Ls: Ls is 1 only in the first stage (radix 16, base a
+    // multiple of 16, so the 16 outputs share one padded row), else a multiple of 16
+    const int sl = Ls == 1 ? 1 : pstride(Ls);
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int j = lt + u * T;
         const int k = j & (Ls - 1);
         const int base = (j - k) * RX + k;
+        if (NS > 0) {
+            C* dst = s + padi(base);
 #pragma unroll
-        for (int q = 0; q < RX; ++q) s[padi(base + q * Ls)] = x[u][q];
+            for (int q = 0; q < RX; ++q) dst[q * sl] = x[u][q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < RX; ++q) s[padi(base + q * Ls)] = x[u][q];
+        }
     }
     __syncthreads();
 }
@@ -173,13 +200,15 @@ __device__ __forceinline__ void stockham_last_odd(C* s, const C* __restrict__ tw
                                                   int lt, int T) {
     typedef typename Re<C>::T R;
     constexpr int H = (Q - 1) / 2;
-    const int nb = N / Q;
+    const int nb = N / Q;          // 256 q / Q: a multiple of 16
+    const int sn = pstride(nb);
     for (int j = lt; j < nb; j += T) {
+        C* row = s + padi(j);
         C y0, S[H], D[H];
         {
             C x[Q];
 #pragma unroll
-            for (int r = 0; r < Q; ++r) x[r] = s[padi(j + r * nb)];
+            for (int r = 0; r < Q; ++r) x[r] = row[r * sn];
             if (j > 0) {
 #pragma unroll
                 for (int r = 1; r < Q; ++r) x[r] = cmul(x[r], tw[r * j]);
@@ -194,7 +223,7 @@ __device__ __forceinline__ void stockham_last_odd(C* s, const C* __restrict__ tw
         C X0 = y0;
 #pragma unroll
         for (int r = 0; r < H; ++r) X0 = cadd(X0, S[r]);
-        s[padi(j)] = X0;
+        row[0] = X0;
 #pragma unroll 1
         for (int q = 1; q <= H; ++q) {
             C A = y0, B;
@@ -216,8 +245,8 @@ __device__ __forceinline__ void stockham_last_odd(C* s, const C* __restrict__ tw
             Xq.y = A.y - B.x;
             Xm.x = A.x - B.y;
             Xm.y = A.y + B.x;
-            s[padi(j + q * nb)] = Xq;
-            s[padi(j + (Q - q) * nb)] = Xm;
+            row[q * sn] = Xq;
+            row[(Q - q) * sn] = Xm;
         }
     }
     __syncthreads();
@@ -226,17 +255,17 @@ __device__ __forceinline__ void stockham_last_odd(C* s, const C* __restrict__ tw
 // Forward FFT of length N = 256 q, q = 2^a Q: radix-16 stages, one radix-2/4/8
 // stage for the rest of the power of two and, when Q > 1, one radix-Q stage
 // (sroot is a 32-entry shared scratch for its roots).
-template <int Q, typename C>
+template <int Q, int NS, typename C>
 __device__ __forceinline__ void fft_stages(C* s, const C* __restrict__ tw, C* sroot, int N, int lt, int T, int Ls,
                                            int rem) {
     while ((rem & 15) == 0) {
-        stockham_stage<16>(s, tw, N, Ls, lt, T);
+        stockham_stage<16, NS>(s, tw, N, Ls, lt, T);
         Ls *= 16;
         rem >>= 4;
     }
-    if ((rem & 7) == 0) { stockham_stage<8>(s, tw, N, Ls, lt, T); Ls *= 8; rem >>= 3; }
-    else if ((rem & 3) == 0) { stockham_stage<4>(s, tw, N, Ls, lt, T); Ls *= 4; rem >>= 2; }
-    else if ((rem & 1) == 0) { stockham_stage<2>(s, tw, N, Ls, lt, T); Ls *= 2; rem >>= 1; }
+    if ((rem & 7) == 0) { stockham_stage<8, NS>(s, tw, N, Ls, lt, T); Ls *= 8; rem >>= 3; }
+    else if ((rem & 3) == 0) { stockham_stage<4, NS>(s, tw, N, Ls, lt, T); Ls *= 4; rem >>= 2; }
+    else if ((rem & 1) == 0) { stockham_stage<2, NS>(s, tw, N, Ls, lt, T); Ls *= 2; rem >>= 1; }
     if (Q == 1) return;
     for (int m = threadIdx.x; m < Q; m += blockDim.x) sroot[m] = tw[m * (N / Q)];   // W_Q^m
     __syncthreads();
@@ -249,14 +278,15 @@ __device__ __forceinline__ void fft_stages(C* s, const C* __restrict__ tw, C* sr
 // That stage runs on the registers and writes its outputs 16 lt + q to the
 // line's shared buffer s, then the remaining stages follow (fft_stages).
 // The caller must have finished every read of s before the call.
-template <int Q, typename C>
+template <int Q, int NS, typename C>
 __device__ __forceinline__ void fft_from_registers(C* s, C* x, const C* __restrict__ tw, C* sroot, int N, int lt,
                                                    int T) {
     dft16(x);
+    C* dst = s + 17 * lt;   // padi(16 lt + q) for q < 16
 #pragma unroll
-    for (int q = 0; q < 16; ++q) s[padi(16 * lt + q)] = x[q];
+    for (int q = 0; q < 16; ++q) dst[q] = x[q];
     __syncthreads();
-    fft_stages<Q>(s, tw, sroot, N, lt, T, 16, N >> 4);
+    fft_stages<Q, NS>(s, tw, sroot, N, lt, T, 16, N >> 4);
 }
 
 __device__ __forceinline__ int find_group(const GroupTable& g, int chan) {
@@ -317,9 +347,11 @@ __device__ __forceinline__ int scale_exp(float nrm) {
 }
 
 // Forward transform.  FP32 kernels: at most 64 registers, so two CTAs of
-// up to 512 threads (one line of N/16 threads each) fit on an SM.
-template <typename R, int MODE, int Q>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTable g, int N, int cplx, const R* __restrict__ in,
+// up to 512 threads (one line of N/16 threads each) fit on an SM.  NS > 0 is
+// the grid size fixed at compile time (every index step a constant), NS = 0
+// takes N at run time.
+template <typename R, int MODE, int Q, int NS>
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTable g, int Nrt, int cplx, const R* __restrict__ in,
                                                  void* __restrict__ out0, void* __restrict__ out1,
                                                  float* __restrict__ scale,
                                                  const typename Cx<R>::T* __restrict__ tw,
@@ -327,6 +359,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float spart[32];   // per 16 threads (<= 512 threads): partial sums of |psi_i|^2
+    const int N = NS ? NS : Nrt;
     const int T = N >> 4;
     const int G = lines_per_cta(N);
     const int grp = threadIdx.x / T, lt = threadIdx.x % T;
@@ -363,12 +396,22 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
         for (int u = 0; u < 8; ++u)
             part += (float)(a[u].x * a[u].x + a[u].y * a[u].y) + (float)(b[u].x * b[u].x + b[u].y * b[u].y);
     }
+    {
+        C* lo = s + padi(lt);            // v_j, j = lt + u T
+        C* hi = s + padi(N - 1 - lt);    // v_{N-1-j}
+        const int st = pstride(T);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int j = lt + u * T;
-        if (even) { b[u].x = -b[u].x; b[u].y = -b[u].y; }
-        s[padi(j)] = a[u];
-        s[padi(N - 1 - j)] = b[u];
+        for (int u = 0; u < 8; ++u) {
+            if (even) { b[u].x = -b[u].x; b[u].y = -b[u].y; }
+            if (NS > 0) {
+                lo[u * st] = a[u];
+                hi[-u * st] = b[u];
+            } else {
+                const int j = lt + u * T;
+                s[padi(j)] = a[u];
+                s[padi(N - 1 - j)] = b[u];
+            }
+        }
     }
     __syncthreads();
     if (MODE == kSplitF16) {
@@ -383,7 +426,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
         if ((threadIdx.x & 15) == 0) spart[threadIdx.x >> 4] = part;
     }
     __shared__ C sroot[32];
-    fft_stages<Q>(s, tw, sroot, N, lt, T, 1, N);
+    fft_stages<Q, NS>(s, tw, sroot, N, lt, T, 1, N);
     if (!live) return;
     const R sc1 = (R)sqrt(2.0 / (double)N), sc0 = (R)sqrt(1.0 / (double)N);
     const int line = g.line0[gi] + (cplx ? 2 * local : local);
@@ -398,12 +441,17 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
             if (cplx) scale[line + 1] = ldexpf(1.f, -e);
         }
     }
-    for (int m = lt; m < (N >> 1); m += T) {
+    const int st2 = pstride(2 * T);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {   // m = lt + i T, N / 2 = 8 T
+        const int m = lt + i * T;
         C X[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int k = 2 * m + e;
-            const C a = s[padi(k)], b = s[padi(k == 0 ? 0 : N - k)];
+            // V_k and V_{N-k} (V_0 for k = 0)
+            const C a = NS > 0 ? s[padi(2 * lt + e) + i * st2] : s[padi(k)];
+            const C b = (k == 0) ? a : (NS > 0 ? s[padi(N - 2 * lt - e) - i * st2] : s[padi(N - k)]);
             const C w = post[k];
             C v;   // 1/2 (w a + conj(w) b)
             v.x = (R)0.5 * ((w.x * a.x - w.y * a.y) + (w.x * b.x + w.y * b.y));
@@ -456,13 +504,14 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_fwd(GroupTa
     }
 }
 
-// Inverse transform F_l^T: planar lines -> caller layout.
-template <typename R, int Q>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_inv(GroupTable g, int N, int cplx, const R* __restrict__ in,
+// Inverse transform F_l^T: planar lines -> caller layout (NS as in k_dct_fwd).
+template <typename R, int Q, int NS>
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_inv(GroupTable g, int Nrt, int cplx, const R* __restrict__ in,
                                                  R* __restrict__ out, const typename Cx<R>::T* __restrict__ tw,
                                                  const typename Cx<R>::T* __restrict__ post) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = NS ? NS : Nrt;
     const int T = N >> 4;
     const int G = lines_per_cta(N);
     const int grp = threadIdx.x / T, lt = threadIdx.x % T;
@@ -493,29 +542,39 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_inv(GroupTa
             if (cplx) ld_real_pair(li + N + idx, im[u][0], im[u][1]);
         }
     }
+    {
+        C* dst = s + padi(2 * lt);       // X_{2m}, X_{2m+1} (same padded row), m = lt + u T
+        const int st2 = pstride(2 * T);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int m = lt + u * T;
-        C X0, X1;
-        X0.x = even ? re[u][1] : re[u][0];
-        X0.y = even ? im[u][1] : im[u][0];
-        X1.x = even ? re[u][0] : re[u][1];
-        X1.y = even ? im[u][0] : im[u][1];
-        const R s0 = (m == 0) ? isc0 : isc1;
-        X0.x *= s0; X0.y *= s0;
-        X1.x *= isc1; X1.y *= isc1;
-        s[padi(2 * m)] = X0;
-        s[padi(2 * m + 1)] = X1;
+        for (int u = 0; u < 8; ++u) {
+            const int m = lt + u * T;
+            C X0, X1;
+            X0.x = even ? re[u][1] : re[u][0];
+            X0.y = even ? im[u][1] : im[u][0];
+            X1.x = even ? re[u][0] : re[u][1];
+            X1.y = even ? im[u][0] : im[u][1];
+            const R s0 = (m == 0) ? isc0 : isc1;
+            X0.x *= s0; X0.y *= s0;
+            X1.x *= isc1; X1.y *= isc1;
+            if (NS > 0) {
+                dst[u * st2] = X0;
+                dst[u * st2 + 1] = X1;
+            } else {
+                s[padi(2 * m)] = X0;
+                s[padi(2 * m + 1)] = X1;
+            }
+        }
     }
     __syncthreads();
     // V_k = conj(w_k) (X_k - i X_{N-k}); keep conj(V_k) for the IFFT-by-FFT
     C vk[16];
+    const int st1 = pstride(T);
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
         const int k = lt + u * T;
-        const C a = s[padi(k)];
+        const C a = NS > 0 ? s[padi(lt) + u * st1] : s[padi(k)];
         C b;
-        if (k == 0) { b.x = (R)0; b.y = (R)0; } else b = s[padi(N - k)];
+        if (k == 0) { b.x = (R)0; b.y = (R)0; } else b = NS > 0 ? s[padi(N - lt) - u * st1] : s[padi(N - k)];
         C t;   // a - i b
         t.x = a.x + b.y;
         t.y = a.y - b.x;
@@ -525,12 +584,18 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_dct_inv(GroupTa
     }
     __syncthreads();   // every read of X from s is done
     __shared__ C sroot[32];
-    fft_from_registers<Q>(s, vk, tw, sroot, N, lt, T);
+    fft_from_registers<Q, NS>(s, vk, tw, sroot, N, lt, T);
     if (!live) return;
     const size_t ubase = g.uoff ? (size_t)g.uoff[chan] : (size_t)chan * N;   // caller's element offset
     const R invN = (R)(1.0 / (double)N);
-    for (int j = lt; j < (N >> 1); j += T) {
-        C a = s[padi(j)], b = s[padi(N - 1 - j)];   // x_{2j}, x_{2j+1} (conjugated, unscaled)
+    const C* lo = s + padi(lt);
+    const C* hi = s + padi(N - 1 - lt);
+    const int st1b = pstride(T);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {   // j = lt + i T, N / 2 = 8 T
+        const int j = lt + i * T;
+        C a = NS > 0 ? lo[i * st1b] : s[padi(j)];             // x_{2j} (conjugated, unscaled)
+        C b = NS > 0 ? hi[-i * st1b] : s[padi(N - 1 - j)];    // x_{2j+1}
         a.x *= invN; a.y = -a.y * invN;
         b.x *= invN; b.y = -b.y * invN;
         if (even) { b.x = -b.x; b.y = -b.y; }
@@ -573,11 +638,16 @@ using FwdKernel = void (*)(GroupTable, int, int, const R*, void*, void*, float*,
 template <typename R>
 using InvKernel = void (*)(GroupTable, int, int, const R*, R*, const typename Cx<R>::T*, const typename Cx<R>::T*);
 
+// Grids with their own compile-time instantiation (the power-of-two sizes of
+// the common workloads); the rest take N at run time.
 template <typename R, int MODE>
 static FwdKernel<R> fwd_kernel(int N) {
+    if (N == 2048) return k_dct_fwd<R, MODE, 1, 2048>;
+    if (N == 4096) return k_dct_fwd<R, MODE, 1, 4096>;
+    if (N == 8192) return k_dct_fwd<R, MODE, 1, 8192>;
     switch (odd_part(N)) {
 #define DSBT_CASE(q) \
-    case q: return k_dct_fwd<R, MODE, q>;
+    case q: return k_dct_fwd<R, MODE, q, 0>;
         DSBT_DCT_Q_CASES(DSBT_CASE)
 #undef DSBT_CASE
     }
@@ -586,9 +656,12 @@ static FwdKernel<R> fwd_kernel(int N) {
 
 template <typename R>
 static InvKernel<R> inv_kernel(int N) {
+    if (N == 2048) return k_dct_inv<R, 1, 2048>;
+    if (N == 4096) return k_dct_inv<R, 1, 4096>;
+    if (N == 8192) return k_dct_inv<R, 1, 8192>;
     switch (odd_part(N)) {
 #define DSBT_CASE(q) \
-    case q: return k_dct_inv<R, q>;
+    case q: return k_dct_inv<R, q, 0>;
         DSBT_DCT_Q_CASES(DSBT_CASE)
 #undef DSBT_CASE
     }
