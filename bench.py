@@ -671,7 +671,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tdse", action="store_true", help="skip the TDSE propagation/adjoint leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch leg")
-    ap.add_argument("--e2e-chunks", type=int, default=8, help="chunks of the host-streamed e2e call")
+    ap.add_argument("--e2e-chunks", type=int, default=16, help="chunks of the host-streamed e2e call")
     ap.add_argument("--no-probe", action="store_true",
                     help="skip the matmul / copy probes (profiler runs); fractions then use nominal ratios")
     ap.add_argument("--dense", action="store_true",
