@@ -96,7 +96,8 @@ extern "C" {
                               data (1.2 GB at N = 4096, l_max = 63) plus
                               16 B x 64 x N x N/128 for the interval bases, and
                               4 B x 64 x (N/128 + log2(N/128)) per line of
-                              workspace. */
+                              workspace (plus one 4-byte counter per 256
+                              lines). */
 #define DSBT_PLAN_FAST_TF32 DSBT_PLAN_FAST_SPLIT /* earlier name of the same flag */
 
 /* element types of the caller's arrays */

@@ -25,6 +25,7 @@ def test_hooks_reject_null_plan_on_host():
     assert lib.dsbt_plan_check(None, None, None) == -1
     assert lib.dsbt_plan_set_spin_limit(None, 1) == -1
     assert lib.dsbt_plan_perturb_T(None, 0, 0, 0, 1.0, None) == -1
+    assert lib.dsbt_plan_set_fast_lag(None, 1) == -1
 
 
 @pytest.mark.gpu
