@@ -72,7 +72,7 @@ using namespace tc;
 constexpr int BM = 128;
 constexpr int BK = 64;                             // K elements per block: one 128-byte swizzle row of FP16
 constexpr int BN_MAX = 256;
-constexpr int BBOX = 64;                           // rows per B TMA box
+constexpr int BBOX = 256;                          // rows per B TMA box (one box per operand half; 64 and 128: 1 % slower)
 constexpr int STAGES = 2;
 // K blocks per chunk.  The tensor cores accumulate with truncation, and all
 // three split products of a chunk go into one buffer, so the chunk is one K
