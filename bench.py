@@ -672,6 +672,8 @@ def main():
     ap.add_argument("--no-tdse", action="store_true", help="skip the TDSE propagation/adjoint leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch leg")
     ap.add_argument("--e2e-chunks", type=int, default=16, help="chunks of the host-streamed e2e call")
+    ap.add_argument("--fast-lag", type=int, default=0,
+                    help="tile order of the interval-scheme contraction (dsbt_plan_set_fast_lag; 0: the default)")
     ap.add_argument("--no-probe", action="store_true",
                     help="skip the matmul / copy probes (profiler runs); fractions then use nominal ratios")
     ap.add_argument("--dense", action="store_true",
@@ -713,6 +715,8 @@ def main():
     # (needs N / 64 a power of two)
     fast64 = (not args.no_fp64) and (N // 64) & (N // 64 - 1) == 0 and N % 64 == 0
     plan = dsbt.Plan(N, R_MAX, L_MAX, fp64=not args.no_fp64, tf32x3=not fast, fast_split=fast, fast64=fast64)
+    if fast and args.fast_lag > 0:
+        plan.set_fast_lag(args.fast_lag)
     x = inputs.gaussian_sum(rank_seed(rank), N, DR, counts, dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
     ws = plan.workspace(nchan, torch.complex64)
