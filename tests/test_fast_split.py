@@ -182,15 +182,18 @@ def test_fast_split_any_leaf_count(lib, N):
 
 
 @pytest.mark.gpu
-def test_fast_split_tile_order_does_not_change_results(lib):
+@pytest.mark.parametrize("N", [2048, 6400])
+def test_fast_split_tile_order_does_not_change_results(lib, N):
     """Each direction is one launch in which a unit's row tiles wait on a
     device counter for its moment (weight) tiles; the lag between the two in
     the tile order only moves work in time.  Lags 1, 2, 5 and the plain order
     (every first tile, then every row tile) give bit-identical forward, inverse
     and kinetic results, within the split-precision bar of the FP64 path; the
     status word shows no wait that gave up.  Groups span up to five column
-    tiles of 256 lines, with l = 0 (no moments) and empty groups among them."""
-    N, r_max, lmax = 2048, 204.8, 24
+    tiles of 256 lines, with l = 0 (no moments) and empty groups among them;
+    N = 6400 has 50 leaves (partial siblings, greedy right intervals).  Real
+    lines go through the same launches."""
+    r_max, lmax = 0.1 * N, 24
     counts = [0 if l in (5, 6) else (160 if l % 3 == 0 else 7) for l in range(lmax + 1)]
     x = inputs.gaussian_sum(57, N, r_max / N, counts)
     nrm = np.linalg.norm(x, axis=1)
@@ -219,3 +222,15 @@ def test_fast_split_tile_order_does_not_change_results(lib):
     for lag in (2, 5, 1 << 20):
         for a, c in zip(out[1], out[lag]):
             assert np.array_equal(a, c), lag
+    # real lines (DSBT_F32), lag 1 against the plain order
+    xr = torch.from_numpy(x.real.astype(np.float32)).cuda()
+    plan = lib.Plan(N, r_max, lmax, fp64=False, tf32x3=False, fast_split=True)
+    res = []
+    for lag in (1, 1 << 20):
+        plan.set_fast_lag(lag)
+        br = plan.forward_grouped(counts, xr)
+        res.append((br.cpu().numpy(), plan.inverse_grouped(counts, br).cpu().numpy()))
+    assert plan.device_status() == 0
+    plan.close()
+    for a, c in zip(res[0], res[1]):
+        assert np.array_equal(a, c)
