@@ -829,6 +829,9 @@ def main():
                 "algorithmic_bytes_rule": "16 N B per complex64 channel-transform, 2 per channel per step, "
                                           "shared over the contraction launches of the step",
                 "traffic_ratio": (traffic / bytes_launch) if traffic else None,
+                # the rate at which the launch moves its measured DRAM bytes
+                "traffic_gbs": (traffic / (avg_ms * 1e-3) / 1e9) if traffic else None,
+                "traffic_frac": (traffic / (avg_ms * 1e-3) / 1e9 / hbm) if traffic else None,
                 "avg_launch_ms": avg_ms, "launches_per_step": launches_per_step,
                 "whole_step": {"achieved": bytes_step / (step_ms * 1e-3) / 1e9, "frac": bytes_step / (step_ms * 1e-3) / 1e9 / hbm,
                                "ms": step_ms},
