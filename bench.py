@@ -548,6 +548,44 @@ def tdse_leg(dsbt, inputs, torch, dev, fp64_peak):
                                       "peak_source": "measured fp64 matmul (burst, this run)"}}
 
 
+# ---------------------------------------------------------------- plain FP64 leg (C2)
+
+def c2_leg(dsbt, inputs, torch, dev, steps=5):
+    """Plain FP64 complex128 DSBT: N = 2048, r_max = 204.8, l <= 31 all m (1024
+    channels, seeded Gaussian sums), forward + inverse round trip per step, on
+    the O(N l log N) FP64 plan (DSBT_PLAN_FAST64) and on the dense FP64 plan."""
+    N2, R2, L2 = 2048, 204.8, 31
+    counts = inputs.all_m_counts(L2, 1)
+    n = sum(counts)
+    x = inputs.gaussian_sum(400, N2, R2 / N2, counts, dtype=torch.complex128, device=dev)
+    nrm = torch.linalg.vector_norm(x, dim=1)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {"config": "N=2048, r_max=204.8, l=0..31 all m = 1024 complex128 channels; step = forward + inverse",
+           "unit": UNIT}
+    for name, fast in (("fast64", True), ("dense_fp64", False)):
+        p = dsbt.Plan(N2, R2, L2, fp64=True, tf32x3=False, fast64=fast)
+        ws = torch.empty(p.workspace_bytes(n, torch.complex128), dtype=torch.uint8, device=dev)
+        b = torch.empty_like(x)
+        y = torch.empty_like(x)
+        for _ in range(2):
+            p.forward_grouped(counts, x, out=b, workspace=ws)
+            p.inverse_grouped(counts, b, out=y, workspace=ws)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(steps):
+            p.forward_grouped(counts, x, out=b, workspace=ws)
+            p.inverse_grouped(counts, b, out=y, workspace=ws)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        err = ((y - x).abs().amax(dim=1) / nrm).max().item()
+        res[name] = {"value": 2 * n / (ms * 1e-3), "ms_per_step": ms, "round_trip_max_rel_err": err}
+        p.close()
+        del ws, b, y
+    return res
+
+
 # ---------------------------------------------------------------- uneven batch leg
 
 def batch_leg(dsbt, inputs, torch, dev, steps, warmup, peak, scheme="interval"):
@@ -923,6 +961,10 @@ def main():
     # ---------------------------------------------------------- TDSE (propagator + adjoint)
     if rank == 0 and not args.no_tdse and args.workload == "precision":
         line["tdse"] = tdse_leg(dsbt, inputs, torch, dev, probes["fp64_tflops"])
+
+    # ---------------------------------------------------------- plain FP64 round trip (C2)
+    if rank == 0 and not args.no_fp64 and args.workload == "precision":
+        line["c2_fp64"] = c2_leg(dsbt, inputs, torch, dev)
 
     # ---------------------------------------------------------- uneven batch (one launch, graph)
     if rank == 0 and not args.no_batch and args.workload == "precision":
